@@ -1,0 +1,9 @@
+"""FP64 CPU oracle (test infrastructure only; see ``upols_oracle``)."""
+from .upols_oracle import (  # noqa: F401
+    UpolsOracle,
+    afc_closed_loop,
+    mimo_fir,
+    mimo_fir_sample,
+    num_partitions,
+    upols,
+)
