@@ -1,0 +1,158 @@
+/*
+ * conv.h - C ABI of the GB300 streaming partitioned-convolution engine.
+ *
+ * The engine runs the hot path of H. Rosseel and T. van Waterschoot,
+ * "Accelerated Interactive Auralization of Highly Reverberant Spaces using
+ * Graphics Hardware" (arXiv 2509.04390) entirely on one GPU:
+ *
+ *   synthesis   l(t) = H_aur^T * m~(t)            (Sec. 3.1, Eqs. 1-2)
+ *   feedback    c(t) = F_hat * l(t)               (Sec. 3.1, Eq. 3)
+ *   both as uniformly-partitioned overlap-save convolution with a
+ *   frequency-domain delay line, n_f = 2 n_x      (Sec. 4, Eq. 6)
+ *   the prediction over block n is subtracted from microphone block n+1
+ *                                                 (Sec. 5)
+ *
+ * Every call returns CONV_OK (0) or a negative CONV_E_* code; the message of
+ * the last failure on the calling thread is in conv_last_error().  Handles are
+ * not thread-safe; separate handles are independent.  All float data are
+ * row-major float32.  Host pointers are only read or written during the call
+ * (the engine copies what it keeps); device pointers must stay valid until the
+ * work enqueued on the given stream has finished.
+ *
+ * Output block n is exactly samples [n*block, (n+1)*block) of the causal
+ * linear convolution with zero initial state; the engine adds no latency.
+ */
+#ifndef GB300_CONV_H
+#define GB300_CONV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CONV_OK 0
+#define CONV_E_INVAL (-1)    /* bad argument or size                              */
+#define CONV_E_STATE (-2)    /* call not valid in the handle's current state      */
+#define CONV_E_NOMEM (-3)    /* device or pinned-host memory does not fit         */
+#define CONV_E_CUDA (-4)     /* a CUDA runtime call failed (message has details)  */
+#define CONV_E_TIMEOUT (-5)  /* a bounded device-side wait gave up                */
+#define CONV_E_UNSTABLE (-6) /* closed-loop guard tripped; loop state was reset   */
+
+/* storage precision of the filter and delay-line spectra (conv_set_precision) */
+#define CONV_FP32 0 /* complex float32                                             */
+#define CONV_FP16 1 /* complex float16, power-of-two scale per partition, FP32 MAC */
+#define CONV_BF16 2 /* complex bfloat16, same scaling, FP32 MAC                    */
+
+typedef struct conv_engine conv_engine; /* opaque; owns all device state */
+
+/* Plan and size figures of a handle (conv_get_info).  Byte counts are the
+ * algorithmic bytes one block moves through the named kernel. */
+typedef struct conv_info {
+    long long block;          /* n_x                                              */
+    long long n_in;           /* inputs (microphones)                             */
+    long long n_out;          /* outputs (loudspeakers)                           */
+    long long taps;           /* n_h of the synthesis filters                     */
+    long long K;              /* synthesis partitions, ceil(taps / block)         */
+    long long taps_fb;        /* feedback-path length, 0 if none                  */
+    long long K_fb;           /* feedback partitions, 0 if none                   */
+    long long precision;      /* CONV_FP32 / CONV_FP16 / CONV_BF16                */
+    long long mac_bytes;      /* synthesis FDL MAC: filters + delay line + partials */
+    long long mac_fb_bytes;   /* feedback FDL MAC, 0 if none                      */
+    long long mac_ctas;       /* CTAs of one synthesis MAC launch                 */
+    long long mac_splits;     /* partition splits per output tile                 */
+    long long mac_smem;       /* dynamic shared memory per MAC CTA, bytes         */
+    long long device_bytes;   /* device memory held by the handle                 */
+    long long kernels_per_block;    /* kernels conv_process_block launches        */
+    long long kernels_per_afc_block; /* kernels afc_process_block launches        */
+} conv_info;
+
+/* Create an engine for n_in inputs, n_out outputs and filters of `taps` taps
+ * at block size `block` (n_x, Sec. 4).  fs (Hz) only sets the block period
+ * used in statistics.  block must be a power of two in [16, 4096] (the block
+ * range of Sec. 6); n_in, n_out in [1, 1024]; taps >= 1.  Allocates all device
+ * state on the current CUDA device (fails with NULL and conv_last_error() set,
+ * e.g. when the footprint does not fit in free device memory).
+ * Storage precision defaults to CONV_FP32. */
+conv_engine* conv_create(double fs, int block, int n_in, int n_out, long long taps);
+
+/* Choose the storage precision of filter and delay-line spectra (one of
+ * CONV_FP32, CONV_FP16, CONV_BF16).  FFTs and accumulation stay FP32.  Only
+ * valid before conv_set_filters (CONV_E_STATE afterwards). */
+int conv_set_precision(conv_engine* e, int mode);
+
+/* Set the synthesis filters H_aur (Sec. 3.1, Eq. 2): host array
+ * h[n_out][n_in][taps] float32 (h[l][q] filters input q into output l).  The
+ * engine partitions every filter into K sub-filters of `block` taps, pads each
+ * with `block` zeros and takes its 2*block-point R2C FFT on the device (Sec. 4,
+ * initialisation).  Copied; the caller keeps ownership.  Resets the stream. */
+int conv_set_filters(conv_engine* e, const float* h);
+
+/* Set the a-priori feedback-path estimates F_hat (Sec. 3.1, Eq. 3): host array
+ * f[n_in][n_out][taps_fb] float32 (f[p][l] is loudspeaker l -> microphone p).
+ * Allocates the canceller's spectra and delay line.  Copied.  Resets the
+ * stream. */
+int afc_set_paths(conv_engine* e, const float* f, long long taps_fb);
+
+/* Process one block, host buffers: in[n_in][block] -> out[n_out][block].
+ * Copies in, runs the path on the engine's stream, copies out, and returns
+ * when out is written.  Needs conv_set_filters (CONV_E_STATE otherwise). */
+int conv_process_block(conv_engine* e, const float* in, float* out);
+
+/* Same as conv_process_block with device pointers d_in[n_in][block] and
+ * d_out[n_out][block], enqueued on `cuda_stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  Returns once the work is enqueued. */
+int conv_process_block_async(conv_engine* e, const float* d_in, float* d_out, void* cuda_stream);
+
+/* One block of synthesis with feedback cancellation, host buffers:
+ * e = mic - c_prev; out = H_aur^T * e; c = F_hat * out is kept and subtracted
+ * from the next block (Sec. 5).  mic[n_in][block], out[n_out][block];
+ * e_or_null (if not NULL) receives e[n_in][block].  Needs conv_set_filters and
+ * afc_set_paths (CONV_E_STATE otherwise).  Returns CONV_E_UNSTABLE and resets
+ * the loop state if the RMS of e exceeds the guard set by afc_set_guard. */
+int afc_process_block(conv_engine* e, const float* mic, float* out, float* e_or_null);
+
+/* Device-pointer form of afc_process_block, enqueued on `cuda_stream`.
+ * d_e may be NULL.  The divergence guard is not evaluated (no host sync). */
+int afc_process_block_async(conv_engine* e, const float* d_mic, float* d_out, float* d_e, void* cuda_stream);
+
+/* Divergence guard of afc_process_block: if rms(e) over a block exceeds
+ * `max_rms` (> 0), the call returns CONV_E_UNSTABLE and resets the loop
+ * state.  0 disables the guard (the default). */
+int afc_set_guard(conv_engine* e, double max_rms);
+
+/* Zero the delay lines, sliding windows and the pending feedback prediction
+ * (start of a new stream).  Filters are kept. */
+int conv_reset(conv_engine* e);
+
+/* Wait for all work the engine enqueued and report a device-side error
+ * (CONV_E_TIMEOUT if a bounded wait gave up). */
+int conv_synchronize(conv_engine* e);
+
+/* Fill *out with the plan and size figures of the handle. */
+int conv_get_info(const conv_engine* e, conv_info* out);
+
+/* Kernel timing: while enabled, every block records CUDA events around the
+ * synthesis FDL MAC kernel on the stream it is launched on.  conv_profile_read
+ * waits for the recorded work, returns the summed kernel time in milliseconds
+ * and the number of launches timed, and clears the record. */
+int conv_profile_enable(conv_engine* e, int enable);
+int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches);
+
+/* Host-only dry run of the kernel tiling the engine would choose for these
+ * sizes: replays the FDL MAC kernel's copy and store addresses for every CTA
+ * and stage against the buffer and shared-memory sizes.  Needs no device.
+ * precision is CONV_FP32/FP16/BF16, n_src/n_dst the convolution's inputs and
+ * outputs, num_sms the SM count to plan for.  CONV_OK or CONV_E_INVAL. */
+int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms);
+
+/* Free everything the handle owns.  NULL-safe. */
+void conv_destroy(conv_engine* e);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* conv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_CONV_H */

@@ -1,0 +1,731 @@
+// engine.cu - the streaming convolution engine behind the C ABI of conv.h.
+//
+// One engine = one auralization stream on one GPU: the synthesis convolution
+// (n_in inputs -> n_out outputs, Sec. 3.1 Eq. 2) and optionally the feedback
+// canceller (n_out loudspeakers -> n_in microphones, Eq. 3), each a uniformly
+// partitioned overlap-save convolution with a frequency-domain delay line
+// (Sec. 4).  All state (filter spectra, delay lines, sliding windows, pending
+// feedback prediction) stays resident in device memory; per block only the
+// n_in x B input samples and n_out x B output samples cross to the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "conv.h"
+#include "kernels.h"
+
+using namespace gbconv;
+
+namespace {
+
+thread_local std::string g_err;
+
+int set_err(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return set_err(CONV_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                              __FILE__, __LINE__);                                        \
+    } while (0)
+
+inline int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int pow2_ceil(int v) {
+    int r = 1;
+    while (r < v) r <<= 1;
+    return r;
+}
+
+// Tiling of one FDL MAC.  Chooses bin/output tiles, the consumer thread layout,
+// the pipeline stage size and depth, and the number of partition splits so
+// that the grid covers every SM about once (1 CTA/SM at these shared-memory
+// sizes) while each CTA still streams at least a few stages.
+MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms) {
+    MacPlan p{};
+    p.B = B;
+    p.n_src = n_src;
+    p.n_dst = n_dst;
+    p.K = K;
+    p.R = n_src * K;
+    p.es = prec == PREC_FP32 ? 8 : 4;
+    p.VEC = 16 / p.es;
+    p.LPT = prec == PREC_FP32 ? 8 : 4;
+    p.BT = std::min(B, 256);
+    p.n_kt = B / p.BT;
+    p.kthreads = p.BT / p.VEC;
+    const int rest = (MAC_CONSUMER_WARPS * 32) / p.kthreads;
+    p.LT = std::min(n_dst, 16);
+    p.n_lt = (n_dst + p.LT - 1) / p.LT;
+    p.NLG = pow2_ceil((p.LT + p.LPT - 1) / p.LPT);
+    if (p.NLG > rest) p.NLG = rest;
+    p.NRL = rest / p.NLG;
+    const size_t per_r = (size_t)(p.LT + 1) * p.BT * p.es;
+    int rs = (int)std::max<size_t>(1, (32768 + per_r / 2) / per_r);
+    rs = (rs + p.NRL - 1) / p.NRL * p.NRL;  // whole r-lanes per stage
+    p.RS = std::max(1, std::min(rs, p.R));
+    const size_t hpart = align_up((size_t)p.RS * p.LT * p.BT * p.es, 128);
+    const size_t xpart = align_up((size_t)p.RS * p.BT * p.es, 128);
+    p.xoff = (unsigned)hpart;
+    p.stage_bytes = (unsigned)(hpart + xpart);
+    const size_t budget = 200 * 1024 - MAC_HDR_BYTES;
+    p.nstage = (int)std::min<size_t>(MAX_STAGES, std::max<size_t>(2, budget / p.stage_bytes));
+    // scratch for combining r-lanes reuses (and if needed extends) the stage ring
+    const size_t red = (size_t)(p.NRL - 1) * p.LT * p.BT * sizeof(float2);
+    p.smem = MAC_HDR_BYTES + std::max((size_t)p.nstage * p.stage_bytes, align_up(red, 128));
+    const int tiles = p.n_kt * p.n_lt;
+    const size_t tile_bytes = (size_t)p.R * p.LT * p.BT * p.es;
+    const int by_work = (int)std::max<size_t>(1, tile_bytes / (2 * (size_t)p.stage_bytes));
+    int S = std::max(1, (num_sms + tiles / 2) / tiles);
+    S = std::min(S, std::min(by_work, p.R));
+    p.S = std::max(1, S);
+    p.ctas = tiles * p.S;
+    p.h_bytes = (size_t)n_dst * p.R * B * p.es;
+    p.x_bytes = (size_t)p.R * B * p.es;
+    p.partial_bytes = (size_t)p.S * n_dst * B * sizeof(float2);
+    return p;
+}
+
+// Host replay of the address arithmetic of one FDL MAC launch (producer bulk
+// copies, consumer shared-memory reads, r-lane scratch, partial writes) against
+// the buffer and shared-memory sizes of the plan, for every CTA and stage.
+// Returns 0 or a description of the first violation in `why`.
+int check_plan(const MacPlan& p, std::string* why) {
+    char buf[256];
+    auto bad = [&](const char* what) {
+        snprintf(buf, sizeof(buf), "plan check failed: %s (B=%d n_src=%d n_dst=%d K=%d)", what, p.B, p.n_src, p.n_dst,
+                 p.K);
+        *why = buf;
+        return -1;
+    };
+    if (p.nstage < 1 || p.nstage > MAX_STAGES) return bad("stage count");
+    if (p.smem > 227 * 1024) return bad("shared memory above 227 KB");
+    if (p.kthreads * p.VEC != p.BT || p.kthreads > MAC_CONSUMER_WARPS * 32) return bad("bin threads");
+    const int rest = (MAC_CONSUMER_WARPS * 32) / p.kthreads;
+    if (p.kthreads * rest != MAC_CONSUMER_WARPS * 32 || p.NLG * p.NRL != rest) return bad("thread layout");
+    if ((p.LT + p.NLG - 1) / p.NLG > p.LPT) return bad("outputs per thread above LPT");
+    if (p.S < 1 || p.S > p.R) return bad("split count");
+    if (p.B % p.BT) return bad("bin tile");
+    const size_t hrow = (size_t)p.BT * p.es;
+    if (hrow % 16) return bad("row not a multiple of 16 bytes");
+    if (p.stage_bytes % 16 || p.xoff % 16) return bad("stage alignment");
+    if ((size_t)(p.NRL - 1) * p.LT * p.BT * 8 > p.smem - MAC_HDR_BYTES) return bad("r-lane scratch");
+    if ((size_t)p.nstage * p.stage_bytes > p.smem - MAC_HDR_BYTES) return bad("stage ring");
+    for (int cta = 0; cta < p.ctas; ++cta) {
+        const int tile = cta / p.S, split = cta % p.S;
+        const int kt = tile / p.n_lt, lt = tile % p.n_lt;
+        if (kt >= p.n_kt) return bad("tile index");
+        const int l0 = lt * p.LT, LTt = std::min(p.LT, p.n_dst - l0);
+        if (LTt < 1) return bad("empty output tile");
+        const int r0 = (int)((long long)split * p.R / p.S), r1 = (int)((long long)(split + 1) * p.R / p.S);
+        if (r1 <= r0) return bad("empty split");
+        const size_t hr = (size_t)LTt * hrow;
+        const size_t hb = ((size_t)kt * p.n_dst + l0) * (size_t)p.R * hrow;
+        const size_t xb = (size_t)kt * p.n_src * p.K * hrow;
+        for (int ra = r0; ra < r1; ra += p.RS) {
+            const int rb = std::min(ra + p.RS, r1), nr = rb - ra;
+            const size_t tx = (size_t)nr * (hr + hrow);
+            if (tx >= (1u << 20)) return bad("transaction bytes");
+            if (hb + (size_t)rb * hr > p.h_bytes) return bad("filter copy past the spectra");
+            if ((size_t)nr * hr > p.xoff) return bad("filter copy past its stage part");
+            size_t got = (size_t)nr * hr;
+            int r = ra, j = 0;
+            while (r < rb) {
+                const int q = r / p.K, pp = r % p.K;
+                for (int slot0 = 0; slot0 < p.K; slot0 += std::max(1, p.K / 7)) {
+                    int slot = slot0 + pp;
+                    if (slot >= p.K) slot -= p.K;
+                    const int run = std::min(rb - r, std::min(p.K - pp, p.K - slot));
+                    if (run < 1) return bad("empty delay-line run");
+                    if (xb + ((size_t)q * p.K + slot + run) * hrow > p.x_bytes) return bad("delay-line copy past the ring");
+                }
+                int slot = pp;  // slot0 = 0 case drives the run split used below
+                const int run = std::min(rb - r, std::min(p.K - pp, p.K - slot));
+                if (p.xoff + (size_t)(j + run) * hrow > p.stage_bytes) return bad("delay-line copy past its stage");
+                got += (size_t)run * hrow;
+                r += run;
+                j += run;
+            }
+            if (got != tx) return bad("transaction byte count");
+        }
+        const size_t last = (((size_t)split * p.n_dst + l0 + LTt - 1) * p.B + (size_t)kt * p.BT + p.BT);
+        if (last * sizeof(float2) > p.partial_bytes) return bad("partial write past the buffer");
+    }
+    return 0;
+}
+
+// One partitioned convolution: spectra, delay line, window and split partials.
+struct Part {
+    int n_src = 0, n_dst = 0, K = 0;
+    long long taps = 0;
+    MacPlan plan{};
+    void* H = nullptr;
+    float* sH = nullptr;
+    void* X = nullptr;
+    float* sX = nullptr;
+    float* win = nullptr;
+    float2* partial = nullptr;
+    bool allocated = false;
+    bool ready = false;
+};
+
+size_t part_bytes(const MacPlan& p, int prec) {
+    size_t b = p.h_bytes + p.x_bytes + p.partial_bytes + (size_t)p.n_src * p.B * sizeof(float);
+    if (prec != PREC_FP32) b += ((size_t)p.n_dst * p.R + (size_t)p.R) * sizeof(float);
+    return b;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct conv_engine {
+    int dev = 0;
+    double fs = 48000.0;
+    int B = 0, log2B = 0, n_in = 0, n_out = 0;
+    long long taps = 0;
+    int prec = CONV_FP32;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    float2* tw = nullptr;
+    float *d_in = nullptr, *d_out = nullptr, *d_e = nullptr, *d_c = nullptr;
+    float *h_in = nullptr, *h_out = nullptr, *h_e = nullptr;
+    int* h_err = nullptr;
+    int* d_err = nullptr;
+    Part syn, fb;
+    long long nblk = 0;
+    double guard = 0.0;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev0, ev1;
+    size_t ev_used = 0;
+    size_t dev_bytes = 0;
+};
+
+namespace {
+
+template <typename T>
+int dev_alloc(conv_engine* e, T** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t r = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (r != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_err(r == cudaErrorMemoryAllocation ? CONV_E_NOMEM : CONV_E_CUDA, "cudaMalloc(%zu): %s", bytes,
+                       cudaGetErrorString(r));
+    }
+    e->dev_bytes += bytes;
+    return CONV_OK;
+}
+
+template <typename T>
+void dev_free(conv_engine* e, T** p, size_t bytes) {
+    if (*p) {
+        cudaFree(*p);
+        e->dev_bytes -= bytes ? bytes : 16;
+    }
+    *p = nullptr;
+}
+
+void part_free(conv_engine* e, Part& P) {
+    if (!P.allocated) return;
+    const MacPlan& p = P.plan;
+    dev_free(e, &P.H, p.h_bytes);
+    dev_free(e, &P.X, p.x_bytes);
+    dev_free(e, &P.partial, p.partial_bytes);
+    dev_free(e, &P.win, (size_t)P.n_src * e->B * sizeof(float));
+    if (P.sH) dev_free(e, &P.sH, (size_t)p.n_dst * p.R * sizeof(float));
+    if (P.sX) dev_free(e, &P.sX, (size_t)p.R * sizeof(float));
+    P.allocated = false;
+    P.ready = false;
+}
+
+int check_fits(size_t need) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t margin = 64ull << 20;
+    if (need + margin > free_b)
+        return set_err(CONV_E_NOMEM, "device footprint %zu bytes does not fit in %zu free bytes", need, free_b);
+    return CONV_OK;
+}
+
+int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps) {
+    part_free(e, P);
+    P.n_src = n_src;
+    P.n_dst = n_dst;
+    P.taps = taps;
+    const long long K = (taps + e->B - 1) / e->B;
+    if (K <= 0 || (long long)n_src * K > 0x7fffffffLL / 2)
+        return set_err(CONV_E_INVAL, "taps %lld gives too many partitions", taps);
+    P.K = (int)K;
+    P.plan = plan_mac(e->prec, e->B, n_src, n_dst, P.K, e->num_sms);
+    const MacPlan& p = P.plan;
+    std::string why;
+    if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());
+    int rc = check_fits(part_bytes(p, e->prec));
+    if (rc) return rc;
+    P.allocated = true;  // partial allocations are released by part_free
+    if ((rc = dev_alloc(e, &P.H, p.h_bytes))) return rc;
+    if ((rc = dev_alloc(e, &P.X, p.x_bytes))) return rc;
+    if ((rc = dev_alloc(e, &P.partial, p.partial_bytes))) return rc;
+    if ((rc = dev_alloc(e, &P.win, (size_t)n_src * e->B * sizeof(float)))) return rc;
+    if (e->prec != PREC_FP32) {
+        if ((rc = dev_alloc(e, &P.sH, (size_t)p.n_dst * p.R * sizeof(float)))) return rc;
+        if ((rc = dev_alloc(e, &P.sX, (size_t)p.R * sizeof(float)))) return rc;
+    }
+    CK(cudaMemsetAsync(P.H, 0, p.h_bytes, e->stream));
+    CK(cudaMemsetAsync(P.partial, 0, p.partial_bytes, e->stream));
+    return CONV_OK;
+}
+
+int part_reset(conv_engine* e, Part& P) {
+    if (!P.allocated) return CONV_OK;
+    CK(cudaMemsetAsync(P.X, 0, P.plan.x_bytes, e->stream));
+    CK(cudaMemsetAsync(P.win, 0, (size_t)P.n_src * e->B * sizeof(float), e->stream));
+    if (P.sX) CK(cudaMemsetAsync(P.sX, 0, (size_t)P.plan.R * sizeof(float), e->stream));
+    return CONV_OK;
+}
+
+// Upload time-domain filters [n_dst][n_src][taps] and build their spectra.
+int part_set_filters(conv_engine* e, Part& P, const float* h) {
+    const size_t bytes = (size_t)P.n_dst * P.n_src * (size_t)P.taps * sizeof(float);
+    float* d_h = nullptr;
+    int rc = dev_alloc(e, &d_h, bytes);
+    if (rc) return rc;
+    cudaError_t r = cudaMemcpyAsync(d_h, h, bytes, cudaMemcpyHostToDevice, e->stream);
+    FilterArgs a{};
+    a.h = d_h;
+    a.taps = P.taps;
+    a.n_dst = P.n_dst;
+    a.n_src = P.n_src;
+    a.K = P.K;
+    a.B = e->B;
+    a.log2B = e->log2B;
+    a.BT = P.plan.BT;
+    a.LT = P.plan.LT;
+    a.H = P.H;
+    a.sH = P.sH;
+    a.tw = e->tw;
+    if (r == cudaSuccess) r = launch_filter_r2c(e->prec, a, e->stream);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
+    dev_free(e, &d_h, bytes);
+    if (r != cudaSuccess) return set_err(CONV_E_CUDA, "filter spectra: %s", cudaGetErrorString(r));
+    P.ready = true;
+    return CONV_OK;
+}
+
+inline int slot0_for(long long n, int K) {
+    const int m = (int)(n % K);
+    return m == 0 ? 0 : K - m;
+}
+
+int enqueue_pack(conv_engine* e, Part& P, const float* src, int stride, const float* sub, float* e_out,
+                 cudaStream_t s) {
+    PackArgs a{};
+    a.in = src;
+    a.in_stride = stride;
+    a.sub = sub;
+    a.e_out = e_out;
+    a.win = P.win;
+    a.X = P.X;
+    a.sX = P.sX;
+    a.B = e->B;
+    a.log2B = e->log2B;
+    a.BT = P.plan.BT;
+    a.n_ch = P.n_src;
+    a.K = P.K;
+    a.slot = slot0_for(e->nblk, P.K);
+    a.tw = e->tw;
+    CK(launch_pack_r2c(e->prec, a, s));
+    return CONV_OK;
+}
+
+int enqueue_mac(conv_engine* e, Part& P, cudaStream_t s, bool timed) {
+    const MacPlan& p = P.plan;
+    MacArgs a{};
+    a.H = P.H;
+    a.X = P.X;
+    a.sH = P.sH;
+    a.sX = P.sX;
+    a.partial = P.partial;
+    a.B = p.B;
+    a.BT = p.BT;
+    a.n_kt = p.n_kt;
+    a.n_dst = p.n_dst;
+    a.LT = p.LT;
+    a.n_lt = p.n_lt;
+    a.n_src = p.n_src;
+    a.K = p.K;
+    a.S = p.S;
+    a.RS = p.RS;
+    a.nstage = p.nstage;
+    a.kthreads = p.kthreads;
+    a.NLG = p.NLG;
+    a.NRL = p.NRL;
+    a.slot0 = slot0_for(e->nblk, P.K);
+    a.stage_bytes = p.stage_bytes;
+    a.xoff = p.xoff;
+    a.err = e->d_err;
+    const bool rec = timed && e->prof && e->ev_used < e->ev0.size();
+    if (rec) CK(cudaEventRecord(e->ev0[e->ev_used], s));
+    CK(launch_fdl_mac(e->prec, p, a, s));
+    if (rec) {
+        CK(cudaEventRecord(e->ev1[e->ev_used], s));
+        ++e->ev_used;
+    }
+    return CONV_OK;
+}
+
+int enqueue_out(conv_engine* e, Part& P, float* out, cudaStream_t s) {
+    ReduceArgs a{};
+    a.partial = P.partial;
+    a.S = P.plan.S;
+    a.n_dst = P.n_dst;
+    a.B = e->B;
+    a.log2B = e->log2B;
+    a.tw = e->tw;
+    a.out = out;
+    a.out_stride = e->B;
+    CK(launch_reduce_c2r(a, s));
+    return CONV_OK;
+}
+
+int check_dev_err(conv_engine* e) {
+    const int v = *(volatile int*)e->h_err;
+    if (v != DEVERR_NONE) {
+        *(volatile int*)e->h_err = DEVERR_NONE;
+        return set_err(CONV_E_TIMEOUT, "device-side wait gave up (code %d); results of the block are invalid", v);
+    }
+    return CONV_OK;
+}
+
+int engine_reset(conv_engine* e) {
+    int rc;
+    if ((rc = part_reset(e, e->syn))) return rc;
+    if ((rc = part_reset(e, e->fb))) return rc;
+    if (e->d_c) CK(cudaMemsetAsync(e->d_c, 0, (size_t)e->n_in * e->B * sizeof(float), e->stream));
+    CK(cudaStreamSynchronize(e->stream));
+    e->nblk = 0;
+    return CONV_OK;
+}
+
+int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t s) {
+    int rc;
+    if ((rc = enqueue_pack(e, e->syn, d_in, e->B, nullptr, nullptr, s))) return rc;
+    if ((rc = enqueue_mac(e, e->syn, s, true))) return rc;
+    if ((rc = enqueue_out(e, e->syn, d_out, s))) return rc;
+    ++e->nblk;
+    return CONV_OK;
+}
+
+int enqueue_afc_block(conv_engine* e, const float* d_mic, float* d_out, float* d_e, cudaStream_t s) {
+    int rc;
+    // e = mic - c_prev; synthesis (Eq. 2)
+    if ((rc = enqueue_pack(e, e->syn, d_mic, e->B, e->d_c, d_e, s))) return rc;
+    if ((rc = enqueue_mac(e, e->syn, s, true))) return rc;
+    if ((rc = enqueue_out(e, e->syn, d_out, s))) return rc;
+    // c = F_hat * l (Eq. 3), kept for the next block (Sec. 5)
+    if ((rc = enqueue_pack(e, e->fb, d_out, e->B, nullptr, nullptr, s))) return rc;
+    if ((rc = enqueue_mac(e, e->fb, s, false))) return rc;
+    if ((rc = enqueue_out(e, e->fb, e->d_c, s))) return rc;
+    ++e->nblk;
+    return CONV_OK;
+}
+
+void engine_free(conv_engine* e) {
+    if (!e) return;
+    DeviceGuard g(e->dev);
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    part_free(e, e->syn);
+    part_free(e, e->fb);
+    dev_free(e, &e->tw, 0);
+    dev_free(e, &e->d_in, 0);
+    dev_free(e, &e->d_out, 0);
+    dev_free(e, &e->d_e, 0);
+    dev_free(e, &e->d_c, 0);
+    if (e->h_in) cudaFreeHost(e->h_in);
+    if (e->h_out) cudaFreeHost(e->h_out);
+    if (e->h_e) cudaFreeHost(e->h_e);
+    if (e->h_err) cudaFreeHost(e->h_err);
+    for (auto ev : e->ev0) cudaEventDestroy(ev);
+    for (auto ev : e->ev1) cudaEventDestroy(ev);
+    if (e->stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long long taps) {
+    if (!(fs > 0.0) || !std::isfinite(fs)) return set_err(CONV_E_INVAL, "fs must be positive");
+    if (block < 16 || block > 4096 || (block & (block - 1)))
+        return set_err(CONV_E_INVAL, "block %d must be a power of two in [16, 4096]", block);
+    if (n_in < 1 || n_in > 1024 || n_out < 1 || n_out > 1024)
+        return set_err(CONV_E_INVAL, "n_in %d / n_out %d must be in [1, 1024]", n_in, n_out);
+    if (taps < 1) return set_err(CONV_E_INVAL, "taps must be >= 1");
+    e->fs = fs;
+    e->B = block;
+    e->log2B = ilog2(block);
+    e->n_in = n_in;
+    e->n_out = n_out;
+    e->taps = taps;
+    CK(cudaGetDevice(&e->dev));
+    cudaDeviceProp prop{};
+    CK(cudaGetDeviceProperties(&prop, e->dev));
+    e->num_sms = prop.multiProcessorCount;
+    CK(prepare_kernels(200 * 1024));
+    CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+    // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once to FP32
+    std::vector<float2> tw(2 * (size_t)block);
+    const double pi = 3.14159265358979323846264338327950288;
+    for (int j = 0; j < 2 * block; ++j) {
+        const double ang = -pi * (double)j / (double)block;
+        tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    int rc;
+    if ((rc = dev_alloc(e, &e->tw, tw.size() * sizeof(float2)))) return rc;
+    CK(cudaMemcpy(e->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    if ((rc = dev_alloc(e, &e->d_in, (size_t)n_in * block * sizeof(float)))) return rc;
+    if ((rc = dev_alloc(e, &e->d_out, (size_t)n_out * block * sizeof(float)))) return rc;
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_in), (size_t)n_in * block * sizeof(float), cudaHostAllocDefault));
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_out), (size_t)n_out * block * sizeof(float),
+                     cudaHostAllocDefault));
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_e), (size_t)n_in * block * sizeof(float), cudaHostAllocDefault));
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_err), sizeof(int), cudaHostAllocMapped));
+    *e->h_err = 0;
+    CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->d_err), e->h_err, 0));
+    if ((rc = part_alloc(e, e->syn, n_in, n_out, taps))) return rc;
+    return engine_reset(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+conv_engine* conv_create(double fs, int block, int n_in, int n_out, long long taps) {
+    conv_engine* e = new (std::nothrow) conv_engine();
+    if (!e) {
+        set_err(CONV_E_NOMEM, "out of host memory");
+        return nullptr;
+    }
+    if (create_impl(e, fs, block, n_in, n_out, taps) != CONV_OK) {
+        const std::string msg = g_err;
+        engine_free(e);
+        g_err = msg;
+        return nullptr;
+    }
+    g_err.clear();
+    return e;
+}
+
+int conv_set_precision(conv_engine* e, int mode) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    if (mode != CONV_FP32 && mode != CONV_FP16 && mode != CONV_BF16)
+        return set_err(CONV_E_INVAL, "unknown precision %d", mode);
+    if (e->syn.ready || e->fb.allocated)
+        return set_err(CONV_E_STATE, "precision must be set before conv_set_filters / afc_set_paths");
+    if (mode == e->prec) return CONV_OK;
+    DeviceGuard g(e->dev);
+    e->prec = mode;
+    int rc = part_alloc(e, e->syn, e->n_in, e->n_out, e->taps);
+    if (rc) return rc;
+    return engine_reset(e);
+}
+
+int conv_set_filters(conv_engine* e, const float* h) {
+    if (!e || !h) return set_err(CONV_E_INVAL, "null argument");
+    DeviceGuard g(e->dev);
+    int rc = part_set_filters(e, e->syn, h);
+    if (rc) return rc;
+    return engine_reset(e);
+}
+
+int afc_set_paths(conv_engine* e, const float* f, long long taps_fb) {
+    if (!e || !f) return set_err(CONV_E_INVAL, "null argument");
+    if (taps_fb < 1) return set_err(CONV_E_INVAL, "taps_fb must be >= 1");
+    DeviceGuard g(e->dev);
+    int rc;
+    if ((rc = part_alloc(e, e->fb, e->n_out, e->n_in, taps_fb))) return rc;
+    if (!e->d_c && (rc = dev_alloc(e, &e->d_c, (size_t)e->n_in * e->B * sizeof(float)))) return rc;
+    if (!e->d_e && (rc = dev_alloc(e, &e->d_e, (size_t)e->n_in * e->B * sizeof(float)))) return rc;
+    if ((rc = part_set_filters(e, e->fb, f))) return rc;
+    return engine_reset(e);
+}
+
+int conv_process_block_async(conv_engine* e, const float* d_in, float* d_out, void* cuda_stream) {
+    if (!e || !d_in || !d_out) return set_err(CONV_E_INVAL, "null argument");
+    if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
+    DeviceGuard g(e->dev);
+    return enqueue_block(e, d_in, d_out, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int conv_process_block(conv_engine* e, const float* in, float* out) {
+    if (!e || !in || !out) return set_err(CONV_E_INVAL, "null argument");
+    if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
+    DeviceGuard g(e->dev);
+    const size_t ib = (size_t)e->n_in * e->B * sizeof(float), ob = (size_t)e->n_out * e->B * sizeof(float);
+    std::memcpy(e->h_in, in, ib);
+    CK(cudaMemcpyAsync(e->d_in, e->h_in, ib, cudaMemcpyHostToDevice, e->stream));
+    int rc = enqueue_block(e, e->d_in, e->d_out, e->stream);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(e->h_out, e->d_out, ob, cudaMemcpyDeviceToHost, e->stream));
+    CK(cudaStreamSynchronize(e->stream));
+    if ((rc = check_dev_err(e))) return rc;
+    std::memcpy(out, e->h_out, ob);
+    return CONV_OK;
+}
+
+int afc_process_block_async(conv_engine* e, const float* d_mic, float* d_out, float* d_e, void* cuda_stream) {
+    if (!e || !d_mic || !d_out) return set_err(CONV_E_INVAL, "null argument");
+    if (!e->syn.ready || !e->fb.ready) return set_err(CONV_E_STATE, "filters or feedback paths not set");
+    DeviceGuard g(e->dev);
+    return enqueue_afc_block(e, d_mic, d_out, d_e, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int afc_process_block(conv_engine* e, const float* mic, float* out, float* e_or_null) {
+    if (!e || !mic || !out) return set_err(CONV_E_INVAL, "null argument");
+    if (!e->syn.ready || !e->fb.ready) return set_err(CONV_E_STATE, "filters or feedback paths not set");
+    DeviceGuard g(e->dev);
+    const size_t ib = (size_t)e->n_in * e->B * sizeof(float), ob = (size_t)e->n_out * e->B * sizeof(float);
+    const bool want_e = e_or_null != nullptr || e->guard > 0.0;
+    std::memcpy(e->h_in, mic, ib);
+    CK(cudaMemcpyAsync(e->d_in, e->h_in, ib, cudaMemcpyHostToDevice, e->stream));
+    int rc = enqueue_afc_block(e, e->d_in, e->d_out, e->d_e, e->stream);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(e->h_out, e->d_out, ob, cudaMemcpyDeviceToHost, e->stream));
+    if (want_e) CK(cudaMemcpyAsync(e->h_e, e->d_e, ib, cudaMemcpyDeviceToHost, e->stream));
+    CK(cudaStreamSynchronize(e->stream));
+    if ((rc = check_dev_err(e))) return rc;
+    if (e->guard > 0.0) {
+        double ss = 0.0;
+        const size_t n = (size_t)e->n_in * e->B;
+        for (size_t i = 0; i < n; ++i) ss += (double)e->h_e[i] * e->h_e[i];
+        const double rms = std::sqrt(ss / (double)n);
+        if (!(rms <= e->guard)) {
+            engine_reset(e);
+            return set_err(CONV_E_UNSTABLE, "closed-loop guard: rms(e) = %g exceeds %g; loop state reset", rms,
+                           e->guard);
+        }
+    }
+    std::memcpy(out, e->h_out, ob);
+    if (e_or_null) std::memcpy(e_or_null, e->h_e, ib);
+    return CONV_OK;
+}
+
+int afc_set_guard(conv_engine* e, double max_rms) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    if (!(max_rms >= 0.0)) return set_err(CONV_E_INVAL, "guard must be >= 0");
+    e->guard = max_rms;
+    return CONV_OK;
+}
+
+int conv_reset(conv_engine* e) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    DeviceGuard g(e->dev);
+    return engine_reset(e);
+}
+
+int conv_synchronize(conv_engine* e) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    DeviceGuard g(e->dev);
+    CK(cudaDeviceSynchronize());
+    return check_dev_err(e);
+}
+
+int conv_get_info(const conv_engine* e, conv_info* out) {
+    if (!e || !out) return set_err(CONV_E_INVAL, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    const MacPlan& p = e->syn.plan;
+    out->block = e->B;
+    out->n_in = e->n_in;
+    out->n_out = e->n_out;
+    out->taps = e->taps;
+    out->K = e->syn.K;
+    out->taps_fb = e->fb.allocated ? e->fb.taps : 0;
+    out->K_fb = e->fb.allocated ? e->fb.K : 0;
+    out->precision = e->prec;
+    out->mac_bytes = (long long)(p.h_bytes + p.x_bytes);
+    out->mac_fb_bytes = e->fb.allocated ? (long long)(e->fb.plan.h_bytes + e->fb.plan.x_bytes) : 0;
+    out->mac_ctas = p.ctas;
+    out->mac_splits = p.S;
+    out->mac_smem = (long long)p.smem;
+    out->device_bytes = (long long)e->dev_bytes;
+    out->kernels_per_block = 3;
+    out->kernels_per_afc_block = 6;
+    return CONV_OK;
+}
+
+int conv_profile_enable(conv_engine* e, int enable) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    DeviceGuard g(e->dev);
+    e->prof = enable > 0;
+    if (e->prof) {
+        const size_t want = enable > 1 ? (size_t)enable : 4096;
+        while (e->ev0.size() < want) {
+            cudaEvent_t a, b;
+            CK(cudaEventCreate(&a));
+            CK(cudaEventCreate(&b));
+            e->ev0.push_back(a);
+            e->ev1.push_back(b);
+        }
+    }
+    e->ev_used = 0;
+    return CONV_OK;
+}
+
+int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches) {
+    if (!e || !mac_ms_total || !launches) return set_err(CONV_E_INVAL, "null argument");
+    DeviceGuard g(e->dev);
+    double tot = 0.0;
+    for (size_t i = 0; i < e->ev_used; ++i) {
+        CK(cudaEventSynchronize(e->ev1[i]));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e->ev0[i], e->ev1[i]));
+        tot += ms;
+    }
+    *mac_ms_total = tot;
+    *launches = (long long)e->ev_used;
+    e->ev_used = 0;
+    return CONV_OK;
+}
+
+int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms) {
+    if (precision < CONV_FP32 || precision > CONV_BF16 || block < 16 || block > 4096 || (block & (block - 1)) ||
+        n_src < 1 || n_dst < 1 || taps < 1 || num_sms < 1)
+        return set_err(CONV_E_INVAL, "invalid plan arguments");
+    const long long K = (taps + block - 1) / block;
+    if ((long long)n_src * K > 0x7fffffffLL / 2) return set_err(CONV_E_INVAL, "too many partitions");
+    const MacPlan p = plan_mac(precision, block, n_src, n_dst, (int)K, num_sms);
+    std::string why;
+    if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());
+    return CONV_OK;
+}
+
+void conv_destroy(conv_engine* e) { engine_free(e); }
+
+const char* conv_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

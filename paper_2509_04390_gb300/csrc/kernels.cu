@@ -1,0 +1,454 @@
+// kernels.cu - the engine's CUDA kernels (sm_103a) and their host launchers.
+//
+// Data layouts (B = n_x, block size; K partitions; R = n_src * K reduction
+// indices r = q*K + p; BT bin-tile width, n_kt = B / BT; LT output-tile height):
+//   filter spectra  H[kt][l0..][r][LTt][BT]  (for each bin tile kt and output
+//                   tile starting at l0 with LTt rows, all r are contiguous)
+//   FDL ring        X[kt][q][slot][BT]       (slot of partition p at block n:
+//                   (p - n) mod K, so a run of partitions is a run of slots)
+//   partials        P[split][l][B]           float2, one row per partition split
+// All spectra use the packed layout described in kernels.h.
+#include <cuda_runtime.h>
+
+#include "device_util.cuh"
+#include "kernels.h"
+
+namespace gbconv {
+
+namespace {
+
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;  // 1 s: far beyond any legitimate wait
+
+__device__ float block_max(float v, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? red[lane] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) red[0] = v;
+    }
+    __syncthreads();
+    const float r = red[0];
+    return r;
+}
+
+// Element index of bin k of ring slot `slot` of channel c (layout X[kt][c][slot][BT]).
+struct RingIndex {
+    int BT, n_ch, c, K, slot;
+    __device__ size_t operator()(int k) const {
+        const int kt = k / BT, kl = k - kt * BT;
+        return (((size_t)kt * n_ch + c) * K + slot) * BT + kl;
+    }
+};
+
+// Element index of bin k of sub-filter r of output l (layout H[kt][l0..][r][LTt][BT]).
+struct FilterIndex {
+    int BT, n_dst, l0, R, r, LTt, ll;
+    __device__ size_t operator()(int k) const {
+        const int kt = k / BT, kl = k - kt * BT;
+        return (((size_t)kt * n_dst + l0) * (size_t)R + (size_t)r * LTt + ll) * BT + kl;
+    }
+};
+
+// Writes the packed spectrum Xs[0..B) (shared memory) in storage precision.
+// `dst_index(k)` gives the element index of bin k.  Returns the scale used.
+template <int PREC, typename IndexFn>
+__device__ float store_spectrum(const float2* Xs, int B, void* dst, IndexFn dst_index, float* red) {
+    float scale = 1.0f;
+    if (PREC != PREC_FP32) {
+        float mx = 0.0f;
+        for (int k = threadIdx.x; k < B; k += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(Xs[k].x), fabsf(Xs[k].y)));
+        mx = block_max(mx, red);
+        scale = block_scale<PREC>(mx);
+    }
+    const float inv = 1.0f / scale;  // exact: scale is a power of two
+    for (int k = threadIdx.x; k < B; k += blockDim.x) Store<PREC>::store1(dst, dst_index(k), cscale(Xs[k], inv));
+    return scale;
+}
+
+// ------------------------------------------------------------ pack + R2C
+// One CTA per channel.  w = [previous block, in - sub]; z[n] = w[2n] + i w[2n+1];
+// B-point FFT; real-FFT post-processing; push into the ring slot.
+template <int PREC>
+__global__ void k_pack_r2c(const PackArgs a) {
+    extern __shared__ float2 fsm[];
+    __shared__ float red[32];
+    const int B = a.B, half = B >> 1, c = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    float2* bufA = fsm;
+    float2* bufB = fsm + B;
+    const float* in = a.in + (size_t)c * a.in_stride;
+    const float* sub = a.sub ? a.sub + (size_t)c * B : nullptr;
+    float* win = a.win + (size_t)c * B;
+
+    for (int n = tid; n < B; n += nth) {
+        float2 z;
+        if (n < half) {
+            z = make_float2(win[2 * n], win[2 * n + 1]);
+        } else {
+            const int t = 2 * n - B;
+            float v0 = in[t], v1 = in[t + 1];
+            if (sub) {
+                v0 -= sub[t];
+                v1 -= sub[t + 1];
+            }
+            z = make_float2(v0, v1);
+        }
+        bufA[n] = z;
+    }
+    __syncthreads();
+    for (int t = tid; t < B; t += nth) {
+        const float v = sub ? in[t] - sub[t] : in[t];
+        win[t] = v;
+        if (a.e_out) a.e_out[(size_t)c * B + t] = v;
+    }
+    float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, a.tw, a.log2B + 1, tid, nth);
+    float2* Xs = (Z == bufA) ? bufB : bufA;
+    for (int k = tid; k < B; k += nth) Xs[k] = r2c_post(Z, k, B, a.tw);
+    __syncthreads();
+    const float scale = store_spectrum<PREC>(Xs, B, a.X, RingIndex{a.BT, a.n_ch, c, a.K, a.slot}, red);
+    if (PREC != PREC_FP32 && tid == 0) a.sX[(size_t)c * a.K + a.slot] = scale;
+}
+
+// --------------------------------------------------- filter partitions R2C
+// One CTA per (l, q, p): sub-filter h_lq[pB, pB+B) zero-padded to 2B, R2C.
+template <int PREC>
+__global__ void k_filter_r2c(const FilterArgs a) {
+    extern __shared__ float2 fsm[];
+    __shared__ float red[32];
+    const int B = a.B, half = B >> 1, tid = threadIdx.x, nth = blockDim.x;
+    const int K = a.K, R = a.n_src * K;
+    const int l = blockIdx.x / R;
+    const int r = blockIdx.x - l * R;
+    const int q = r / K, p = r - q * K;
+    const float* h = a.h + ((size_t)l * a.n_src + q) * (size_t)a.taps;
+    const long long t0 = (long long)p * B;
+    float2* bufA = fsm;
+    float2* bufB = fsm + B;
+    for (int n = tid; n < B; n += nth) {
+        float2 z = make_float2(0.0f, 0.0f);
+        if (n < half) {
+            const long long t = t0 + 2 * n;
+            z.x = t < a.taps ? h[t] : 0.0f;
+            z.y = t + 1 < a.taps ? h[t + 1] : 0.0f;
+        }
+        bufA[n] = z;
+    }
+    __syncthreads();
+    float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, a.tw, a.log2B + 1, tid, nth);
+    float2* Xs = (Z == bufA) ? bufB : bufA;
+    for (int k = tid; k < B; k += nth) Xs[k] = r2c_post(Z, k, B, a.tw);
+    __syncthreads();
+    const int l0 = (l / a.LT) * a.LT;
+    const int LTt = min(a.LT, a.n_dst - l0), ll = l - l0;
+    const float scale =
+        store_spectrum<PREC>(Xs, B, a.H, FilterIndex{a.BT, a.n_dst, l0, R, r, LTt, ll}, red);
+    if (PREC != PREC_FP32 && tid == 0) a.sH[(size_t)l * R + r] = scale;
+}
+
+// ----------------------------------------------------------- FDL MAC
+// Y[l][k] += sum_{r in split} H[l][r][k] * X[q(r)][slot(r)][k]   (Eq. 6 per bin)
+//
+// One CTA per (bin tile, output tile, partition split).  Warp 8 is the
+// producer: one elected lane streams the split's contiguous filter-spectrum
+// range and the matching delay-line slots into an nstage-deep shared-memory
+// ring with 1-D bulk copies (TMA), completion tracked by mbarriers (filters
+// with an evict-first L2 policy: they are read once per block; the delay line
+// with evict-last: it is re-read by every output tile and by the next blocks).
+// Warps 0-7 consume: each thread owns VEC bins x up to LPT outputs for one
+// r-lane and accumulates in FP32 registers; r-lanes are combined in a fixed
+// order through shared memory at the end, and the split's sums go to P[split].
+template <int PREC, int LPT>
+__global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
+    using St = Store<PREC>;
+    constexpr int VEC = St::VEC;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + MAX_STAGES;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + MAX_STAGES);
+    unsigned char* stages = smem + MAC_HDR_BYTES;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x / a.S, split = blockIdx.x - tile * a.S;
+    const int kt = tile / a.n_lt, lt = tile - kt * a.n_lt;
+    const int l0 = lt * a.LT, LTt = min(a.LT, a.n_dst - l0);
+    const int K = a.K, R = a.n_src * K;
+    const int r0 = (int)((long long)split * R / a.S), r1 = (int)((long long)(split + 1) * R / a.S);
+    const int nit = (r1 - r0 + a.RS - 1) / a.RS;
+    const size_t hrow = (size_t)a.BT * St::BYTES;
+    const size_t hr_bytes = (size_t)LTt * hrow;
+    const unsigned char* Hb =
+        static_cast<const unsigned char*>(a.H) + ((size_t)kt * a.n_dst + l0) * (size_t)R * hrow;
+    const unsigned char* Xb = static_cast<const unsigned char*>(a.X) + (size_t)kt * a.n_src * K * hrow;
+
+    if (tid == 0) {
+        for (int i = 0; i < a.nstage; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], MAC_CONSUMER_WARPS);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == MAC_CONSUMER_WARPS) {
+        if (lane != 0) return;
+        const uint64_t pol_stream = policy_evict_first();
+        const uint64_t pol_keep = policy_evict_last();
+        int issued = 0;
+        bool ok = true;
+        for (int it = 0; it < nit; ++it) {
+            const int st = it % a.nstage;
+            if (it >= a.nstage &&
+                !mbar_wait_bounded(&empty[st], ((it / a.nstage) - 1) & 1, abort_flag, WAIT_LIMIT_NS)) {
+                *abort_flag = 1;
+                if (a.err) *(volatile int*)a.err = DEVERR_TIMEOUT_PRODUCER;
+                ok = false;
+                break;
+            }
+            const int ra = r0 + it * a.RS, rb = min(ra + a.RS, r1), nr = rb - ra;
+            unsigned char* sh = stages + (size_t)st * a.stage_bytes;
+            unsigned char* sx = sh + a.xoff;
+            mbar_arrive_expect_tx(&full[st], (uint32_t)((size_t)nr * (hr_bytes + hrow)));
+            bulk_g2s(sh, Hb + (size_t)ra * hr_bytes, (uint32_t)((size_t)nr * hr_bytes), &full[st], pol_stream);
+            int r = ra, j = 0;
+            while (r < rb) {
+                const int q = r / K, p = r - q * K;
+                int slot = a.slot0 + p;
+                if (slot >= K) slot -= K;
+                const int run = min(rb - r, min(K - p, K - slot));
+                bulk_g2s(sx + (size_t)j * hrow, Xb + ((size_t)q * K + slot) * hrow, (uint32_t)(run * hrow),
+                         &full[st], pol_keep);
+                r += run;
+                j += run;
+            }
+            ++issued;
+        }
+        if (!ok) {
+            // let copies already in flight land before the CTA's shared memory goes away
+            for (int it = issued > a.nstage ? issued - a.nstage : 0; it < issued; ++it)
+                mbar_wait_bounded(&full[it % a.nstage], (it / a.nstage) & 1, nullptr, WAIT_LIMIT_NS);
+        }
+        return;
+    }
+
+    // consumers
+    const int kv = tid % a.kthreads, rest = tid / a.kthreads;
+    const int lg = rest % a.NLG, rl = rest / a.NLG;
+    const int kglob = kt * a.BT + kv * VEC;
+    const bool dc = (kglob == 0);
+    float2 acc[LPT][VEC];
+#pragma unroll
+    for (int i = 0; i < LPT; ++i)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[i][v] = make_float2(0.0f, 0.0f);
+
+    bool ok = true;
+    for (int it = 0; it < nit; ++it) {
+        const int st = it % a.nstage;
+        if (!mbar_wait_bounded(&full[st], (it / a.nstage) & 1, abort_flag, WAIT_LIMIT_NS)) {
+            *abort_flag = 1;
+            if (a.err) *(volatile int*)a.err = DEVERR_TIMEOUT_CONSUMER;
+            ok = false;
+            break;
+        }
+        const int ra = r0 + it * a.RS, nr = min(a.RS, r1 - ra);
+        const unsigned char* sh = stages + (size_t)st * a.stage_bytes;
+        const unsigned char* sx = sh + a.xoff;
+        for (int j = rl; j < nr; j += a.NRL) {
+            float2 xv[VEC];
+            St::load16(sx + (size_t)j * hrow + (size_t)kv * 16, xv);
+            float sxs = 1.0f;
+            if (PREC != PREC_FP32) {
+                const int r = ra + j, q = r / K, p = r - q * K;
+                int slot = a.slot0 + p;
+                if (slot >= K) slot -= K;
+                sxs = __ldg(a.sX + (size_t)q * K + slot);
+            }
+#pragma unroll
+            for (int i = 0; i < LPT; ++i) {
+                const int ll = lg + i * a.NLG;
+                if (ll < LTt) {
+                    float2 hv[VEC];
+                    St::load16(sh + ((size_t)j * LTt + ll) * hrow + (size_t)kv * 16, hv);
+                    if (PREC == PREC_FP32) {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            if (v == 0 && dc)
+                                rmac2(acc[i][v], hv[v], xv[v]);
+                            else
+                                cmac(acc[i][v], hv[v], xv[v]);
+                        }
+                    } else {
+                        const float sc = sxs * __ldg(a.sH + (size_t)(l0 + ll) * R + ra + j);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            float2 t = make_float2(0.0f, 0.0f);
+                            if (v == 0 && dc)
+                                rmac2(t, hv[v], xv[v]);
+                            else
+                                cmac(t, hv[v], xv[v]);
+                            acc[i][v].x = fmaf(sc, t.x, acc[i][v].x);
+                            acc[i][v].y = fmaf(sc, t.y, acc[i][v].y);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+    }
+
+    // combine r-lanes in a fixed order (stage memory is free: every stage has landed)
+    if (a.NRL > 1) {
+        named_barrier_sync(1, MAC_CONSUMER_WARPS * 32);
+        float2* red = reinterpret_cast<float2*>(stages);
+        const int LT = a.LT, BT = a.BT;
+        if (rl > 0) {
+#pragma unroll
+            for (int i = 0; i < LPT; ++i) {
+                const int ll = lg + i * a.NLG;
+                if (ll < LTt)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) red[((size_t)(rl - 1) * LT + ll) * BT + kv * VEC + v] = acc[i][v];
+            }
+        }
+        named_barrier_sync(1, MAC_CONSUMER_WARPS * 32);
+        if (rl == 0) {
+            for (int rr = 1; rr < a.NRL; ++rr)
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) {
+                    const int ll = lg + i * a.NLG;
+                    if (ll < LTt)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v)
+                            acc[i][v] = cadd(acc[i][v], red[((size_t)(rr - 1) * LT + ll) * BT + kv * VEC + v]);
+                }
+        }
+    }
+    if (rl != 0 || !ok || *abort_flag) return;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        const int ll = lg + i * a.NLG;
+        if (ll < LTt) {
+            float2* dst = a.partial + ((size_t)split * a.n_dst + l0 + ll) * a.B + kglob;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) dst[v] = acc[i][v];
+        }
+    }
+}
+
+// ------------------------------------------------- reduce + C2R + OLS
+// One CTA per output channel: sum the partition splits in a fixed two-level
+// order, C2R IFFT (1/2B), keep the last B samples (overlap-save).
+__global__ void k_reduce_c2r(const ReduceArgs a) {
+    extern __shared__ float2 fsm[];
+    const int B = a.B, l = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    float2* P = fsm;
+    float2* W = fsm + B;
+    const size_t stride = (size_t)a.n_dst * B;
+    for (int k = tid; k < B; k += nth) {
+        const float2* src = a.partial + (size_t)l * B + k;
+        float2 tot = make_float2(0.0f, 0.0f);
+        for (int s0 = 0; s0 < a.S; s0 += 16) {
+            const int s1 = min(s0 + 16, a.S);
+            float2 part = make_float2(0.0f, 0.0f);
+            for (int s = s0; s < s1; ++s) part = cadd(part, src[(size_t)s * stride]);
+            tot = cadd(tot, part);
+        }
+        P[k] = tot;
+    }
+    __syncthreads();
+    for (int k = tid; k < B; k += nth) W[k] = c2r_pre(P, k, B, a.tw);
+    __syncthreads();
+    const float2* z = fft_smem<true>(W, P, B, a.log2B, a.tw, a.log2B + 1, tid, nth);
+    const float invB = 1.0f / (float)B;
+    float* out = a.out + (size_t)l * a.out_stride;
+    for (int t = tid; t < B; t += nth) {
+        const int u = B + t, n = u >> 1;
+        out[t] = ((u & 1) ? z[n].y : z[n].x) * invB;
+    }
+}
+
+template <int PREC>
+constexpr int lpt_for() {
+    return PREC == PREC_FP32 ? 8 : 4;
+}
+
+}  // namespace
+
+int fft_threads(int B) {
+    int t = B / 4;
+    if (t < 32) t = 32;
+    if (t > 256) t = 256;
+    return t;
+}
+
+size_t fft_smem_bytes(int B) { return (size_t)2 * B * sizeof(float2); }
+
+cudaError_t prepare_kernels(size_t mac_smem) {
+    const int fft_max = (int)fft_smem_bytes(4096);
+    cudaError_t e;
+#define GB_ATTR(kern, bytes)                                                                     \
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
+    if (e != cudaSuccess) return e;
+    GB_ATTR(k_pack_r2c<PREC_FP32>, fft_max)
+    GB_ATTR(k_pack_r2c<PREC_FP16>, fft_max)
+    GB_ATTR(k_pack_r2c<PREC_BF16>, fft_max)
+    GB_ATTR(k_filter_r2c<PREC_FP32>, fft_max)
+    GB_ATTR(k_filter_r2c<PREC_FP16>, fft_max)
+    GB_ATTR(k_filter_r2c<PREC_BF16>, fft_max)
+    GB_ATTR(k_reduce_c2r, fft_max)
+    GB_ATTR((k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>()>), mac_smem)
+    GB_ATTR((k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>()>), mac_smem)
+    GB_ATTR((k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>()>), mac_smem)
+#undef GB_ATTR
+    return cudaSuccess;
+}
+
+cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s) {
+    const dim3 grid(a.n_ch), block(fft_threads(a.B));
+    const size_t sm = fft_smem_bytes(a.B);
+    switch (prec) {
+        case PREC_FP32: k_pack_r2c<PREC_FP32><<<grid, block, sm, s>>>(a); break;
+        case PREC_FP16: k_pack_r2c<PREC_FP16><<<grid, block, sm, s>>>(a); break;
+        case PREC_BF16: k_pack_r2c<PREC_BF16><<<grid, block, sm, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s) {
+    const long long n = (long long)a.n_dst * a.n_src * a.K;
+    if (n <= 0 || n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)n), block(fft_threads(a.B));
+    const size_t sm = fft_smem_bytes(a.B);
+    switch (prec) {
+        case PREC_FP32: k_filter_r2c<PREC_FP32><<<grid, block, sm, s>>>(a); break;
+        case PREC_FP16: k_filter_r2c<PREC_FP16><<<grid, block, sm, s>>>(a); break;
+        case PREC_BF16: k_filter_r2c<PREC_BF16><<<grid, block, sm, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
+    const dim3 grid(p.ctas), block(MAC_THREADS);
+    switch (prec) {
+        case PREC_FP32: k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>()><<<grid, block, p.smem, s>>>(a); break;
+        case PREC_FP16: k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>()><<<grid, block, p.smem, s>>>(a); break;
+        case PREC_BF16: k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>()><<<grid, block, p.smem, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_c2r(const ReduceArgs& a, cudaStream_t s) {
+    k_reduce_c2r<<<a.n_dst, fft_threads(a.B), fft_smem_bytes(a.B), s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gbconv

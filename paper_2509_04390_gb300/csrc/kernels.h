@@ -1,0 +1,103 @@
+// kernels.h - argument blocks and host launchers of the engine's CUDA kernels.
+//
+// Kernels (all hand-written for sm_103a, FP32 arithmetic):
+//   pack_r2c    input packing + 2B-point R2C FFT + FDL push   (Sec. 4, stage 1)
+//   filter_r2c  sub-filter zero-padding + R2C FFT            (Sec. 4, initialisation)
+//   fdl_mac     FDL complex multiply-accumulate over all partitions and
+//               input->output pairs, split over partition ranges (Sec. 4, stage 2; Eq. 6)
+//   reduce_c2r  fixed-order reduction of the partition splits, C2R IFFT and
+//               overlap-save discard                          (Sec. 4, stage 3)
+//
+// Spectra are "packed": bins 0..B-1 of the 2B-point real FFT, with the real
+// Nyquist bin B stored in the imaginary slot of bin 0 (both are real for a
+// real signal), so every row is B complex values.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace gbconv {
+
+enum Prec { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2 };
+
+// Device error codes written to the engine's host-mapped error word.
+enum DevErr { DEVERR_NONE = 0, DEVERR_TIMEOUT_PRODUCER = 1, DEVERR_TIMEOUT_CONSUMER = 2 };
+
+constexpr int MAC_CONSUMER_WARPS = 8;
+constexpr int MAC_THREADS = (MAC_CONSUMER_WARPS + 1) * 32;  // + one producer warp
+constexpr int MAC_HDR_BYTES = 1024;                          // mbarriers + flags
+constexpr int MAX_STAGES = 8;
+
+// Tiling of one FDL MAC (one partitioned convolution with n_src inputs, n_dst
+// outputs and K partitions).  Spectra of a (bin tile, output tile) pair are
+// stored contiguously over the reduction index r = q*K + p, so each CTA streams
+// one contiguous range.
+struct MacPlan {
+    int B, n_src, n_dst, K, R;
+    int es;        // bytes per stored complex value (8 fp32, 4 fp16/bf16)
+    int VEC;       // complex values per 16-byte load
+    int LPT;       // max outputs per consumer thread
+    int BT, n_kt;  // bin tile width, number of bin tiles
+    int LT, n_lt;  // output tile height, number of output tiles
+    int kthreads, NLG, NRL;  // consumer thread layout: bins x output groups x r-lanes
+    int RS;        // reduction indices per pipeline stage
+    int nstage;    // pipeline depth
+    int S;         // partition splits per tile
+    unsigned stage_bytes, xoff;
+    size_t smem;   // dynamic shared memory per CTA
+    int ctas;
+    size_t h_bytes, x_bytes, partial_bytes;
+};
+
+struct MacArgs {
+    const void* H;
+    const void* X;
+    const float* sH;  // [n_dst][R] per-partition scales (reduced precision), else null
+    const float* sX;  // [n_src][K] per-slot scales (reduced precision), else null
+    float2* partial;  // [S][n_dst][B]
+    int B, BT, n_kt, n_dst, LT, n_lt, n_src, K, S, RS, nstage;
+    int kthreads, NLG, NRL;
+    int slot0;  // ring slot of partition 0 for this block
+    unsigned stage_bytes, xoff;
+    int* err;   // device-visible error word (host-mapped)
+};
+
+struct PackArgs {
+    const float* in;  // [n_ch][in_stride], first B samples of each row used
+    int in_stride;
+    const float* sub;  // [n_ch][B] subtracted from `in` (feedback prediction), or null
+    float* e_out;      // [n_ch][B] receives in - sub, or null
+    float* win;        // [n_ch][B] previous block (sliding-window state)
+    void* X;           // FDL ring [n_kt][n_ch][K][BT] (storage type)
+    float* sX;         // [n_ch][K] slot scales (reduced precision), else null
+    int B, log2B, BT, n_ch, K, slot;
+    const float2* tw;  // W_2B^j = exp(-i pi j / B), j in [0, 2B)
+};
+
+struct FilterArgs {
+    const float* h;  // [n_dst][n_src][taps]
+    long long taps;
+    int n_dst, n_src, K, B, log2B, BT, LT;
+    void* H;    // tiled spectra
+    float* sH;  // [n_dst][n_src*K] scales (reduced precision), else null
+    const float2* tw;
+};
+
+struct ReduceArgs {
+    const float2* partial;  // [S][n_dst][B]
+    int S, n_dst, B, log2B;
+    const float2* tw;
+    float* out;  // [n_dst][out_stride]
+    int out_stride;
+};
+
+int fft_threads(int B);
+size_t fft_smem_bytes(int B);
+
+cudaError_t prepare_kernels(size_t mac_smem);
+cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s);
+cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s);
+cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_c2r(const ReduceArgs& a, cudaStream_t s);
+
+}  // namespace gbconv

@@ -1,0 +1,319 @@
+"""Thin ctypes binding of the engine's C ABI (``include/conv.h``).
+
+Function names match the C entry points; this module only marshals arguments
+(numpy arrays for host buffers, raw device addresses or torch tensors for the
+``*_async`` forms) and turns negative status codes into ``ConvError``.  All
+computation runs in the CUDA library; if it has not been built, loading fails
+with an error instead of falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CONV_OK = 0
+CONV_E_INVAL = -1
+CONV_E_STATE = -2
+CONV_E_NOMEM = -3
+CONV_E_CUDA = -4
+CONV_E_TIMEOUT = -5
+CONV_E_UNSTABLE = -6
+
+CONV_FP32 = 0
+CONV_FP16 = 1
+CONV_BF16 = 2
+
+PRECISIONS = {"fp32": CONV_FP32, "fp16": CONV_FP16, "bf16": CONV_BF16}
+
+
+class ConvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class conv_info(ctypes.Structure):
+    _fields_ = [
+        (name, ctypes.c_longlong)
+        for name in (
+            "block",
+            "n_in",
+            "n_out",
+            "taps",
+            "K",
+            "taps_fb",
+            "K_fb",
+            "precision",
+            "mac_bytes",
+            "mac_fb_bytes",
+            "mac_ctas",
+            "mac_splits",
+            "mac_smem",
+            "device_bytes",
+            "kernels_per_block",
+            "kernels_per_afc_block",
+        )
+    ]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.lib_path()
+
+
+def load():
+    """Load the engine library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA engine library not found at {path}; build it with "
+            "`python -m paper_2509_04390_gb300.build` (there is no CPU fallback)"
+        )
+    L = ctypes.CDLL(path)
+    vp, i, ll, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+    sig = {
+        "conv_create": (vp, [d, i, i, i, ll]),
+        "conv_set_precision": (i, [vp, i]),
+        "conv_set_filters": (i, [vp, vp]),
+        "afc_set_paths": (i, [vp, vp, ll]),
+        "conv_process_block": (i, [vp, vp, vp]),
+        "conv_process_block_async": (i, [vp, vp, vp, vp]),
+        "afc_process_block": (i, [vp, vp, vp, vp]),
+        "afc_process_block_async": (i, [vp, vp, vp, vp, vp]),
+        "afc_set_guard": (i, [vp, d]),
+        "conv_reset": (i, [vp]),
+        "conv_synchronize": (i, [vp]),
+        "conv_get_info": (i, [vp, ctypes.POINTER(conv_info)]),
+        "conv_profile_enable": (i, [vp, i]),
+        "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+        "conv_plan_check": (i, [i, i, i, i, ll, i]),
+        "conv_destroy": (None, [vp]),
+        "conv_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def conv_last_error() -> str:
+    return load().conv_last_error().decode(errors="replace")
+
+
+def _check(rc: int) -> int:
+    if rc != CONV_OK:
+        raise ConvError(rc, conv_last_error())
+    return rc
+
+
+def _host_ptr(a: np.ndarray, shape, writable=False):
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float32 numpy array")
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {a.shape}")
+    if writable and not a.flags["WRITEABLE"]:
+        raise ValueError("output array is read-only")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t):
+    """Device address of a torch tensor (float32, contiguous, CUDA) or an int."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    import torch
+
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- C names
+
+
+def conv_create(fs: float, block: int, n_in: int, n_out: int, taps: int):
+    h = load().conv_create(float(fs), int(block), int(n_in), int(n_out), int(taps))
+    if not h:
+        raise ConvError(CONV_E_INVAL, conv_last_error())
+    return h
+
+
+def conv_set_precision(h, mode):
+    mode = PRECISIONS.get(mode, mode)
+    return _check(load().conv_set_precision(h, int(mode)))
+
+
+def conv_set_filters(h, filters: np.ndarray):
+    info = conv_get_info(h)
+    return _check(load().conv_set_filters(h, _host_ptr(filters, (info["n_out"], info["n_in"], info["taps"]))))
+
+
+def afc_set_paths(h, paths: np.ndarray):
+    info = conv_get_info(h)
+    if paths.ndim != 3:
+        raise ValueError("paths must be [n_in][n_out][taps_fb]")
+    _host_ptr(paths, (info["n_in"], info["n_out"], paths.shape[2]))
+    return _check(load().afc_set_paths(h, paths.ctypes.data_as(ctypes.c_void_p), int(paths.shape[2])))
+
+
+def conv_process_block(h, inp: np.ndarray, out: np.ndarray, _shape=None):
+    n_in, n_out, B = _shape if _shape else _dims(h)
+    return _check(load().conv_process_block(h, _host_ptr(inp, (n_in, B)), _host_ptr(out, (n_out, B), True)))
+
+
+def conv_process_block_async(h, d_in, d_out, stream=None):
+    return _check(load().conv_process_block_async(h, _dev_ptr(d_in), _dev_ptr(d_out), _stream_ptr(stream)))
+
+
+def afc_process_block(h, mic: np.ndarray, out: np.ndarray, e_out: np.ndarray | None = None, _shape=None):
+    n_in, n_out, B = _shape if _shape else _dims(h)
+    ep = _host_ptr(e_out, (n_in, B), True) if e_out is not None else None
+    return _check(load().afc_process_block(h, _host_ptr(mic, (n_in, B)), _host_ptr(out, (n_out, B), True), ep))
+
+
+def afc_process_block_async(h, d_mic, d_out, d_e=None, stream=None):
+    return _check(
+        load().afc_process_block_async(h, _dev_ptr(d_mic), _dev_ptr(d_out), _dev_ptr(d_e), _stream_ptr(stream))
+    )
+
+
+def afc_set_guard(h, max_rms: float):
+    return _check(load().afc_set_guard(h, float(max_rms)))
+
+
+def conv_reset(h):
+    return _check(load().conv_reset(h))
+
+
+def conv_synchronize(h):
+    return _check(load().conv_synchronize(h))
+
+
+def conv_get_info(h) -> dict:
+    info = conv_info()
+    _check(load().conv_get_info(h, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def conv_profile_enable(h, enable: int):
+    return _check(load().conv_profile_enable(h, int(enable)))
+
+
+def conv_profile_read(h):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(load().conv_profile_read(h, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def conv_plan_check(precision, block, n_src, n_dst, taps, num_sms=152):
+    precision = PRECISIONS.get(precision, precision)
+    return _check(load().conv_plan_check(int(precision), int(block), int(n_src), int(n_dst), int(taps), int(num_sms)))
+
+
+def conv_destroy(h):
+    if h:
+        load().conv_destroy(h)
+
+
+def _dims(h):
+    i = conv_get_info(h)
+    return i["n_in"], i["n_out"], i["block"]
+
+
+# ------------------------------------------------------------ convenience
+
+
+class Engine:
+    """Owning wrapper: ``with Engine(fs, block, n_in, n_out, taps) as e: ...``."""
+
+    def __init__(self, fs, block, n_in, n_out, taps, precision="fp32"):
+        self.h = conv_create(fs, block, n_in, n_out, taps)
+        self.shape = (int(n_in), int(n_out), int(block))
+        try:
+            if precision not in ("fp32", CONV_FP32):
+                conv_set_precision(self.h, precision)
+        except Exception:
+            conv_destroy(self.h)
+            raise
+
+    def set_filters(self, h: np.ndarray):
+        conv_set_filters(self.h, np.ascontiguousarray(h, dtype=np.float32))
+
+    def set_paths(self, f: np.ndarray):
+        afc_set_paths(self.h, np.ascontiguousarray(f, dtype=np.float32))
+
+    def process(self, x_block: np.ndarray, out: np.ndarray | None = None) -> np.ndarray:
+        n_in, n_out, B = self.shape
+        if out is None:
+            out = np.empty((n_out, B), dtype=np.float32)
+        conv_process_block(self.h, np.ascontiguousarray(x_block, dtype=np.float32), out, self.shape)
+        return out
+
+    def process_afc(self, mic_block, out=None, e_out=None):
+        n_in, n_out, B = self.shape
+        if out is None:
+            out = np.empty((n_out, B), dtype=np.float32)
+        afc_process_block(self.h, np.ascontiguousarray(mic_block, dtype=np.float32), out, e_out, self.shape)
+        return out
+
+    def run(self, x: np.ndarray) -> np.ndarray:
+        """Stream a whole [n_in][T] signal (zero-extended to whole blocks)."""
+        n_in, n_out, B = self.shape
+        T = x.shape[1]
+        nb = -(-T // B)
+        xp = np.zeros((n_in, nb * B), dtype=np.float32)
+        xp[:, :T] = x
+        y = np.empty((n_out, nb * B), dtype=np.float32)
+        blk = np.empty((n_out, B), dtype=np.float32)
+        for b in range(nb):
+            self.process(np.ascontiguousarray(xp[:, b * B : (b + 1) * B]), blk)
+            y[:, b * B : (b + 1) * B] = blk
+        return y
+
+    def info(self):
+        return conv_get_info(self.h)
+
+    def reset(self):
+        conv_reset(self.h)
+
+    def close(self):
+        if self.h:
+            conv_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,103 @@
+"""The C-ABI library builds, loads and exports every entry point of include/conv.h.
+
+No compute calls: these run on machines without a GPU.
+"""
+
+import os
+import re
+
+import pytest
+
+from paper_2509_04390_gb300 import build, upols
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        text = re.sub(r"#[^\n]*", " ", text)
+        text = re.sub(r"typedef[^;]*;", " ", text)
+        text = re.sub(r"typedef\s+struct\s+\w+\s*\{.*?\}\s*\w+\s*;", " ", text, flags=re.S)
+        for m in re.finditer(r"\b([A-Za-z_]\w*)\s*\(([^;{}]*)\)\s*;", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(build.lib_path()):
+        build.build()
+    return upols.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in (
+        "conv_create",
+        "conv_set_precision",
+        "conv_set_filters",
+        "afc_set_paths",
+        "conv_process_block",
+        "conv_process_block_async",
+        "afc_process_block",
+        "conv_reset",
+        "conv_destroy",
+        "conv_last_error",
+    ):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    for n in declared_functions():
+        assert hasattr(upols, n), n
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.conv_reset(None) == upols.CONV_E_INVAL
+    assert lib.conv_set_filters(None, None) == upols.CONV_E_INVAL
+    assert lib.conv_process_block(None, None, None) == upols.CONV_E_INVAL
+    assert "null" in upols.conv_last_error()
+    lib.conv_destroy(None)  # NULL-safe
+
+
+def test_invalid_sizes_fail_before_touching_a_device(lib):
+    assert not lib.conv_create(48000.0, 100, 1, 2, 1000)  # not a power of two
+    assert "power of two" in upols.conv_last_error()
+    assert not lib.conv_create(48000.0, 8192, 1, 2, 1000)  # above 4096
+    assert not lib.conv_create(48000.0, 256, 0, 2, 1000)
+    assert not lib.conv_create(48000.0, 256, 1, 2, 0)
+    assert not lib.conv_create(-1.0, 256, 1, 2, 10)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_mac_plan_addresses_stay_in_bounds(lib, precision):
+    # every tiling the engine would pick for these sizes replays in bounds
+    shapes = [
+        (1, 1, 1),
+        (1, 2, 48000),
+        (4, 16, 384000),
+        (16, 4, 24000),
+        (3, 20, 1000),
+        (2, 5, 4000),
+        (8, 32, 200000),
+        (1, 64, 720000),
+        (5, 7, 2048),
+        (4, 33, 3000),
+        (7, 1024, 100),
+        (1024, 3, 50),
+    ]
+    for B in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096):
+        for n_src, n_dst, taps in shapes:
+            for sms in (152, 148, 8):
+                upols.conv_plan_check(precision, B, n_src, n_dst, taps, sms)

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA engine, called through its C ABI, against the FP64 oracle.
+
+Tolerance: output SNR against the oracle, 10 log10(sum ref^2 / sum err^2),
+pooled over all channels and samples.  FP32 spectra must reach 120 dB (and
+115 dB on the worst single channel).  Reduced-precision storage is bounded by
+its rounding: FP16 keeps 11 significant bits (relative rounding error
+2^-12 ~ 2.4e-4 per stored value; with filter and delay line both rounded,
+about 3.4e-4 rms per product -> ~69 dB), BF16 keeps 8 bits (~2.8e-3 -> ~51 dB);
+the tests require 60 dB and 42 dB.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import RoomPlant, sample_points, snr_db, snr_per_channel_db
+from oracle import afc_closed_loop, mimo_fir_sample, upols
+from paper_2509_04390_gb300 import build, signals
+from paper_2509_04390_gb300 import upols as U
+
+pytestmark = pytest.mark.gpu
+
+FP32_DB = 120.0
+FP32_CH_DB = 115.0
+FP16_DB = 60.0
+BF16_DB = 42.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def engine_lib():
+    if not os.path.exists(build.lib_path()):
+        build.build()
+    U.load()
+
+
+def run_gpu(w, precision="fp32", n_blocks=None):
+    x = w.x
+    if n_blocks is not None:
+        x = x[:, : n_blocks * w.block]
+    with U.Engine(w.fs, w.block, w.n_in, w.n_out, w.taps, precision) as e:
+        e.set_filters(w.h)
+        return e.run(x)
+
+
+def oracle_out(w, n_blocks=None):
+    x = w.x.astype(np.float64)
+    if n_blocks is not None:
+        x = x[:, : n_blocks * w.block]
+    return upols(w.h.astype(np.float64), x, w.block)
+
+
+# ----------------------------------------------------------- exact cases
+
+
+@pytest.mark.parametrize("B", [16, 32, 64, 128, 256, 512, 1024, 2048, 4096])
+def test_identity_filter_every_block_size(B):
+    # h = delta: output = input, exercising every FFT size (odd and even log2 B)
+    rng = np.random.default_rng(B)
+    h = np.zeros((2, 2, 3 * B + 5), dtype=np.float32)
+    h[0, 0, 0] = 1.0
+    h[1, 1, 0] = 1.0
+    x = rng.standard_normal((2, 6 * B)).astype(np.float32)
+    with U.Engine(48000, B, 2, 2, h.shape[2]) as e:
+        e.set_filters(h)
+        y = e.run(x)
+    assert snr_db(y, x) >= FP32_DB
+    np.testing.assert_allclose(y, x, atol=2e-6)
+
+
+@pytest.mark.parametrize("B", [16, 128, 1024])
+def test_dirac_input_returns_filter(B):
+    rng = np.random.default_rng(3 + B)
+    taps = 5 * B + 3
+    h = rng.standard_normal((3, 1, taps)).astype(np.float32)
+    x = np.zeros((1, 7 * B), dtype=np.float32)
+    x[0, 0] = 1.0
+    with U.Engine(48000, B, 1, 3, taps) as e:
+        e.set_filters(h)
+        y = e.run(x)
+    assert snr_db(y[:, :taps], h[:, 0, :]) >= FP32_DB
+    assert np.max(np.abs(y[:, taps:])) < 1e-5
+
+
+# ------------------------------------------------------------- plain 1x2
+
+
+def test_plain_1x2_full_signal_fp32():
+    """1 input x 2 outputs, 1 s filters, 2 s white noise, block 256: every sample."""
+    w = signals.plain_1x2()
+    y = run_gpu(w)
+    ref = oracle_out(w)
+    assert snr_db(y, ref) >= FP32_DB
+    assert min(snr_per_channel_db(y, ref)) >= FP32_CH_DB
+
+
+@pytest.mark.parametrize("precision,bound", [("fp16", FP16_DB), ("bf16", BF16_DB)])
+def test_plain_1x2_reduced_precision(precision, bound):
+    w = signals.plain_1x2()
+    y = run_gpu(w, precision)
+    ref = oracle_out(w)
+    s = snr_db(y, ref)
+    print(f"{precision}: SNR {s:.1f} dB")
+    assert s >= bound
+
+
+# ------------------------------------------------ tiles, splits, ragged
+
+
+@pytest.mark.parametrize(
+    "n_in,n_out,taps,B,nb",
+    [
+        (1, 1, 1, 16, 4),  # single tap, K = 1
+        (2, 3, 37, 16, 8),  # ragged last partition
+        (3, 20, 1000, 64, 24),  # two output tiles, the second ragged (16 + 4)
+        (2, 5, 4000, 512, 12),  # two bin tiles
+        (1, 2, 9000, 4096, 5),  # 16 bin tiles, K = 3
+        (5, 7, 2048, 128, 30),  # K = 16 exactly
+        (4, 33, 3000, 32, 100),  # three output tiles, many partitions per split
+    ],
+)
+def test_random_shapes_fp32(n_in, n_out, taps, B, nb):
+    w = signals.random_case(1000 + taps, n_in, n_out, taps, B, nb)
+    y = run_gpu(w)
+    ref = oracle_out(w)
+    assert snr_db(y, ref) >= FP32_DB
+    assert min(snr_per_channel_db(y, ref)) >= FP32_CH_DB
+
+
+@pytest.mark.parametrize("precision,bound", [("fp16", FP16_DB), ("bf16", BF16_DB)])
+def test_random_shapes_reduced_precision(precision, bound):
+    w = signals.random_case(77, 3, 20, 5000, 128, 60, decay_s=0.05)
+    y = run_gpu(w, precision)
+    ref = oracle_out(w)
+    assert snr_db(y, ref) >= bound
+
+
+# --------------------------------------------------- streaming behaviour
+
+
+def test_reset_restarts_the_stream_bit_exactly():
+    w = signals.random_case(5, 2, 3, 700, 64, 20)
+    with U.Engine(w.fs, w.block, w.n_in, w.n_out, w.taps) as e:
+        e.set_filters(w.h)
+        a = e.run(w.x)
+        e.reset()
+        b = e.run(w.x)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_device_pointer_path_matches_host_path():
+    torch = pytest.importorskip("torch")
+    w = signals.random_case(6, 2, 4, 900, 128, 16)
+    B = w.block
+    with U.Engine(w.fs, B, w.n_in, w.n_out, w.taps) as e:
+        e.set_filters(w.h)
+        host = e.run(w.x)
+        e.reset()
+        d_x = torch.from_numpy(w.x).cuda()
+        d_y = torch.empty((w.n_out, w.x.shape[1]), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+        for b in range(w.x.shape[1] // B):
+            blk_in = d_x[:, b * B : (b + 1) * B].contiguous()
+            blk_out = torch.empty((w.n_out, B), dtype=torch.float32, device="cuda")
+            U.conv_process_block_async(e.h, blk_in, blk_out, stream)
+            d_y[:, b * B : (b + 1) * B] = blk_out
+        torch.cuda.synchronize()
+        U.conv_synchronize(e.h)
+    np.testing.assert_array_equal(d_y.cpu().numpy(), host)
+
+
+def test_state_errors():
+    with U.Engine(48000, 64, 1, 1, 100) as e:
+        with pytest.raises(U.ConvError) as ei:
+            e.process(np.zeros((1, 64), np.float32))
+        assert ei.value.code == U.CONV_E_STATE
+        e.set_filters(np.ones((1, 1, 100), np.float32))
+        with pytest.raises(U.ConvError) as ei:
+            U.conv_set_precision(e.h, "fp16")
+        assert ei.value.code == U.CONV_E_STATE
+        with pytest.raises(U.ConvError) as ei:
+            e.process_afc(np.zeros((1, 64), np.float32))
+        assert ei.value.code == U.CONV_E_STATE
+
+
+# ------------------------------------------------------ paper scale, sampled
+
+
+@pytest.mark.parametrize("B", [128, 256, 512])
+def test_paper_4x16_sampled(B):
+    """4x16, 8 s filters, 9 s of pink noise: past the 8 s ring wrap; sampled samples
+    against the definition (Eq. 2) computed one at a time."""
+    w = signals.paper_4x16(block=B, seconds=9.0)
+    y = run_gpu(w)
+    rng = np.random.default_rng(B)
+    T = w.x.shape[1]
+    pts = sample_points(rng, w.n_out, 0, T, 150) + sample_points(rng, w.n_out, w.taps, T, 150)
+    ref = np.array([mimo_fir_sample(w.h, w.x, l, t) for l, t in pts])
+    got = np.array([y[l, t] for l, t in pts])
+    assert snr_db(got, ref) >= FP32_DB
+
+
+# ------------------------------------------------------- feedback loop
+
+
+def run_gpu_closed_loop(h, f_true, f_hat, s, B, precision="fp32"):
+    """Drive the engine's canceller in a simulated room (true paths f_true)."""
+    L, P, n_h = h.shape
+    room = RoomPlant(f_true, B)
+    nb = s.shape[1] // B
+    out = np.zeros((L, nb * B), np.float32)
+    err = np.zeros((P, nb * B), np.float32)
+    fb = np.zeros((P, B))
+    with U.Engine(48000, B, P, L, n_h, precision) as e:
+        e.set_filters(h)
+        e.set_paths(f_hat)
+        l_n = np.empty((L, B), np.float32)
+        e_n = np.empty((P, B), np.float32)
+        for b in range(nb):
+            m_n = (s[:, b * B : (b + 1) * B].astype(np.float64) + fb).astype(np.float32)
+            e.process_afc(m_n, l_n, e_n)
+            out[:, b * B : (b + 1) * B] = l_n
+            err[:, b * B : (b + 1) * B] = e_n
+            fb = room.step(l_n)
+    return out, err
+
+
+def test_closed_loop_small_against_oracle():
+    rng = np.random.default_rng(41)
+    P, L, B = 2, 3, 64
+    h = (rng.standard_normal((L, P, 700)) * np.exp(-np.arange(700) / 200.0) * 0.08).astype(np.float32)
+    f = (rng.standard_normal((P, L, 300)) * np.exp(-np.arange(300) / 60.0) * 0.05).astype(np.float32)
+    fh = (0.5 * f).astype(np.float32)  # imperfect estimate: residual feedback recirculates
+    s = (rng.standard_normal((P, 40 * B)) * 0.1).astype(np.float32)
+    y, e = run_gpu_closed_loop(h, f, fh, s, B)
+    ref_l, ref_e, _ = afc_closed_loop(h, f, fh, s, B)
+    # the loop is driven with float32 microphone blocks; the oracle sees the same s,
+    # and its own FP64 room: compare with the FP32 bound
+    assert snr_db(y, ref_l) >= 110.0
+    assert snr_db(e, ref_e) >= 110.0
+
+
+def test_closed_loop_perfect_estimate_removes_feedback():
+    rng = np.random.default_rng(42)
+    P, L, B = 2, 4, 128
+    h = (rng.standard_normal((L, P, 3000)) * np.exp(-np.arange(3000) / 800.0) * 0.06).astype(np.float32)
+    f = (rng.standard_normal((P, L, 900)) * np.exp(-np.arange(900) / 150.0) * 0.06).astype(np.float32)
+    s = (rng.standard_normal((P, 50 * B)) * 0.1).astype(np.float32)
+    y, e = run_gpu_closed_loop(h, f, f, s, B)
+    ref = upols(h.astype(np.float64), s.astype(np.float64), B)
+    assert snr_db(e, s) >= 110.0  # the error signal is the dry source
+    assert snr_db(y, ref) >= 110.0  # and the output is open-loop synthesis of it
