@@ -1,0 +1,465 @@
+"""Benchmark: streaming FDL convolution throughput on GB300.
+
+One step = one block of the whole hot path (input pack + R2C FFT + FDL push,
+FDL MAC over every partition and input->output pair, split reduction + C2R +
+overlap-save) for the paper-scale workload: 4 microphone inputs x 16
+loudspeaker outputs, 8 s filters (384,000 taps) at 48 kHz, block 256, FP32
+spectra, synthetic pink-noise input and exponentially decaying noise filters
+with early reflections.
+
+Prints ONE JSON line (rank 0):
+  value      Gtap*ch/s = n_in * n_out * taps * block / block time, inputs resident
+             in device memory, all ranks together (each rank runs its own session)
+  e2e        the same metric through the host-buffer C call, host<->device copies
+             of every block inside the timed region; with p50/p99 block latency
+  roofline   the FDL MAC kernel: algorithmic bytes / its CUDA-event duration
+  cpu_baseline  the FP64 oracle timed on this host's cores on a bounded sample
+
+``--impl reference`` times the FP64 oracle instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gtap*ch/s of FDL convolution (% HBM roofline); p99 block latency vs block period"
+UNIT = "Gtap*ch/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def env_rank():
+    return (
+        int(os.environ.get("RANK", "0")),
+        int(os.environ.get("LOCAL_RANK", "0")),
+        int(os.environ.get("WORLD_SIZE", "1")),
+    )
+
+
+def aggregate(elapsed_s: float, units: float, dist=None):
+    """Whole-job figures: max elapsed over ranks, sum of units over ranks."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return elapsed_s, units
+    import torch
+
+    t = torch.tensor([elapsed_s], dtype=torch.float64)
+    u = torch.tensor([units], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t, u = t.cuda(), u.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "device_util.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2509_04390_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per MAC launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fdl_mac_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    entry = rec.get(workload)
+    if not entry or entry.get("kernel_hash") != kernel_source_hash():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.window = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = []
+        for ts, line in self.samples:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((ts, parts))
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        use = inside if inside else rows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(p[1]) for _, p in use if p[1].replace(".", "", 1).isdigit()]
+        smax = [float(p[2]) for _, p in use if p[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, p in use for i in range(4) if p[5 + i].lower() == "active"})
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": reasons,
+            "samples": len(use),
+            "in_timed_region": bool(inside),
+        }
+
+
+def make_workload(args):
+    from paper_2509_04390_gb300 import signals
+
+    return signals.paper_4x16(block=args.block, seconds=args.seconds, taps=args.taps)
+
+
+def workload_name(args):
+    return f"paper_4x16_{args.taps}taps_B{args.block}_{args.precision}"
+
+
+def tapch(w):
+    return float(w.n_in) * w.n_out * w.taps * w.block
+
+
+# ----------------------------------------------------------- CPU baseline
+
+
+def time_oracle(w, budget_s: float, max_blocks: int | None = None, n_sub: int | None = None):
+    """Time the FP64 oracle as it stands on a bounded sample of the workload:
+    ``n_sub`` of the outputs for as many blocks as fit in ``budget_s``."""
+    from oracle import UpolsOracle
+
+    n_sub = w.n_out if n_sub is None else n_sub
+    sub = np.ascontiguousarray(w.h[:n_sub])
+    eng = UpolsOracle(sub, w.block)
+    B = w.block
+    nb_avail = w.x.shape[1] // B
+    times = []
+    t_start = time.perf_counter()
+    b = 0
+    while True:
+        xb = w.x[:, (b % nb_avail) * B : (b % nb_avail + 1) * B]
+        t0 = time.perf_counter()
+        eng.process_block(xb)
+        times.append(time.perf_counter() - t0)
+        b += 1
+        if time.perf_counter() - t_start > budget_s or (max_blocks and b >= max_blocks):
+            break
+    per_block = statistics.median(times)
+    value = float(w.n_in) * n_sub * w.taps * B / per_block / 1e9
+    return value, per_block, b, n_sub
+
+
+# ------------------------------------------------------------------- arms
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return 0
+    w = make_workload(args)
+    from oracle import UpolsOracle
+
+    # size each step so that warmup + steps finish within ~150 s
+    probe = UpolsOracle(np.ascontiguousarray(w.h[:1]), w.block)
+    t0 = time.perf_counter()
+    probe.process_block(w.x[:, : w.block])
+    t1 = time.perf_counter() - t0
+    del probe
+    per_output = max(t1, 1e-4)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n_sub = int(max(1, min(w.n_out, budget // per_output)))
+    from oracle import UpolsOracle as _U
+
+    eng = _U(np.ascontiguousarray(w.h[:n_sub]), w.block)
+    B = w.block
+    nb = w.x.shape[1] // B
+    for i in range(args.warmup):
+        eng.process_block(w.x[:, (i % nb) * B : (i % nb + 1) * B])
+    times = []
+    for i in range(args.steps):
+        j = (args.warmup + i) % nb
+        t0 = time.perf_counter()
+        eng.process_block(w.x[:, j * B : (j + 1) * B])
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = float(w.n_in) * n_sub * w.taps * B * args.steps / total / 1e9
+    sample = f"{n_sub} of {w.n_out} outputs, {args.steps} blocks of {B} (FP64 numpy oracle, single thread)"
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": config_dict(args, w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args, w):
+    return {
+        "workload": workload_name(args),
+        "n_in": w.n_in,
+        "n_out": w.n_out,
+        "taps": w.taps,
+        "filter_s": w.taps / w.fs,
+        "block": w.block,
+        "fs": w.fs,
+        "precision": args.precision,
+        "global_batch": 1,
+        "parallelism": "replicas",
+        "l2": "inputs larger than L2: the filter spectra streamed every step exceed the 126 MB L2",
+    }
+
+
+def run_ours(args):
+    import torch
+
+    rank, local_rank, world = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required (the engine has no CPU path)")
+    torch.cuda.set_device(local_rank)
+
+    from paper_2509_04390_gb300 import upols as U
+
+    w = make_workload(args)
+    B = w.block
+    prec = args.precision
+    eng = U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, prec)
+    eng.set_filters(w.h)
+    info = eng.info()
+    nb = w.x.shape[1] // B
+    d_x = torch.from_numpy(np.ascontiguousarray(w.x[:, : nb * B])).cuda()
+    # block-major copy so each block's [n_in][B] input is contiguous
+    d_blocks = d_x.reshape(w.n_in, nb, B).permute(1, 0, 2).contiguous()
+    d_out = torch.empty((2, w.n_out, B), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        U.conv_process_block_async(eng.h, d_blocks[i % nb], d_out[i & 1], stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    U.conv_profile_enable(eng.h, args.steps + 16)
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
+    time.sleep(0.5)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    if dist is not None:
+        dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    mac_ms, mac_n = U.conv_profile_read(eng.h)
+    U.conv_profile_enable(eng.h, 0)
+    U.conv_synchronize(eng.h)
+    clocks.stop()
+    units = tapch(w) * args.steps
+    t_max, units_all = aggregate(elapsed, units, dist)
+    value = units_all / t_max / 1e9
+
+    # end to end through the host-buffer call: copies in and out every block
+    eng.reset()
+    h_in = np.empty((w.n_in, B), np.float32)
+    h_out = np.empty((w.n_out, B), np.float32)
+    e2e_steps = min(args.steps, args.e2e_steps)
+    lat = []
+    for i in range(min(args.warmup, 50)):
+        np.copyto(h_in, w.x[:, (i % nb) * B : (i % nb + 1) * B])
+        U.conv_process_block(eng.h, h_in, h_out, (w.n_in, w.n_out, B))
+    if dist is not None:
+        dist.barrier()
+    te0 = time.perf_counter()
+    for i in range(e2e_steps):
+        j = (i + 50) % nb
+        t0 = time.perf_counter_ns()
+        np.copyto(h_in, w.x[:, j * B : (j + 1) * B])
+        U.conv_process_block(eng.h, h_in, h_out, (w.n_in, w.n_out, B))
+        lat.append(time.perf_counter_ns() - t0)
+    te1 = time.perf_counter()
+    e_t, e_units = aggregate(te1 - te0, tapch(w) * e2e_steps, dist)
+    e2e_value = e_units / e_t / 1e9
+    lat_us = np.array(lat) / 1e3
+    period_us = B / w.fs * 1e6
+
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    mac_avg_s = mac_ms / 1e3 / max(mac_n, 1)
+    achieved = info["mac_bytes"] / mac_avg_s / 1e9 if mac_n else None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cv, per_block, nblk, n_sub = time_oracle(w, args.cpu_budget)
+        cpu = {
+            "value": cv,
+            "unit": UNIT,
+            "cores": 1,
+            "kind": "oracle",
+            "sample": f"{nblk} blocks of {B} on all {n_sub} outputs, FP64 numpy oracle, single thread "
+                      f"(median {per_block * 1e3:.1f} ms per block)",
+        }
+
+    clk = clocks.summary(tw0, tw1)
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps * 1e3,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else f"{prec} storage, f32 arithmetic",
+            "data": "synthetic: seeded pink-noise input, exponentially decaying noise filters with early reflections",
+            "config": config_dict(args, w),
+            "e2e": {
+                "value": e2e_value,
+                "unit": UNIT,
+                "h2d_bytes_per_step": w.n_in * B * 4,
+                "d2h_bytes_per_step": w.n_out * B * 4,
+                "steps": e2e_steps,
+                "latency_us": {
+                    "p50": float(np.percentile(lat_us, 50)),
+                    "p99": float(np.percentile(lat_us, 99)),
+                    "max": float(np.max(lat_us)),
+                    "block_period": period_us,
+                    "p99_over_period": float(np.percentile(lat_us, 99)) / period_us,
+                },
+            },
+            "roofline": {
+                "bound": "hbm",
+                "kernel": "k_fdl_mac",
+                "achieved": achieved,
+                "peak": peak,
+                "peak_kind": f"{peak_kind} hbm_gbs (copy test)",
+                "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": ncu_traffic(workload_name(args)),
+                "algorithmic_bytes_per_launch": info["mac_bytes"],
+                "avg_launch_us": mac_avg_s * 1e6,
+                "launches_timed": mac_n,
+            },
+            "cpu_baseline": cpu,
+            "gpu_launches": args.steps * info["kernels_per_block"],
+            "clocks": clk,
+            "plan": {k: info[k] for k in ("K", "mac_ctas", "mac_splits", "mac_smem", "device_bytes")},
+        }
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--taps", type=int, default=384000)
+    ap.add_argument("--seconds", type=float, default=30.0)
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--e2e-steps", type=int, default=5000)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
