@@ -312,25 +312,34 @@ def run_ours(args):
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
-    U.conv_profile_enable(eng.h, args.steps + 16)
     clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     clocks.start()
     time.sleep(0.5)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def timed_region(first):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(first + i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        return ev0.elapsed_time(ev1) / 1e3
+
+    # region A: the measured value (kernels back to back, nothing in between)
     tw0 = time.time()
-    ev0.record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    elapsed = timed_region(args.warmup)
     tw1 = time.time()
-    if dist is not None:
-        dist.barrier()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
+    # region B: the same steps with CUDA events around every FDL MAC launch on
+    # its stream (events between kernels serialise them, so this region is
+    # only used for the kernel's own duration)
+    U.conv_profile_enable(eng.h, args.steps + 16)
+    elapsed_prof = timed_region(args.warmup + args.steps)
     mac_ms, mac_n = U.conv_profile_read(eng.h)
     U.conv_profile_enable(eng.h, 0)
     U.conv_synchronize(eng.h)
@@ -422,6 +431,8 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": info["mac_bytes"],
                 "avg_launch_us": mac_avg_s * 1e6,
                 "launches_timed": mac_n,
+                "timing": "CUDA events around each launch on its stream, second timed region of the same steps "
+                          f"({elapsed_prof / args.steps * 1e6:.1f} us per step there)",
             },
             "cpu_baseline": cpu,
             "gpu_launches": args.steps * info["kernels_per_block"],

@@ -189,13 +189,26 @@ __device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
 // buffer that holds the result (a or b).
 
 template <bool INV>
-__device__ __forceinline__ float2 tw_at(const float2* __restrict__ tw, int idx) {
-    const float2 w = __ldg(tw + idx);
+__device__ __forceinline__ float2 tw_at(const float2* tw, int idx) {
+    const float2 w = tw[idx];
     return INV ? make_float2(w.x, -w.y) : w;
 }
 
+// Copy the twiddle table W_2B^j, j in [0, 2B), into shared memory.
+__device__ __forceinline__ void load_twiddles(float2* dst, const float2* __restrict__ tw, int B) {
+    for (int j = threadIdx.x; j < 2 * B; j += blockDim.x) dst[j] = __ldg(tw + j);
+}
+
+// Programmatic dependent launch: let the next kernel in the stream start its
+// independent prologue now / wait until the previous kernel has completed and
+// its writes are visible.  Both are no-ops for ordinary launches.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <bool INV>
-__device__ float2* fft_smem(float2* a, float2* b, int N, int log2N, const float2* __restrict__ tw, int log2twN,
+__device__ float2* fft_smem(float2* a, float2* b, int N, int log2N, const float2* tw, int log2twN,
                             int tid, int nth) {
     int Ns = 1, log2Ns = 0;
     if (log2N & 1) {
@@ -247,21 +260,21 @@ __device__ float2* fft_smem(float2* a, float2* b, int N, int log2N, const float2
 // Real FFT of length 2B from the B-point complex FFT Z of z[n] = w[2n] + i w[2n+1]:
 //   X[k] = E[k] + W_2B^k O[k],  E = (Z[k] + conj Z[B-k]) / 2,  O = (Z[k] - conj Z[B-k]) / 2i
 // packed: X[0] = (Re Z0 + Im Z0, Re Z0 - Im Z0) = (DC, Nyquist).
-__device__ __forceinline__ float2 r2c_post(const float2* Z, int k, int B, const float2* __restrict__ tw) {
+__device__ __forceinline__ float2 r2c_post(const float2* Z, int k, int B, const float2* tw) {
     if (k == 0) return make_float2(Z[0].x + Z[0].y, Z[0].x - Z[0].y);
     const float2 zk = Z[k];
     const float2 zm = conjf2(Z[B - k]);
     const float2 E = cscale(cadd(zk, zm), 0.5f);
     const float2 D = cscale(csub(zk, zm), 0.5f);
     const float2 O = make_float2(D.y, -D.x);  // D / i
-    return cadd(E, cmul(__ldg(tw + k), O));
+    return cadd(E, cmul(tw[k], O));
 }
 
 // Inverse of r2c_post: from a packed Hermitian spectrum Y to Z such that the
 // unscaled inverse B-point FFT of Z, times 1/B, is z[n] = w[2n] + i w[2n+1]
 // with w = IFFT_2B(Y) (scaled by 1/2B).
 //   A = (Y[k] + conj Y[B-k]) / 2,  Bv = (Y[k] - conj Y[B-k]) / 2 * W_2B^-k,  Z = A + i Bv
-__device__ __forceinline__ float2 c2r_pre(const float2* Y, int k, int B, const float2* __restrict__ tw) {
+__device__ __forceinline__ float2 c2r_pre(const float2* Y, int k, int B, const float2* tw) {
     if (k == 0) {
         const float dc = Y[0].x, ny = Y[0].y;
         return make_float2(0.5f * (dc + ny), 0.5f * (dc - ny));
@@ -269,7 +282,7 @@ __device__ __forceinline__ float2 c2r_pre(const float2* Y, int k, int B, const f
     const float2 yk = Y[k];
     const float2 ym = conjf2(Y[B - k]);
     const float2 A = cscale(cadd(yk, ym), 0.5f);
-    const float2 Bv = cmul(cscale(csub(yk, ym), 0.5f), conjf2(__ldg(tw + k)));
+    const float2 Bv = cmul(cscale(csub(yk, ym), 0.5f), conjf2(tw[k]));
     return make_float2(A.x - Bv.y, A.y + Bv.x);
 }
 

@@ -69,12 +69,19 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms) {
     p.es = prec == PREC_FP32 ? 8 : 4;
     p.VEC = 16 / p.es;
     p.LPT = prec == PREC_FP32 ? 8 : 4;
-    p.BT = std::min(B, 256);
+    p.LT = std::min(n_dst, 16);
+    p.n_lt = (n_dst + p.LT - 1) / p.LT;
+    // Bin tiles: enough (bin tile x output tile) pairs that ~16-20 partition
+    // splits per tile cover the SMs.  Few splits keep the split partials (which
+    // the output kernel must read back) a small fraction of the streamed bytes.
+    int want_kt = std::max(1, num_sms / (16 * p.n_lt));
+    int n_kt = 1;
+    while (n_kt * 2 <= want_kt) n_kt *= 2;
+    p.BT = std::max(16, std::min(256, B / n_kt));
+    if (p.BT > B) p.BT = B;
     p.n_kt = B / p.BT;
     p.kthreads = p.BT / p.VEC;
     const int rest = (MAC_CONSUMER_WARPS * 32) / p.kthreads;
-    p.LT = std::min(n_dst, 16);
-    p.n_lt = (n_dst + p.LT - 1) / p.LT;
     p.NLG = pow2_ceil((p.LT + p.LPT - 1) / p.LPT);
     if (p.NLG > rest) p.NLG = rest;
     p.NRL = rest / p.NLG;

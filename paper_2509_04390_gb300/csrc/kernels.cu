@@ -80,6 +80,10 @@ __global__ void k_pack_r2c(const PackArgs a) {
     const int B = a.B, half = B >> 1, c = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
     float2* bufA = fsm;
     float2* bufB = fsm + B;
+    float2* tws = fsm + 2 * B;
+    griddep_launch_dependents();
+    load_twiddles(tws, a.tw, B);
+    griddep_wait();  // input, feedback prediction and ring slot belong to earlier work
     const float* in = a.in + (size_t)c * a.in_stride;
     const float* sub = a.sub ? a.sub + (size_t)c * B : nullptr;
     float* win = a.win + (size_t)c * B;
@@ -105,9 +109,9 @@ __global__ void k_pack_r2c(const PackArgs a) {
         win[t] = v;
         if (a.e_out) a.e_out[(size_t)c * B + t] = v;
     }
-    float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, a.tw, a.log2B + 1, tid, nth);
+    float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, tws, a.log2B + 1, tid, nth);
     float2* Xs = (Z == bufA) ? bufB : bufA;
-    for (int k = tid; k < B; k += nth) Xs[k] = r2c_post(Z, k, B, a.tw);
+    for (int k = tid; k < B; k += nth) Xs[k] = r2c_post(Z, k, B, tws);
     __syncthreads();
     const float scale = store_spectrum<PREC>(Xs, B, a.X, RingIndex{a.BT, a.n_ch, c, a.K, a.slot}, red);
     if (PREC != PREC_FP32 && tid == 0) a.sX[(size_t)c * a.K + a.slot] = scale;
@@ -128,6 +132,8 @@ __global__ void k_filter_r2c(const FilterArgs a) {
     const long long t0 = (long long)p * B;
     float2* bufA = fsm;
     float2* bufB = fsm + B;
+    float2* tws = fsm + 2 * B;
+    load_twiddles(tws, a.tw, B);
     for (int n = tid; n < B; n += nth) {
         float2 z = make_float2(0.0f, 0.0f);
         if (n < half) {
@@ -138,9 +144,9 @@ __global__ void k_filter_r2c(const FilterArgs a) {
         bufA[n] = z;
     }
     __syncthreads();
-    float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, a.tw, a.log2B + 1, tid, nth);
+    float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, tws, a.log2B + 1, tid, nth);
     float2* Xs = (Z == bufA) ? bufB : bufA;
-    for (int k = tid; k < B; k += nth) Xs[k] = r2c_post(Z, k, B, a.tw);
+    for (int k = tid; k < B; k += nth) Xs[k] = r2c_post(Z, k, B, tws);
     __syncthreads();
     const int l0 = (l / a.LT) * a.LT;
     const int LTt = min(a.LT, a.n_dst - l0), ll = l - l0;
@@ -196,24 +202,20 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
 
     if (warp == MAC_CONSUMER_WARPS) {
         if (lane != 0) return;
+        griddep_launch_dependents();
         const uint64_t pol_stream = policy_evict_first();
         const uint64_t pol_keep = policy_evict_last();
-        int issued = 0;
-        bool ok = true;
-        for (int it = 0; it < nit; ++it) {
+        auto issue_h = [&](int it) {
             const int st = it % a.nstage;
-            if (it >= a.nstage &&
-                !mbar_wait_bounded(&empty[st], ((it / a.nstage) - 1) & 1, abort_flag, WAIT_LIMIT_NS)) {
-                *abort_flag = 1;
-                if (a.err) *(volatile int*)a.err = DEVERR_TIMEOUT_PRODUCER;
-                ok = false;
-                break;
-            }
             const int ra = r0 + it * a.RS, rb = min(ra + a.RS, r1), nr = rb - ra;
             unsigned char* sh = stages + (size_t)st * a.stage_bytes;
-            unsigned char* sx = sh + a.xoff;
             mbar_arrive_expect_tx(&full[st], (uint32_t)((size_t)nr * (hr_bytes + hrow)));
             bulk_g2s(sh, Hb + (size_t)ra * hr_bytes, (uint32_t)((size_t)nr * hr_bytes), &full[st], pol_stream);
+        };
+        auto issue_x = [&](int it) {
+            const int st = it % a.nstage;
+            const int ra = r0 + it * a.RS, rb = min(ra + a.RS, r1);
+            unsigned char* sx = stages + (size_t)st * a.stage_bytes + a.xoff;
             int r = ra, j = 0;
             while (r < rb) {
                 const int q = r / K, p = r - q * K;
@@ -225,6 +227,26 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
                 r += run;
                 j += run;
             }
+        };
+        // The filter spectra are constant: stream the first stages while the
+        // previous kernel (the pack of this block) is still running, then wait for
+        // it before touching the delay line it writes.
+        const int npre = min(nit, a.nstage);
+        for (int it = 0; it < npre; ++it) issue_h(it);
+        griddep_wait();
+        for (int it = 0; it < npre; ++it) issue_x(it);
+        int issued = npre;
+        bool ok = true;
+        for (int it = npre; it < nit; ++it) {
+            const int st = it % a.nstage;
+            if (!mbar_wait_bounded(&empty[st], ((it / a.nstage) - 1) & 1, abort_flag, WAIT_LIMIT_NS)) {
+                *abort_flag = 1;
+                if (a.err) *(volatile int*)a.err = DEVERR_TIMEOUT_PRODUCER;
+                ok = false;
+                break;
+            }
+            issue_h(it);
+            issue_x(it);
             ++issued;
         }
         if (!ok) {
@@ -236,6 +258,7 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
     }
 
     // consumers
+    griddep_wait();  // the split partials are still being read by the previous block's output kernel
     const int kv = tid % a.kthreads, rest = tid / a.kthreads;
     const int lg = rest % a.NLG, rl = rest / a.NLG;
     const int kglob = kt * a.BT + kv * VEC;
@@ -342,29 +365,38 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
 }
 
 // ------------------------------------------------- reduce + C2R + OLS
-// One CTA per output channel: sum the partition splits in a fixed two-level
-// order, C2R IFFT (1/2B), keep the last B samples (overlap-save).
+// One CTA per output channel: sum the partition splits in a fixed order
+// (independent loads in groups of 8, pairwise within a group), C2R IFFT
+// (1/2B), keep the last B samples (overlap-save).
 __global__ void k_reduce_c2r(const ReduceArgs a) {
     extern __shared__ float2 fsm[];
     const int B = a.B, l = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
     float2* P = fsm;
     float2* W = fsm + B;
+    float2* tws = fsm + 2 * B;
+    griddep_launch_dependents();
+    load_twiddles(tws, a.tw, B);
+    griddep_wait();
     const size_t stride = (size_t)a.n_dst * B;
+    const int S = a.S;
     for (int k = tid; k < B; k += nth) {
         const float2* src = a.partial + (size_t)l * B + k;
         float2 tot = make_float2(0.0f, 0.0f);
-        for (int s0 = 0; s0 < a.S; s0 += 16) {
-            const int s1 = min(s0 + 16, a.S);
-            float2 part = make_float2(0.0f, 0.0f);
-            for (int s = s0; s < s1; ++s) part = cadd(part, src[(size_t)s * stride]);
-            tot = cadd(tot, part);
+        int s = 0;
+        for (; s + 8 <= S; s += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = src[(size_t)(s + i) * stride];
+            const float2 g = cadd(cadd(cadd(v[0], v[1]), cadd(v[2], v[3])), cadd(cadd(v[4], v[5]), cadd(v[6], v[7])));
+            tot = cadd(tot, g);
         }
+        for (; s < S; ++s) tot = cadd(tot, src[(size_t)s * stride]);
         P[k] = tot;
     }
     __syncthreads();
-    for (int k = tid; k < B; k += nth) W[k] = c2r_pre(P, k, B, a.tw);
+    for (int k = tid; k < B; k += nth) W[k] = c2r_pre(P, k, B, tws);
     __syncthreads();
-    const float2* z = fft_smem<true>(W, P, B, a.log2B, a.tw, a.log2B + 1, tid, nth);
+    const float2* z = fft_smem<true>(W, P, B, a.log2B, tws, a.log2B + 1, tid, nth);
     const float invB = 1.0f / (float)B;
     float* out = a.out + (size_t)l * a.out_stride;
     for (int t = tid; t < B; t += nth) {
@@ -387,7 +419,37 @@ int fft_threads(int B) {
     return t;
 }
 
-size_t fft_smem_bytes(int B) { return (size_t)2 * B * sizeof(float2); }
+int out_threads(int B) {
+    int t = B;
+    if (t < 32) t = 32;
+    if (t > 256) t = 256;
+    return t;
+}
+
+// two work buffers of B complex values plus the 2B-entry twiddle table
+size_t fft_smem_bytes(int B) { return (size_t)4 * B * sizeof(float2); }
+
+namespace {
+
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous kernel in the stream finishes; it orders itself with
+// griddepcontrol.wait before touching anything that kernel produces.
+template <typename Kern, typename Arg>
+cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const Arg& arg) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
+}  // namespace
 
 cudaError_t prepare_kernels(size_t mac_smem) {
     const int fft_max = (int)fft_smem_bytes(4096);
@@ -413,12 +475,11 @@ cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s) {
     const dim3 grid(a.n_ch), block(fft_threads(a.B));
     const size_t sm = fft_smem_bytes(a.B);
     switch (prec) {
-        case PREC_FP32: k_pack_r2c<PREC_FP32><<<grid, block, sm, s>>>(a); break;
-        case PREC_FP16: k_pack_r2c<PREC_FP16><<<grid, block, sm, s>>>(a); break;
-        case PREC_BF16: k_pack_r2c<PREC_BF16><<<grid, block, sm, s>>>(a); break;
+        case PREC_FP32: return launch_pdl(k_pack_r2c<PREC_FP32>, grid, block, sm, s, a);
+        case PREC_FP16: return launch_pdl(k_pack_r2c<PREC_FP16>, grid, block, sm, s, a);
+        case PREC_BF16: return launch_pdl(k_pack_r2c<PREC_BF16>, grid, block, sm, s, a);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s) {
@@ -438,17 +499,15 @@ cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s) {
 cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
     const dim3 grid(p.ctas), block(MAC_THREADS);
     switch (prec) {
-        case PREC_FP32: k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>()><<<grid, block, p.smem, s>>>(a); break;
-        case PREC_FP16: k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>()><<<grid, block, p.smem, s>>>(a); break;
-        case PREC_BF16: k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>()><<<grid, block, p.smem, s>>>(a); break;
+        case PREC_FP32: return launch_pdl(k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>()>, grid, block, p.smem, s, a);
+        case PREC_FP16: return launch_pdl(k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>()>, grid, block, p.smem, s, a);
+        case PREC_BF16: return launch_pdl(k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>()>, grid, block, p.smem, s, a);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_c2r(const ReduceArgs& a, cudaStream_t s) {
-    k_reduce_c2r<<<a.n_dst, fft_threads(a.B), fft_smem_bytes(a.B), s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_reduce_c2r, dim3(a.n_dst), dim3(out_threads(a.B)), fft_smem_bytes(a.B), s, a);
 }
 
 }  // namespace gbconv

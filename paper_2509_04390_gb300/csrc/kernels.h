@@ -92,6 +92,7 @@ struct ReduceArgs {
 };
 
 int fft_threads(int B);
+int out_threads(int B);
 size_t fft_smem_bytes(int B);
 
 cudaError_t prepare_kernels(size_t mac_smem);
