@@ -145,6 +145,37 @@ int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches)
  * outputs, num_sms the SM count to plan for.  CONV_OK or CONV_E_INVAL. */
 int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms);
 
+/* FDL MAC and output transform of one block over caller-owned buffers,
+ * allocating nothing.  (The paper has no counterpart: this serves callers that
+ * cannot allocate device memory, such as a real-time audio callback, where an
+ * allocation can block past the block deadline, or a plugin whose host owns
+ * every device buffer.)
+ *
+ * Computes y[l][t] = the last `block` samples of the 2*block-point C2R IFFT
+ * (scaled 1/(2*block)) of  sum_q sum_p H[q][p][l] * X[q][(slot0 + p) mod K],
+ * i.e. stages 2 and 3 of the engine for one block, with the spectra given:
+ *   d_H  device, [n_in][K][n_out][block] complex float (re, im interleaved):
+ *        the 2*block-point R2C spectra of the zero-padded sub-filters, packed
+ *        (bin 0 holds (DC, Nyquist) as (re, im); bins 1..block-1 as usual);
+ *   d_X  device, [n_in][K][block] complex float, packed the same way: the
+ *        delay-line ring; slot0 is the slot of the newest input spectrum and
+ *        partition p reads slot (slot0 + p) mod K;
+ *   d_y  device, [n_out][block] float, written.
+ * Enqueued on `cuda_stream` (NULL = legacy default stream); d_H and d_X must
+ * be complete in stream order.  FP32 only.  Limits: block a power of two in
+ * [16, 256], n_out in [1, 16], n_in*K <= 2^30; CONV_E_INVAL beyond them.
+ *
+ * The split partials live in a 2 MiB file-scope device array (plus 8 KB of
+ * twiddle tables) that every GPU loading this library holds until exit.  The
+ * first call on a device, with that device current, resolves the arrays'
+ * device addresses and uploads the twiddles; make that first call before any
+ * stream capture.  All calls share the array, and every call writes all the
+ * partials it reads, so nothing needs clearing; calls that overlap on the GPU
+ * race on the array.  Returns CONV_OK or a negative CONV_E_* code with the
+ * message in conv_last_error(). */
+int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int block, int n_in, int n_out, long long K,
+                         long long slot0, float* d_y, void* cuda_stream);
+
 /* Free everything the handle owns.  NULL-safe. */
 void conv_destroy(conv_engine* e);
 

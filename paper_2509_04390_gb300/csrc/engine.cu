@@ -213,6 +213,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void gbconv::set_last_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
 struct conv_engine {
     int dev = 0;
     double fs = 48000.0;

@@ -95,6 +95,9 @@ int fft_threads(int B);
 int out_threads(int B);
 size_t fft_smem_bytes(int B);
 
+// Sets the message conv_last_error() returns on the calling thread.
+void set_last_error_message(const char* msg);
+
 cudaError_t prepare_kernels(size_t mac_smem);
 cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s);
 cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s);

@@ -100,6 +100,7 @@ def load():
         "conv_profile_enable": (i, [vp, i]),
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "conv_plan_check": (i, [i, i, i, i, ll, i]),
+        "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
         "conv_destroy": (None, [vp]),
         "conv_last_error": (ctypes.c_char_p, []),
     }
@@ -233,6 +234,15 @@ def conv_profile_read(h):
 def conv_plan_check(precision, block, n_src, n_dst, taps, num_sms=152):
     precision = PRECISIONS.get(precision, precision)
     return _check(load().conv_plan_check(int(precision), int(block), int(n_src), int(n_dst), int(taps), int(num_sms)))
+
+
+def conv_fdl_mac_noalloc(d_H, d_X, block, n_in, n_out, K, slot0, d_y, stream=None):
+    return _check(
+        load().conv_fdl_mac_noalloc(
+            _dev_ptr(d_H), _dev_ptr(d_X), int(block), int(n_in), int(n_out), int(K), int(slot0), _dev_ptr(d_y),
+            _stream_ptr(stream),
+        )
+    )
 
 
 def conv_destroy(h):
