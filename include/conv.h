@@ -152,12 +152,12 @@ int conv_plan_check(int precision, int block, int n_src, int n_dst, long long ta
  * every device buffer.)
  *
  * Computes y[l][t] = the last `block` samples of the 2*block-point C2R IFFT
- * (scaled 1/(2*block)) of  sum_q sum_p H[q][p][l] * X[q][(slot0 + p) mod K],
+ * (scaled 1/(2*block)) of  sum_p sum_q H[p][q][l] * X[(slot0 + p) mod K][q],
  * i.e. stages 2 and 3 of the engine for one block, with the spectra given:
- *   d_H  device, [n_in][K][n_out][block] complex float (re, im interleaved):
+ *   d_H  device, [K][n_in][n_out][block] complex float (re, im interleaved):
  *        the 2*block-point R2C spectra of the zero-padded sub-filters, packed
  *        (bin 0 holds (DC, Nyquist) as (re, im); bins 1..block-1 as usual);
- *   d_X  device, [n_in][K][block] complex float, packed the same way: the
+ *   d_X  device, [K][n_in][block] complex float, packed the same way: the
  *        delay-line ring; slot0 is the slot of the newest input spectrum and
  *        partition p reads slot (slot0 + p) mod K;
  *   d_y  device, [n_out][block] float, written.

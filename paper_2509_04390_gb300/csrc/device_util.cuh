@@ -51,6 +51,9 @@ struct Store<PREC_FP32> {
     __device__ __forceinline__ static void store1(void* base, size_t idx, float2 v) {
         reinterpret_cast<float2*>(base)[idx] = v;
     }
+    __device__ __forceinline__ static float2 load1(const void* base, size_t idx) {
+        return reinterpret_cast<const float2*>(base)[idx];
+    }
 };
 
 template <>
@@ -69,6 +72,9 @@ struct Store<PREC_FP16> {
     __device__ __forceinline__ static void store1(void* base, size_t idx, float2 v) {
         reinterpret_cast<__half2*>(base)[idx] = __floats2half2_rn(v.x, v.y);
     }
+    __device__ __forceinline__ static float2 load1(const void* base, size_t idx) {
+        return __half22float2(reinterpret_cast<const __half2*>(base)[idx]);
+    }
 };
 
 template <>
@@ -86,6 +92,9 @@ struct Store<PREC_BF16> {
     }
     __device__ __forceinline__ static void store1(void* base, size_t idx, float2 v) {
         reinterpret_cast<__nv_bfloat162*>(base)[idx] = __floats2bfloat162_rn(v.x, v.y);
+    }
+    __device__ __forceinline__ static float2 load1(const void* base, size_t idx) {
+        return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(base)[idx]);
     }
 };
 

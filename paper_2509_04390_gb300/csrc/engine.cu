@@ -7,6 +7,18 @@
 // (Sec. 4).  All state (filter spectra, delay lines, sliding windows, pending
 // feedback prediction) stays resident in device memory; per block only the
 // n_in x B input samples and n_out x B output samples cross to the host.
+//
+// Split-phase schedule.  Partitions 1..K-1 of block n+1 only need input
+// spectra of blocks <= n, so their MAC (the "tail": all but 1/K of the bytes)
+// is enqueued on a low-priority background stream as soon as block n's
+// spectrum is in the delay line.  When block n+1 arrives, the caller's stream
+// runs only the pack/R2C of the new block and one output kernel that adds
+// partition 0 (the "head") to the tail's split partials and transforms back.
+// Tail partials are double-buffered by block parity:
+//   caller stream:  pack(n) -> [rec packed] -> [wait tail(n)] -> out(n)
+//   background:     [wait packed(n)] -> tail(n+1) -> [rec tail]
+// pack(n+1) overwrites the ring slot of block n+1-K, which tail(n) (already
+// waited for by out(n)) was the last to read; tail(n+1) never reads it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -59,13 +71,15 @@ inline int pow2_ceil(int v) {
 // the pipeline stage size and depth, and the number of partition splits so
 // that the grid covers every SM about once (1 CTA/SM at these shared-memory
 // sizes) while each CTA still streams at least a few stages.
-MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms) {
+MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int r_begin) {
     MacPlan p{};
     p.B = B;
     p.n_src = n_src;
     p.n_dst = n_dst;
     p.K = K;
     p.R = n_src * K;
+    p.r_begin = r_begin;
+    const int Rt = p.R - r_begin;
     p.es = prec == PREC_FP32 ? 8 : 4;
     p.VEC = 16 / p.es;
     p.LPT = prec == PREC_FP32 ? 8 : 4;
@@ -88,7 +102,7 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms) {
     const size_t per_r = (size_t)(p.LT + 1) * p.BT * p.es;
     int rs = (int)std::max<size_t>(1, (32768 + per_r / 2) / per_r);
     rs = (rs + p.NRL - 1) / p.NRL * p.NRL;  // whole r-lanes per stage
-    p.RS = std::max(1, std::min(rs, p.R));
+    p.RS = std::max(1, std::min(rs, std::max(1, Rt)));
     const size_t hpart = align_up((size_t)p.RS * p.LT * p.BT * p.es, 128);
     const size_t xpart = align_up((size_t)p.RS * p.BT * p.es, 128);
     p.xoff = (unsigned)hpart;
@@ -99,15 +113,15 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms) {
     const size_t red = (size_t)(p.NRL - 1) * p.LT * p.BT * sizeof(float2);
     p.smem = MAC_HDR_BYTES + std::max((size_t)p.nstage * p.stage_bytes, align_up(red, 128));
     const int tiles = p.n_kt * p.n_lt;
-    const size_t tile_bytes = (size_t)p.R * p.LT * p.BT * p.es;
+    const size_t tile_bytes = (size_t)Rt * p.LT * p.BT * p.es;
     const int by_work = (int)std::max<size_t>(1, tile_bytes / (2 * (size_t)p.stage_bytes));
     int S = std::max(1, (num_sms + tiles / 2) / tiles);
-    S = std::min(S, std::min(by_work, p.R));
-    p.S = std::max(1, S);
+    S = std::min(S, std::min(by_work, Rt));
+    p.S = Rt > 0 ? std::max(1, S) : 0;
     p.ctas = tiles * p.S;
     p.h_bytes = (size_t)n_dst * p.R * B * p.es;
     p.x_bytes = (size_t)p.R * B * p.es;
-    p.partial_bytes = (size_t)p.S * n_dst * B * sizeof(float2);
+    p.partial_bytes = std::max<size_t>(16, (size_t)p.S * n_dst * B * sizeof(float2));
     return p;
 }
 
@@ -123,13 +137,16 @@ int check_plan(const MacPlan& p, std::string* why) {
         *why = buf;
         return -1;
     };
+    const int Rt = p.R - p.r_begin;
+    if (Rt < 0 || p.r_begin < 0) return bad("reduction range");
+    if (Rt == 0) return p.S == 0 ? 0 : bad("splits over an empty range");
     if (p.nstage < 1 || p.nstage > MAX_STAGES) return bad("stage count");
     if (p.smem > 227 * 1024) return bad("shared memory above 227 KB");
     if (p.kthreads * p.VEC != p.BT || p.kthreads > MAC_CONSUMER_WARPS * 32) return bad("bin threads");
     const int rest = (MAC_CONSUMER_WARPS * 32) / p.kthreads;
     if (p.kthreads * rest != MAC_CONSUMER_WARPS * 32 || p.NLG * p.NRL != rest) return bad("thread layout");
     if ((p.LT + p.NLG - 1) / p.NLG > p.LPT) return bad("outputs per thread above LPT");
-    if (p.S < 1 || p.S > p.R) return bad("split count");
+    if (p.S < 1 || p.S > Rt) return bad("split count");
     if (p.B % p.BT) return bad("bin tile");
     const size_t hrow = (size_t)p.BT * p.es;
     if (hrow % 16) return bad("row not a multiple of 16 bytes");
@@ -142,36 +159,27 @@ int check_plan(const MacPlan& p, std::string* why) {
         if (kt >= p.n_kt) return bad("tile index");
         const int l0 = lt * p.LT, LTt = std::min(p.LT, p.n_dst - l0);
         if (LTt < 1) return bad("empty output tile");
-        const int r0 = (int)((long long)split * p.R / p.S), r1 = (int)((long long)(split + 1) * p.R / p.S);
+        const int r0 = p.r_begin + (int)((long long)split * Rt / p.S);
+        const int r1 = p.r_begin + (int)((long long)(split + 1) * Rt / p.S);
         if (r1 <= r0) return bad("empty split");
         const size_t hr = (size_t)LTt * hrow;
         const size_t hb = ((size_t)kt * p.n_dst + l0) * (size_t)p.R * hrow;
-        const size_t xb = (size_t)kt * p.n_src * p.K * hrow;
+        const size_t xb = (size_t)kt * p.R * hrow;
         for (int ra = r0; ra < r1; ra += p.RS) {
             const int rb = std::min(ra + p.RS, r1), nr = rb - ra;
             const size_t tx = (size_t)nr * (hr + hrow);
             if (tx >= (1u << 20)) return bad("transaction bytes");
             if (hb + (size_t)rb * hr > p.h_bytes) return bad("filter copy past the spectra");
             if ((size_t)nr * hr > p.xoff) return bad("filter copy past its stage part");
-            size_t got = (size_t)nr * hr;
-            int r = ra, j = 0;
-            while (r < rb) {
-                const int q = r / p.K, pp = r % p.K;
-                for (int slot0 = 0; slot0 < p.K; slot0 += std::max(1, p.K / 7)) {
-                    int slot = slot0 + pp;
-                    if (slot >= p.K) slot -= p.K;
-                    const int run = std::min(rb - r, std::min(p.K - pp, p.K - slot));
-                    if (run < 1) return bad("empty delay-line run");
-                    if (xb + ((size_t)q * p.K + slot + run) * hrow > p.x_bytes) return bad("delay-line copy past the ring");
-                }
-                int slot = pp;  // slot0 = 0 case drives the run split used below
-                const int run = std::min(rb - r, std::min(p.K - pp, p.K - slot));
-                if (p.xoff + (size_t)(j + run) * hrow > p.stage_bytes) return bad("delay-line copy past its stage");
-                got += (size_t)run * hrow;
-                r += run;
-                j += run;
+            if (p.xoff + (size_t)nr * hrow > p.stage_bytes) return bad("delay-line copy past its stage");
+            for (int slot0 = 0; slot0 < p.K; slot0 += std::max(1, p.K / 7)) {
+                int start = slot0 * p.n_src + ra;
+                start %= p.R;
+                const int run = std::min(nr, p.R - start);
+                if (run < 1) return bad("empty delay-line run");
+                if (xb + (size_t)(start + run) * hrow > p.x_bytes) return bad("delay-line copy past the ring");
+                if (run < nr && xb + (size_t)(nr - run) * hrow > p.x_bytes) return bad("wrapped copy past the ring");
             }
-            if (got != tx) return bad("transaction byte count");
         }
         const size_t last = (((size_t)split * p.n_dst + l0 + LTt - 1) * p.B + (size_t)kt * p.BT + p.BT);
         if (last * sizeof(float2) > p.partial_bytes) return bad("partial write past the buffer");
@@ -189,13 +197,15 @@ struct Part {
     void* X = nullptr;
     float* sX = nullptr;
     float* win = nullptr;
-    float2* partial = nullptr;
+    float2* partial[2] = {nullptr, nullptr};  // tail partials, by block parity
+    cudaEvent_t ev_packed = nullptr;          // this block's spectrum is in the ring
+    cudaEvent_t ev_tail = nullptr;            // the next block's tail partials are ready
     bool allocated = false;
     bool ready = false;
 };
 
 size_t part_bytes(const MacPlan& p, int prec) {
-    size_t b = p.h_bytes + p.x_bytes + p.partial_bytes + (size_t)p.n_src * p.B * sizeof(float);
+    size_t b = p.h_bytes + p.x_bytes + 2 * p.partial_bytes + (size_t)p.n_src * p.B * sizeof(float);
     if (prec != PREC_FP32) b += ((size_t)p.n_dst * p.R + (size_t)p.R) * sizeof(float);
     return b;
 }
@@ -222,7 +232,9 @@ struct conv_engine {
     long long taps = 0;
     int prec = CONV_FP32;
     int num_sms = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;     // the engine's own stream for host-buffer calls
+    cudaStream_t bg = nullptr;         // low-priority stream for the tail MACs
+    cudaEvent_t ev_done = nullptr;     // output of the current host-buffer call is on the host
     float2* tw = nullptr;
     float *d_in = nullptr, *d_out = nullptr, *d_e = nullptr, *d_c = nullptr;
     float *h_in = nullptr, *h_out = nullptr, *h_e = nullptr;
@@ -267,7 +279,8 @@ void part_free(conv_engine* e, Part& P) {
     const MacPlan& p = P.plan;
     dev_free(e, &P.H, p.h_bytes);
     dev_free(e, &P.X, p.x_bytes);
-    dev_free(e, &P.partial, p.partial_bytes);
+    dev_free(e, &P.partial[0], p.partial_bytes);
+    dev_free(e, &P.partial[1], p.partial_bytes);
     dev_free(e, &P.win, (size_t)P.n_src * e->B * sizeof(float));
     if (P.sH) dev_free(e, &P.sH, (size_t)p.n_dst * p.R * sizeof(float));
     if (P.sX) dev_free(e, &P.sX, (size_t)p.R * sizeof(float));
@@ -293,7 +306,7 @@ int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps) {
     if (K <= 0 || (long long)n_src * K > 0x7fffffffLL / 2)
         return set_err(CONV_E_INVAL, "taps %lld gives too many partitions", taps);
     P.K = (int)K;
-    P.plan = plan_mac(e->prec, e->B, n_src, n_dst, P.K, e->num_sms);
+    P.plan = plan_mac(e->prec, e->B, n_src, n_dst, P.K, e->num_sms, n_src);
     const MacPlan& p = P.plan;
     std::string why;
     if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());
@@ -302,14 +315,16 @@ int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps) {
     P.allocated = true;  // partial allocations are released by part_free
     if ((rc = dev_alloc(e, &P.H, p.h_bytes))) return rc;
     if ((rc = dev_alloc(e, &P.X, p.x_bytes))) return rc;
-    if ((rc = dev_alloc(e, &P.partial, p.partial_bytes))) return rc;
+    if ((rc = dev_alloc(e, &P.partial[0], p.partial_bytes))) return rc;
+    if ((rc = dev_alloc(e, &P.partial[1], p.partial_bytes))) return rc;
+    if (!P.ev_packed) CK(cudaEventCreateWithFlags(&P.ev_packed, cudaEventDisableTiming));
+    if (!P.ev_tail) CK(cudaEventCreateWithFlags(&P.ev_tail, cudaEventDisableTiming));
     if ((rc = dev_alloc(e, &P.win, (size_t)n_src * e->B * sizeof(float)))) return rc;
     if (e->prec != PREC_FP32) {
         if ((rc = dev_alloc(e, &P.sH, (size_t)p.n_dst * p.R * sizeof(float)))) return rc;
         if ((rc = dev_alloc(e, &P.sX, (size_t)p.R * sizeof(float)))) return rc;
     }
     CK(cudaMemsetAsync(P.H, 0, p.h_bytes, e->stream));
-    CK(cudaMemsetAsync(P.partial, 0, p.partial_bytes, e->stream));
     return CONV_OK;
 }
 
@@ -318,6 +333,9 @@ int part_reset(conv_engine* e, Part& P) {
     CK(cudaMemsetAsync(P.X, 0, P.plan.x_bytes, e->stream));
     CK(cudaMemsetAsync(P.win, 0, (size_t)P.n_src * e->B * sizeof(float), e->stream));
     if (P.sX) CK(cudaMemsetAsync(P.sX, 0, (size_t)P.plan.R * sizeof(float), e->stream));
+    CK(cudaMemsetAsync(P.partial[0], 0, P.plan.partial_bytes, e->stream));
+    CK(cudaMemsetAsync(P.partial[1], 0, P.plan.partial_bytes, e->stream));
+    CK(cudaEventRecord(P.ev_tail, e->stream));  // block 0's tail: zero partials
     return CONV_OK;
 }
 
@@ -375,14 +393,17 @@ int enqueue_pack(conv_engine* e, Part& P, const float* src, int stride, const fl
     return CONV_OK;
 }
 
-int enqueue_mac(conv_engine* e, Part& P, cudaStream_t s, bool timed) {
+// Tail MAC for block `blk`: partitions 1..K-1, into the partial buffer of the
+// block's parity.
+int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool timed) {
     const MacPlan& p = P.plan;
+    if (p.S == 0) return CONV_OK;  // K = 1: no tail
     MacArgs a{};
     a.H = P.H;
     a.X = P.X;
     a.sH = P.sH;
     a.sX = P.sX;
-    a.partial = P.partial;
+    a.partial = P.partial[blk & 1];
     a.B = p.B;
     a.BT = p.BT;
     a.n_kt = p.n_kt;
@@ -394,10 +415,11 @@ int enqueue_mac(conv_engine* e, Part& P, cudaStream_t s, bool timed) {
     a.S = p.S;
     a.RS = p.RS;
     a.nstage = p.nstage;
+    a.r_begin = p.r_begin;
     a.kthreads = p.kthreads;
     a.NLG = p.NLG;
     a.NRL = p.NRL;
-    a.slot0 = slot0_for(e->nblk, P.K);
+    a.slot0 = slot0_for(blk, P.K);
     a.stage_bytes = p.stage_bytes;
     a.xoff = p.xoff;
     a.err = e->d_err;
@@ -411,17 +433,46 @@ int enqueue_mac(conv_engine* e, Part& P, cudaStream_t s, bool timed) {
     return CONV_OK;
 }
 
-int enqueue_out(conv_engine* e, Part& P, float* out, cudaStream_t s) {
-    ReduceArgs a{};
-    a.partial = P.partial;
-    a.S = P.plan.S;
+// Output of block `blk`: head (partition 0) + tail partials + C2R + OLS.
+int enqueue_out(conv_engine* e, Part& P, long long blk, float* out, cudaStream_t s) {
+    const MacPlan& p = P.plan;
+    OutArgs a{};
+    a.partial = P.partial[blk & 1];
+    a.S = p.S;
     a.n_dst = P.n_dst;
     a.B = e->B;
     a.log2B = e->log2B;
     a.tw = e->tw;
     a.out = out;
     a.out_stride = e->B;
-    CK(launch_reduce_c2r(a, s));
+    a.head = 1;
+    a.H = P.H;
+    a.X = P.X;
+    a.sH = P.sH;
+    a.sX = P.sX;
+    a.n_src = P.n_src;
+    a.K = P.K;
+    a.R = p.R;
+    a.BT = p.BT;
+    a.LT = p.LT;
+    a.slot0 = slot0_for(blk, P.K);
+    CK(launch_out_c2r(e->prec, a, s));
+    return CONV_OK;
+}
+
+// One block of one partitioned convolution on stream s (see the schedule at
+// the top of this file).
+int enqueue_conv(conv_engine* e, Part& P, const float* src, const float* sub, float* e_out, float* out,
+                 cudaStream_t s, bool timed) {
+    int rc;
+    const long long n = e->nblk;
+    if ((rc = enqueue_pack(e, P, src, e->B, sub, e_out, s))) return rc;
+    CK(cudaEventRecord(P.ev_packed, s));
+    CK(cudaStreamWaitEvent(s, P.ev_tail, 0));
+    if ((rc = enqueue_out(e, P, n, out, s))) return rc;
+    CK(cudaStreamWaitEvent(e->bg, P.ev_packed, 0));
+    if ((rc = enqueue_tail(e, P, n + 1, e->bg, timed))) return rc;
+    CK(cudaEventRecord(P.ev_tail, e->bg));
     return CONV_OK;
 }
 
@@ -436,6 +487,8 @@ int check_dev_err(conv_engine* e) {
 
 int engine_reset(conv_engine* e) {
     int rc;
+    CK(cudaStreamSynchronize(e->bg));
+    CK(cudaStreamSynchronize(e->stream));
     if ((rc = part_reset(e, e->syn))) return rc;
     if ((rc = part_reset(e, e->fb))) return rc;
     if (e->d_c) CK(cudaMemsetAsync(e->d_c, 0, (size_t)e->n_in * e->B * sizeof(float), e->stream));
@@ -445,24 +498,22 @@ int engine_reset(conv_engine* e) {
 }
 
 int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t s) {
-    int rc;
-    if ((rc = enqueue_pack(e, e->syn, d_in, e->B, nullptr, nullptr, s))) return rc;
-    if ((rc = enqueue_mac(e, e->syn, s, true))) return rc;
-    if ((rc = enqueue_out(e, e->syn, d_out, s))) return rc;
+    int rc = enqueue_conv(e, e->syn, d_in, nullptr, nullptr, d_out, s, true);
+    if (rc) return rc;
     ++e->nblk;
     return CONV_OK;
 }
 
-int enqueue_afc_block(conv_engine* e, const float* d_mic, float* d_out, float* d_e, cudaStream_t s) {
-    int rc;
-    // e = mic - c_prev; synthesis (Eq. 2)
-    if ((rc = enqueue_pack(e, e->syn, d_mic, e->B, e->d_c, d_e, s))) return rc;
-    if ((rc = enqueue_mac(e, e->syn, s, true))) return rc;
-    if ((rc = enqueue_out(e, e->syn, d_out, s))) return rc;
-    // c = F_hat * l (Eq. 3), kept for the next block (Sec. 5)
-    if ((rc = enqueue_pack(e, e->fb, d_out, e->B, nullptr, nullptr, s))) return rc;
-    if ((rc = enqueue_mac(e, e->fb, s, false))) return rc;
-    if ((rc = enqueue_out(e, e->fb, e->d_c, s))) return rc;
+// Synthesis with feedback cancellation (Sec. 5): e = mic - c_prev, l = H^T * e
+// (first half), then c = F_hat * l, kept for the next block (second half).
+// The host-buffer call copies l and e out between the halves.
+int enqueue_afc_synthesis(conv_engine* e, const float* d_mic, float* d_out, float* d_e, cudaStream_t s) {
+    return enqueue_conv(e, e->syn, d_mic, e->d_c, d_e, d_out, s, true);
+}
+
+int enqueue_afc_prediction(conv_engine* e, const float* d_out, cudaStream_t s) {
+    int rc = enqueue_conv(e, e->fb, d_out, nullptr, nullptr, e->d_c, s, false);
+    if (rc) return rc;
     ++e->nblk;
     return CONV_OK;
 }
@@ -471,6 +522,11 @@ void engine_free(conv_engine* e) {
     if (!e) return;
     DeviceGuard g(e->dev);
     if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->bg) cudaStreamSynchronize(e->bg);
+    for (Part* P : {&e->syn, &e->fb}) {
+        if (P->ev_packed) cudaEventDestroy(P->ev_packed);
+        if (P->ev_tail) cudaEventDestroy(P->ev_tail);
+    }
     part_free(e, e->syn);
     part_free(e, e->fb);
     dev_free(e, &e->tw, 0);
@@ -484,6 +540,8 @@ void engine_free(conv_engine* e) {
     if (e->h_err) cudaFreeHost(e->h_err);
     for (auto ev : e->ev0) cudaEventDestroy(ev);
     for (auto ev : e->ev1) cudaEventDestroy(ev);
+    if (e->ev_done) cudaEventDestroy(e->ev_done);
+    if (e->bg) cudaStreamDestroy(e->bg);
     if (e->stream) cudaStreamDestroy(e->stream);
     delete e;
 }
@@ -506,7 +564,11 @@ int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long 
     CK(cudaGetDeviceProperties(&prop, e->dev));
     e->num_sms = prop.multiProcessorCount;
     CK(prepare_kernels(200 * 1024));
-    CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+    int prio_low = 0, prio_high = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    CK(cudaStreamCreateWithPriority(&e->stream, cudaStreamNonBlocking, prio_high));
+    CK(cudaStreamCreateWithPriority(&e->bg, cudaStreamNonBlocking, prio_low));
+    CK(cudaEventCreateWithFlags(&e->ev_done, cudaEventDisableTiming | cudaEventBlockingSync));
     // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once to FP32
     std::vector<float2> tw(2 * (size_t)block);
     const double pi = 3.14159265358979323846264338327950288;
@@ -601,7 +663,8 @@ int conv_process_block(conv_engine* e, const float* in, float* out) {
     int rc = enqueue_block(e, e->d_in, e->d_out, e->stream);
     if (rc) return rc;
     CK(cudaMemcpyAsync(e->h_out, e->d_out, ob, cudaMemcpyDeviceToHost, e->stream));
-    CK(cudaStreamSynchronize(e->stream));
+    CK(cudaEventRecord(e->ev_done, e->stream));
+    CK(cudaEventSynchronize(e->ev_done));  // the next block's tail keeps running
     if ((rc = check_dev_err(e))) return rc;
     std::memcpy(out, e->h_out, ob);
     return CONV_OK;
@@ -611,7 +674,10 @@ int afc_process_block_async(conv_engine* e, const float* d_mic, float* d_out, fl
     if (!e || !d_mic || !d_out) return set_err(CONV_E_INVAL, "null argument");
     if (!e->syn.ready || !e->fb.ready) return set_err(CONV_E_STATE, "filters or feedback paths not set");
     DeviceGuard g(e->dev);
-    return enqueue_afc_block(e, d_mic, d_out, d_e, static_cast<cudaStream_t>(cuda_stream));
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int rc = enqueue_afc_synthesis(e, d_mic, d_out, d_e, s);
+    if (rc) return rc;
+    return enqueue_afc_prediction(e, d_out, s);
 }
 
 int afc_process_block(conv_engine* e, const float* mic, float* out, float* e_or_null) {
@@ -622,11 +688,14 @@ int afc_process_block(conv_engine* e, const float* mic, float* out, float* e_or_
     const bool want_e = e_or_null != nullptr || e->guard > 0.0;
     std::memcpy(e->h_in, mic, ib);
     CK(cudaMemcpyAsync(e->d_in, e->h_in, ib, cudaMemcpyHostToDevice, e->stream));
-    int rc = enqueue_afc_block(e, e->d_in, e->d_out, e->d_e, e->stream);
+    int rc = enqueue_afc_synthesis(e, e->d_in, e->d_out, e->d_e, e->stream);
     if (rc) return rc;
     CK(cudaMemcpyAsync(e->h_out, e->d_out, ob, cudaMemcpyDeviceToHost, e->stream));
     if (want_e) CK(cudaMemcpyAsync(e->h_e, e->d_e, ib, cudaMemcpyDeviceToHost, e->stream));
-    CK(cudaStreamSynchronize(e->stream));
+    CK(cudaEventRecord(e->ev_done, e->stream));
+    // the prediction for the next block runs while this block's output is copied out
+    if ((rc = enqueue_afc_prediction(e, e->d_out, e->stream))) return rc;
+    CK(cudaEventSynchronize(e->ev_done));
     if ((rc = check_dev_err(e))) return rc;
     if (e->guard > 0.0) {
         double ss = 0.0;
@@ -660,6 +729,8 @@ int conv_reset(conv_engine* e) {
 int conv_synchronize(conv_engine* e) {
     if (!e) return set_err(CONV_E_INVAL, "null handle");
     DeviceGuard g(e->dev);
+    CK(cudaStreamSynchronize(e->bg));
+    CK(cudaStreamSynchronize(e->stream));
     CK(cudaDeviceSynchronize());
     return check_dev_err(e);
 }
@@ -676,8 +747,14 @@ int conv_get_info(const conv_engine* e, conv_info* out) {
     out->taps_fb = e->fb.allocated ? e->fb.taps : 0;
     out->K_fb = e->fb.allocated ? e->fb.K : 0;
     out->precision = e->prec;
-    out->mac_bytes = (long long)(p.h_bytes + p.x_bytes);
-    out->mac_fb_bytes = e->fb.allocated ? (long long)(e->fb.plan.h_bytes + e->fb.plan.x_bytes) : 0;
+    // algorithmic bytes of one tail MAC launch: partitions 1..K-1 of every
+    // filter spectrum plus the matching delay-line rows, each read once
+    auto tail_bytes = [](const MacPlan& q) {
+        const size_t Rt = (size_t)(q.R - q.r_begin);
+        return (long long)(((size_t)q.n_dst + 1) * Rt * q.B * q.es);
+    };
+    out->mac_bytes = tail_bytes(p);
+    out->mac_fb_bytes = e->fb.allocated ? tail_bytes(e->fb.plan) : 0;
     out->mac_ctas = p.ctas;
     out->mac_splits = p.S;
     out->mac_smem = (long long)p.smem;
@@ -727,7 +804,7 @@ int conv_plan_check(int precision, int block, int n_src, int n_dst, long long ta
         return set_err(CONV_E_INVAL, "invalid plan arguments");
     const long long K = (taps + block - 1) / block;
     if ((long long)n_src * K > 0x7fffffffLL / 2) return set_err(CONV_E_INVAL, "too many partitions");
-    const MacPlan p = plan_mac(precision, block, n_src, n_dst, (int)K, num_sms);
+    const MacPlan p = plan_mac(precision, block, n_src, n_dst, (int)K, num_sms, n_src);
     std::string why;
     if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());
     return CONV_OK;

@@ -1,11 +1,13 @@
 // kernels.cu - the engine's CUDA kernels (sm_103a) and their host launchers.
 //
 // Data layouts (B = n_x, block size; K partitions; R = n_src * K reduction
-// indices r = q*K + p; BT bin-tile width, n_kt = B / BT; LT output-tile height):
+// indices r = p*n_src + q; BT bin-tile width, n_kt = B / BT; LT output-tile height):
 //   filter spectra  H[kt][l0..][r][LTt][BT]  (for each bin tile kt and output
 //                   tile starting at l0 with LTt rows, all r are contiguous)
-//   FDL ring        X[kt][q][slot][BT]       (slot of partition p at block n:
-//                   (p - n) mod K, so a run of partitions is a run of slots)
+//   FDL ring        X[kt][slot][q][BT]       (slot of partition p at block n:
+//                   (p - n) mod K; ring row slot*n_src + q of reduction index r
+//                   is (slot0*n_src + r) mod R, so a run of r is a run of rows
+//                   with at most one wrap)
 //   partials        P[split][l][B]           float2, one row per partition split
 // All spectra use the packed layout described in kernels.h.
 #include <cuda_runtime.h>
@@ -36,12 +38,12 @@ __device__ float block_max(float v, float* red) {
     return r;
 }
 
-// Element index of bin k of ring slot `slot` of channel c (layout X[kt][c][slot][BT]).
+// Element index of bin k of ring slot `slot` of channel c (layout X[kt][slot][c][BT]).
 struct RingIndex {
     int BT, n_ch, c, K, slot;
     __device__ size_t operator()(int k) const {
         const int kt = k / BT, kl = k - kt * BT;
-        return (((size_t)kt * n_ch + c) * K + slot) * BT + kl;
+        return (((size_t)kt * K + slot) * n_ch + c) * BT + kl;
     }
 };
 
@@ -114,11 +116,12 @@ __global__ void k_pack_r2c(const PackArgs a) {
     for (int k = tid; k < B; k += nth) Xs[k] = r2c_post(Z, k, B, tws);
     __syncthreads();
     const float scale = store_spectrum<PREC>(Xs, B, a.X, RingIndex{a.BT, a.n_ch, c, a.K, a.slot}, red);
-    if (PREC != PREC_FP32 && tid == 0) a.sX[(size_t)c * a.K + a.slot] = scale;
+    if (PREC != PREC_FP32 && tid == 0) a.sX[(size_t)a.slot * a.n_ch + c] = scale;
 }
 
 // --------------------------------------------------- filter partitions R2C
-// One CTA per (l, q, p): sub-filter h_lq[pB, pB+B) zero-padded to 2B, R2C.
+// One CTA per (l, q, p): sub-filter h_lq[pB, pB+B) zero-padded to 2B, R2C,
+// stored at reduction index p * n_src + q.
 template <int PREC>
 __global__ void k_filter_r2c(const FilterArgs a) {
     extern __shared__ float2 fsm[];
@@ -126,8 +129,9 @@ __global__ void k_filter_r2c(const FilterArgs a) {
     const int B = a.B, half = B >> 1, tid = threadIdx.x, nth = blockDim.x;
     const int K = a.K, R = a.n_src * K;
     const int l = blockIdx.x / R;
-    const int r = blockIdx.x - l * R;
-    const int q = r / K, p = r - q * K;
+    const int qp = blockIdx.x - l * R;
+    const int q = qp / K, p = qp - q * K;
+    const int r = p * a.n_src + q;
     const float* h = a.h + ((size_t)l * a.n_src + q) * (size_t)a.taps;
     const long long t0 = (long long)p * B;
     float2* bufA = fsm;
@@ -156,7 +160,8 @@ __global__ void k_filter_r2c(const FilterArgs a) {
 }
 
 // ----------------------------------------------------------- FDL MAC
-// Y[l][k] += sum_{r in split} H[l][r][k] * X[q(r)][slot(r)][k]   (Eq. 6 per bin)
+// Y[l][k] += sum_{r in split} H[l][r][k] * X[slot(r)][q(r)][k]   (Eq. 6 per bin)
+// over r in [r_begin, R), split into S contiguous ranges per tile.
 //
 // One CTA per (bin tile, output tile, partition split).  Warp 8 is the
 // producer: one elected lane streams the split's contiguous filter-spectrum
@@ -181,14 +186,16 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
     const int tile = blockIdx.x / a.S, split = blockIdx.x - tile * a.S;
     const int kt = tile / a.n_lt, lt = tile - kt * a.n_lt;
     const int l0 = lt * a.LT, LTt = min(a.LT, a.n_dst - l0);
-    const int K = a.K, R = a.n_src * K;
-    const int r0 = (int)((long long)split * R / a.S), r1 = (int)((long long)(split + 1) * R / a.S);
+    const int K = a.K, R = a.n_src * K, Rt = R - a.r_begin;
+    const int r0 = a.r_begin + (int)((long long)split * Rt / a.S);
+    const int r1 = a.r_begin + (int)((long long)(split + 1) * Rt / a.S);
+    const int ring0 = a.slot0 * a.n_src;  // ring row of r = 0
     const int nit = (r1 - r0 + a.RS - 1) / a.RS;
     const size_t hrow = (size_t)a.BT * St::BYTES;
     const size_t hr_bytes = (size_t)LTt * hrow;
     const unsigned char* Hb =
         static_cast<const unsigned char*>(a.H) + ((size_t)kt * a.n_dst + l0) * (size_t)R * hrow;
-    const unsigned char* Xb = static_cast<const unsigned char*>(a.X) + (size_t)kt * a.n_src * K * hrow;
+    const unsigned char* Xb = static_cast<const unsigned char*>(a.X) + (size_t)kt * R * hrow;
 
     if (tid == 0) {
         for (int i = 0; i < a.nstage; ++i) {
@@ -214,19 +221,14 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
         };
         auto issue_x = [&](int it) {
             const int st = it % a.nstage;
-            const int ra = r0 + it * a.RS, rb = min(ra + a.RS, r1);
+            const int ra = r0 + it * a.RS, rb = min(ra + a.RS, r1), nr = rb - ra;
             unsigned char* sx = stages + (size_t)st * a.stage_bytes + a.xoff;
-            int r = ra, j = 0;
-            while (r < rb) {
-                const int q = r / K, p = r - q * K;
-                int slot = a.slot0 + p;
-                if (slot >= K) slot -= K;
-                const int run = min(rb - r, min(K - p, K - slot));
-                bulk_g2s(sx + (size_t)j * hrow, Xb + ((size_t)q * K + slot) * hrow, (uint32_t)(run * hrow),
-                         &full[st], pol_keep);
-                r += run;
-                j += run;
-            }
+            int start = ring0 + ra;
+            if (start >= R) start -= R;
+            const int run = min(nr, R - start);
+            bulk_g2s(sx, Xb + (size_t)start * hrow, (uint32_t)(run * hrow), &full[st], pol_keep);
+            if (run < nr)
+                bulk_g2s(sx + (size_t)run * hrow, Xb, (uint32_t)((nr - run) * hrow), &full[st], pol_keep);
         };
         // The filter spectra are constant: stream the first stages while the
         // previous kernel (the pack of this block) is still running, then wait for
@@ -286,10 +288,9 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
             St::load16(sx + (size_t)j * hrow + (size_t)kv * 16, xv);
             float sxs = 1.0f;
             if (PREC != PREC_FP32) {
-                const int r = ra + j, q = r / K, p = r - q * K;
-                int slot = a.slot0 + p;
-                if (slot >= K) slot -= K;
-                sxs = __ldg(a.sX + (size_t)q * K + slot);
+                int row = ring0 + ra + j;
+                if (row >= R) row -= R;
+                sxs = __ldg(a.sX + row);
             }
 #pragma unroll
             for (int i = 0; i < LPT; ++i) {
@@ -364,11 +365,15 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
     }
 }
 
-// ------------------------------------------------- reduce + C2R + OLS
-// One CTA per output channel: sum the partition splits in a fixed order
-// (independent loads in groups of 8, pairwise within a group), C2R IFFT
-// (1/2B), keep the last B samples (overlap-save).
-__global__ void k_reduce_c2r(const ReduceArgs a) {
+// --------------------------------------------- head + reduce + C2R + OLS
+// One CTA per output channel l.  Per bin: the fixed-order sum of the S split
+// partials (independent loads in groups of 8, pairwise within a group), then
+// partition 0 of this block, sum_q H[l][q][k] * X_n[q][k] (the only term that
+// needs the new input), then the C2R IFFT (1/2B) and the last B samples
+// (overlap-save).
+template <int PREC>
+__global__ void k_out_c2r(const OutArgs a) {
+    using St = Store<PREC>;
     extern __shared__ float2 fsm[];
     const int B = a.B, l = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
     float2* P = fsm;
@@ -379,6 +384,8 @@ __global__ void k_reduce_c2r(const ReduceArgs a) {
     griddep_wait();
     const size_t stride = (size_t)a.n_dst * B;
     const int S = a.S;
+    const int l0 = a.head ? (l / a.LT) * a.LT : 0;
+    const int LTt = a.head ? min(a.LT, a.n_dst - l0) : 0, ll = l - l0;
     for (int k = tid; k < B; k += nth) {
         const float2* src = a.partial + (size_t)l * B + k;
         float2 tot = make_float2(0.0f, 0.0f);
@@ -391,6 +398,27 @@ __global__ void k_reduce_c2r(const ReduceArgs a) {
             tot = cadd(tot, g);
         }
         for (; s < S; ++s) tot = cadd(tot, src[(size_t)s * stride]);
+        if (a.head) {
+            const int kt = k / a.BT, kl = k - kt * a.BT;
+            const size_t hbase = (((size_t)kt * a.n_dst + l0) * (size_t)a.R) * a.BT + (size_t)ll * a.BT + kl;
+            const size_t xbase = (((size_t)kt * a.K + a.slot0) * a.n_src) * a.BT + kl;
+            float2 hd = make_float2(0.0f, 0.0f);
+            for (int q = 0; q < a.n_src; ++q) {
+                const float2 h = St::load1(a.H, hbase + (size_t)q * LTt * a.BT);
+                const float2 x = St::load1(a.X, xbase + (size_t)q * a.BT);
+                float2 t = make_float2(0.0f, 0.0f);
+                if (k == 0)
+                    rmac2(t, h, x);
+                else
+                    cmac(t, h, x);
+                const float sc = PREC == PREC_FP32
+                                     ? 1.0f
+                                     : __ldg(a.sH + (size_t)l * a.R + q) * __ldg(a.sX + (size_t)a.slot0 * a.n_src + q);
+                hd.x = fmaf(sc, t.x, hd.x);
+                hd.y = fmaf(sc, t.y, hd.y);
+            }
+            tot = cadd(tot, hd);
+        }
         P[k] = tot;
     }
     __syncthreads();
@@ -463,7 +491,9 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR(k_filter_r2c<PREC_FP32>, fft_max)
     GB_ATTR(k_filter_r2c<PREC_FP16>, fft_max)
     GB_ATTR(k_filter_r2c<PREC_BF16>, fft_max)
-    GB_ATTR(k_reduce_c2r, fft_max)
+    GB_ATTR(k_out_c2r<PREC_FP32>, fft_max)
+    GB_ATTR(k_out_c2r<PREC_FP16>, fft_max)
+    GB_ATTR(k_out_c2r<PREC_BF16>, fft_max)
     GB_ATTR((k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>()>), mac_smem)
     GB_ATTR((k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>()>), mac_smem)
     GB_ATTR((k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>()>), mac_smem)
@@ -506,8 +536,15 @@ cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStr
     }
 }
 
-cudaError_t launch_reduce_c2r(const ReduceArgs& a, cudaStream_t s) {
-    return launch_pdl(k_reduce_c2r, dim3(a.n_dst), dim3(out_threads(a.B)), fft_smem_bytes(a.B), s, a);
+cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s) {
+    const dim3 grid(a.n_dst), block(out_threads(a.B));
+    const size_t sm = fft_smem_bytes(a.B);
+    switch (prec) {
+        case PREC_FP32: return launch_pdl(k_out_c2r<PREC_FP32>, grid, block, sm, s, a);
+        case PREC_FP16: return launch_pdl(k_out_c2r<PREC_FP16>, grid, block, sm, s, a);
+        case PREC_BF16: return launch_pdl(k_out_c2r<PREC_BF16>, grid, block, sm, s, a);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace gbconv

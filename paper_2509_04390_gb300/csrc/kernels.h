@@ -3,14 +3,21 @@
 // Kernels (all hand-written for sm_103a, FP32 arithmetic):
 //   pack_r2c    input packing + 2B-point R2C FFT + FDL push   (Sec. 4, stage 1)
 //   filter_r2c  sub-filter zero-padding + R2C FFT            (Sec. 4, initialisation)
-//   fdl_mac     FDL complex multiply-accumulate over all partitions and
-//               input->output pairs, split over partition ranges (Sec. 4, stage 2; Eq. 6)
-//   reduce_c2r  fixed-order reduction of the partition splits, C2R IFFT and
-//               overlap-save discard                          (Sec. 4, stage 3)
+//   fdl_mac     FDL complex multiply-accumulate over a range of partitions of
+//               all input->output pairs, split over partition ranges (Sec. 4,
+//               stage 2; Eq. 6).  The engine runs it over partitions 1..K-1 of
+//               the NEXT block as soon as the current block's spectrum is in
+//               the delay line (they only need past input).
+//   out_c2r     partition 0 of this block (the only part that needs the new
+//               input) + fixed-order reduction of the split partials, C2R IFFT
+//               and overlap-save discard                      (Sec. 4, stage 3)
 //
 // Spectra are "packed": bins 0..B-1 of the 2B-point real FFT, with the real
 // Nyquist bin B stored in the imaginary slot of bin 0 (both are real for a
 // real signal), so every row is B complex values.
+//
+// Reduction index: r = p * n_src + q (partition-major), so partition 0 of all
+// inputs is r in [0, n_src) and partitions 1..K-1 are one contiguous range.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstddef>
@@ -29,11 +36,12 @@ constexpr int MAC_HDR_BYTES = 1024;                          // mbarriers + flag
 constexpr int MAX_STAGES = 8;
 
 // Tiling of one FDL MAC (one partitioned convolution with n_src inputs, n_dst
-// outputs and K partitions).  Spectra of a (bin tile, output tile) pair are
-// stored contiguously over the reduction index r = q*K + p, so each CTA streams
-// one contiguous range.
+// outputs and K partitions) over the reduction range [r_begin, R).  Spectra of
+// a (bin tile, output tile) pair are stored contiguously over r, so each CTA
+// streams one contiguous range.
 struct MacPlan {
     int B, n_src, n_dst, K, R;
+    int r_begin;   // first reduction index the MAC covers
     int es;        // bytes per stored complex value (8 fp32, 4 fp16/bf16)
     int VEC;       // complex values per 16-byte load
     int LPT;       // max outputs per consumer thread
@@ -42,7 +50,7 @@ struct MacPlan {
     int kthreads, NLG, NRL;  // consumer thread layout: bins x output groups x r-lanes
     int RS;        // reduction indices per pipeline stage
     int nstage;    // pipeline depth
-    int S;         // partition splits per tile
+    int S;         // partition splits per tile (0: empty range, no MAC launch)
     unsigned stage_bytes, xoff;
     size_t smem;   // dynamic shared memory per CTA
     int ctas;
@@ -50,16 +58,17 @@ struct MacPlan {
 };
 
 struct MacArgs {
-    const void* H;
-    const void* X;
+    const void* H;    // filter spectra [kt][l0..][r][LTt][BT]
+    const void* X;    // FDL ring [kt][slot][q][BT]
     const float* sH;  // [n_dst][R] per-partition scales (reduced precision), else null
-    const float* sX;  // [n_src][K] per-slot scales (reduced precision), else null
+    const float* sX;  // [K][n_src] per-slot scales (reduced precision), else null
     float2* partial;  // [S][n_dst][B]
     int B, BT, n_kt, n_dst, LT, n_lt, n_src, K, S, RS, nstage;
+    int r_begin;
     int kthreads, NLG, NRL;
-    int slot0;  // ring slot of partition 0 for this block
+    int slot0;  // ring slot of partition 0 for the block this MAC serves
     unsigned stage_bytes, xoff;
-    int* err;   // device-visible error word (host-mapped)
+    int* err;   // device-visible error word (host-mapped), or null
 };
 
 struct PackArgs {
@@ -68,8 +77,8 @@ struct PackArgs {
     const float* sub;  // [n_ch][B] subtracted from `in` (feedback prediction), or null
     float* e_out;      // [n_ch][B] receives in - sub, or null
     float* win;        // [n_ch][B] previous block (sliding-window state)
-    void* X;           // FDL ring [n_kt][n_ch][K][BT] (storage type)
-    float* sX;         // [n_ch][K] slot scales (reduced precision), else null
+    void* X;           // FDL ring [n_kt][K][n_ch][BT] (storage type)
+    float* sX;         // [K][n_ch] slot scales (reduced precision), else null
     int B, log2B, BT, n_ch, K, slot;
     const float2* tw;  // W_2B^j = exp(-i pi j / B), j in [0, 2B)
 };
@@ -79,16 +88,23 @@ struct FilterArgs {
     long long taps;
     int n_dst, n_src, K, B, log2B, BT, LT;
     void* H;    // tiled spectra
-    float* sH;  // [n_dst][n_src*K] scales (reduced precision), else null
+    float* sH;  // [n_dst][R] scales (reduced precision), else null
     const float2* tw;
 };
 
-struct ReduceArgs {
-    const float2* partial;  // [S][n_dst][B]
+struct OutArgs {
+    const float2* partial;  // [S][n_dst][B] (S may be 0)
     int S, n_dst, B, log2B;
     const float2* tw;
     float* out;  // [n_dst][out_stride]
     int out_stride;
+    // partition 0 of this block, added after the split partials (head = 0: none)
+    int head;
+    const void* H;
+    const void* X;
+    const float* sH;
+    const float* sX;
+    int n_src, K, R, BT, LT, slot0;
 };
 
 int fft_threads(int B);
@@ -102,6 +118,6 @@ cudaError_t prepare_kernels(size_t mac_smem);
 cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s);
 cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s);
 cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s);
-cudaError_t launch_reduce_c2r(const ReduceArgs& a, cudaStream_t s);
+cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s);
 
 }  // namespace gbconv

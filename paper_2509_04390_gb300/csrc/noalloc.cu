@@ -112,13 +112,14 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     if (e != cudaSuccess) return fail(CONV_E_CUDA, "SM count", e);
 
     // One tile covering every bin and every output: the engine's tiled filter
-    // layout then reduces to H[q][p][l][k], and its ring to X[q][slot][k].
+    // layout then reduces to H[p][q][l][k], and its ring to X[slot][q][k].
     MacPlan p{};
     p.B = block;
     p.n_src = n_in;
     p.n_dst = n_out;
     p.K = (int)K;
     p.R = n_in * (int)K;
+    p.r_begin = 0;
     p.es = 8;
     p.VEC = 2;
     p.LPT = 8;
@@ -177,6 +178,7 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     a.kthreads = p.kthreads;
     a.NLG = p.NLG;
     a.NRL = p.NRL;
+    a.r_begin = 0;
     a.slot0 = (int)slot0;
     a.stage_bytes = p.stage_bytes;
     a.xoff = p.xoff;
@@ -186,7 +188,7 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
 
     int log2B = 0;
     while ((1 << log2B) < block) ++log2B;
-    ReduceArgs r{};
+    OutArgs r{};
     r.partial = d->scratch;
     r.S = p.S;
     r.n_dst = n_out;
@@ -195,7 +197,8 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     r.tw = d->tw + tw_offset(block);
     r.out = d_y;
     r.out_stride = block;
-    e = launch_reduce_c2r(r, s);
+    r.head = 0;
+    e = launch_out_c2r(PREC_FP32, r, s);
     if (e != cudaSuccess) return fail(CONV_E_CUDA, "output-transform launch", e);
     return CONV_OK;
 }

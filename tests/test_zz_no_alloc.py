@@ -50,12 +50,12 @@ def test_noalloc_matches_engine_on_two_calls(n_in, n_out, taps, B, nb):
         e.set_filters(w.h)
         y_ref = e.run(w.x)
 
-    # caller-owned spectra in the documented layout: H[q][p][l][k], ring X[q][slot][k]
+    # caller-owned spectra in the documented layout: H[p][q][l][k], ring X[slot][q][k]
     hp = np.zeros((n_out, n_in, K * B))
     hp[:, :, :taps] = w.h
     sub = hp.reshape(n_out, n_in, K, B)  # [l][q][p][:]
-    H = packed_rfft(sub, B).transpose(1, 2, 0, 3, 4).copy()  # [q][p][l][k][2]
-    ring = np.zeros((n_in, K, B, 2), np.float32)
+    H = packed_rfft(sub, B).transpose(2, 1, 0, 3, 4).copy()  # [p][q][l][k][2]
+    ring = np.zeros((K, n_in, B, 2), np.float32)
     x = w.x.astype(np.float64)
 
     d_H = torch.from_numpy(H).cuda()
@@ -67,7 +67,7 @@ def test_noalloc_matches_engine_on_two_calls(n_in, n_out, taps, B, nb):
         prev = x[:, (b - 1) * B : b * B] if b > 0 else np.zeros((n_in, B))
         win = np.concatenate([prev, x[:, b * B : (b + 1) * B]], axis=1)
         slot0 = (-b) % K
-        ring[:, slot0] = packed_rfft(win, B)
+        ring[slot0] = packed_rfft(win, B)
         if b in last_two:
             d_X = torch.from_numpy(ring).cuda()
             torch.cuda.synchronize()
