@@ -71,7 +71,13 @@ inline int pow2_ceil(int v) {
 // the pipeline stage size and depth, and the number of partition splits so
 // that the grid covers every SM about once (1 CTA/SM at these shared-memory
 // sizes) while each CTA still streams at least a few stages.
-MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int r_begin) {
+// Tiling fields a caller (the autotuner) may fix; 0 leaves a field to the planner.
+struct TileOverride {
+    int bin_tile = 0, stages = 0, stage_kib = 0, splits = 0;
+};
+
+MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int r_begin,
+                 const TileOverride& o = TileOverride()) {
     MacPlan p{};
     p.B = B;
     p.n_src = n_src;
@@ -92,6 +98,7 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     int n_kt = 1;
     while (n_kt * 2 <= want_kt) n_kt *= 2;
     p.BT = std::max(16, std::min(256, B / n_kt));
+    if (o.bin_tile) p.BT = std::max(16, std::min(256, o.bin_tile));
     if (p.BT > B) p.BT = B;
     p.n_kt = B / p.BT;
     p.kthreads = p.BT / p.VEC;
@@ -100,23 +107,39 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     if (p.NLG > rest) p.NLG = rest;
     p.NRL = rest / p.NLG;
     const size_t per_r = (size_t)(p.LT + 1) * p.BT * p.es;
-    int rs = (int)std::max<size_t>(1, (32768 + per_r / 2) / per_r);
-    rs = (rs + p.NRL - 1) / p.NRL * p.NRL;  // whole r-lanes per stage
+    // ~64 KB stages: large 1-D bulk copies stream best (measured against 32 KB x 5)
+    const size_t stage_target = o.stage_kib ? (size_t)o.stage_kib * 1024 : 65536;
+    int rs = (int)std::max<size_t>(1, (stage_target + per_r / 2) / per_r);
     p.RS = std::max(1, std::min(rs, std::max(1, Rt)));
+    const size_t budget = MAC_SMEM_LIMIT - MAC_HDR_BYTES;
+    const bool scaled = prec != PREC_FP32;
+    // scale parts: a run widened to 16-byte boundaries at both ends (+ a wrapped second run for sX)
+    auto sh_part = [&](int RS) { return scaled ? align_up(((size_t)RS * p.LT + 8) * 4, 128) : 0; };
+    auto sx_part = [&](int RS) { return scaled ? align_up(((size_t)RS + 12) * 4, 128) : 0; };
+    auto stage_size = [&](int RS) {
+        return align_up((size_t)RS * p.LT * p.BT * p.es, 128) + align_up((size_t)RS * p.BT * p.es, 128) +
+               sh_part(RS) + sx_part(RS);
+    };
+    while (p.RS > 1 && 2 * stage_size(p.RS) > budget) --p.RS;  // at least double buffering
     const size_t hpart = align_up((size_t)p.RS * p.LT * p.BT * p.es, 128);
-    const size_t xpart = align_up((size_t)p.RS * p.BT * p.es, 128);
     p.xoff = (unsigned)hpart;
-    p.stage_bytes = (unsigned)(hpart + xpart);
-    const size_t budget = 200 * 1024 - MAC_HDR_BYTES;
-    p.nstage = (int)std::min<size_t>(MAX_STAGES, std::max<size_t>(2, budget / p.stage_bytes));
+    p.soff = (unsigned)(hpart + align_up((size_t)p.RS * p.BT * p.es, 128));
+    p.sxoff = (unsigned)(p.soff + sh_part(p.RS));
+    p.stage_bytes = (unsigned)stage_size(p.RS);
+    const int fit = (int)std::max<size_t>(2, budget / p.stage_bytes);
+    p.nstage = std::min(MAX_STAGES, fit);
+    if (o.stages) p.nstage = std::max(2, std::min(o.stages, fit));
     // scratch for combining r-lanes reuses (and if needed extends) the stage ring
     const size_t red = (size_t)(p.NRL - 1) * p.LT * p.BT * sizeof(float2);
     p.smem = MAC_HDR_BYTES + std::max((size_t)p.nstage * p.stage_bytes, align_up(red, 128));
     const int tiles = p.n_kt * p.n_lt;
     const size_t tile_bytes = (size_t)Rt * p.LT * p.BT * p.es;
     const int by_work = (int)std::max<size_t>(1, tile_bytes / (2 * (size_t)p.stage_bytes));
-    int S = std::max(1, (num_sms + tiles / 2) / tiles);
+    // never a second wave: the grid fits the SMs at the occupancy shared memory allows
+    const int per_sm = (int)std::max<size_t>(1, SM_SMEM_BYTES / (p.smem + CTA_SMEM_RESERVED));
+    int S = std::max(1, num_sms * per_sm / tiles);
     S = std::min(S, std::min(by_work, Rt));
+    if (o.splits) S = std::min(o.splits, Rt);
     p.S = Rt > 0 ? std::max(1, S) : 0;
     p.ctas = tiles * p.S;
     p.h_bytes = (size_t)n_dst * p.R * B * p.es;
@@ -141,7 +164,7 @@ int check_plan(const MacPlan& p, std::string* why) {
     if (Rt < 0 || p.r_begin < 0) return bad("reduction range");
     if (Rt == 0) return p.S == 0 ? 0 : bad("splits over an empty range");
     if (p.nstage < 1 || p.nstage > MAX_STAGES) return bad("stage count");
-    if (p.smem > 227 * 1024) return bad("shared memory above 227 KB");
+    if (p.smem > MAC_SMEM_LIMIT) return bad("shared memory above the kernel's limit");
     if (p.kthreads * p.VEC != p.BT || p.kthreads > MAC_CONSUMER_WARPS * 32) return bad("bin threads");
     const int rest = (MAC_CONSUMER_WARPS * 32) / p.kthreads;
     if (p.kthreads * rest != MAC_CONSUMER_WARPS * 32 || p.NLG * p.NRL != rest) return bad("thread layout");
@@ -172,6 +195,21 @@ int check_plan(const MacPlan& p, std::string* why) {
             if (hb + (size_t)rb * hr > p.h_bytes) return bad("filter copy past the spectra");
             if ((size_t)nr * hr > p.xoff) return bad("filter copy past its stage part");
             if (p.xoff + (size_t)nr * hrow > p.stage_bytes) return bad("delay-line copy past its stage");
+            if (p.es == 4) {
+                const int fo = l0 * p.R + ra * LTt;
+                const int a0 = fo & ~3, a1 = (fo + nr * LTt + 3) & ~3;
+                if ((size_t)a1 > (size_t)p.n_dst * p.R + 4) return bad("filter scales past their buffer");
+                if (p.soff + 4 * (size_t)(a1 - a0) > p.sxoff) return bad("filter scales past their stage part");
+                for (int slot0 = 0; slot0 < p.K; slot0 += std::max(1, p.K / 7)) {
+                    const int start = (slot0 * p.n_src + ra) % p.R;
+                    const int run = std::min(nr, p.R - start);
+                    const int b0 = start & ~3, b1 = (start + run + 3) & ~3;
+                    const int c1 = run < nr ? ((nr - run + 3) & ~3) : 0;
+                    if ((size_t)b1 > (size_t)p.R + 4 || (size_t)c1 > (size_t)p.R + 4) return bad("slot scales past their buffer");
+                    if (p.sxoff + 4 * (size_t)((b1 - b0) + c1) > p.stage_bytes) return bad("slot scales past their stage part");
+                    if (tx + 4 * (size_t)((a1 - a0) + (b1 - b0) + c1) >= (1u << 20)) return bad("transaction bytes");
+                }
+            }
             for (int slot0 = 0; slot0 < p.K; slot0 += std::max(1, p.K / 7)) {
                 int start = slot0 * p.n_src + ra;
                 start %= p.R;
@@ -206,7 +244,7 @@ struct Part {
 
 size_t part_bytes(const MacPlan& p, int prec) {
     size_t b = p.h_bytes + p.x_bytes + 2 * p.partial_bytes + (size_t)p.n_src * p.B * sizeof(float);
-    if (prec != PREC_FP32) b += ((size_t)p.n_dst * p.R + (size_t)p.R) * sizeof(float);
+    if (prec != PREC_FP32) b += ((size_t)p.n_dst * p.R + (size_t)p.R + 8) * sizeof(float);
     return b;
 }
 
@@ -240,6 +278,7 @@ struct conv_engine {
     float *h_in = nullptr, *h_out = nullptr, *h_e = nullptr;
     int* h_err = nullptr;
     int* d_err = nullptr;
+    TileOverride tiling;  // applies to the synthesis convolution
     Part syn, fb;
     long long nblk = 0;
     double guard = 0.0;
@@ -282,8 +321,8 @@ void part_free(conv_engine* e, Part& P) {
     dev_free(e, &P.partial[0], p.partial_bytes);
     dev_free(e, &P.partial[1], p.partial_bytes);
     dev_free(e, &P.win, (size_t)P.n_src * e->B * sizeof(float));
-    if (P.sH) dev_free(e, &P.sH, (size_t)p.n_dst * p.R * sizeof(float));
-    if (P.sX) dev_free(e, &P.sX, (size_t)p.R * sizeof(float));
+    if (P.sH) dev_free(e, &P.sH, ((size_t)p.n_dst * p.R + 4) * sizeof(float));
+    if (P.sX) dev_free(e, &P.sX, ((size_t)p.R + 4) * sizeof(float));
     P.allocated = false;
     P.ready = false;
 }
@@ -297,7 +336,8 @@ int check_fits(size_t need) {
     return CONV_OK;
 }
 
-int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps) {
+int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps,
+               const TileOverride& o = TileOverride()) {
     part_free(e, P);
     P.n_src = n_src;
     P.n_dst = n_dst;
@@ -306,7 +346,7 @@ int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps) {
     if (K <= 0 || (long long)n_src * K > 0x7fffffffLL / 2)
         return set_err(CONV_E_INVAL, "taps %lld gives too many partitions", taps);
     P.K = (int)K;
-    P.plan = plan_mac(e->prec, e->B, n_src, n_dst, P.K, e->num_sms, n_src);
+    P.plan = plan_mac(e->prec, e->B, n_src, n_dst, P.K, e->num_sms, n_src, o);
     const MacPlan& p = P.plan;
     std::string why;
     if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());
@@ -321,8 +361,10 @@ int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps) {
     if (!P.ev_tail) CK(cudaEventCreateWithFlags(&P.ev_tail, cudaEventDisableTiming));
     if ((rc = dev_alloc(e, &P.win, (size_t)n_src * e->B * sizeof(float)))) return rc;
     if (e->prec != PREC_FP32) {
-        if ((rc = dev_alloc(e, &P.sH, (size_t)p.n_dst * p.R * sizeof(float)))) return rc;
-        if ((rc = dev_alloc(e, &P.sX, (size_t)p.R * sizeof(float)))) return rc;
+        // +4 floats: scale runs are read widened to 16-byte boundaries
+        if ((rc = dev_alloc(e, &P.sH, ((size_t)p.n_dst * p.R + 4) * sizeof(float)))) return rc;
+        if ((rc = dev_alloc(e, &P.sX, ((size_t)p.R + 4) * sizeof(float)))) return rc;
+        CK(cudaMemsetAsync(P.sH, 0, ((size_t)p.n_dst * p.R + 4) * sizeof(float), e->stream));
     }
     CK(cudaMemsetAsync(P.H, 0, p.h_bytes, e->stream));
     return CONV_OK;
@@ -332,7 +374,7 @@ int part_reset(conv_engine* e, Part& P) {
     if (!P.allocated) return CONV_OK;
     CK(cudaMemsetAsync(P.X, 0, P.plan.x_bytes, e->stream));
     CK(cudaMemsetAsync(P.win, 0, (size_t)P.n_src * e->B * sizeof(float), e->stream));
-    if (P.sX) CK(cudaMemsetAsync(P.sX, 0, (size_t)P.plan.R * sizeof(float), e->stream));
+    if (P.sX) CK(cudaMemsetAsync(P.sX, 0, ((size_t)P.plan.R + 4) * sizeof(float), e->stream));
     CK(cudaMemsetAsync(P.partial[0], 0, P.plan.partial_bytes, e->stream));
     CK(cudaMemsetAsync(P.partial[1], 0, P.plan.partial_bytes, e->stream));
     CK(cudaEventRecord(P.ev_tail, e->stream));  // block 0's tail: zero partials
@@ -422,6 +464,8 @@ int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool ti
     a.slot0 = slot0_for(blk, P.K);
     a.stage_bytes = p.stage_bytes;
     a.xoff = p.xoff;
+    a.soff = p.soff;
+    a.sxoff = p.sxoff;
     a.err = e->d_err;
     const bool rec = timed && e->prof && e->ev_used < e->ev0.size();
     if (rec) CK(cudaEventRecord(e->ev0[e->ev_used], s));
@@ -563,12 +607,13 @@ int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long 
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, e->dev));
     e->num_sms = prop.multiProcessorCount;
-    CK(prepare_kernels(200 * 1024));
+    CK(prepare_kernels(MAC_SMEM_LIMIT));
     int prio_low = 0, prio_high = 0;
     CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
     CK(cudaStreamCreateWithPriority(&e->stream, cudaStreamNonBlocking, prio_high));
     CK(cudaStreamCreateWithPriority(&e->bg, cudaStreamNonBlocking, prio_low));
-    CK(cudaEventCreateWithFlags(&e->ev_done, cudaEventDisableTiming | cudaEventBlockingSync));
+    // spin-wait on completion: a blocking wait would add the host's wake-up latency to every block
+    CK(cudaEventCreateWithFlags(&e->ev_done, cudaEventDisableTiming));
     // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once to FP32
     std::vector<float2> tw(2 * (size_t)block);
     const double pi = 3.14159265358979323846264338327950288;
@@ -621,8 +666,37 @@ int conv_set_precision(conv_engine* e, int mode) {
     if (mode == e->prec) return CONV_OK;
     DeviceGuard g(e->dev);
     e->prec = mode;
-    int rc = part_alloc(e, e->syn, e->n_in, e->n_out, e->taps);
+    int rc = part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling);
     if (rc) return rc;
+    return engine_reset(e);
+}
+
+int conv_set_tiling(conv_engine* e, int bin_tile, int stages, int stage_kib, int splits) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    if (e->syn.ready || e->fb.allocated)
+        return set_err(CONV_E_STATE, "tiling must be set before conv_set_filters / afc_set_paths");
+    if (bin_tile < 0 || (bin_tile && (bin_tile < 16 || bin_tile > 256 || (bin_tile & (bin_tile - 1)))))
+        return set_err(CONV_E_INVAL, "bin_tile must be 0 or a power of two in [16, 256]");
+    if (stages < 0 || (stages && (stages < 2 || stages > MAX_STAGES)))
+        return set_err(CONV_E_INVAL, "stages must be 0 or in [2, %d]", MAX_STAGES);
+    if (stage_kib < 0 || stage_kib > 96) return set_err(CONV_E_INVAL, "stage_kib must be in [0, 96]");
+    if (splits < 0) return set_err(CONV_E_INVAL, "splits must be >= 0");
+    DeviceGuard g(e->dev);
+    TileOverride o;
+    o.bin_tile = bin_tile;
+    o.stages = stages;
+    o.stage_kib = stage_kib;
+    o.splits = splits;
+    const TileOverride old = e->tiling;
+    e->tiling = o;
+    int rc = part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling);
+    if (rc) {
+        e->tiling = old;
+        const std::string msg = g_err;
+        if (part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling) == CONV_OK) engine_reset(e);
+        g_err = msg;
+        return rc;
+    }
     return engine_reset(e);
 }
 
@@ -758,6 +832,9 @@ int conv_get_info(const conv_engine* e, conv_info* out) {
     out->mac_ctas = p.ctas;
     out->mac_splits = p.S;
     out->mac_smem = (long long)p.smem;
+    out->mac_bin_tile = p.BT;
+    out->mac_stages = p.nstage;
+    out->mac_stage_bytes = p.stage_bytes;
     out->device_bytes = (long long)e->dev_bytes;
     out->kernels_per_block = 3;
     out->kernels_per_afc_block = 6;
@@ -798,13 +875,21 @@ int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches)
     return CONV_OK;
 }
 
-int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms) {
+int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms, int bin_tile,
+                    int stages, int stage_kib, int splits) {
     if (precision < CONV_FP32 || precision > CONV_BF16 || block < 16 || block > 4096 || (block & (block - 1)) ||
-        n_src < 1 || n_dst < 1 || taps < 1 || num_sms < 1)
+        n_src < 1 || n_dst < 1 || taps < 1 || num_sms < 1 || bin_tile < 0 || stages < 0 || stage_kib < 0 ||
+        splits < 0 || (bin_tile && (bin_tile < 16 || bin_tile > 256 || (bin_tile & (bin_tile - 1)))) ||
+        (stages && (stages < 2 || stages > MAX_STAGES)) || stage_kib > 96)
         return set_err(CONV_E_INVAL, "invalid plan arguments");
     const long long K = (taps + block - 1) / block;
     if ((long long)n_src * K > 0x7fffffffLL / 2) return set_err(CONV_E_INVAL, "too many partitions");
-    const MacPlan p = plan_mac(precision, block, n_src, n_dst, (int)K, num_sms, n_src);
+    TileOverride o;
+    o.bin_tile = bin_tile;
+    o.stages = stages;
+    o.stage_kib = stage_kib;
+    o.splits = splits;
+    const MacPlan p = plan_mac(precision, block, n_src, n_dst, (int)K, num_sms, n_src, o);
     std::string why;
     if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());
     return CONV_OK;

@@ -156,7 +156,7 @@ __global__ void k_filter_r2c(const FilterArgs a) {
     const int LTt = min(a.LT, a.n_dst - l0), ll = l - l0;
     const float scale =
         store_spectrum<PREC>(Xs, B, a.H, FilterIndex{a.BT, a.n_dst, l0, R, r, LTt, ll}, red);
-    if (PREC != PREC_FP32 && tid == 0) a.sH[(size_t)l * R + r] = scale;
+    if (PREC != PREC_FP32 && tid == 0) a.sH[(size_t)l0 * R + (size_t)r * LTt + ll] = scale;
 }
 
 // ----------------------------------------------------------- FDL MAC
@@ -212,12 +212,34 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
         griddep_launch_dependents();
         const uint64_t pol_stream = policy_evict_first();
         const uint64_t pol_keep = policy_evict_last();
+        // Reduced precision: the stage's per-partition scales travel with it.
+        // Their runs are widened to 16-byte boundaries (the buffers carry 16
+        // bytes of padding); consumers index from the run's first element.
+        auto scale_runs = [&](int ra, int nr, int start, int run, int (&w)[3][2]) {
+            const int fo = l0 * R + ra * LTt;  // sH tile rows [r][LTt]
+            w[0][0] = fo & ~3;
+            w[0][1] = (fo + nr * LTt + 3) & ~3;
+            w[1][0] = start & ~3;  // sX ring rows, first run
+            w[1][1] = (start + run + 3) & ~3;
+            w[2][0] = 0;  // wrapped run
+            w[2][1] = run < nr ? ((nr - run + 3) & ~3) : 0;
+        };
         auto issue_h = [&](int it) {
             const int st = it % a.nstage;
             const int ra = r0 + it * a.RS, rb = min(ra + a.RS, r1), nr = rb - ra;
             unsigned char* sh = stages + (size_t)st * a.stage_bytes;
-            mbar_arrive_expect_tx(&full[st], (uint32_t)((size_t)nr * (hr_bytes + hrow)));
+            size_t tx = (size_t)nr * (hr_bytes + hrow);
+            int w[3][2];
+            if (PREC != PREC_FP32) {
+                int start = ring0 + ra;
+                if (start >= R) start -= R;
+                scale_runs(ra, nr, start, min(nr, R - start), w);
+                tx += (size_t)4 * ((w[0][1] - w[0][0]) + (w[1][1] - w[1][0]) + (w[2][1] - w[2][0]));
+            }
+            mbar_arrive_expect_tx(&full[st], (uint32_t)tx);
             bulk_g2s(sh, Hb + (size_t)ra * hr_bytes, (uint32_t)((size_t)nr * hr_bytes), &full[st], pol_stream);
+            if (PREC != PREC_FP32)
+                bulk_g2s(sh + a.soff, a.sH + w[0][0], (uint32_t)(4 * (w[0][1] - w[0][0])), &full[st], pol_keep);
         };
         auto issue_x = [&](int it) {
             const int st = it % a.nstage;
@@ -229,6 +251,14 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
             bulk_g2s(sx, Xb + (size_t)start * hrow, (uint32_t)(run * hrow), &full[st], pol_keep);
             if (run < nr)
                 bulk_g2s(sx + (size_t)run * hrow, Xb, (uint32_t)((nr - run) * hrow), &full[st], pol_keep);
+            if (PREC != PREC_FP32) {
+                int w[3][2];
+                scale_runs(ra, nr, start, run, w);
+                unsigned char* ss = stages + (size_t)st * a.stage_bytes + a.sxoff;
+                const uint32_t b1 = 4 * (w[1][1] - w[1][0]);
+                bulk_g2s(ss, a.sX + w[1][0], b1, &full[st], pol_keep);
+                if (w[2][1] > 0) bulk_g2s(ss + b1, a.sX, (uint32_t)(4 * w[2][1]), &full[st], pol_keep);
+            }
         };
         // The filter spectra are constant: stream the first stages while the
         // previous kernel (the pack of this block) is still running, then wait for
@@ -283,15 +313,25 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
         const int ra = r0 + it * a.RS, nr = min(a.RS, r1 - ra);
         const unsigned char* sh = stages + (size_t)st * a.stage_bytes;
         const unsigned char* sx = sh + a.xoff;
+        // reduced precision: where this stage's scales start in shared memory
+        const float* ssh = reinterpret_cast<const float*>(sh + a.soff);
+        const float* ssx = reinterpret_cast<const float*>(sh + a.sxoff);
+        int sh0 = 0, sx0 = 0, sx2 = 0, xrun = nr;
+        if (PREC != PREC_FP32) {
+            const int fo = l0 * R + ra * LTt;
+            sh0 = fo - (fo & ~3);
+            int start = ring0 + ra;
+            if (start >= R) start -= R;
+            xrun = min(nr, R - start);
+            sx0 = start - (start & ~3);
+            // the wrapped second run (ring rows 0..) lands after the first run's padded span
+            sx2 = (((start + xrun + 3) & ~3) - (start & ~3)) - xrun;
+        }
         for (int j = rl; j < nr; j += a.NRL) {
             float2 xv[VEC];
             St::load16(sx + (size_t)j * hrow + (size_t)kv * 16, xv);
             float sxs = 1.0f;
-            if (PREC != PREC_FP32) {
-                int row = ring0 + ra + j;
-                if (row >= R) row -= R;
-                sxs = __ldg(a.sX + row);
-            }
+            if (PREC != PREC_FP32) sxs = j < xrun ? ssx[sx0 + j] : ssx[sx2 + j];
 #pragma unroll
             for (int i = 0; i < LPT; ++i) {
                 const int ll = lg + i * a.NLG;
@@ -307,7 +347,7 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
                                 cmac(acc[i][v], hv[v], xv[v]);
                         }
                     } else {
-                        const float sc = sxs * __ldg(a.sH + (size_t)(l0 + ll) * R + ra + j);
+                        const float sc = sxs * ssh[sh0 + j * LTt + ll];
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
                             float2 t = make_float2(0.0f, 0.0f);
@@ -411,9 +451,9 @@ __global__ void k_out_c2r(const OutArgs a) {
                     rmac2(t, h, x);
                 else
                     cmac(t, h, x);
-                const float sc = PREC == PREC_FP32
-                                     ? 1.0f
-                                     : __ldg(a.sH + (size_t)l * a.R + q) * __ldg(a.sX + (size_t)a.slot0 * a.n_src + q);
+                const float sc = PREC == PREC_FP32 ? 1.0f
+                                                   : __ldg(a.sH + (size_t)l0 * a.R + (size_t)q * LTt + ll) *
+                                                         __ldg(a.sX + (size_t)a.slot0 * a.n_src + q);
                 hd.x = fmaf(sc, t.x, hd.x);
                 hd.y = fmaf(sc, t.y, hd.y);
             }

@@ -34,6 +34,9 @@ constexpr int MAC_CONSUMER_WARPS = 8;
 constexpr int MAC_THREADS = (MAC_CONSUMER_WARPS + 1) * 32;  // + one producer warp
 constexpr int MAC_HDR_BYTES = 1024;                          // mbarriers + flags
 constexpr int MAX_STAGES = 8;
+constexpr size_t MAC_SMEM_LIMIT = 227 * 1024;  // dynamic shared memory the MAC may use (sm_100 family maximum)
+constexpr size_t SM_SMEM_BYTES = 228 * 1024;   // shared memory per SM
+constexpr size_t CTA_SMEM_RESERVED = 1024;     // per-CTA system reservation
 
 // Tiling of one FDL MAC (one partitioned convolution with n_src inputs, n_dst
 // outputs and K partitions) over the reduction range [r_begin, R).  Spectra of
@@ -52,6 +55,7 @@ struct MacPlan {
     int nstage;    // pipeline depth
     int S;         // partition splits per tile (0: empty range, no MAC launch)
     unsigned stage_bytes, xoff;
+    unsigned soff, sxoff;  // reduced precision: filter / delay-line scale parts of a stage
     size_t smem;   // dynamic shared memory per CTA
     int ctas;
     size_t h_bytes, x_bytes, partial_bytes;
@@ -60,14 +64,14 @@ struct MacPlan {
 struct MacArgs {
     const void* H;    // filter spectra [kt][l0..][r][LTt][BT]
     const void* X;    // FDL ring [kt][slot][q][BT]
-    const float* sH;  // [n_dst][R] per-partition scales (reduced precision), else null
+    const float* sH;  // [lt tile][r][LTt] per-partition scales (reduced precision), else null
     const float* sX;  // [K][n_src] per-slot scales (reduced precision), else null
     float2* partial;  // [S][n_dst][B]
     int B, BT, n_kt, n_dst, LT, n_lt, n_src, K, S, RS, nstage;
     int r_begin;
     int kthreads, NLG, NRL;
     int slot0;  // ring slot of partition 0 for the block this MAC serves
-    unsigned stage_bytes, xoff;
+    unsigned stage_bytes, xoff, soff, sxoff;
     int* err;   // device-visible error word (host-mapped), or null
 };
 
@@ -88,7 +92,7 @@ struct FilterArgs {
     long long taps;
     int n_dst, n_src, K, B, log2B, BT, LT;
     void* H;    // tiled spectra
-    float* sH;  // [n_dst][R] scales (reduced precision), else null
+    float* sH;  // [lt tile][r][LTt] scales (reduced precision), else null
     const float2* tw;
 };
 

@@ -79,7 +79,7 @@ int setup_device(int dev, DeviceSlot** out) {
             }
         e = cudaMemcpyToSymbol(g_noalloc_tw, host, sizeof(host));
         if (e != cudaSuccess) return fail(CONV_E_CUDA, "twiddle upload", e);
-        e = prepare_kernels(200 * 1024);
+        e = prepare_kernels(MAC_SMEM_LIMIT);
         if (e != cudaSuccess) return fail(CONV_E_CUDA, "kernel attributes", e);
         d.ready = true;
     }

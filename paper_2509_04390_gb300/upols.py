@@ -57,6 +57,9 @@ class conv_info(ctypes.Structure):
             "device_bytes",
             "kernels_per_block",
             "kernels_per_afc_block",
+            "mac_bin_tile",
+            "mac_stages",
+            "mac_stage_bytes",
         )
     ]
 
@@ -88,6 +91,7 @@ def load():
         "conv_create": (vp, [d, i, i, i, ll]),
         "conv_set_precision": (i, [vp, i]),
         "conv_set_filters": (i, [vp, vp]),
+        "conv_set_tiling": (i, [vp, i, i, i, i]),
         "afc_set_paths": (i, [vp, vp, ll]),
         "conv_process_block": (i, [vp, vp, vp]),
         "conv_process_block_async": (i, [vp, vp, vp, vp]),
@@ -99,7 +103,7 @@ def load():
         "conv_get_info": (i, [vp, ctypes.POINTER(conv_info)]),
         "conv_profile_enable": (i, [vp, i]),
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
-        "conv_plan_check": (i, [i, i, i, i, ll, i]),
+        "conv_plan_check": (i, [i, i, i, i, ll, i, i, i, i, i]),
         "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
         "conv_destroy": (None, [vp]),
         "conv_last_error": (ctypes.c_char_p, []),
@@ -168,6 +172,10 @@ def conv_set_precision(h, mode):
     return _check(load().conv_set_precision(h, int(mode)))
 
 
+def conv_set_tiling(h, bin_tile=0, stages=0, stage_kib=0, splits=0):
+    return _check(load().conv_set_tiling(h, int(bin_tile), int(stages), int(stage_kib), int(splits)))
+
+
 def conv_set_filters(h, filters: np.ndarray):
     info = conv_get_info(h)
     return _check(load().conv_set_filters(h, _host_ptr(filters, (info["n_out"], info["n_in"], info["taps"]))))
@@ -231,9 +239,14 @@ def conv_profile_read(h):
     return ms.value, n.value
 
 
-def conv_plan_check(precision, block, n_src, n_dst, taps, num_sms=152):
+def conv_plan_check(precision, block, n_src, n_dst, taps, num_sms=152, bin_tile=0, stages=0, stage_kib=0, splits=0):
     precision = PRECISIONS.get(precision, precision)
-    return _check(load().conv_plan_check(int(precision), int(block), int(n_src), int(n_dst), int(taps), int(num_sms)))
+    return _check(
+        load().conv_plan_check(
+            int(precision), int(block), int(n_src), int(n_dst), int(taps), int(num_sms), int(bin_tile), int(stages),
+            int(stage_kib), int(splits),
+        )
+    )
 
 
 def conv_fdl_mac_noalloc(d_H, d_X, block, n_in, n_out, K, slot0, d_y, stream=None):

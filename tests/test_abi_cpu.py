@@ -101,3 +101,19 @@ def test_mac_plan_addresses_stay_in_bounds(lib, precision):
         for n_src, n_dst, taps in shapes:
             for sms in (152, 148, 8):
                 upols.conv_plan_check(precision, B, n_src, n_dst, taps, sms)
+
+
+def test_tiling_overrides_stay_in_bounds(lib):
+    # the autotuner's candidate space at paper scale and a small shape
+    for precision in ("fp32", "fp16"):
+        for B in (64, 128, 256, 512):
+            for n_src, n_dst, taps in ((4, 16, 384000), (3, 20, 1000)):
+                for bt in (16, 32, 64, 128, 256):
+                    for stages, kib in ((2, 64), (3, 32), (4, 48), (5, 32), (8, 16), (8, 24)):
+                        for splits in (0, 1, 9, 38, 1000000):
+                            upols.conv_plan_check(precision, B, n_src, n_dst, taps, 152, bt, stages, kib, splits)
+
+
+def test_tiling_override_arguments_are_validated(lib):
+    with pytest.raises(upols.ConvError):
+        upols.conv_plan_check("fp32", 256, 4, 16, 384000, 152, 24, 0, 0, 0)  # not a power of two
