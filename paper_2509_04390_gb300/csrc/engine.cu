@@ -67,15 +67,22 @@ inline int pow2_ceil(int v) {
     return r;
 }
 
-// Tiling of one FDL MAC.  Chooses bin/output tiles, the consumer thread layout,
-// the pipeline stage size and depth, and the number of partition splits so
-// that the grid covers every SM about once (1 CTA/SM at these shared-memory
-// sizes) while each CTA still streams at least a few stages.
 // Tiling fields a caller (the autotuner) may fix; 0 leaves a field to the planner.
 struct TileOverride {
-    int bin_tile = 0, stages = 0, stage_kib = 0, splits = 0;
+    int bin_tile = 0, stages = 0, stage_kib = 0, splits = 0, warps = 0;
 };
 
+inline bool is_pow2(size_t v) { return v && !(v & (v - 1)); }
+inline size_t pow2_floor(size_t v) {
+    size_t r = 1;
+    while (r * 2 <= v) r *= 2;
+    return r;
+}
+
+// Tiling of one FDL MAC.  Chooses bin/output tiles, the consumer thread layout,
+// the pipeline stage size and depth, and the number of partition splits so
+// that the grid covers every SM once (no second wave) while each CTA still
+// streams at least a few stages.
 MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int r_begin,
                  const TileOverride& o = TileOverride()) {
     MacPlan p{};
@@ -89,6 +96,7 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     p.es = prec == PREC_FP32 ? 8 : 4;
     p.VEC = 16 / p.es;
     p.LPT = prec == PREC_FP32 ? 8 : 4;
+    p.nw = o.warps ? o.warps : MAC_CONSUMER_WARPS;
     p.LT = std::min(n_dst, 16);
     p.n_lt = (n_dst + p.LT - 1) / p.LT;
     // Bin tiles: enough (bin tile x output tile) pairs that ~16-20 partition
@@ -102,47 +110,58 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     if (p.BT > B) p.BT = B;
     p.n_kt = B / p.BT;
     p.kthreads = p.BT / p.VEC;
-    const int rest = (MAC_CONSUMER_WARPS * 32) / p.kthreads;
+    const int rest = (p.nw * 32) / p.kthreads;
     p.NLG = pow2_ceil((p.LT + p.LPT - 1) / p.LPT);
     if (p.NLG > rest) p.NLG = rest;
     p.NRL = rest / p.NLG;
-    const size_t per_r = (size_t)(p.LT + 1) * p.BT * p.es;
-    // ~64 KB stages: large 1-D bulk copies stream best (measured against 32 KB x 5)
+    // Stage pitch: filter copies of a power-of-two size (64 KiB by default),
+    // which, with 64 KiB-aligned tiles and a global stage grid, keeps every
+    // copy aligned to its size across the HBM channel interleave (measured:
+    // 32/64 KiB copies stream faster than 40-60 KiB ones).
+    const size_t per_r_h = (size_t)p.LT * p.BT * p.es;
+    const size_t per_r = per_r_h + (size_t)p.BT * p.es;
     const size_t stage_target = o.stage_kib ? (size_t)o.stage_kib * 1024 : 65536;
-    int rs = (int)std::max<size_t>(1, (stage_target + per_r / 2) / per_r);
-    p.RS = std::max(1, std::min(rs, std::max(1, Rt)));
+    int rs;
+    if (is_pow2(per_r_h) && per_r_h <= stage_target)
+        rs = (int)(pow2_floor(stage_target) / per_r_h);
+    else
+        rs = (int)std::max<size_t>(1, (stage_target + per_r / 2) / per_r);
+    p.RS = std::max(1, std::min(rs, std::max(1, p.R)));
     const size_t budget = MAC_SMEM_LIMIT - MAC_HDR_BYTES;
     const bool scaled = prec != PREC_FP32;
     // scale parts: a run widened to 16-byte boundaries at both ends (+ a wrapped second run for sX)
-    auto sh_part = [&](int RS) { return scaled ? align_up(((size_t)RS * p.LT + 8) * 4, 128) : 0; };
+    auto sh_part = [&](int RS) { return scaled ? align_up(((size_t)RS + 8) * 4, 128) : 0; };
     auto sx_part = [&](int RS) { return scaled ? align_up(((size_t)RS + 12) * 4, 128) : 0; };
     auto stage_size = [&](int RS) {
         return align_up((size_t)RS * p.LT * p.BT * p.es, 128) + align_up((size_t)RS * p.BT * p.es, 128) +
                sh_part(RS) + sx_part(RS);
     };
-    while (p.RS > 1 && 2 * stage_size(p.RS) > budget) --p.RS;  // at least double buffering
+    while (p.RS > 1 && 2 * stage_size(p.RS) > budget) p.RS = is_pow2(per_r_h) ? p.RS / 2 : p.RS - 1;
     const size_t hpart = align_up((size_t)p.RS * p.LT * p.BT * p.es, 128);
     p.xoff = (unsigned)hpart;
     p.soff = (unsigned)(hpart + align_up((size_t)p.RS * p.BT * p.es, 128));
     p.sxoff = (unsigned)(p.soff + sh_part(p.RS));
     p.stage_bytes = (unsigned)stage_size(p.RS);
     const int fit = (int)std::max<size_t>(2, budget / p.stage_bytes);
-    p.nstage = std::min(MAX_STAGES, fit);
+    // two large stages measured best; deeper rings only added bytes in flight
+    p.nstage = std::min(2, fit);
     if (o.stages) p.nstage = std::max(2, std::min(o.stages, fit));
     // scratch for combining r-lanes reuses (and if needed extends) the stage ring
     const size_t red = (size_t)(p.NRL - 1) * p.LT * p.BT * sizeof(float2);
     p.smem = MAC_HDR_BYTES + std::max((size_t)p.nstage * p.stage_bytes, align_up(red, 128));
     const int tiles = p.n_kt * p.n_lt;
-    const size_t tile_bytes = (size_t)Rt * p.LT * p.BT * p.es;
-    const int by_work = (int)std::max<size_t>(1, tile_bytes / (2 * (size_t)p.stage_bytes));
+    const int gt = Rt > 0 ? (p.R + p.RS - 1) / p.RS - r_begin / p.RS : 0;  // stages on the grid
+    const int by_work = std::max(1, gt / 2);
     // never a second wave: the grid fits the SMs at the occupancy shared memory allows
     const int per_sm = (int)std::max<size_t>(1, SM_SMEM_BYTES / (p.smem + CTA_SMEM_RESERVED));
     int S = std::max(1, num_sms * per_sm / tiles);
-    S = std::min(S, std::min(by_work, Rt));
-    if (o.splits) S = std::min(o.splits, Rt);
+    S = std::min(S, by_work);
+    if (o.splits) S = o.splits;
+    S = std::min(S, gt);
     p.S = Rt > 0 ? std::max(1, S) : 0;
     p.ctas = tiles * p.S;
-    p.h_bytes = (size_t)n_dst * p.R * B * p.es;
+    p.tile_elems = align_up((size_t)p.R * p.LT * p.BT * p.es, 65536) / p.es;
+    p.h_bytes = (size_t)tiles * p.tile_elems * p.es;
     p.x_bytes = (size_t)p.R * B * p.es;
     p.partial_bytes = std::max<size_t>(16, (size_t)p.S * n_dst * B * sizeof(float2));
     return p;
@@ -165,11 +184,15 @@ int check_plan(const MacPlan& p, std::string* why) {
     if (Rt == 0) return p.S == 0 ? 0 : bad("splits over an empty range");
     if (p.nstage < 1 || p.nstage > MAX_STAGES) return bad("stage count");
     if (p.smem > MAC_SMEM_LIMIT) return bad("shared memory above the kernel's limit");
-    if (p.kthreads * p.VEC != p.BT || p.kthreads > MAC_CONSUMER_WARPS * 32) return bad("bin threads");
-    const int rest = (MAC_CONSUMER_WARPS * 32) / p.kthreads;
-    if (p.kthreads * rest != MAC_CONSUMER_WARPS * 32 || p.NLG * p.NRL != rest) return bad("thread layout");
+    if (p.nw != 8 && p.nw != 16) return bad("consumer warps");
+    if (p.kthreads * p.VEC != p.BT || p.kthreads > p.nw * 32) return bad("bin threads");
+    const int rest = (p.nw * 32) / p.kthreads;
+    if (p.kthreads * rest != p.nw * 32 || p.NLG * p.NRL != rest) return bad("thread layout");
     if ((p.LT + p.NLG - 1) / p.NLG > p.LPT) return bad("outputs per thread above LPT");
-    if (p.S < 1 || p.S > Rt) return bad("split count");
+    const int gb = p.r_begin / p.RS, gt = (p.R + p.RS - 1) / p.RS - gb;
+    if (p.S < 1 || p.S > gt) return bad("split count");
+    if ((size_t)p.n_kt * p.n_lt * p.tile_elems * p.es > p.h_bytes) return bad("tile pitch");
+    if ((size_t)p.R * p.LT * p.BT > p.tile_elems) return bad("tile pitch below a tile");
     if (p.B % p.BT) return bad("bin tile");
     const size_t hrow = (size_t)p.BT * p.es;
     if (hrow % 16) return bad("row not a multiple of 16 bytes");
@@ -182,23 +205,25 @@ int check_plan(const MacPlan& p, std::string* why) {
         if (kt >= p.n_kt) return bad("tile index");
         const int l0 = lt * p.LT, LTt = std::min(p.LT, p.n_dst - l0);
         if (LTt < 1) return bad("empty output tile");
-        const int r0 = p.r_begin + (int)((long long)split * Rt / p.S);
-        const int r1 = p.r_begin + (int)((long long)(split + 1) * Rt / p.S);
-        if (r1 <= r0) return bad("empty split");
+        const int g0 = gb + (int)((long long)split * gt / p.S);
+        const int g1 = gb + (int)((long long)(split + 1) * gt / p.S);
+        if (g1 <= g0) return bad("empty split");
         const size_t hr = (size_t)LTt * hrow;
-        const size_t hb = ((size_t)kt * p.n_dst + l0) * (size_t)p.R * hrow;
+        const size_t hb = (size_t)tile * p.tile_elems * p.es;
         const size_t xb = (size_t)kt * p.R * hrow;
-        for (int ra = r0; ra < r1; ra += p.RS) {
-            const int rb = std::min(ra + p.RS, r1), nr = rb - ra;
+        for (int g = g0; g < g1; ++g) {
+            const int ra = std::max(p.r_begin, g * p.RS), rb = std::min(p.R, (g + 1) * p.RS), nr = rb - ra;
+            if (nr < 1) return bad("empty stage");
             const size_t tx = (size_t)nr * (hr + hrow);
             if (tx >= (1u << 20)) return bad("transaction bytes");
+            if ((size_t)rb * hr > (size_t)p.tile_elems * p.es) return bad("filter copy past its tile");
             if (hb + (size_t)rb * hr > p.h_bytes) return bad("filter copy past the spectra");
             if ((size_t)nr * hr > p.xoff) return bad("filter copy past its stage part");
             if (p.xoff + (size_t)nr * hrow > p.stage_bytes) return bad("delay-line copy past its stage");
             if (p.es == 4) {
-                const int fo = l0 * p.R + ra * LTt;
-                const int a0 = fo & ~3, a1 = (fo + nr * LTt + 3) & ~3;
-                if ((size_t)a1 > (size_t)p.n_dst * p.R + 4) return bad("filter scales past their buffer");
+                const int fo = lt * p.R + ra;
+                const int a0 = fo & ~3, a1 = (fo + nr + 3) & ~3;
+                if ((size_t)a1 > (size_t)p.n_lt * p.R + 4) return bad("filter scales past their buffer");
                 if (p.soff + 4 * (size_t)(a1 - a0) > p.sxoff) return bad("filter scales past their stage part");
                 for (int slot0 = 0; slot0 < p.K; slot0 += std::max(1, p.K / 7)) {
                     const int start = (slot0 * p.n_src + ra) % p.R;
@@ -244,7 +269,7 @@ struct Part {
 
 size_t part_bytes(const MacPlan& p, int prec) {
     size_t b = p.h_bytes + p.x_bytes + 2 * p.partial_bytes + (size_t)p.n_src * p.B * sizeof(float);
-    if (prec != PREC_FP32) b += ((size_t)p.n_dst * p.R + (size_t)p.R + 8) * sizeof(float);
+    if (prec != PREC_FP32) b += ((size_t)p.n_lt * p.R + (size_t)p.R + 8) * sizeof(float);
     return b;
 }
 
@@ -321,7 +346,7 @@ void part_free(conv_engine* e, Part& P) {
     dev_free(e, &P.partial[0], p.partial_bytes);
     dev_free(e, &P.partial[1], p.partial_bytes);
     dev_free(e, &P.win, (size_t)P.n_src * e->B * sizeof(float));
-    if (P.sH) dev_free(e, &P.sH, ((size_t)p.n_dst * p.R + 4) * sizeof(float));
+    if (P.sH) dev_free(e, &P.sH, ((size_t)p.n_lt * p.R + 4) * sizeof(float));
     if (P.sX) dev_free(e, &P.sX, ((size_t)p.R + 4) * sizeof(float));
     P.allocated = false;
     P.ready = false;
@@ -362,9 +387,9 @@ int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps,
     if ((rc = dev_alloc(e, &P.win, (size_t)n_src * e->B * sizeof(float)))) return rc;
     if (e->prec != PREC_FP32) {
         // +4 floats: scale runs are read widened to 16-byte boundaries
-        if ((rc = dev_alloc(e, &P.sH, ((size_t)p.n_dst * p.R + 4) * sizeof(float)))) return rc;
+        if ((rc = dev_alloc(e, &P.sH, ((size_t)p.n_lt * p.R + 4) * sizeof(float)))) return rc;
         if ((rc = dev_alloc(e, &P.sX, ((size_t)p.R + 4) * sizeof(float)))) return rc;
-        CK(cudaMemsetAsync(P.sH, 0, ((size_t)p.n_dst * p.R + 4) * sizeof(float), e->stream));
+        CK(cudaMemsetAsync(P.sH, 0, ((size_t)p.n_lt * p.R + 4) * sizeof(float), e->stream));
     }
     CK(cudaMemsetAsync(P.H, 0, p.h_bytes, e->stream));
     return CONV_OK;
@@ -384,9 +409,15 @@ int part_reset(conv_engine* e, Part& P) {
 // Upload time-domain filters [n_dst][n_src][taps] and build their spectra.
 int part_set_filters(conv_engine* e, Part& P, const float* h) {
     const size_t bytes = (size_t)P.n_dst * P.n_src * (size_t)P.taps * sizeof(float);
+    const size_t mbytes = e->prec != PREC_FP32 ? (size_t)P.n_dst * P.plan.R * sizeof(float) : 0;
     float* d_h = nullptr;
+    float* d_max = nullptr;
     int rc = dev_alloc(e, &d_h, bytes);
     if (rc) return rc;
+    if (mbytes && (rc = dev_alloc(e, &d_max, mbytes))) {
+        dev_free(e, &d_h, bytes);
+        return rc;
+    }
     cudaError_t r = cudaMemcpyAsync(d_h, h, bytes, cudaMemcpyHostToDevice, e->stream);
     FilterArgs a{};
     a.h = d_h;
@@ -400,10 +431,21 @@ int part_set_filters(conv_engine* e, Part& P, const float* h) {
     a.LT = P.plan.LT;
     a.H = P.H;
     a.sH = P.sH;
+    a.maxabs = d_max;
+    a.tile_elems = P.plan.tile_elems;
     a.tw = e->tw;
+    if (e->prec != PREC_FP32) {
+        // pass 0: per-sub-filter maxima; one scale per (output tile, r); pass 1: store
+        a.pass = 0;
+        if (r == cudaSuccess) r = launch_filter_r2c(e->prec, a, e->stream);
+        if (r == cudaSuccess)
+            r = launch_tile_scales(e->prec, d_max, P.sH, P.n_dst, P.plan.R, P.plan.LT, e->stream);
+    }
+    a.pass = 1;
     if (r == cudaSuccess) r = launch_filter_r2c(e->prec, a, e->stream);
     if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
     dev_free(e, &d_h, bytes);
+    if (d_max) dev_free(e, &d_max, mbytes);
     if (r != cudaSuccess) return set_err(CONV_E_CUDA, "filter spectra: %s", cudaGetErrorString(r));
     P.ready = true;
     return CONV_OK;
@@ -466,6 +508,7 @@ int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool ti
     a.xoff = p.xoff;
     a.soff = p.soff;
     a.sxoff = p.sxoff;
+    a.tile_elems = p.tile_elems;
     a.err = e->d_err;
     const bool rec = timed && e->prof && e->ev_used < e->ev0.size();
     if (rec) CK(cudaEventRecord(e->ev0[e->ev_used], s));
@@ -500,6 +543,7 @@ int enqueue_out(conv_engine* e, Part& P, long long blk, float* out, cudaStream_t
     a.BT = p.BT;
     a.LT = p.LT;
     a.slot0 = slot0_for(blk, P.K);
+    a.tile_elems = p.tile_elems;
     CK(launch_out_c2r(e->prec, a, s));
     return CONV_OK;
 }
@@ -671,7 +715,7 @@ int conv_set_precision(conv_engine* e, int mode) {
     return engine_reset(e);
 }
 
-int conv_set_tiling(conv_engine* e, int bin_tile, int stages, int stage_kib, int splits) {
+int conv_set_tiling(conv_engine* e, int bin_tile, int stages, int stage_kib, int splits, int warps) {
     if (!e) return set_err(CONV_E_INVAL, "null handle");
     if (e->syn.ready || e->fb.allocated)
         return set_err(CONV_E_STATE, "tiling must be set before conv_set_filters / afc_set_paths");
@@ -681,8 +725,10 @@ int conv_set_tiling(conv_engine* e, int bin_tile, int stages, int stage_kib, int
         return set_err(CONV_E_INVAL, "stages must be 0 or in [2, %d]", MAX_STAGES);
     if (stage_kib < 0 || stage_kib > 96) return set_err(CONV_E_INVAL, "stage_kib must be in [0, 96]");
     if (splits < 0) return set_err(CONV_E_INVAL, "splits must be >= 0");
+    if (warps != 0 && warps != 8 && warps != 16) return set_err(CONV_E_INVAL, "warps must be 0, 8 or 16");
     DeviceGuard g(e->dev);
     TileOverride o;
+    o.warps = warps;
     o.bin_tile = bin_tile;
     o.stages = stages;
     o.stage_kib = stage_kib;
@@ -835,6 +881,7 @@ int conv_get_info(const conv_engine* e, conv_info* out) {
     out->mac_bin_tile = p.BT;
     out->mac_stages = p.nstage;
     out->mac_stage_bytes = p.stage_bytes;
+    out->mac_warps = p.nw;
     out->device_bytes = (long long)e->dev_bytes;
     out->kernels_per_block = 3;
     out->kernels_per_afc_block = 6;
@@ -876,11 +923,11 @@ int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches)
 }
 
 int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms, int bin_tile,
-                    int stages, int stage_kib, int splits) {
+                    int stages, int stage_kib, int splits, int warps) {
     if (precision < CONV_FP32 || precision > CONV_BF16 || block < 16 || block > 4096 || (block & (block - 1)) ||
         n_src < 1 || n_dst < 1 || taps < 1 || num_sms < 1 || bin_tile < 0 || stages < 0 || stage_kib < 0 ||
         splits < 0 || (bin_tile && (bin_tile < 16 || bin_tile > 256 || (bin_tile & (bin_tile - 1)))) ||
-        (stages && (stages < 2 || stages > MAX_STAGES)) || stage_kib > 96)
+        (stages && (stages < 2 || stages > MAX_STAGES)) || stage_kib > 96 || (warps != 0 && warps != 8 && warps != 16))
         return set_err(CONV_E_INVAL, "invalid plan arguments");
     const long long K = (taps + block - 1) / block;
     if ((long long)n_src * K > 0x7fffffffLL / 2) return set_err(CONV_E_INVAL, "too many partitions");
@@ -889,6 +936,7 @@ int conv_plan_check(int precision, int block, int n_src, int n_dst, long long ta
     o.stages = stages;
     o.stage_kib = stage_kib;
     o.splits = splits;
+    o.warps = warps;
     const MacPlan p = plan_mac(precision, block, n_src, n_dst, (int)K, num_sms, n_src, o);
     std::string why;
     if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());

@@ -47,28 +47,37 @@ struct RingIndex {
     }
 };
 
-// Element index of bin k of sub-filter r of output l (layout H[kt][l0..][r][LTt][BT]).
+// Element index of bin k of sub-filter r of output l: tile (kt, lt) starts at
+// (kt * n_lt + lt) * tile_elems, then [r][LTt][BT].
 struct FilterIndex {
-    int BT, n_dst, l0, R, r, LTt, ll;
+    int BT, n_lt, lt, r, LTt, ll;
+    size_t tile_elems;
     __device__ size_t operator()(int k) const {
         const int kt = k / BT, kl = k - kt * BT;
-        return (((size_t)kt * n_dst + l0) * (size_t)R + (size_t)r * LTt + ll) * BT + kl;
+        return ((size_t)kt * n_lt + lt) * tile_elems + ((size_t)r * LTt + ll) * BT + kl;
     }
 };
 
-// Writes the packed spectrum Xs[0..B) (shared memory) in storage precision.
-// `dst_index(k)` gives the element index of bin k.  Returns the scale used.
+// Largest |re| or |im| of the packed spectrum Xs[0..B) (shared memory).
+__device__ float spectrum_max(const float2* Xs, int B, float* red) {
+    float mx = 0.0f;
+    for (int k = threadIdx.x; k < B; k += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(Xs[k].x), fabsf(Xs[k].y)));
+    return block_max(mx, red);
+}
+
+// Writes the packed spectrum Xs[0..B) divided by `scale` (a power of two, so
+// exactly) in storage precision; `dst_index(k)` gives the element of bin k.
+template <int PREC, typename IndexFn>
+__device__ void store_scaled(const float2* Xs, int B, void* dst, IndexFn dst_index, float scale) {
+    const float inv = 1.0f / scale;
+    for (int k = threadIdx.x; k < B; k += blockDim.x) Store<PREC>::store1(dst, dst_index(k), cscale(Xs[k], inv));
+}
+
+// Writes Xs with its own power-of-two scale (FP32: scale 1).  Returns the scale.
 template <int PREC, typename IndexFn>
 __device__ float store_spectrum(const float2* Xs, int B, void* dst, IndexFn dst_index, float* red) {
-    float scale = 1.0f;
-    if (PREC != PREC_FP32) {
-        float mx = 0.0f;
-        for (int k = threadIdx.x; k < B; k += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(Xs[k].x), fabsf(Xs[k].y)));
-        mx = block_max(mx, red);
-        scale = block_scale<PREC>(mx);
-    }
-    const float inv = 1.0f / scale;  // exact: scale is a power of two
-    for (int k = threadIdx.x; k < B; k += blockDim.x) Store<PREC>::store1(dst, dst_index(k), cscale(Xs[k], inv));
+    const float scale = PREC == PREC_FP32 ? 1.0f : block_scale<PREC>(spectrum_max(Xs, B, red));
+    store_scaled<PREC>(Xs, B, dst, dst_index, scale);
     return scale;
 }
 
@@ -121,7 +130,10 @@ __global__ void k_pack_r2c(const PackArgs a) {
 
 // --------------------------------------------------- filter partitions R2C
 // One CTA per (l, q, p): sub-filter h_lq[pB, pB+B) zero-padded to 2B, R2C,
-// stored at reduction index p * n_src + q.
+// stored at reduction index p * n_src + q.  Reduced precision runs this twice:
+// pass 0 only records each sub-filter's largest component in `maxabs`; after
+// k_tile_scales has turned those into one power-of-two scale per (output
+// tile, r), pass 1 stores the spectra divided by their tile's scale.
 template <int PREC>
 __global__ void k_filter_r2c(const FilterArgs a) {
     extern __shared__ float2 fsm[];
@@ -154,9 +166,29 @@ __global__ void k_filter_r2c(const FilterArgs a) {
     __syncthreads();
     const int l0 = (l / a.LT) * a.LT;
     const int LTt = min(a.LT, a.n_dst - l0), ll = l - l0;
-    const float scale =
-        store_spectrum<PREC>(Xs, B, a.H, FilterIndex{a.BT, a.n_dst, l0, R, r, LTt, ll}, red);
-    if (PREC != PREC_FP32 && tid == 0) a.sH[(size_t)l0 * R + (size_t)r * LTt + ll] = scale;
+    if (PREC != PREC_FP32 && a.pass == 0) {
+        const float mx = spectrum_max(Xs, B, red);
+        if (tid == 0) a.maxabs[(size_t)l * R + r] = mx;
+        return;
+    }
+    const float scale = PREC == PREC_FP32 ? 1.0f : __ldg(a.sH + (size_t)(l / a.LT) * R + r);
+    const int n_lt = (a.n_dst + a.LT - 1) / a.LT;
+    store_scaled<PREC>(Xs, B, a.H, FilterIndex{a.BT, n_lt, l / a.LT, r, LTt, ll, a.tile_elems}, scale);
+}
+
+// One power-of-two scale per (output tile, reduction index): from the largest
+// component over the tile's outputs (reduced precision set-up, between the two
+// filter passes).
+template <int PREC>
+__global__ void k_tile_scales(const float* __restrict__ maxabs, float* __restrict__ sH, int n_dst, int R, int LT) {
+    const int n_lt = (n_dst + LT - 1) / LT;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n_lt * R) return;
+    const int lt = (int)(i / R), r = (int)(i - (long long)lt * R);
+    const int l0 = lt * LT, l1 = min(n_dst, l0 + LT);
+    float mx = 0.0f;
+    for (int l = l0; l < l1; ++l) mx = fmaxf(mx, maxabs[(size_t)l * R + r]);
+    sH[i] = block_scale<PREC>(mx);
 }
 
 // ----------------------------------------------------------- FDL MAC
@@ -169,11 +201,15 @@ __global__ void k_filter_r2c(const FilterArgs a) {
 // ring with 1-D bulk copies (TMA), completion tracked by mbarriers (filters
 // with an evict-first L2 policy: they are read once per block; the delay line
 // with evict-last: it is re-read by every output tile and by the next blocks).
-// Warps 0-7 consume: each thread owns VEC bins x up to LPT outputs for one
+// The NW consumer warps: each thread owns VEC bins x up to LPT outputs for one
 // r-lane and accumulates in FP32 registers; r-lanes are combined in a fixed
 // order through shared memory at the end, and the split's sums go to P[split].
-template <int PREC, int LPT>
-__global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
+//
+// Stages follow a global grid over r (stage g holds r in [g*RS, (g+1)*RS)),
+// and every filter tile starts on a 64 KiB boundary, so each filter copy is an
+// aligned, usually power-of-two-sized chunk of HBM; splits own whole stages.
+template <int PREC, int LPT, int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) k_fdl_mac(const MacArgs a) {
     using St = Store<PREC>;
     constexpr int VEC = St::VEC;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -186,28 +222,34 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
     const int tile = blockIdx.x / a.S, split = blockIdx.x - tile * a.S;
     const int kt = tile / a.n_lt, lt = tile - kt * a.n_lt;
     const int l0 = lt * a.LT, LTt = min(a.LT, a.n_dst - l0);
-    const int K = a.K, R = a.n_src * K, Rt = R - a.r_begin;
-    const int r0 = a.r_begin + (int)((long long)split * Rt / a.S);
-    const int r1 = a.r_begin + (int)((long long)(split + 1) * Rt / a.S);
+    const int K = a.K, R = a.n_src * K;
+    const int gb = a.r_begin / a.RS, gt = (R + a.RS - 1) / a.RS - gb;  // stage grid
+    const int g0 = gb + (int)((long long)split * gt / a.S);
+    const int g1 = gb + (int)((long long)(split + 1) * gt / a.S);
+    const int nit = g1 - g0;
     const int ring0 = a.slot0 * a.n_src;  // ring row of r = 0
-    const int nit = (r1 - r0 + a.RS - 1) / a.RS;
     const size_t hrow = (size_t)a.BT * St::BYTES;
     const size_t hr_bytes = (size_t)LTt * hrow;
     const unsigned char* Hb =
-        static_cast<const unsigned char*>(a.H) + ((size_t)kt * a.n_dst + l0) * (size_t)R * hrow;
+        static_cast<const unsigned char*>(a.H) + (size_t)tile * a.tile_elems * St::BYTES;
     const unsigned char* Xb = static_cast<const unsigned char*>(a.X) + (size_t)kt * R * hrow;
+    auto stage_range = [&](int it, int& ra, int& rb) {
+        const int g = g0 + it;
+        ra = max(a.r_begin, g * a.RS);
+        rb = min(R, (g + 1) * a.RS);
+    };
 
     if (tid == 0) {
         for (int i = 0; i < a.nstage; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], MAC_CONSUMER_WARPS);
+            mbar_init(&empty[i], NW);
         }
         *abort_flag = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
-    if (warp == MAC_CONSUMER_WARPS) {
+    if (warp == NW) {
         if (lane != 0) return;
         griddep_launch_dependents();
         const uint64_t pol_stream = policy_evict_first();
@@ -216,9 +258,9 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
         // Their runs are widened to 16-byte boundaries (the buffers carry 16
         // bytes of padding); consumers index from the run's first element.
         auto scale_runs = [&](int ra, int nr, int start, int run, int (&w)[3][2]) {
-            const int fo = l0 * R + ra * LTt;  // sH tile rows [r][LTt]
+            const int fo = lt * R + ra;  // sH: one scale per (output tile, r)
             w[0][0] = fo & ~3;
-            w[0][1] = (fo + nr * LTt + 3) & ~3;
+            w[0][1] = (fo + nr + 3) & ~3;
             w[1][0] = start & ~3;  // sX ring rows, first run
             w[1][1] = (start + run + 3) & ~3;
             w[2][0] = 0;  // wrapped run
@@ -226,7 +268,9 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
         };
         auto issue_h = [&](int it) {
             const int st = it % a.nstage;
-            const int ra = r0 + it * a.RS, rb = min(ra + a.RS, r1), nr = rb - ra;
+            int ra, rb;
+            stage_range(it, ra, rb);
+            const int nr = rb - ra;
             unsigned char* sh = stages + (size_t)st * a.stage_bytes;
             size_t tx = (size_t)nr * (hr_bytes + hrow);
             int w[3][2];
@@ -243,7 +287,9 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
         };
         auto issue_x = [&](int it) {
             const int st = it % a.nstage;
-            const int ra = r0 + it * a.RS, rb = min(ra + a.RS, r1), nr = rb - ra;
+            int ra, rb;
+            stage_range(it, ra, rb);
+            const int nr = rb - ra;
             unsigned char* sx = stages + (size_t)st * a.stage_bytes + a.xoff;
             int start = ring0 + ra;
             if (start >= R) start -= R;
@@ -310,7 +356,9 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
             ok = false;
             break;
         }
-        const int ra = r0 + it * a.RS, nr = min(a.RS, r1 - ra);
+        int ra, rb;
+        stage_range(it, ra, rb);
+        const int nr = rb - ra;
         const unsigned char* sh = stages + (size_t)st * a.stage_bytes;
         const unsigned char* sx = sh + a.xoff;
         // reduced precision: where this stage's scales start in shared memory
@@ -318,7 +366,7 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
         const float* ssx = reinterpret_cast<const float*>(sh + a.sxoff);
         int sh0 = 0, sx0 = 0, sx2 = 0, xrun = nr;
         if (PREC != PREC_FP32) {
-            const int fo = l0 * R + ra * LTt;
+            const int fo = lt * R + ra;
             sh0 = fo - (fo & ~3);
             int start = ring0 + ra;
             if (start >= R) start -= R;
@@ -330,34 +378,24 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
         for (int j = rl; j < nr; j += a.NRL) {
             float2 xv[VEC];
             St::load16(sx + (size_t)j * hrow + (size_t)kv * 16, xv);
-            float sxs = 1.0f;
-            if (PREC != PREC_FP32) sxs = j < xrun ? ssx[sx0 + j] : ssx[sx2 + j];
+            if (PREC != PREC_FP32) {
+                // both scales are per reduction index: fold them into x once
+                const float sc = (j < xrun ? ssx[sx0 + j] : ssx[sx2 + j]) * ssh[sh0 + j];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) xv[v] = cscale(xv[v], sc);
+            }
 #pragma unroll
             for (int i = 0; i < LPT; ++i) {
                 const int ll = lg + i * a.NLG;
                 if (ll < LTt) {
                     float2 hv[VEC];
                     St::load16(sh + ((size_t)j * LTt + ll) * hrow + (size_t)kv * 16, hv);
-                    if (PREC == PREC_FP32) {
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            if (v == 0 && dc)
-                                rmac2(acc[i][v], hv[v], xv[v]);
-                            else
-                                cmac(acc[i][v], hv[v], xv[v]);
-                        }
-                    } else {
-                        const float sc = sxs * ssh[sh0 + j * LTt + ll];
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            float2 t = make_float2(0.0f, 0.0f);
-                            if (v == 0 && dc)
-                                rmac2(t, hv[v], xv[v]);
-                            else
-                                cmac(t, hv[v], xv[v]);
-                            acc[i][v].x = fmaf(sc, t.x, acc[i][v].x);
-                            acc[i][v].y = fmaf(sc, t.y, acc[i][v].y);
-                        }
+                    for (int v = 0; v < VEC; ++v) {
+                        if (v == 0 && dc)
+                            rmac2(acc[i][v], hv[v], xv[v]);
+                        else
+                            cmac(acc[i][v], hv[v], xv[v]);
                     }
                 }
             }
@@ -368,7 +406,7 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
 
     // combine r-lanes in a fixed order (stage memory is free: every stage has landed)
     if (a.NRL > 1) {
-        named_barrier_sync(1, MAC_CONSUMER_WARPS * 32);
+        named_barrier_sync(1, NW * 32);
         float2* red = reinterpret_cast<float2*>(stages);
         const int LT = a.LT, BT = a.BT;
         if (rl > 0) {
@@ -380,7 +418,7 @@ __global__ void __launch_bounds__(MAC_THREADS, 1) k_fdl_mac(const MacArgs a) {
                     for (int v = 0; v < VEC; ++v) red[((size_t)(rl - 1) * LT + ll) * BT + kv * VEC + v] = acc[i][v];
             }
         }
-        named_barrier_sync(1, MAC_CONSUMER_WARPS * 32);
+        named_barrier_sync(1, NW * 32);
         if (rl == 0) {
             for (int rr = 1; rr < a.NRL; ++rr)
 #pragma unroll
@@ -440,7 +478,8 @@ __global__ void k_out_c2r(const OutArgs a) {
         for (; s < S; ++s) tot = cadd(tot, src[(size_t)s * stride]);
         if (a.head) {
             const int kt = k / a.BT, kl = k - kt * a.BT;
-            const size_t hbase = (((size_t)kt * a.n_dst + l0) * (size_t)a.R) * a.BT + (size_t)ll * a.BT + kl;
+            const int n_lt = (a.n_dst + a.LT - 1) / a.LT;
+            const size_t hbase = ((size_t)kt * n_lt + l / a.LT) * a.tile_elems + (size_t)ll * a.BT + kl;
             const size_t xbase = (((size_t)kt * a.K + a.slot0) * a.n_src) * a.BT + kl;
             float2 hd = make_float2(0.0f, 0.0f);
             for (int q = 0; q < a.n_src; ++q) {
@@ -452,7 +491,7 @@ __global__ void k_out_c2r(const OutArgs a) {
                 else
                     cmac(t, h, x);
                 const float sc = PREC == PREC_FP32 ? 1.0f
-                                                   : __ldg(a.sH + (size_t)l0 * a.R + (size_t)q * LTt + ll) *
+                                                   : __ldg(a.sH + (size_t)(l / a.LT) * a.R + q) *
                                                          __ldg(a.sX + (size_t)a.slot0 * a.n_src + q);
                 hd.x = fmaf(sc, t.x, hd.x);
                 hd.y = fmaf(sc, t.y, hd.y);
@@ -534,9 +573,12 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR(k_out_c2r<PREC_FP32>, fft_max)
     GB_ATTR(k_out_c2r<PREC_FP16>, fft_max)
     GB_ATTR(k_out_c2r<PREC_BF16>, fft_max)
-    GB_ATTR((k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>()>), mac_smem)
-    GB_ATTR((k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>()>), mac_smem)
-    GB_ATTR((k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>()>), mac_smem)
+    GB_ATTR((k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>(), 8>), mac_smem)
+    GB_ATTR((k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>(), 8>), mac_smem)
+    GB_ATTR((k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>(), 8>), mac_smem)
+    GB_ATTR((k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>(), 16>), mac_smem)
+    GB_ATTR((k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>(), 16>), mac_smem)
+    GB_ATTR((k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>(), 16>), mac_smem)
 #undef GB_ATTR
     return cudaSuccess;
 }
@@ -566,12 +608,32 @@ cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
-    const dim3 grid(p.ctas), block(MAC_THREADS);
+cudaError_t launch_tile_scales(int prec, const float* maxabs, float* sH, int n_dst, int R, int LT, cudaStream_t s) {
+    const long long n = (long long)((n_dst + LT - 1) / LT) * R;
+    const unsigned grid = (unsigned)((n + 255) / 256);
     switch (prec) {
-        case PREC_FP32: return launch_pdl(k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>()>, grid, block, p.smem, s, a);
-        case PREC_FP16: return launch_pdl(k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>()>, grid, block, p.smem, s, a);
-        case PREC_BF16: return launch_pdl(k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>()>, grid, block, p.smem, s, a);
+        case PREC_FP16: k_tile_scales<PREC_FP16><<<grid, 256, 0, s>>>(maxabs, sH, n_dst, R, LT); break;
+        case PREC_BF16: k_tile_scales<PREC_BF16><<<grid, 256, 0, s>>>(maxabs, sH, n_dst, R, LT); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int NW>
+cudaError_t launch_fdl_mac_nw(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
+    const dim3 grid(p.ctas), block((NW + 1) * 32);
+    switch (prec) {
+        case PREC_FP32: return launch_pdl(k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>(), NW>, grid, block, p.smem, s, a);
+        case PREC_FP16: return launch_pdl(k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>(), NW>, grid, block, p.smem, s, a);
+        case PREC_BF16: return launch_pdl(k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>(), NW>, grid, block, p.smem, s, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
+    switch (p.nw) {
+        case 8: return launch_fdl_mac_nw<8>(prec, p, a, s);
+        case 16: return launch_fdl_mac_nw<16>(prec, p, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -30,8 +30,7 @@ enum Prec { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2 };
 // Device error codes written to the engine's host-mapped error word.
 enum DevErr { DEVERR_NONE = 0, DEVERR_TIMEOUT_PRODUCER = 1, DEVERR_TIMEOUT_CONSUMER = 2 };
 
-constexpr int MAC_CONSUMER_WARPS = 8;
-constexpr int MAC_THREADS = (MAC_CONSUMER_WARPS + 1) * 32;  // + one producer warp
+constexpr int MAC_CONSUMER_WARPS = 8;  // default consumer warps (8 or 16), plus one producer warp
 constexpr int MAC_HDR_BYTES = 1024;                          // mbarriers + flags
 constexpr int MAX_STAGES = 8;
 constexpr size_t MAC_SMEM_LIMIT = 227 * 1024;  // dynamic shared memory the MAC may use (sm_100 family maximum)
@@ -50,21 +49,23 @@ struct MacPlan {
     int LPT;       // max outputs per consumer thread
     int BT, n_kt;  // bin tile width, number of bin tiles
     int LT, n_lt;  // output tile height, number of output tiles
+    int nw;        // consumer warps (8 or 16)
     int kthreads, NLG, NRL;  // consumer thread layout: bins x output groups x r-lanes
-    int RS;        // reduction indices per pipeline stage
+    int RS;        // reduction indices per pipeline stage (the stage grid's pitch)
     int nstage;    // pipeline depth
     int S;         // partition splits per tile (0: empty range, no MAC launch)
     unsigned stage_bytes, xoff;
     unsigned soff, sxoff;  // reduced precision: filter / delay-line scale parts of a stage
     size_t smem;   // dynamic shared memory per CTA
     int ctas;
+    size_t tile_elems;  // filter tile pitch in stored values (64 KiB aligned)
     size_t h_bytes, x_bytes, partial_bytes;
 };
 
 struct MacArgs {
-    const void* H;    // filter spectra [kt][l0..][r][LTt][BT]
+    const void* H;    // filter spectra: tile (kt, lt) at (kt*n_lt + lt)*tile_elems, then [r][LTt][BT]
     const void* X;    // FDL ring [kt][slot][q][BT]
-    const float* sH;  // [lt tile][r][LTt] per-partition scales (reduced precision), else null
+    const float* sH;  // [lt tile][r] per-partition scales (reduced precision), else null
     const float* sX;  // [K][n_src] per-slot scales (reduced precision), else null
     float2* partial;  // [S][n_dst][B]
     int B, BT, n_kt, n_dst, LT, n_lt, n_src, K, S, RS, nstage;
@@ -72,6 +73,7 @@ struct MacArgs {
     int kthreads, NLG, NRL;
     int slot0;  // ring slot of partition 0 for the block this MAC serves
     unsigned stage_bytes, xoff, soff, sxoff;
+    size_t tile_elems;
     int* err;   // device-visible error word (host-mapped), or null
 };
 
@@ -92,7 +94,10 @@ struct FilterArgs {
     long long taps;
     int n_dst, n_src, K, B, log2B, BT, LT;
     void* H;    // tiled spectra
-    float* sH;  // [lt tile][r][LTt] scales (reduced precision), else null
+    const float* sH;  // [lt tile][r] scales (reduced precision pass 1), else null
+    float* maxabs;    // [n_dst][R] largest components (reduced precision pass 0)
+    int pass;         // reduced precision: 0 = record maxabs, 1 = store scaled
+    size_t tile_elems;
     const float2* tw;
 };
 
@@ -109,6 +114,7 @@ struct OutArgs {
     const float* sH;
     const float* sX;
     int n_src, K, R, BT, LT, slot0;
+    size_t tile_elems;
 };
 
 int fft_threads(int B);
@@ -121,6 +127,7 @@ void set_last_error_message(const char* msg);
 cudaError_t prepare_kernels(size_t mac_smem);
 cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s);
 cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s);
+cudaError_t launch_tile_scales(int prec, const float* maxabs, float* sH, int n_dst, int R, int LT, cudaStream_t s);
 cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s);
 cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s);
 

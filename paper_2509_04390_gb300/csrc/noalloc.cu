@@ -127,8 +127,9 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     p.n_kt = 1;
     p.LT = n_out;
     p.n_lt = 1;
+    p.nw = MAC_CONSUMER_WARPS;
     p.kthreads = block / 2;
-    const int rest = (MAC_CONSUMER_WARPS * 32) / p.kthreads;
+    const int rest = (p.nw * 32) / p.kthreads;
     p.NLG = n_out > 8 ? 2 : 1;
     p.NRL = rest / p.NLG;
     const size_t per_r = (size_t)(p.LT + 1) * p.BT * p.es;
@@ -146,13 +147,15 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     const size_t ring = (size_t)p.nstage * p.stage_bytes;
     p.smem = MAC_HDR_BYTES + (ring > red ? ring : (red + 127) / 128 * 128);
     if (p.smem > 200 * 1024) return fail(CONV_E_INVAL, "tiling needs more shared memory than planned");
+    const long long grid_stages = (p.R + p.RS - 1) / p.RS;  // stage grid from r = 0
     long long S = sms;
     const long long fit = (long long)(NOALLOC_SCRATCH_BYTES / row);
     if (S > fit) S = fit;
-    if (S > p.R) S = p.R;
+    if (S > grid_stages) S = grid_stages;
     if (S < 1) S = 1;
     p.S = (int)S;
     p.ctas = p.S;
+    p.tile_elems = (size_t)n_out * p.R * block;  // one tile: the caller's layout, no padding
     p.h_bytes = (size_t)n_out * p.R * block * p.es;
     p.x_bytes = (size_t)p.R * block * p.es;
     p.partial_bytes = (size_t)p.S * row;
@@ -182,6 +185,7 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     a.slot0 = (int)slot0;
     a.stage_bytes = p.stage_bytes;
     a.xoff = p.xoff;
+    a.tile_elems = p.tile_elems;
     a.err = nullptr;
     e = launch_fdl_mac(PREC_FP32, p, a, s);
     if (e != cudaSuccess) return fail(CONV_E_CUDA, "MAC launch", e);

@@ -60,6 +60,7 @@ class conv_info(ctypes.Structure):
             "mac_bin_tile",
             "mac_stages",
             "mac_stage_bytes",
+            "mac_warps",
         )
     ]
 
@@ -91,7 +92,7 @@ def load():
         "conv_create": (vp, [d, i, i, i, ll]),
         "conv_set_precision": (i, [vp, i]),
         "conv_set_filters": (i, [vp, vp]),
-        "conv_set_tiling": (i, [vp, i, i, i, i]),
+        "conv_set_tiling": (i, [vp, i, i, i, i, i]),
         "afc_set_paths": (i, [vp, vp, ll]),
         "conv_process_block": (i, [vp, vp, vp]),
         "conv_process_block_async": (i, [vp, vp, vp, vp]),
@@ -103,7 +104,7 @@ def load():
         "conv_get_info": (i, [vp, ctypes.POINTER(conv_info)]),
         "conv_profile_enable": (i, [vp, i]),
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
-        "conv_plan_check": (i, [i, i, i, i, ll, i, i, i, i, i]),
+        "conv_plan_check": (i, [i, i, i, i, ll, i, i, i, i, i, i]),
         "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
         "conv_destroy": (None, [vp]),
         "conv_last_error": (ctypes.c_char_p, []),
@@ -172,8 +173,8 @@ def conv_set_precision(h, mode):
     return _check(load().conv_set_precision(h, int(mode)))
 
 
-def conv_set_tiling(h, bin_tile=0, stages=0, stage_kib=0, splits=0):
-    return _check(load().conv_set_tiling(h, int(bin_tile), int(stages), int(stage_kib), int(splits)))
+def conv_set_tiling(h, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0):
+    return _check(load().conv_set_tiling(h, int(bin_tile), int(stages), int(stage_kib), int(splits), int(warps)))
 
 
 def conv_set_filters(h, filters: np.ndarray):
@@ -239,12 +240,14 @@ def conv_profile_read(h):
     return ms.value, n.value
 
 
-def conv_plan_check(precision, block, n_src, n_dst, taps, num_sms=152, bin_tile=0, stages=0, stage_kib=0, splits=0):
+def conv_plan_check(
+    precision, block, n_src, n_dst, taps, num_sms=152, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0
+):
     precision = PRECISIONS.get(precision, precision)
     return _check(
         load().conv_plan_check(
             int(precision), int(block), int(n_src), int(n_dst), int(taps), int(num_sms), int(bin_tile), int(stages),
-            int(stage_kib), int(splits),
+            int(stage_kib), int(splits), int(warps),
         )
     )
 

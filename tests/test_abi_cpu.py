@@ -110,10 +110,10 @@ def test_tiling_overrides_stay_in_bounds(lib):
             for n_src, n_dst, taps in ((4, 16, 384000), (3, 20, 1000)):
                 for bt in (16, 32, 64, 128, 256):
                     for stages, kib in ((2, 64), (3, 32), (4, 48), (5, 32), (8, 16), (8, 24)):
-                        for splits in (0, 1, 9, 38, 1000000):
-                            upols.conv_plan_check(precision, B, n_src, n_dst, taps, 152, bt, stages, kib, splits)
+                        for splits, nw in ((0, 0), (1, 8), (9, 16), (38, 8), (1000000, 16)):
+                            upols.conv_plan_check(precision, B, n_src, n_dst, taps, 152, bt, stages, kib, splits, nw)
 
 
 def test_tiling_override_arguments_are_validated(lib):
     with pytest.raises(upols.ConvError):
-        upols.conv_plan_check("fp32", 256, 4, 16, 384000, 152, 24, 0, 0, 0)  # not a power of two
+        upols.conv_plan_check("fp32", 256, 4, 16, 384000, 152, 24, 0, 0, 0, 0)  # not a power of two
