@@ -68,6 +68,7 @@ typedef struct conv_info {
     long long mac_stages;     /* MAC pipeline depth                               */
     long long mac_stage_bytes; /* bytes per MAC pipeline stage                    */
     long long mac_warps;      /* MAC consumer warps                               */
+    long long mac_kernel;     /* CONV_KERNEL_TMA / _DIRECT1 / _DIRECT2            */
 } conv_info;
 
 /* Create an engine for n_in inputs, n_out outputs and filters of `taps` taps
@@ -84,15 +85,28 @@ conv_engine* conv_create(double fs, int block, int n_in, int n_out, long long ta
  * valid before conv_set_filters (CONV_E_STATE afterwards). */
 int conv_set_precision(conv_engine* e, int mode);
 
-/* Fix fields of the synthesis FDL MAC tiling instead of the planner's choice
- * (the hook the autotuner uses).  bin_tile: bins per tile, a power of two in
- * [16, 256] (capped at block); stages: pipeline depth in [2, 8]; stage_kib:
- * target bytes per pipeline stage in KiB, [1, 96]; splits: partition splits
- * per tile (capped at the number of stages); warps: consumer warps per CTA,
- * 8 or 16.  0 leaves a field to the planner.  Re-plans and re-allocates; only
- * valid before conv_set_filters and afc_set_paths (CONV_E_STATE afterwards).
- * On failure the previous tiling is kept. */
-int conv_set_tiling(conv_engine* e, int bin_tile, int stages, int stage_kib, int splits, int warps);
+/* FDL MAC kernels (conv_tiling.kernel) */
+#define CONV_KERNEL_AUTO 0    /* planner's choice                                        */
+#define CONV_KERNEL_TMA 1     /* producer warp streams 1-D bulk copies (TMA) into a ring */
+#define CONV_KERNEL_DIRECT1 2 /* direct 16-byte loads, 1 partition in flight, 3 CTAs/SM */
+#define CONV_KERNEL_DIRECT2 3 /* direct 16-byte loads, 2 partitions in flight, 2 CTAs/SM */
+
+/* Tiling of the synthesis FDL MAC; every field 0 = the planner's choice.
+ *   kernel     CONV_KERNEL_*
+ *   bin_tile   bins per tile, a power of two in [16, 256] (capped at block)
+ *   stages     TMA ring depth, [2, 8]
+ *   stage_kib  target bytes of filter spectra per TMA stage, KiB, [1, 96]
+ *   splits     partition splits per tile (capped at what the tile allows)
+ *   warps      TMA consumer warps, 8 or 16 */
+typedef struct conv_tiling {
+    int kernel, bin_tile, stages, stage_kib, splits, warps;
+} conv_tiling;
+
+/* Fix the synthesis FDL MAC tiling instead of the planner's choice (the hook
+ * the autotuner uses).  t may be NULL (all automatic).  Re-plans and
+ * re-allocates; only valid before conv_set_filters and afc_set_paths
+ * (CONV_E_STATE afterwards).  On failure the previous tiling is kept. */
+int conv_set_tiling(conv_engine* e, const conv_tiling* t);
 
 /* Set the synthesis filters H_aur (Sec. 3.1, Eq. 2): host array
  * h[n_out][n_in][taps] float32 (h[l][q] filters input q into output l).  The
@@ -156,10 +170,10 @@ int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches)
  * sizes: replays the FDL MAC kernel's copy and store addresses for every CTA
  * and stage against the buffer and shared-memory sizes.  Needs no device.
  * precision is CONV_FP32/FP16/BF16, n_src/n_dst the convolution's inputs and
- * outputs, num_sms the SM count to plan for; the last five fields are the
- * conv_set_tiling overrides (0 = planner).  CONV_OK or CONV_E_INVAL. */
-int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms, int bin_tile,
-                    int stages, int stage_kib, int splits, int warps);
+ * outputs, num_sms the SM count to plan for, t the conv_set_tiling override
+ * (NULL = planner).  CONV_OK or CONV_E_INVAL. */
+int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms,
+                    const conv_tiling* t);
 
 /* FDL MAC and output transform of one block over caller-owned buffers,
  * allocating nothing.  (The paper has no counterpart: this serves callers that

@@ -69,8 +69,32 @@ inline int pow2_ceil(int v) {
 
 // Tiling fields a caller (the autotuner) may fix; 0 leaves a field to the planner.
 struct TileOverride {
-    int bin_tile = 0, stages = 0, stage_kib = 0, splits = 0, warps = 0;
+    int kernel = 0, bin_tile = 0, stages = 0, stage_kib = 0, splits = 0, warps = 0;
 };
+
+TileOverride from_api(const conv_tiling* t) {
+    TileOverride o;
+    if (t) {
+        o.kernel = t->kernel;
+        o.bin_tile = t->bin_tile;
+        o.stages = t->stages;
+        o.stage_kib = t->stage_kib;
+        o.splits = t->splits;
+        o.warps = t->warps;
+    }
+    return o;
+}
+
+const char* check_override(const TileOverride& o) {
+    if (o.kernel < CONV_KERNEL_AUTO || o.kernel > CONV_KERNEL_DIRECT2) return "unknown kernel";
+    if (o.bin_tile < 0 || (o.bin_tile && (o.bin_tile < 16 || o.bin_tile > 256 || (o.bin_tile & (o.bin_tile - 1)))))
+        return "bin_tile must be 0 or a power of two in [16, 256]";
+    if (o.stages < 0 || (o.stages && (o.stages < 2 || o.stages > MAX_STAGES))) return "stages must be 0 or in [2, 8]";
+    if (o.stage_kib < 0 || o.stage_kib > 96) return "stage_kib must be in [0, 96]";
+    if (o.splits < 0) return "splits must be >= 0";
+    if (o.warps != 0 && o.warps != 8 && o.warps != 16) return "warps must be 0, 8 or 16";
+    return nullptr;
+}
 
 inline bool is_pow2(size_t v) { return v && !(v & (v - 1)); }
 inline size_t pow2_floor(size_t v) {
@@ -95,8 +119,9 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     const int Rt = p.R - r_begin;
     p.es = prec == PREC_FP32 ? 8 : 4;
     p.VEC = 16 / p.es;
-    p.LPT = prec == PREC_FP32 ? 8 : 4;
-    p.nw = o.warps ? o.warps : MAC_CONSUMER_WARPS;
+    p.direct = o.kernel == CONV_KERNEL_DIRECT1 ? 1 : (o.kernel == CONV_KERNEL_DIRECT2 ? 2 : 0);
+    p.LPT = (prec == PREC_FP32 && !p.direct) ? 8 : 4;
+    p.nw = p.direct ? 8 : (o.warps ? o.warps : MAC_CONSUMER_WARPS);
     p.LT = std::min(n_dst, 16);
     p.n_lt = (n_dst + p.LT - 1) / p.LT;
     // Bin tiles: enough (bin tile x output tile) pairs that ~16-20 partition
@@ -113,6 +138,10 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     const int rest = (p.nw * 32) / p.kthreads;
     p.NLG = pow2_ceil((p.LT + p.LPT - 1) / p.LPT);
     if (p.NLG > rest) p.NLG = rest;
+    if (p.LT > p.LPT * p.NLG) {  // too few threads per bin for the tile: shorter output tiles
+        p.LT = p.LPT * p.NLG;
+        p.n_lt = (n_dst + p.LT - 1) / p.LT;
+    }
     p.NRL = rest / p.NLG;
     // Stage pitch: filter copies of a power-of-two size (64 KiB by default),
     // which, with 64 KiB-aligned tiles and a global stage grid, keeps every
@@ -150,10 +179,20 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     const size_t red = (size_t)(p.NRL - 1) * p.LT * p.BT * sizeof(float2);
     p.smem = MAC_HDR_BYTES + std::max((size_t)p.nstage * p.stage_bytes, align_up(red, 128));
     const int tiles = p.n_kt * p.n_lt;
-    const int gt = Rt > 0 ? (p.R + p.RS - 1) / p.RS - r_begin / p.RS : 0;  // stages on the grid
-    const int by_work = std::max(1, gt / 2);
+    int gt = Rt > 0 ? (p.R + p.RS - 1) / p.RS - r_begin / p.RS : 0;  // stages on the grid
+    int by_work = std::max(1, gt / 2);
     // never a second wave: the grid fits the SMs at the occupancy shared memory allows
-    const int per_sm = (int)std::max<size_t>(1, SM_SMEM_BYTES / (p.smem + CTA_SMEM_RESERVED));
+    int per_sm = (int)std::max<size_t>(1, SM_SMEM_BYTES / (p.smem + CTA_SMEM_RESERVED));
+    if (p.direct) {
+        // no stage ring: shared memory only holds the r-lane scratch; the
+        // register budget sets the CTAs per SM (3 or 2)
+        p.nstage = 0;
+        p.stage_bytes = 0;
+        p.smem = std::max<size_t>(16, align_up(red, 128));
+        per_sm = std::min(p.direct == 1 ? 3 : 2, (int)(SM_SMEM_BYTES / (p.smem + CTA_SMEM_RESERVED)));
+        gt = Rt;  // splits are plain ranges of reduction indices
+        by_work = std::max(1, Rt / (p.NRL * 4));
+    }
     int S = std::max(1, num_sms * per_sm / tiles);
     S = std::min(S, by_work);
     if (o.splits) S = o.splits;
@@ -165,6 +204,47 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     p.x_bytes = (size_t)p.R * B * p.es;
     p.partial_bytes = std::max<size_t>(16, (size_t)p.S * n_dst * B * sizeof(float2));
     return p;
+}
+
+// Host replay for the direct-load MAC: every thread's filter and delay-line
+// rows, the r-lane scratch and the partial rows, against the buffer sizes.
+int check_direct_plan(const MacPlan& p, std::string* why) {
+    char buf[256];
+    auto bad = [&](const char* what) {
+        snprintf(buf, sizeof(buf), "plan check failed (direct): %s (B=%d n_src=%d n_dst=%d K=%d)", what, p.B, p.n_src,
+                 p.n_dst, p.K);
+        *why = buf;
+        return -1;
+    };
+    const int Rt = p.R - p.r_begin;
+    if (p.nw != 8 || p.LPT != 4) return bad("thread shape");
+    if (p.kthreads * p.VEC != p.BT || p.kthreads > 256) return bad("bin threads");
+    const int rest = 256 / p.kthreads;
+    if (p.kthreads * rest != 256 || p.NLG * p.NRL != rest) return bad("thread layout");
+    if ((p.LT + p.NLG - 1) / p.NLG > p.LPT) return bad("outputs per thread above LPT");
+    if (p.S < 1 || p.S > Rt) return bad("split count");
+    if ((size_t)(p.NRL - 1) * p.LT * p.BT * 8 > p.smem) return bad("r-lane scratch");
+    if (p.smem > MAC_SMEM_LIMIT) return bad("shared memory");
+    const size_t hrow = (size_t)p.BT * p.es;
+    if ((size_t)p.R * p.LT * p.BT > p.tile_elems) return bad("tile pitch below a tile");
+    if ((size_t)p.n_kt * p.n_lt * p.tile_elems * p.es > p.h_bytes) return bad("tile pitch");
+    for (int tile = 0; tile < p.n_kt * p.n_lt; ++tile) {
+        const int kt = tile / p.n_lt, lt = tile % p.n_lt;
+        const int l0 = lt * p.LT, LTt = std::min(p.LT, p.n_dst - l0);
+        if (LTt < 1) return bad("empty output tile");
+        // last row of the last r of the tile, last 16 bytes
+        const size_t hend = (size_t)tile * p.tile_elems * p.es + ((size_t)(p.R - 1) * LTt + LTt - 1) * hrow + hrow;
+        if (hend > p.h_bytes) return bad("filter row past the spectra");
+        if ((size_t)kt * p.R * hrow + (size_t)p.R * hrow > p.x_bytes) return bad("delay-line row past the ring");
+        for (int split = 0; split < p.S; ++split) {
+            const int r0 = p.r_begin + (int)((long long)split * Rt / p.S);
+            const int r1 = p.r_begin + (int)((long long)(split + 1) * Rt / p.S);
+            if (r1 <= r0) return bad("empty split");
+            const size_t last = (((size_t)split * p.n_dst + l0 + LTt - 1) * p.B + (size_t)kt * p.BT + p.BT);
+            if (last * sizeof(float2) > p.partial_bytes) return bad("partial write past the buffer");
+        }
+    }
+    return 0;
 }
 
 // Host replay of the address arithmetic of one FDL MAC launch (producer bulk
@@ -182,6 +262,7 @@ int check_plan(const MacPlan& p, std::string* why) {
     const int Rt = p.R - p.r_begin;
     if (Rt < 0 || p.r_begin < 0) return bad("reduction range");
     if (Rt == 0) return p.S == 0 ? 0 : bad("splits over an empty range");
+    if (p.direct) return check_direct_plan(p, why);
     if (p.nstage < 1 || p.nstage > MAX_STAGES) return bad("stage count");
     if (p.smem > MAC_SMEM_LIMIT) return bad("shared memory above the kernel's limit");
     if (p.nw != 8 && p.nw != 16) return bad("consumer warps");
@@ -715,24 +796,13 @@ int conv_set_precision(conv_engine* e, int mode) {
     return engine_reset(e);
 }
 
-int conv_set_tiling(conv_engine* e, int bin_tile, int stages, int stage_kib, int splits, int warps) {
+int conv_set_tiling(conv_engine* e, const conv_tiling* t) {
     if (!e) return set_err(CONV_E_INVAL, "null handle");
     if (e->syn.ready || e->fb.allocated)
         return set_err(CONV_E_STATE, "tiling must be set before conv_set_filters / afc_set_paths");
-    if (bin_tile < 0 || (bin_tile && (bin_tile < 16 || bin_tile > 256 || (bin_tile & (bin_tile - 1)))))
-        return set_err(CONV_E_INVAL, "bin_tile must be 0 or a power of two in [16, 256]");
-    if (stages < 0 || (stages && (stages < 2 || stages > MAX_STAGES)))
-        return set_err(CONV_E_INVAL, "stages must be 0 or in [2, %d]", MAX_STAGES);
-    if (stage_kib < 0 || stage_kib > 96) return set_err(CONV_E_INVAL, "stage_kib must be in [0, 96]");
-    if (splits < 0) return set_err(CONV_E_INVAL, "splits must be >= 0");
-    if (warps != 0 && warps != 8 && warps != 16) return set_err(CONV_E_INVAL, "warps must be 0, 8 or 16");
+    const TileOverride o = from_api(t);
+    if (const char* msg = check_override(o)) return set_err(CONV_E_INVAL, "%s", msg);
     DeviceGuard g(e->dev);
-    TileOverride o;
-    o.warps = warps;
-    o.bin_tile = bin_tile;
-    o.stages = stages;
-    o.stage_kib = stage_kib;
-    o.splits = splits;
     const TileOverride old = e->tiling;
     e->tiling = o;
     int rc = part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling);
@@ -882,6 +952,7 @@ int conv_get_info(const conv_engine* e, conv_info* out) {
     out->mac_stages = p.nstage;
     out->mac_stage_bytes = p.stage_bytes;
     out->mac_warps = p.nw;
+    out->mac_kernel = p.direct == 0 ? CONV_KERNEL_TMA : (p.direct == 1 ? CONV_KERNEL_DIRECT1 : CONV_KERNEL_DIRECT2);
     out->device_bytes = (long long)e->dev_bytes;
     out->kernels_per_block = 3;
     out->kernels_per_afc_block = 6;
@@ -922,21 +993,15 @@ int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches)
     return CONV_OK;
 }
 
-int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms, int bin_tile,
-                    int stages, int stage_kib, int splits, int warps) {
+int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms,
+                    const conv_tiling* t) {
     if (precision < CONV_FP32 || precision > CONV_BF16 || block < 16 || block > 4096 || (block & (block - 1)) ||
-        n_src < 1 || n_dst < 1 || taps < 1 || num_sms < 1 || bin_tile < 0 || stages < 0 || stage_kib < 0 ||
-        splits < 0 || (bin_tile && (bin_tile < 16 || bin_tile > 256 || (bin_tile & (bin_tile - 1)))) ||
-        (stages && (stages < 2 || stages > MAX_STAGES)) || stage_kib > 96 || (warps != 0 && warps != 8 && warps != 16))
+        n_src < 1 || n_dst < 1 || taps < 1 || num_sms < 1)
         return set_err(CONV_E_INVAL, "invalid plan arguments");
+    const TileOverride o = from_api(t);
+    if (const char* msg = check_override(o)) return set_err(CONV_E_INVAL, "%s", msg);
     const long long K = (taps + block - 1) / block;
     if ((long long)n_src * K > 0x7fffffffLL / 2) return set_err(CONV_E_INVAL, "too many partitions");
-    TileOverride o;
-    o.bin_tile = bin_tile;
-    o.stages = stages;
-    o.stage_kib = stage_kib;
-    o.splits = splits;
-    o.warps = warps;
     const MacPlan p = plan_mac(precision, block, n_src, n_dst, (int)K, num_sms, n_src, o);
     std::string why;
     if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());

@@ -443,6 +443,127 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) k_fdl_mac(const MacArgs a) {
     }
 }
 
+// ------------------------------------------------ FDL MAC, direct loads
+// Same work and output as k_fdl_mac, without the TMA producer: every thread
+// streams its own 16-byte loads straight from HBM (filter rows with the
+// streaming cache hint, delay-line rows through L1, where the threads of the
+// other output groups find them), U reduction indices in flight at a time.
+// Several CTAs share an SM (no stage ring in shared memory), so the grid has
+// more splits.  r-lanes are combined as in k_fdl_mac.
+template <int PREC>
+__device__ __forceinline__ void load16_global_stream(const void* p, float2 (&v)[Store<PREC>::VEC]) {
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    Store<PREC>::load16(&t, v);
+}
+
+template <int PREC, int LPT, int NW, int U, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_fdl_mac_ldg(const MacArgs a) {
+    using St = Store<PREC>;
+    constexpr int VEC = St::VEC;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x / a.S, split = blockIdx.x - tile * a.S;
+    const int kt = tile / a.n_lt, lt = tile - kt * a.n_lt;
+    const int l0 = lt * a.LT, LTt = min(a.LT, a.n_dst - l0);
+    const int K = a.K, R = a.n_src * K, Rt = R - a.r_begin;
+    const int r0 = a.r_begin + (int)((long long)split * Rt / a.S);
+    const int r1 = a.r_begin + (int)((long long)(split + 1) * Rt / a.S);
+    const int ring0 = a.slot0 * a.n_src;
+    const size_t hrow = (size_t)a.BT * St::BYTES;
+    const unsigned char* Hb = static_cast<const unsigned char*>(a.H) + (size_t)tile * a.tile_elems * St::BYTES;
+    const unsigned char* Xb = static_cast<const unsigned char*>(a.X) + (size_t)kt * R * hrow;
+    const int kv = tid % a.kthreads, rest = tid / a.kthreads;
+    const int lg = rest % a.NLG, rl = rest / a.NLG;
+    const int kglob = kt * a.BT + kv * VEC;
+    const bool dc = (kglob == 0);
+    float2 acc[LPT][VEC];
+#pragma unroll
+    for (int i = 0; i < LPT; ++i)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[i][v] = make_float2(0.0f, 0.0f);
+
+    griddep_launch_dependents();
+    griddep_wait();  // the delay line and the split partials belong to earlier kernels
+    const int step = a.NRL * U;
+    for (int rb = r0 + rl; rb < r1; rb += step) {
+        float2 hv[U][LPT][VEC];
+        float2 xv[U][VEC];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = rb + u * a.NRL;
+            if (r < r1) {
+                int row = ring0 + r;
+                if (row >= R) row -= R;
+                const float4 t = __ldg(reinterpret_cast<const float4*>(Xb + (size_t)row * hrow + (size_t)kv * 16));
+                St::load16(&t, xv[u]);
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) {
+                    const int ll = lg + i * a.NLG;
+                    if (ll < LTt) load16_global_stream<PREC>(Hb + ((size_t)r * LTt + ll) * hrow + (size_t)kv * 16, hv[u][i]);
+                }
+                if (PREC != PREC_FP32) {
+                    const float sc = __ldg(a.sX + row) * __ldg(a.sH + (size_t)lt * R + r);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) xv[u][v] = cscale(xv[u][v], sc);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (rb + u * a.NRL < r1) {
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) {
+                    if (lg + i * a.NLG < LTt) {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            if (v == 0 && dc)
+                                rmac2(acc[i][v], hv[u][i][v], xv[u][v]);
+                            else
+                                cmac(acc[i][v], hv[u][i][v], xv[u][v]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    if (a.NRL > 1) {
+        float2* red = reinterpret_cast<float2*>(smem);
+        const int LT = a.LT, BT = a.BT;
+        if (rl > 0) {
+#pragma unroll
+            for (int i = 0; i < LPT; ++i) {
+                const int ll = lg + i * a.NLG;
+                if (ll < LTt)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) red[((size_t)(rl - 1) * LT + ll) * BT + kv * VEC + v] = acc[i][v];
+            }
+        }
+        __syncthreads();
+        if (rl == 0) {
+            for (int rr = 1; rr < a.NRL; ++rr)
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) {
+                    const int ll = lg + i * a.NLG;
+                    if (ll < LTt)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v)
+                            acc[i][v] = cadd(acc[i][v], red[((size_t)(rr - 1) * LT + ll) * BT + kv * VEC + v]);
+                }
+        }
+    }
+    if (rl != 0) return;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        const int ll = lg + i * a.NLG;
+        if (ll < LTt) {
+            float2* dst = a.partial + ((size_t)split * a.n_dst + l0 + ll) * a.B + kglob;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) dst[v] = acc[i][v];
+        }
+    }
+}
+
 // --------------------------------------------- head + reduce + C2R + OLS
 // One CTA per output channel l.  Per bin: the fixed-order sum of the S split
 // partials (independent loads in groups of 8, pairwise within a group), then
@@ -579,6 +700,12 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR((k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>(), 16>), mac_smem)
     GB_ATTR((k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>(), 16>), mac_smem)
     GB_ATTR((k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>(), 16>), mac_smem)
+    GB_ATTR((k_fdl_mac_ldg<PREC_FP32, 4, 8, 1, 3>), mac_smem)
+    GB_ATTR((k_fdl_mac_ldg<PREC_FP16, 4, 8, 1, 3>), mac_smem)
+    GB_ATTR((k_fdl_mac_ldg<PREC_BF16, 4, 8, 1, 3>), mac_smem)
+    GB_ATTR((k_fdl_mac_ldg<PREC_FP32, 4, 8, 2, 2>), mac_smem)
+    GB_ATTR((k_fdl_mac_ldg<PREC_FP16, 4, 8, 2, 2>), mac_smem)
+    GB_ATTR((k_fdl_mac_ldg<PREC_BF16, 4, 8, 2, 2>), mac_smem)
 #undef GB_ATTR
     return cudaSuccess;
 }
@@ -630,7 +757,23 @@ cudaError_t launch_fdl_mac_nw(int prec, const MacPlan& p, const MacArgs& a, cuda
     }
 }
 
+template <int U, int MINB>
+cudaError_t launch_fdl_mac_direct_u(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
+    const dim3 grid(p.ctas), block(8 * 32);
+    switch (prec) {
+        case PREC_FP32: return launch_pdl(k_fdl_mac_ldg<PREC_FP32, 4, 8, U, MINB>, grid, block, p.smem, s, a);
+        case PREC_FP16: return launch_pdl(k_fdl_mac_ldg<PREC_FP16, 4, 8, U, MINB>, grid, block, p.smem, s, a);
+        case PREC_BF16: return launch_pdl(k_fdl_mac_ldg<PREC_BF16, 4, 8, U, MINB>, grid, block, p.smem, s, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fdl_mac_direct(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
+    return p.direct == 1 ? launch_fdl_mac_direct_u<1, 3>(prec, p, a, s) : launch_fdl_mac_direct_u<2, 2>(prec, p, a, s);
+}
+
 cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
+    if (p.direct) return launch_fdl_mac_direct(prec, p, a, s);
     switch (p.nw) {
         case 8: return launch_fdl_mac_nw<8>(prec, p, a, s);
         case 16: return launch_fdl_mac_nw<16>(prec, p, a, s);

@@ -50,6 +50,8 @@ struct MacPlan {
     int BT, n_kt;  // bin tile width, number of bin tiles
     int LT, n_lt;  // output tile height, number of output tiles
     int nw;        // consumer warps (8 or 16)
+    int direct;    // direct-load MAC (no TMA ring, 8 warps): 1 = one partition in flight per
+                   // thread, 3 CTAs/SM; 2 = two in flight, 2 CTAs/SM; 0 = TMA pipeline
     int kthreads, NLG, NRL;  // consumer thread layout: bins x output groups x r-lanes
     int RS;        // reduction indices per pipeline stage (the stage grid's pitch)
     int nstage;    // pipeline depth

@@ -37,6 +37,21 @@ class ConvError(RuntimeError):
         self.code = code
 
 
+CONV_KERNEL_AUTO = 0
+CONV_KERNEL_TMA = 1
+CONV_KERNEL_DIRECT1 = 2
+CONV_KERNEL_DIRECT2 = 3
+KERNELS = {"auto": 0, "tma": 1, "direct1": 2, "direct2": 3}
+
+
+class conv_tiling(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("kernel", "bin_tile", "stages", "stage_kib", "splits", "warps")]
+
+
+def make_tiling(kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0):
+    return conv_tiling(KERNELS.get(kernel, kernel), bin_tile, stages, stage_kib, splits, warps)
+
+
 class conv_info(ctypes.Structure):
     _fields_ = [
         (name, ctypes.c_longlong)
@@ -61,6 +76,7 @@ class conv_info(ctypes.Structure):
             "mac_stages",
             "mac_stage_bytes",
             "mac_warps",
+            "mac_kernel",
         )
     ]
 
@@ -92,7 +108,7 @@ def load():
         "conv_create": (vp, [d, i, i, i, ll]),
         "conv_set_precision": (i, [vp, i]),
         "conv_set_filters": (i, [vp, vp]),
-        "conv_set_tiling": (i, [vp, i, i, i, i, i]),
+        "conv_set_tiling": (i, [vp, ctypes.POINTER(conv_tiling)]),
         "afc_set_paths": (i, [vp, vp, ll]),
         "conv_process_block": (i, [vp, vp, vp]),
         "conv_process_block_async": (i, [vp, vp, vp, vp]),
@@ -104,7 +120,7 @@ def load():
         "conv_get_info": (i, [vp, ctypes.POINTER(conv_info)]),
         "conv_profile_enable": (i, [vp, i]),
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
-        "conv_plan_check": (i, [i, i, i, i, ll, i, i, i, i, i, i]),
+        "conv_plan_check": (i, [i, i, i, i, ll, i, ctypes.POINTER(conv_tiling)]),
         "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
         "conv_destroy": (None, [vp]),
         "conv_last_error": (ctypes.c_char_p, []),
@@ -173,8 +189,9 @@ def conv_set_precision(h, mode):
     return _check(load().conv_set_precision(h, int(mode)))
 
 
-def conv_set_tiling(h, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0):
-    return _check(load().conv_set_tiling(h, int(bin_tile), int(stages), int(stage_kib), int(splits), int(warps)))
+def conv_set_tiling(h, kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0):
+    t = make_tiling(kernel, bin_tile, stages, stage_kib, splits, warps)
+    return _check(load().conv_set_tiling(h, ctypes.byref(t)))
 
 
 def conv_set_filters(h, filters: np.ndarray):
@@ -241,13 +258,13 @@ def conv_profile_read(h):
 
 
 def conv_plan_check(
-    precision, block, n_src, n_dst, taps, num_sms=152, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0
+    precision, block, n_src, n_dst, taps, num_sms=152, kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0
 ):
     precision = PRECISIONS.get(precision, precision)
+    t = make_tiling(kernel, bin_tile, stages, stage_kib, splits, warps)
     return _check(
         load().conv_plan_check(
-            int(precision), int(block), int(n_src), int(n_dst), int(taps), int(num_sms), int(bin_tile), int(stages),
-            int(stage_kib), int(splits), int(warps),
+            int(precision), int(block), int(n_src), int(n_dst), int(taps), int(num_sms), ctypes.byref(t)
         )
     )
 
@@ -277,12 +294,14 @@ def _dims(h):
 class Engine:
     """Owning wrapper: ``with Engine(fs, block, n_in, n_out, taps) as e: ...``."""
 
-    def __init__(self, fs, block, n_in, n_out, taps, precision="fp32"):
+    def __init__(self, fs, block, n_in, n_out, taps, precision="fp32", tiling=None):
         self.h = conv_create(fs, block, n_in, n_out, taps)
         self.shape = (int(n_in), int(n_out), int(block))
         try:
             if precision not in ("fp32", CONV_FP32):
                 conv_set_precision(self.h, precision)
+            if tiling:
+                conv_set_tiling(self.h, **tiling)
         except Exception:
             conv_destroy(self.h)
             raise

@@ -100,7 +100,8 @@ def test_mac_plan_addresses_stay_in_bounds(lib, precision):
     for B in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096):
         for n_src, n_dst, taps in shapes:
             for sms in (152, 148, 8):
-                upols.conv_plan_check(precision, B, n_src, n_dst, taps, sms)
+                for kernel in ("auto", "direct1", "direct2"):
+                    upols.conv_plan_check(precision, B, n_src, n_dst, taps, sms, kernel)
 
 
 def test_tiling_overrides_stay_in_bounds(lib):
@@ -111,9 +112,14 @@ def test_tiling_overrides_stay_in_bounds(lib):
                 for bt in (16, 32, 64, 128, 256):
                     for stages, kib in ((2, 64), (3, 32), (4, 48), (5, 32), (8, 16), (8, 24)):
                         for splits, nw in ((0, 0), (1, 8), (9, 16), (38, 8), (1000000, 16)):
-                            upols.conv_plan_check(precision, B, n_src, n_dst, taps, 152, bt, stages, kib, splits, nw)
+                            for kernel in ("tma", "direct1", "direct2"):
+                                upols.conv_plan_check(
+                                    precision, B, n_src, n_dst, taps, 152, kernel, bt, stages, kib, splits, nw
+                                )
 
 
 def test_tiling_override_arguments_are_validated(lib):
     with pytest.raises(upols.ConvError):
-        upols.conv_plan_check("fp32", 256, 4, 16, 384000, 152, 24, 0, 0, 0, 0)  # not a power of two
+        upols.conv_plan_check("fp32", 256, 4, 16, 384000, 152, 0, 24)  # bin tile not a power of two
+    with pytest.raises(upols.ConvError):
+        upols.conv_plan_check("fp32", 256, 4, 16, 384000, 152, 7)  # unknown kernel

@@ -34,11 +34,11 @@ def engine_lib():
     U.load()
 
 
-def run_gpu(w, precision="fp32", n_blocks=None):
+def run_gpu(w, precision="fp32", n_blocks=None, tiling=None):
     x = w.x
     if n_blocks is not None:
         x = x[:, : n_blocks * w.block]
-    with U.Engine(w.fs, w.block, w.n_in, w.n_out, w.taps, precision) as e:
+    with U.Engine(w.fs, w.block, w.n_in, w.n_out, w.taps, precision, tiling) as e:
         e.set_filters(w.h)
         return e.run(x)
 
@@ -125,6 +125,28 @@ def test_random_shapes_fp32(n_in, n_out, taps, B, nb):
     ref = oracle_out(w)
     assert snr_db(y, ref) >= FP32_DB
     assert min(snr_per_channel_db(y, ref)) >= FP32_CH_DB
+
+
+TILINGS = [
+    {"kernel": "tma"},
+    {"kernel": "tma", "warps": 16},
+    {"kernel": "tma", "stages": 4, "stage_kib": 16},
+    {"kernel": "tma", "bin_tile": 16, "splits": 3},
+    {"kernel": "direct1"},
+    {"kernel": "direct2"},
+    {"kernel": "direct1", "bin_tile": 64, "splits": 5},
+]
+
+
+@pytest.mark.parametrize("tiling", TILINGS, ids=lambda t: "-".join(f"{k}{v}" for k, v in t.items()))
+@pytest.mark.parametrize("precision,bound", [("fp32", FP32_DB), ("fp16", FP16_DB)])
+@pytest.mark.parametrize("n_in,n_out,taps,B,nb", [(3, 20, 2500, 64, 50), (2, 5, 9000, 256, 40)])
+def test_mac_kernels_and_tilings(tiling, precision, bound, n_in, n_out, taps, B, nb):
+    """Every MAC kernel and several tilings (ragged output tiles, ring wrap) against the oracle."""
+    w = signals.random_case(4000 + taps + B, n_in, n_out, taps, B, nb)
+    y = run_gpu(w, precision, tiling=tiling)
+    ref = oracle_out(w)
+    assert snr_db(y, ref) >= bound
 
 
 @pytest.mark.parametrize("precision,bound", [("fp16", FP16_DB), ("bf16", BF16_DB)])
