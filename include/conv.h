@@ -97,10 +97,15 @@ int conv_set_precision(conv_engine* e, int mode);
  *   stages     TMA ring depth, [2, 8]
  *   stage_kib  target bytes of filter spectra per TMA stage, KiB, [1, 96]
  *   splits     partition splits per tile (capped at what the tile allows)
- *   warps      TMA consumer warps, 8 or 16 */
+ *   warps      TMA consumer warps, 8 or 16
+ *   order      CONV_ORDER_*: how the TMA kernel's stages are dealt to splits */
 typedef struct conv_tiling {
-    int kernel, bin_tile, stages, stage_kib, splits, warps;
+    int kernel, bin_tile, stages, stage_kib, splits, warps, order;
 } conv_tiling;
+
+#define CONV_ORDER_AUTO 0        /* planner's choice                                  */
+#define CONV_ORDER_CONTIGUOUS 1  /* split s streams one contiguous range of stages    */
+#define CONV_ORDER_INTERLEAVED 2 /* split s streams stages s, s+S, s+2S, ...          */
 
 /* Fix the synthesis FDL MAC tiling instead of the planner's choice (the hook
  * the autotuner uses).  t may be NULL (all automatic).  Re-plans and

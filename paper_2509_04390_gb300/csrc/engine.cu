@@ -69,7 +69,7 @@ inline int pow2_ceil(int v) {
 
 // Tiling fields a caller (the autotuner) may fix; 0 leaves a field to the planner.
 struct TileOverride {
-    int kernel = 0, bin_tile = 0, stages = 0, stage_kib = 0, splits = 0, warps = 0;
+    int kernel = 0, bin_tile = 0, stages = 0, stage_kib = 0, splits = 0, warps = 0, order = 0;
 };
 
 TileOverride from_api(const conv_tiling* t) {
@@ -81,6 +81,7 @@ TileOverride from_api(const conv_tiling* t) {
         o.stage_kib = t->stage_kib;
         o.splits = t->splits;
         o.warps = t->warps;
+        o.order = t->order;
     }
     return o;
 }
@@ -93,6 +94,7 @@ const char* check_override(const TileOverride& o) {
     if (o.stage_kib < 0 || o.stage_kib > 96) return "stage_kib must be in [0, 96]";
     if (o.splits < 0) return "splits must be >= 0";
     if (o.warps != 0 && o.warps != 8 && o.warps != 16) return "warps must be 0, 8 or 16";
+    if (o.order < 0 || o.order > 2) return "order must be 0, 1 or 2";
     return nullptr;
 }
 
@@ -122,6 +124,7 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     p.direct = o.kernel == CONV_KERNEL_DIRECT1 ? 1 : (o.kernel == CONV_KERNEL_DIRECT2 ? 2 : 0);
     p.LPT = (prec == PREC_FP32 && !p.direct) ? 8 : 4;
     p.nw = p.direct ? 8 : (o.warps ? o.warps : MAC_CONSUMER_WARPS);
+    p.interleave = (!p.direct && o.order == CONV_ORDER_INTERLEAVED) ? 1 : 0;
     p.LT = std::min(n_dst, 16);
     p.n_lt = (n_dst + p.LT - 1) / p.LT;
     // Bin tiles: enough (bin tile x output tile) pairs that ~16-20 partition
@@ -286,13 +289,14 @@ int check_plan(const MacPlan& p, std::string* why) {
         if (kt >= p.n_kt) return bad("tile index");
         const int l0 = lt * p.LT, LTt = std::min(p.LT, p.n_dst - l0);
         if (LTt < 1) return bad("empty output tile");
-        const int g0 = gb + (int)((long long)split * gt / p.S);
-        const int g1 = gb + (int)((long long)(split + 1) * gt / p.S);
+        const int g0 = p.interleave ? gb + split : gb + (int)((long long)split * gt / p.S);
+        const int g1 = p.interleave ? gb + gt : gb + (int)((long long)(split + 1) * gt / p.S);
+        const int gstep = p.interleave ? p.S : 1;
         if (g1 <= g0) return bad("empty split");
         const size_t hr = (size_t)LTt * hrow;
         const size_t hb = (size_t)tile * p.tile_elems * p.es;
         const size_t xb = (size_t)kt * p.R * hrow;
-        for (int g = g0; g < g1; ++g) {
+        for (int g = g0; g < g1; g += gstep) {
             const int ra = std::max(p.r_begin, g * p.RS), rb = std::min(p.R, (g + 1) * p.RS), nr = rb - ra;
             if (nr < 1) return bad("empty stage");
             const size_t tx = (size_t)nr * (hr + hrow);
@@ -581,6 +585,7 @@ int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool ti
     a.RS = p.RS;
     a.nstage = p.nstage;
     a.r_begin = p.r_begin;
+    a.interleave = p.interleave;
     a.kthreads = p.kthreads;
     a.NLG = p.NLG;
     a.NRL = p.NRL;

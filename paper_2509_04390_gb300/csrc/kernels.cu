@@ -224,9 +224,12 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) k_fdl_mac(const MacArgs a) {
     const int l0 = lt * a.LT, LTt = min(a.LT, a.n_dst - l0);
     const int K = a.K, R = a.n_src * K;
     const int gb = a.r_begin / a.RS, gt = (R + a.RS - 1) / a.RS - gb;  // stage grid
-    const int g0 = gb + (int)((long long)split * gt / a.S);
-    const int g1 = gb + (int)((long long)(split + 1) * gt / a.S);
-    const int nit = g1 - g0;
+    // contiguous: split s owns stages [g0, g1); interleaved: stages gb + s + i*S,
+    // so the tile's CTAs sweep the spectra side by side
+    const int g0 = a.interleave ? gb + split : gb + (int)((long long)split * gt / a.S);
+    const int g1 = a.interleave ? gb + gt : gb + (int)((long long)(split + 1) * gt / a.S);
+    const int gstep = a.interleave ? a.S : 1;
+    const int nit = g1 > g0 ? (g1 - g0 + gstep - 1) / gstep : 0;
     const int ring0 = a.slot0 * a.n_src;  // ring row of r = 0
     const size_t hrow = (size_t)a.BT * St::BYTES;
     const size_t hr_bytes = (size_t)LTt * hrow;
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) k_fdl_mac(const MacArgs a) {
         static_cast<const unsigned char*>(a.H) + (size_t)tile * a.tile_elems * St::BYTES;
     const unsigned char* Xb = static_cast<const unsigned char*>(a.X) + (size_t)kt * R * hrow;
     auto stage_range = [&](int it, int& ra, int& rb) {
-        const int g = g0 + it;
+        const int g = g0 + it * gstep;
         ra = max(a.r_begin, g * a.RS);
         rb = min(R, (g + 1) * a.RS);
     };

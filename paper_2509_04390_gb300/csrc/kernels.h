@@ -50,6 +50,7 @@ struct MacPlan {
     int BT, n_kt;  // bin tile width, number of bin tiles
     int LT, n_lt;  // output tile height, number of output tiles
     int nw;        // consumer warps (8 or 16)
+    int interleave;  // TMA MAC: 1 = split s takes stages s, s+S, ... (else contiguous ranges)
     int direct;    // direct-load MAC (no TMA ring, 8 warps): 1 = one partition in flight per
                    // thread, 3 CTAs/SM; 2 = two in flight, 2 CTAs/SM; 0 = TMA pipeline
     int kthreads, NLG, NRL;  // consumer thread layout: bins x output groups x r-lanes
@@ -72,6 +73,7 @@ struct MacArgs {
     float2* partial;  // [S][n_dst][B]
     int B, BT, n_kt, n_dst, LT, n_lt, n_src, K, S, RS, nstage;
     int r_begin;
+    int interleave;
     int kthreads, NLG, NRL;
     int slot0;  // ring slot of partition 0 for the block this MAC serves
     unsigned stage_bytes, xoff, soff, sxoff;

@@ -45,11 +45,16 @@ KERNELS = {"auto": 0, "tma": 1, "direct1": 2, "direct2": 3}
 
 
 class conv_tiling(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int) for n in ("kernel", "bin_tile", "stages", "stage_kib", "splits", "warps")]
+    _fields_ = [(n, ctypes.c_int) for n in ("kernel", "bin_tile", "stages", "stage_kib", "splits", "warps", "order")]
 
 
-def make_tiling(kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0):
-    return conv_tiling(KERNELS.get(kernel, kernel), bin_tile, stages, stage_kib, splits, warps)
+ORDERS = {"auto": 0, "contiguous": 1, "interleaved": 2}
+
+
+def make_tiling(kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0, order=0):
+    return conv_tiling(
+        KERNELS.get(kernel, kernel), bin_tile, stages, stage_kib, splits, warps, ORDERS.get(order, order)
+    )
 
 
 class conv_info(ctypes.Structure):
@@ -189,8 +194,8 @@ def conv_set_precision(h, mode):
     return _check(load().conv_set_precision(h, int(mode)))
 
 
-def conv_set_tiling(h, kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0):
-    t = make_tiling(kernel, bin_tile, stages, stage_kib, splits, warps)
+def conv_set_tiling(h, kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0, order=0):
+    t = make_tiling(kernel, bin_tile, stages, stage_kib, splits, warps, order)
     return _check(load().conv_set_tiling(h, ctypes.byref(t)))
 
 
@@ -258,10 +263,11 @@ def conv_profile_read(h):
 
 
 def conv_plan_check(
-    precision, block, n_src, n_dst, taps, num_sms=152, kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0
+    precision, block, n_src, n_dst, taps, num_sms=152, kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0,
+    warps=0, order=0,
 ):
     precision = PRECISIONS.get(precision, precision)
-    t = make_tiling(kernel, bin_tile, stages, stage_kib, splits, warps)
+    t = make_tiling(kernel, bin_tile, stages, stage_kib, splits, warps, order)
     return _check(
         load().conv_plan_check(
             int(precision), int(block), int(n_src), int(n_dst), int(taps), int(num_sms), ctypes.byref(t)

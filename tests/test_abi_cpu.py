@@ -112,9 +112,9 @@ def test_tiling_overrides_stay_in_bounds(lib):
                 for bt in (16, 32, 64, 128, 256):
                     for stages, kib in ((2, 64), (3, 32), (4, 48), (5, 32), (8, 16), (8, 24)):
                         for splits, nw in ((0, 0), (1, 8), (9, 16), (38, 8), (1000000, 16)):
-                            for kernel in ("tma", "direct1", "direct2"):
+                            for kernel, order in (("tma", 1), ("tma", 2), ("direct1", 0), ("direct2", 0)):
                                 upols.conv_plan_check(
-                                    precision, B, n_src, n_dst, taps, 152, kernel, bt, stages, kib, splits, nw
+                                    precision, B, n_src, n_dst, taps, 152, kernel, bt, stages, kib, splits, nw, order
                                 )
 
 

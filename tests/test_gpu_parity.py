@@ -132,6 +132,8 @@ TILINGS = [
     {"kernel": "tma", "warps": 16},
     {"kernel": "tma", "stages": 4, "stage_kib": 16},
     {"kernel": "tma", "bin_tile": 16, "splits": 3},
+    {"kernel": "tma", "order": "interleaved"},
+    {"kernel": "tma", "order": "interleaved", "stages": 3, "stage_kib": 8, "splits": 7},
     {"kernel": "direct1"},
     {"kernel": "direct2"},
     {"kernel": "direct1", "bin_tile": 64, "splits": 5},
