@@ -165,7 +165,9 @@ int conv_synchronize(conv_engine* e);
 int conv_get_info(const conv_engine* e, conv_info* out);
 
 /* Kernel timing: while enabled, every block records CUDA events around the
- * synthesis FDL MAC kernel on the stream it is launched on.  conv_profile_read
+ * synthesis FDL MAC kernel on the stream it is launched on, and consecutive
+ * MAC launches are kept from overlapping (so each duration is the kernel's
+ * own).  conv_profile_read
  * waits for the recorded work, returns the summed kernel time in milliseconds
  * and the number of launches timed, and clears the record. */
 int conv_profile_enable(conv_engine* e, int enable);

@@ -14,11 +14,16 @@
 // spectrum is in the delay line.  When block n+1 arrives, the caller's stream
 // runs only the pack/R2C of the new block and one output kernel that adds
 // partition 0 (the "head") to the tail's split partials and transforms back.
-// Tail partials are double-buffered by block parity:
-//   caller stream:  pack(n) -> [rec packed] -> [wait tail(n)] -> out(n)
-//   background:     [wait packed(n)] -> tail(n+1) -> [rec tail]
+// Tail partials are double-buffered by block parity, and the tails alternate
+// between two background streams so that, when blocks come back to back, the
+// tail of block n+1 takes over each SM as the tail of block n leaves it (no
+// drain and ramp of the HBM stream between blocks):
+//   caller stream:      pack(n) -> [rec packed] -> [wait tail(n)] -> out(n)
+//   background n+1 & 1: [wait packed(n)] -> tail(n+1) -> [rec tail(n+1 & 1)]
 // pack(n+1) overwrites the ring slot of block n+1-K, which tail(n) (already
 // waited for by out(n)) was the last to read; tail(n+1) never reads it.
+// tail(n+2) reuses the partials out(n) read; it waits for pack(n+1), which
+// the caller stream runs after out(n).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -346,8 +351,8 @@ struct Part {
     float* sX = nullptr;
     float* win = nullptr;
     float2* partial[2] = {nullptr, nullptr};  // tail partials, by block parity
-    cudaEvent_t ev_packed = nullptr;          // this block's spectrum is in the ring
-    cudaEvent_t ev_tail = nullptr;            // the next block's tail partials are ready
+    cudaEvent_t ev_packed = nullptr;           // this block's spectrum is in the ring
+    cudaEvent_t ev_tail[2] = {nullptr, nullptr};  // tail partials of the block of that parity are ready
     bool allocated = false;
     bool ready = false;
 };
@@ -381,7 +386,7 @@ struct conv_engine {
     int prec = CONV_FP32;
     int num_sms = 0;
     cudaStream_t stream = nullptr;     // the engine's own stream for host-buffer calls
-    cudaStream_t bg = nullptr;         // low-priority stream for the tail MACs
+    cudaStream_t bg[2] = {nullptr, nullptr};  // low-priority streams for the tail MACs, by block parity
     cudaEvent_t ev_done = nullptr;     // output of the current host-buffer call is on the host
     float2* tw = nullptr;
     float *d_in = nullptr, *d_out = nullptr, *d_e = nullptr, *d_c = nullptr;
@@ -468,7 +473,8 @@ int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps,
     if ((rc = dev_alloc(e, &P.partial[0], p.partial_bytes))) return rc;
     if ((rc = dev_alloc(e, &P.partial[1], p.partial_bytes))) return rc;
     if (!P.ev_packed) CK(cudaEventCreateWithFlags(&P.ev_packed, cudaEventDisableTiming));
-    if (!P.ev_tail) CK(cudaEventCreateWithFlags(&P.ev_tail, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i)
+        if (!P.ev_tail[i]) CK(cudaEventCreateWithFlags(&P.ev_tail[i], cudaEventDisableTiming));
     if ((rc = dev_alloc(e, &P.win, (size_t)n_src * e->B * sizeof(float)))) return rc;
     if (e->prec != PREC_FP32) {
         // +4 floats: scale runs are read widened to 16-byte boundaries
@@ -487,7 +493,8 @@ int part_reset(conv_engine* e, Part& P) {
     if (P.sX) CK(cudaMemsetAsync(P.sX, 0, ((size_t)P.plan.R + 4) * sizeof(float), e->stream));
     CK(cudaMemsetAsync(P.partial[0], 0, P.plan.partial_bytes, e->stream));
     CK(cudaMemsetAsync(P.partial[1], 0, P.plan.partial_bytes, e->stream));
-    CK(cudaEventRecord(P.ev_tail, e->stream));  // block 0's tail: zero partials
+    CK(cudaEventRecord(P.ev_tail[0], e->stream));  // block 0's tail: zero partials
+    CK(cudaEventRecord(P.ev_tail[1], e->stream));
     return CONV_OK;
 }
 
@@ -642,11 +649,14 @@ int enqueue_conv(conv_engine* e, Part& P, const float* src, const float* sub, fl
     const long long n = e->nblk;
     if ((rc = enqueue_pack(e, P, src, e->B, sub, e_out, s))) return rc;
     CK(cudaEventRecord(P.ev_packed, s));
-    CK(cudaStreamWaitEvent(s, P.ev_tail, 0));
+    CK(cudaStreamWaitEvent(s, P.ev_tail[n & 1], 0));
     if ((rc = enqueue_out(e, P, n, out, s))) return rc;
-    CK(cudaStreamWaitEvent(e->bg, P.ev_packed, 0));
-    if ((rc = enqueue_tail(e, P, n + 1, e->bg, timed))) return rc;
-    CK(cudaEventRecord(P.ev_tail, e->bg));
+    cudaStream_t bg = e->bg[(n + 1) & 1];
+    CK(cudaStreamWaitEvent(bg, P.ev_packed, 0));
+    // kernel timing needs each tail alone on the GPU: then tails run one after another
+    if (timed && e->prof) CK(cudaStreamWaitEvent(bg, P.ev_tail[n & 1], 0));
+    if ((rc = enqueue_tail(e, P, n + 1, bg, timed))) return rc;
+    CK(cudaEventRecord(P.ev_tail[(n + 1) & 1], bg));
     return CONV_OK;
 }
 
@@ -661,7 +671,8 @@ int check_dev_err(conv_engine* e) {
 
 int engine_reset(conv_engine* e) {
     int rc;
-    CK(cudaStreamSynchronize(e->bg));
+    CK(cudaStreamSynchronize(e->bg[0]));
+    CK(cudaStreamSynchronize(e->bg[1]));
     CK(cudaStreamSynchronize(e->stream));
     if ((rc = part_reset(e, e->syn))) return rc;
     if ((rc = part_reset(e, e->fb))) return rc;
@@ -696,10 +707,12 @@ void engine_free(conv_engine* e) {
     if (!e) return;
     DeviceGuard g(e->dev);
     if (e->stream) cudaStreamSynchronize(e->stream);
-    if (e->bg) cudaStreamSynchronize(e->bg);
+    for (int i = 0; i < 2; ++i)
+        if (e->bg[i]) cudaStreamSynchronize(e->bg[i]);
     for (Part* P : {&e->syn, &e->fb}) {
         if (P->ev_packed) cudaEventDestroy(P->ev_packed);
-        if (P->ev_tail) cudaEventDestroy(P->ev_tail);
+        for (int i = 0; i < 2; ++i)
+            if (P->ev_tail[i]) cudaEventDestroy(P->ev_tail[i]);
     }
     part_free(e, e->syn);
     part_free(e, e->fb);
@@ -715,7 +728,8 @@ void engine_free(conv_engine* e) {
     for (auto ev : e->ev0) cudaEventDestroy(ev);
     for (auto ev : e->ev1) cudaEventDestroy(ev);
     if (e->ev_done) cudaEventDestroy(e->ev_done);
-    if (e->bg) cudaStreamDestroy(e->bg);
+    for (int i = 0; i < 2; ++i)
+        if (e->bg[i]) cudaStreamDestroy(e->bg[i]);
     if (e->stream) cudaStreamDestroy(e->stream);
     delete e;
 }
@@ -741,7 +755,7 @@ int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long 
     int prio_low = 0, prio_high = 0;
     CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
     CK(cudaStreamCreateWithPriority(&e->stream, cudaStreamNonBlocking, prio_high));
-    CK(cudaStreamCreateWithPriority(&e->bg, cudaStreamNonBlocking, prio_low));
+    for (int i = 0; i < 2; ++i) CK(cudaStreamCreateWithPriority(&e->bg[i], cudaStreamNonBlocking, prio_low));
     // spin-wait on completion: a blocking wait would add the host's wake-up latency to every block
     CK(cudaEventCreateWithFlags(&e->ev_done, cudaEventDisableTiming));
     // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once to FP32
@@ -924,7 +938,8 @@ int conv_reset(conv_engine* e) {
 int conv_synchronize(conv_engine* e) {
     if (!e) return set_err(CONV_E_INVAL, "null handle");
     DeviceGuard g(e->dev);
-    CK(cudaStreamSynchronize(e->bg));
+    CK(cudaStreamSynchronize(e->bg[0]));
+    CK(cudaStreamSynchronize(e->bg[1]));
     CK(cudaStreamSynchronize(e->stream));
     CK(cudaDeviceSynchronize());
     return check_dev_err(e);
