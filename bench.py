@@ -175,6 +175,14 @@ def tapch(w):
     return float(w.n_in) * w.n_out * w.taps * w.block
 
 
+def step_extra_bytes(w, info):
+    """Algorithmic bytes of a step outside the tail MAC: the head partition
+    (filters + delay-line row), the new spectrum written, input and output."""
+    s = 8 if info["precision"] == 0 else 4
+    B = w.block
+    return int((w.n_out + 1) * w.n_in * B * s + w.n_in * B * s + (w.n_in + w.n_out) * B * 4)
+
+
 # ----------------------------------------------------------- CPU baseline
 
 
@@ -444,6 +452,13 @@ def run_ours(args):
                     "blocks": len(paced_us),
                     "mode": "one call per block period (real-time use)",
                 },
+            },
+            "step_bandwidth": {
+                "algorithmic_bytes_per_step": info["mac_bytes"] + step_extra_bytes(w, info),
+                "achieved_gbs": (info["mac_bytes"] + step_extra_bytes(w, info)) / (t_max / args.steps) / 1e9,
+                "frac_of_peak": (info["mac_bytes"] + step_extra_bytes(w, info)) / (t_max / args.steps) / 1e9 / peak,
+                "note": "whole step (pack, head + output, tail MAC) back to back; consecutive blocks' tail MACs "
+                        "overlap on two streams, and the delay line (n_in*K*B*s bytes) is L2-resident",
             },
             "roofline": {
                 "bound": "hbm",
