@@ -164,15 +164,24 @@ class ClockSampler:
 def make_workload(args):
     from paper_2509_04390_gb300 import signals
 
+    if args.afc:
+        return signals.afc_4x16(block=args.block, seconds=args.seconds, taps=args.taps, taps_fb=args.taps_fb)
     return signals.paper_4x16(block=args.block, seconds=args.seconds, taps=args.taps)
 
 
 def workload_name(args):
+    if args.afc:
+        return f"afc_4x16_{args.taps}taps_fb{args.taps_fb}_B{args.block}_{args.precision}"
     return f"paper_4x16_{args.taps}taps_B{args.block}_{args.precision}"
 
 
 def tapch(w):
-    return float(w.n_in) * w.n_out * w.taps * w.block
+    """Time-domain-equivalent tap*channel MACs of one block (both convolutions
+    when the feedback canceller runs)."""
+    t = float(w.n_in) * w.n_out * w.taps
+    if w.f is not None:
+        t += float(w.f.shape[0]) * w.f.shape[1] * w.f.shape[2]
+    return t * w.block
 
 
 def step_extra_bytes(w, info):
@@ -306,6 +315,8 @@ def run_ours(args):
     prec = args.precision
     eng = U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, prec)
     eng.set_filters(w.h)
+    if args.afc:
+        eng.set_paths(w.f)
     info = eng.info()
     nb = w.x.shape[1] // B
     d_x = torch.from_numpy(np.ascontiguousarray(w.x[:, : nb * B])).cuda()
@@ -315,7 +326,16 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(i):
-        U.conv_process_block_async(eng.h, d_blocks[i % nb], d_out[i & 1], stream)
+        if args.afc:
+            U.afc_process_block_async(eng.h, d_blocks[i % nb], d_out[i & 1], None, stream)
+        else:
+            U.conv_process_block_async(eng.h, d_blocks[i % nb], d_out[i & 1], stream)
+
+    def host_call(h_in, h_out):
+        if args.afc:
+            U.afc_process_block(eng.h, h_in, h_out, None, (w.n_in, w.n_out, B))
+        else:
+            U.conv_process_block(eng.h, h_in, h_out, (w.n_in, w.n_out, B))
 
     for i in range(args.warmup):
         step(i)
@@ -364,7 +384,7 @@ def run_ours(args):
     lat = []
     for i in range(min(args.warmup, 50)):
         np.copyto(h_in, w.x[:, (i % nb) * B : (i % nb + 1) * B])
-        U.conv_process_block(eng.h, h_in, h_out, (w.n_in, w.n_out, B))
+        host_call(h_in, h_out)
     if dist is not None:
         dist.barrier()
     te0 = time.perf_counter()
@@ -372,7 +392,7 @@ def run_ours(args):
         j = (i + 50) % nb
         t0 = time.perf_counter_ns()
         np.copyto(h_in, w.x[:, j * B : (j + 1) * B])
-        U.conv_process_block(eng.h, h_in, h_out, (w.n_in, w.n_out, B))
+        host_call(h_in, h_out)
         lat.append(time.perf_counter_ns() - t0)
     te1 = time.perf_counter()
     e_t, e_units = aggregate(te1 - te0, tapch(w) * e2e_steps, dist)
@@ -391,7 +411,7 @@ def run_ours(args):
             j = (i + 50 + e2e_steps) % nb
             t0 = time.perf_counter_ns()
             np.copyto(h_in, w.x[:, j * B : (j + 1) * B])
-            U.conv_process_block(eng.h, h_in, h_out, (w.n_in, w.n_out, B))
+            host_call(h_in, h_out)
             paced.append(time.perf_counter_ns() - t0)
             t_next += period_ns
     paced_us = np.array(paced) / 1e3 if paced else None
@@ -402,7 +422,7 @@ def run_ours(args):
     achieved = info["mac_bytes"] / mac_avg_s / 1e9 if mac_n else None
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and not args.afc:
         cv, per_block, nblk, n_sub = time_oracle(w, args.cpu_budget)
         cpu = {
             "value": cv,
@@ -476,7 +496,7 @@ def run_ours(args):
                           f"({elapsed_prof / args.steps * 1e6:.1f} us per step there)",
             },
             "cpu_baseline": cpu,
-            "gpu_launches": args.steps * info["kernels_per_block"],
+            "gpu_launches": args.steps * (info["kernels_per_afc_block"] if args.afc else info["kernels_per_block"]),
             "clocks": clk,
             "plan": {k: info[k] for k in ("K", "mac_ctas", "mac_splits", "mac_smem", "device_bytes")},
         }
@@ -498,6 +518,8 @@ def parse(argv=None):
     ap.add_argument("--taps", type=int, default=384000)
     ap.add_argument("--seconds", type=float, default=30.0)
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--afc", action="store_true", help="synthesis + feedback canceller (paths [4][16], 0.5 s)")
+    ap.add_argument("--taps-fb", type=int, default=24000)
     ap.add_argument("--e2e-steps", type=int, default=5000)
     ap.add_argument("--paced-blocks", type=int, default=1000)
     ap.add_argument("--cpu-budget", type=float, default=20.0)

@@ -274,3 +274,28 @@ def test_closed_loop_perfect_estimate_removes_feedback():
     ref = upols(h.astype(np.float64), s.astype(np.float64), B)
     assert snr_db(e, s) >= 110.0  # the error signal is the dry source
     assert snr_db(y, ref) >= 110.0  # and the output is open-loop synthesis of it
+
+
+# ------------------------------------------ feedback loop at paper scale
+
+
+@pytest.mark.parametrize("precision,bound", [("fp32", 110.0), ("fp16", 55.0), ("bf16", 38.0)])
+def test_closed_loop_paper_scale(precision, bound):
+    """4 mics x 16 loudspeakers, 8 s synthesis filters, 0.5 s feedback paths at
+    -20 dB (F_hat = F), block 256, closed loop in a simulated room: the error
+    signal must be the dry source and the output its open-loop synthesis (the
+    definition, Eq. 2, at sampled points)."""
+    w = signals.afc_4x16(block=256, seconds=2.2)
+    B = w.block
+    nb = w.x.shape[1] // B
+    s = np.ascontiguousarray(w.x[:, : nb * B])
+    y, e = run_gpu_closed_loop(w.h, w.f, w.f, s, B, precision)
+    s_e = snr_db(e, s)
+    rng = np.random.default_rng(7)
+    pts = sample_points(rng, w.n_out, 0, nb * B, 120)
+    ref = np.array([mimo_fir_sample(w.h, s, l, t) for l, t in pts])
+    got = np.array([y[l, t] for l, t in pts])
+    s_y = snr_db(got, ref)
+    print(f"closed loop {precision}: e vs s {s_e:.1f} dB, output {s_y:.1f} dB")
+    assert s_e >= bound
+    assert s_y >= bound
