@@ -213,6 +213,47 @@ int conv_plan_check(int precision, int block, int n_src, int n_dst, long long ta
 int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int block, int n_in, int n_out, long long K,
                          long long slot0, float* d_y, void* cuda_stream);
 
+/* ---------------------------------------------------------------- batches
+ * A batch processes one block of each of many independent sessions per step
+ * with one launch per stage for all of them (batched pack + R2C, batched
+ * head + output, batched tail MAC for the next block), whatever their block
+ * sizes, channel counts, filter lengths and tilings.  Sessions keep their own
+ * state; a session in a batch must not be processed on its own (add/remove
+ * hand it over).  All sessions of a batch share the batch's precision and use
+ * the TMA MAC with 8 consumer warps; batches run synthesis only. */
+typedef struct conv_batch conv_batch;
+
+/* Create an empty batch for sessions of the given precision on the current
+ * device.  NULL on failure (conv_last_error()). */
+conv_batch* conv_batch_create(int precision);
+
+/* Add a session (filters set, no feedback paths).  Waits for the session's
+ * own outstanding work and the batch's. */
+int conv_batch_add(conv_batch* b, conv_engine* e);
+
+/* Remove a session; it can be processed on its own again afterwards. */
+int conv_batch_remove(conv_batch* b, conv_engine* e);
+
+/* Number of sessions. */
+int conv_batch_size(const conv_batch* b);
+
+/* One block of every session, in the order they were added: d_in[i] is the
+ * device buffer [n_in_i][block_i] of session i, d_out[i] its output
+ * [n_out_i][block_i].  d_in/d_out are host arrays of device pointers, read
+ * during the call.  Enqueued on `cuda_stream` (NULL: the batch's own
+ * stream); returns once enqueued.  Consecutive calls must use the same
+ * stream. */
+int conv_batch_process_async(conv_batch* b, const float* const* d_in, float* const* d_out, void* cuda_stream);
+
+/* Wait for all of the batch's work; report a device-side error of any session. */
+int conv_batch_synchronize(conv_batch* b);
+
+/* Algorithmic bytes of one step's batched tail MAC (all sessions). */
+long long conv_batch_step_bytes(const conv_batch* b);
+
+/* Free the batch (its sessions are left intact and usable on their own).  NULL-safe. */
+void conv_batch_destroy(conv_batch* b);
+
 /* Free everything the handle owns.  NULL-safe. */
 void conv_destroy(conv_engine* e);
 

@@ -548,8 +548,10 @@ inline int slot0_for(long long n, int K) {
     return m == 0 ? 0 : K - m;
 }
 
-int enqueue_pack(conv_engine* e, Part& P, const float* src, int stride, const float* sub, float* e_out,
-                 cudaStream_t s) {
+// Argument blocks of one block of one partitioned convolution (shared by the
+// single-engine launches and the batched ones).
+PackArgs pack_args(conv_engine* e, Part& P, long long blk, const float* src, int stride, const float* sub,
+                   float* e_out) {
     PackArgs a{};
     a.in = src;
     a.in_stride = stride;
@@ -563,17 +565,13 @@ int enqueue_pack(conv_engine* e, Part& P, const float* src, int stride, const fl
     a.BT = P.plan.BT;
     a.n_ch = P.n_src;
     a.K = P.K;
-    a.slot = slot0_for(e->nblk, P.K);
+    a.slot = slot0_for(blk, P.K);
     a.tw = e->tw;
-    CK(launch_pack_r2c(e->prec, a, s));
-    return CONV_OK;
+    return a;
 }
 
-// Tail MAC for block `blk`: partitions 1..K-1, into the partial buffer of the
-// block's parity.
-int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool timed) {
+MacArgs tail_args(conv_engine* e, Part& P, long long blk) {
     const MacPlan& p = P.plan;
-    if (p.S == 0) return CONV_OK;  // K = 1: no tail
     MacArgs a{};
     a.H = P.H;
     a.X = P.X;
@@ -603,18 +601,10 @@ int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool ti
     a.sxoff = p.sxoff;
     a.tile_elems = p.tile_elems;
     a.err = e->d_err;
-    const bool rec = timed && e->prof && e->ev_used < e->ev0.size();
-    if (rec) CK(cudaEventRecord(e->ev0[e->ev_used], s));
-    CK(launch_fdl_mac(e->prec, p, a, s));
-    if (rec) {
-        CK(cudaEventRecord(e->ev1[e->ev_used], s));
-        ++e->ev_used;
-    }
-    return CONV_OK;
+    return a;
 }
 
-// Output of block `blk`: head (partition 0) + tail partials + C2R + OLS.
-int enqueue_out(conv_engine* e, Part& P, long long blk, float* out, cudaStream_t s) {
+OutArgs out_args(conv_engine* e, Part& P, long long blk, float* out) {
     const MacPlan& p = P.plan;
     OutArgs a{};
     a.partial = P.partial[blk & 1];
@@ -637,7 +627,33 @@ int enqueue_out(conv_engine* e, Part& P, long long blk, float* out, cudaStream_t
     a.LT = p.LT;
     a.slot0 = slot0_for(blk, P.K);
     a.tile_elems = p.tile_elems;
-    CK(launch_out_c2r(e->prec, a, s));
+    return a;
+}
+
+int enqueue_pack(conv_engine* e, Part& P, const float* src, int stride, const float* sub, float* e_out,
+                 cudaStream_t s) {
+    CK(launch_pack_r2c(e->prec, pack_args(e, P, e->nblk, src, stride, sub, e_out), s));
+    return CONV_OK;
+}
+
+// Tail MAC for block `blk`: partitions 1..K-1, into the partial buffer of the
+// block's parity.
+int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool timed) {
+    const MacPlan& p = P.plan;
+    if (p.S == 0) return CONV_OK;  // K = 1: no tail
+    const bool rec = timed && e->prof && e->ev_used < e->ev0.size();
+    if (rec) CK(cudaEventRecord(e->ev0[e->ev_used], s));
+    CK(launch_fdl_mac(e->prec, p, tail_args(e, P, blk), s));
+    if (rec) {
+        CK(cudaEventRecord(e->ev1[e->ev_used], s));
+        ++e->ev_used;
+    }
+    return CONV_OK;
+}
+
+// Output of block `blk`: head (partition 0) + tail partials + C2R + OLS.
+int enqueue_out(conv_engine* e, Part& P, long long blk, float* out, cudaStream_t s) {
+    CK(launch_out_c2r(e->prec, out_args(e, P, blk, out), s));
     return CONV_OK;
 }
 
@@ -1026,6 +1042,243 @@ int conv_plan_check(int precision, int block, int n_src, int n_dst, long long ta
     std::string why;
     if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());
     return CONV_OK;
+}
+
+// ------------------------------------------------------------- batches
+//
+// A batch runs one block of every member session per step with three kernel
+// launches in total (batched pack, batched output, batched tail MAC), each CTA
+// reading its session's arguments from a descriptor table that the step
+// uploads in one copy.  Sessions keep their own state (rings, windows,
+// partials, block counters); the split-phase schedule is the single engine's,
+// across the whole batch.
+
+}  // extern "C"
+
+struct conv_batch {
+    int dev = 0;
+    int prec = CONV_FP32;
+    std::vector<conv_engine*> sessions;
+    cudaStream_t stream = nullptr;
+    cudaStream_t bg[2] = {nullptr, nullptr};
+    cudaEvent_t ev_packed = nullptr, ev_tail[2] = {nullptr, nullptr}, ev_staged[2] = {nullptr, nullptr};
+    // descriptor tables, double-buffered by step parity: host staging (pinned) and device
+    unsigned char* h_tab[2] = {nullptr, nullptr};
+    unsigned char* d_tab[2] = {nullptr, nullptr};
+    size_t tab_cap = 0;
+    long long step = 0;
+};
+
+namespace {
+
+void batch_free_tables(conv_batch* b) {
+    for (int i = 0; i < 2; ++i) {
+        if (b->h_tab[i]) cudaFreeHost(b->h_tab[i]);
+        if (b->d_tab[i]) cudaFree(b->d_tab[i]);
+        b->h_tab[i] = b->d_tab[i] = nullptr;
+    }
+    b->tab_cap = 0;
+}
+
+int batch_sync(conv_batch* b) {
+    CK(cudaStreamSynchronize(b->bg[0]));
+    CK(cudaStreamSynchronize(b->bg[1]));
+    CK(cudaStreamSynchronize(b->stream));
+    return CONV_OK;
+}
+
+size_t align16(size_t v) { return (v + 15) / 16 * 16; }
+
+}  // namespace
+
+extern "C" {
+
+conv_batch* conv_batch_create(int precision) {
+    if (precision < CONV_FP32 || precision > CONV_BF16) {
+        set_err(CONV_E_INVAL, "unknown precision %d", precision);
+        return nullptr;
+    }
+    conv_batch* b = new (std::nothrow) conv_batch();
+    if (!b) {
+        set_err(CONV_E_NOMEM, "out of host memory");
+        return nullptr;
+    }
+    b->prec = precision;
+    auto fail = [&](cudaError_t r, const char* what) {
+        set_err(CONV_E_CUDA, "%s: %s", what, cudaGetErrorString(r));
+        conv_batch_destroy(b);
+        return nullptr;
+    };
+    cudaError_t r = cudaGetDevice(&b->dev);
+    if (r != cudaSuccess) return fail(r, "cudaGetDevice");
+    int lo = 0, hi = 0;
+    if ((r = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return fail(r, "priorities");
+    if ((r = cudaStreamCreateWithPriority(&b->stream, cudaStreamNonBlocking, hi)) != cudaSuccess) return fail(r, "stream");
+    for (int i = 0; i < 2; ++i) {
+        if ((r = cudaStreamCreateWithPriority(&b->bg[i], cudaStreamNonBlocking, lo)) != cudaSuccess) return fail(r, "stream");
+        if ((r = cudaEventCreateWithFlags(&b->ev_tail[i], cudaEventDisableTiming)) != cudaSuccess) return fail(r, "event");
+        if ((r = cudaEventCreateWithFlags(&b->ev_staged[i], cudaEventDisableTiming)) != cudaSuccess)
+            return fail(r, "event");
+        if ((r = cudaEventRecord(b->ev_tail[i], b->stream)) != cudaSuccess) return fail(r, "event");
+        if ((r = cudaEventRecord(b->ev_staged[i], b->stream)) != cudaSuccess) return fail(r, "event");
+    }
+    if ((r = cudaEventCreateWithFlags(&b->ev_packed, cudaEventDisableTiming)) != cudaSuccess) return fail(r, "event");
+    g_err.clear();
+    return b;
+}
+
+int conv_batch_add(conv_batch* b, conv_engine* e) {
+    if (!b || !e) return set_err(CONV_E_INVAL, "null argument");
+    if (e->prec != b->prec) return set_err(CONV_E_INVAL, "session precision differs from the batch's");
+    if (e->dev != b->dev) return set_err(CONV_E_INVAL, "session lives on another device");
+    if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
+    if (e->fb.allocated) return set_err(CONV_E_INVAL, "batches run synthesis only; this session has feedback paths");
+    if (e->syn.plan.direct || e->syn.plan.nw != 8)
+        return set_err(CONV_E_INVAL, "batched sessions use the TMA MAC with 8 consumer warps");
+    for (conv_engine* x : b->sessions)
+        if (x == e) return set_err(CONV_E_INVAL, "session already in the batch");
+    DeviceGuard g(b->dev);
+    int rc;
+    if ((rc = batch_sync(b))) return rc;
+    // the session's own streams may still run its last tail: let it finish
+    CK(cudaStreamSynchronize(e->bg[0]));
+    CK(cudaStreamSynchronize(e->bg[1]));
+    CK(cudaStreamSynchronize(e->stream));
+    b->sessions.push_back(e);
+    return CONV_OK;
+}
+
+int conv_batch_remove(conv_batch* b, conv_engine* e) {
+    if (!b || !e) return set_err(CONV_E_INVAL, "null argument");
+    auto it = std::find(b->sessions.begin(), b->sessions.end(), e);
+    if (it == b->sessions.end()) return set_err(CONV_E_INVAL, "session not in the batch");
+    DeviceGuard g(b->dev);
+    int rc;
+    if ((rc = batch_sync(b))) return rc;
+    b->sessions.erase(it);
+    // its next block's tail partials are complete: mark them ready for its own streams
+    CK(cudaEventRecord(e->syn.ev_tail[e->nblk & 1], e->stream));
+    return CONV_OK;
+}
+
+int conv_batch_size(const conv_batch* b) { return b ? (int)b->sessions.size() : 0; }
+
+int conv_batch_process_async(conv_batch* b, const float* const* d_in, float* const* d_out, void* cuda_stream) {
+    if (!b || !d_in || !d_out) return set_err(CONV_E_INVAL, "null argument");
+    const int n = (int)b->sessions.size();
+    if (n == 0) return CONV_OK;
+    DeviceGuard g(b->dev);
+    cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : b->stream;
+    // count the CTAs of each launch
+    int n_pack = 0, n_out = 0, n_mac = 0, Bmax = 16;
+    size_t mac_smem = 0;
+    for (conv_engine* e : b->sessions) {
+        n_pack += e->syn.n_src;
+        n_out += e->syn.n_dst;
+        n_mac += e->syn.plan.S ? e->syn.plan.ctas : 0;
+        Bmax = std::max(Bmax, e->B);
+        if (e->syn.plan.S) mac_smem = std::max(mac_smem, e->syn.plan.smem);
+    }
+    for (int i = 0; i < n; ++i)
+        if (!d_in[i] || !d_out[i]) return set_err(CONV_E_INVAL, "null session buffer %d", i);
+    const size_t o_pack = 0;
+    const size_t o_out = align16(o_pack + (size_t)n * sizeof(PackArgs));
+    const size_t o_mac = align16(o_out + (size_t)n * sizeof(OutArgs));
+    const size_t o_rp = align16(o_mac + (size_t)n * sizeof(MacArgs));
+    const size_t o_ro = align16(o_rp + (size_t)n_pack * sizeof(BatchRef));
+    const size_t o_rm = align16(o_ro + (size_t)n_out * sizeof(BatchRef));
+    const size_t bytes = align16(o_rm + (size_t)n_mac * sizeof(BatchRef));
+    if (bytes > b->tab_cap) {
+        int rc;
+        if ((rc = batch_sync(b))) return rc;
+        batch_free_tables(b);
+        const size_t cap = bytes * 2;
+        for (int i = 0; i < 2; ++i) {
+            CK(cudaHostAlloc(reinterpret_cast<void**>(&b->h_tab[i]), cap, cudaHostAllocDefault));
+            CK(cudaMalloc(reinterpret_cast<void**>(&b->d_tab[i]), cap));
+        }
+        b->tab_cap = cap;
+    }
+    const int par = (int)(b->step & 1);
+    CK(cudaEventSynchronize(b->ev_staged[par]));  // the copy that last read this staging buffer is done
+    unsigned char* h = b->h_tab[par];
+    unsigned char* d = b->d_tab[par];
+    PackArgs* pk = reinterpret_cast<PackArgs*>(h + o_pack);
+    OutArgs* ot = reinterpret_cast<OutArgs*>(h + o_out);
+    MacArgs* mc = reinterpret_cast<MacArgs*>(h + o_mac);
+    BatchRef* rp = reinterpret_cast<BatchRef*>(h + o_rp);
+    BatchRef* ro = reinterpret_cast<BatchRef*>(h + o_ro);
+    BatchRef* rm = reinterpret_cast<BatchRef*>(h + o_rm);
+    int ip = 0, io = 0, im = 0;
+    for (int i = 0; i < n; ++i) {
+        conv_engine* e = b->sessions[i];
+        Part& P = e->syn;
+        const long long blk = e->nblk;
+        pk[i] = pack_args(e, P, blk, d_in[i], e->B, nullptr, nullptr);
+        ot[i] = out_args(e, P, blk, d_out[i]);
+        mc[i] = tail_args(e, P, blk + 1);
+        for (int c = 0; c < P.n_src; ++c) rp[ip++] = BatchRef{i, c, 0};
+        for (int l = 0; l < P.n_dst; ++l) ro[io++] = BatchRef{i, l, 0};
+        if (P.plan.S)
+            for (int cta = 0; cta < P.plan.ctas; ++cta) rm[im++] = BatchRef{i, cta / P.plan.S, cta % P.plan.S};
+    }
+    CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(b->ev_staged[par], s));
+    const PackArgs* d_pk = reinterpret_cast<const PackArgs*>(d + o_pack);
+    const OutArgs* d_ot = reinterpret_cast<const OutArgs*>(d + o_out);
+    const MacArgs* d_mc = reinterpret_cast<const MacArgs*>(d + o_mac);
+    const BatchRef* d_rp = reinterpret_cast<const BatchRef*>(d + o_rp);
+    const BatchRef* d_ro = reinterpret_cast<const BatchRef*>(d + o_ro);
+    const BatchRef* d_rm = reinterpret_cast<const BatchRef*>(d + o_rm);
+    // caller stream: pack all -> [packed] -> [wait tails of this step] -> outputs
+    CK(launch_pack_batch(b->prec, d_pk, d_rp, n_pack, Bmax, s));
+    CK(cudaEventRecord(b->ev_packed, s));
+    CK(cudaStreamWaitEvent(s, b->ev_tail[par], 0));
+    CK(launch_out_batch(b->prec, d_ot, d_ro, n_out, Bmax, s));
+    // background: the next block's tails of every session, in one launch
+    cudaStream_t bg = b->bg[par ^ 1];
+    CK(cudaStreamWaitEvent(bg, b->ev_packed, 0));
+    CK(launch_mac_batch(b->prec, d_mc, d_rm, n_mac, mac_smem, bg));
+    CK(cudaEventRecord(b->ev_tail[par ^ 1], bg));
+    for (conv_engine* e : b->sessions) ++e->nblk;
+    ++b->step;
+    return CONV_OK;
+}
+
+int conv_batch_synchronize(conv_batch* b) {
+    if (!b) return set_err(CONV_E_INVAL, "null handle");
+    DeviceGuard g(b->dev);
+    int rc = batch_sync(b);
+    if (rc) return rc;
+    for (conv_engine* e : b->sessions)
+        if ((rc = check_dev_err(e))) return rc;
+    return CONV_OK;
+}
+
+long long conv_batch_step_bytes(const conv_batch* b) {
+    if (!b) return 0;
+    long long t = 0;
+    for (conv_engine* e : b->sessions) {
+        const MacPlan& p = e->syn.plan;
+        t += (long long)(((size_t)p.n_dst + 1) * (size_t)(p.R - p.r_begin) * p.B * p.es);
+    }
+    return t;
+}
+
+void conv_batch_destroy(conv_batch* b) {
+    if (!b) return;
+    DeviceGuard g(b->dev);
+    if (b->stream) batch_sync(b);
+    for (conv_engine* e : b->sessions) cudaEventRecord(e->syn.ev_tail[e->nblk & 1], e->stream);
+    batch_free_tables(b);
+    if (b->ev_packed) cudaEventDestroy(b->ev_packed);
+    for (int i = 0; i < 2; ++i) {
+        if (b->ev_tail[i]) cudaEventDestroy(b->ev_tail[i]);
+        if (b->ev_staged[i]) cudaEventDestroy(b->ev_staged[i]);
+        if (b->bg[i]) cudaStreamDestroy(b->bg[i]);
+    }
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
 }
 
 void conv_destroy(conv_engine* e) { engine_free(e); }

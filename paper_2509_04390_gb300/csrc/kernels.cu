@@ -17,6 +17,9 @@
 
 namespace gbconv {
 
+static_assert(2 * MAX_STAGES * sizeof(uint64_t) + sizeof(int) <= MAC_ARGS_OFFSET, "mbarriers overlap the staged arguments");
+static_assert(MAC_ARGS_OFFSET + sizeof(MacArgs) <= MAC_HDR_BYTES, "staged MAC arguments exceed the header");
+
 namespace {
 
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;  // 1 s: far beyond any legitimate wait
@@ -85,10 +88,10 @@ __device__ float store_spectrum(const float2* Xs, int B, void* dst, IndexFn dst_
 // One CTA per channel.  w = [previous block, in - sub]; z[n] = w[2n] + i w[2n+1];
 // B-point FFT; real-FFT post-processing; push into the ring slot.
 template <int PREC>
-__global__ void k_pack_r2c(const PackArgs a) {
+__device__ __forceinline__ void pack_body(const PackArgs& a, const int c) {
     extern __shared__ float2 fsm[];
     __shared__ float red[32];
-    const int B = a.B, half = B >> 1, c = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    const int B = a.B, half = B >> 1, tid = threadIdx.x, nth = blockDim.x;
     float2* bufA = fsm;
     float2* bufB = fsm + B;
     float2* tws = fsm + 2 * B;
@@ -126,6 +129,11 @@ __global__ void k_pack_r2c(const PackArgs a) {
     __syncthreads();
     const float scale = store_spectrum<PREC>(Xs, B, a.X, RingIndex{a.BT, a.n_ch, c, a.K, a.slot}, red);
     if (PREC != PREC_FP32 && tid == 0) a.sX[(size_t)a.slot * a.n_ch + c] = scale;
+}
+
+template <int PREC>
+__global__ void k_pack_r2c(const PackArgs a) {
+    pack_body<PREC>(a, blockIdx.x);
 }
 
 // --------------------------------------------------- filter partitions R2C
@@ -209,17 +217,15 @@ __global__ void k_tile_scales(const float* __restrict__ maxabs, float* __restric
 // and every filter tile starts on a 64 KiB boundary, so each filter copy is an
 // aligned, usually power-of-two-sized chunk of HBM; splits own whole stages.
 template <int PREC, int LPT, int NW>
-__global__ void __launch_bounds__((NW + 1) * 32, 1) k_fdl_mac(const MacArgs a) {
+__device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const int split, unsigned char* smem) {
     using St = Store<PREC>;
     constexpr int VEC = St::VEC;
-    extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + MAX_STAGES;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + MAX_STAGES);
     unsigned char* stages = smem + MAC_HDR_BYTES;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x / a.S, split = blockIdx.x - tile * a.S;
     const int kt = tile / a.n_lt, lt = tile - kt * a.n_lt;
     const int l0 = lt * a.LT, LTt = min(a.LT, a.n_dst - l0);
     const int K = a.K, R = a.n_src * K;
@@ -446,6 +452,26 @@ __global__ void __launch_bounds__((NW + 1) * 32, 1) k_fdl_mac(const MacArgs a) {
     }
 }
 
+template <int PREC, int LPT, int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) k_fdl_mac(const MacArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tile = blockIdx.x / a.S, split = blockIdx.x - tile * a.S;
+    mac_body<PREC, LPT, NW>(a, tile, split, smem);
+}
+
+// Batched: CTA i runs (tile, split) of the session whose arguments are
+// items[refs[i].item]; the arguments are staged in the header of shared memory.
+template <int PREC, int LPT, int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 1) k_fdl_mac_batch(const MacArgs* __restrict__ items,
+                                                                    const BatchRef* __restrict__ refs) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    MacArgs* sa = reinterpret_cast<MacArgs*>(smem + MAC_ARGS_OFFSET);
+    const BatchRef r = refs[blockIdx.x];
+    if (threadIdx.x == 0) *sa = items[r.item];
+    __syncthreads();
+    mac_body<PREC, LPT, NW>(*sa, r.idx, r.idx2, smem);
+}
+
 // ------------------------------------------------ FDL MAC, direct loads
 // Same work and output as k_fdl_mac, without the TMA producer: every thread
 // streams its own 16-byte loads straight from HBM (filter rows with the
@@ -574,10 +600,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_fdl_mac_ldg(const MacArgs a) 
 // needs the new input), then the C2R IFFT (1/2B) and the last B samples
 // (overlap-save).
 template <int PREC>
-__global__ void k_out_c2r(const OutArgs a) {
+__device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
     using St = Store<PREC>;
     extern __shared__ float2 fsm[];
-    const int B = a.B, l = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    const int B = a.B, tid = threadIdx.x, nth = blockDim.x;
     float2* P = fsm;
     float2* W = fsm + B;
     float2* tws = fsm + 2 * B;
@@ -634,6 +660,31 @@ __global__ void k_out_c2r(const OutArgs a) {
         const int u = B + t, n = u >> 1;
         out[t] = ((u & 1) ? z[n].y : z[n].x) * invB;
     }
+}
+
+template <int PREC>
+__global__ void k_out_c2r(const OutArgs a) {
+    out_body<PREC>(a, blockIdx.x);
+}
+
+// Batched pack and output: CTA i serves channel refs[i].idx of the session
+// whose arguments are items[refs[i].item] (staged in static shared memory).
+template <int PREC>
+__global__ void k_pack_batch(const PackArgs* __restrict__ items, const BatchRef* __restrict__ refs) {
+    __shared__ PackArgs sa;
+    const BatchRef r = refs[blockIdx.x];
+    if (threadIdx.x == 0) sa = items[r.item];
+    __syncthreads();
+    pack_body<PREC>(sa, r.idx);
+}
+
+template <int PREC>
+__global__ void k_out_batch(const OutArgs* __restrict__ items, const BatchRef* __restrict__ refs) {
+    __shared__ OutArgs sa;
+    const BatchRef r = refs[blockIdx.x];
+    if (threadIdx.x == 0) sa = items[r.item];
+    __syncthreads();
+    out_body<PREC>(sa, r.idx);
 }
 
 template <int PREC>
@@ -695,6 +746,15 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR(k_filter_r2c<PREC_FP16>, fft_max)
     GB_ATTR(k_filter_r2c<PREC_BF16>, fft_max)
     GB_ATTR(k_out_c2r<PREC_FP32>, fft_max)
+    GB_ATTR(k_pack_batch<PREC_FP32>, fft_max)
+    GB_ATTR(k_pack_batch<PREC_FP16>, fft_max)
+    GB_ATTR(k_pack_batch<PREC_BF16>, fft_max)
+    GB_ATTR(k_out_batch<PREC_FP32>, fft_max)
+    GB_ATTR(k_out_batch<PREC_FP16>, fft_max)
+    GB_ATTR(k_out_batch<PREC_BF16>, fft_max)
+    GB_ATTR((k_fdl_mac_batch<PREC_FP32, lpt_for<PREC_FP32>(), 8>), mac_smem)
+    GB_ATTR((k_fdl_mac_batch<PREC_FP16, lpt_for<PREC_FP16>(), 8>), mac_smem)
+    GB_ATTR((k_fdl_mac_batch<PREC_BF16, lpt_for<PREC_BF16>(), 8>), mac_smem)
     GB_ATTR(k_out_c2r<PREC_FP16>, fft_max)
     GB_ATTR(k_out_c2r<PREC_BF16>, fft_max)
     GB_ATTR((k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>(), 8>), mac_smem)
@@ -791,6 +851,61 @@ cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s) {
         case PREC_FP32: return launch_pdl(k_out_c2r<PREC_FP32>, grid, block, sm, s, a);
         case PREC_FP16: return launch_pdl(k_out_c2r<PREC_FP16>, grid, block, sm, s, a);
         case PREC_BF16: return launch_pdl(k_out_c2r<PREC_BF16>, grid, block, sm, s, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename Kern, typename... Args>
+cudaError_t launch_pdl_n(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+cudaError_t launch_pack_batch(int prec, const PackArgs* items, const BatchRef* refs, int n, int Bmax,
+                              cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid(n), block(fft_threads(Bmax));
+    const size_t sm = fft_smem_bytes(Bmax);
+    switch (prec) {
+        case PREC_FP32: return launch_pdl_n(k_pack_batch<PREC_FP32>, grid, block, sm, s, items, refs);
+        case PREC_FP16: return launch_pdl_n(k_pack_batch<PREC_FP16>, grid, block, sm, s, items, refs);
+        case PREC_BF16: return launch_pdl_n(k_pack_batch<PREC_BF16>, grid, block, sm, s, items, refs);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_out_batch(int prec, const OutArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid(n), block(out_threads(Bmax));
+    const size_t sm = fft_smem_bytes(Bmax);
+    switch (prec) {
+        case PREC_FP32: return launch_pdl_n(k_out_batch<PREC_FP32>, grid, block, sm, s, items, refs);
+        case PREC_FP16: return launch_pdl_n(k_out_batch<PREC_FP16>, grid, block, sm, s, items, refs);
+        case PREC_BF16: return launch_pdl_n(k_out_batch<PREC_BF16>, grid, block, sm, s, items, refs);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_mac_batch(int prec, const MacArgs* items, const BatchRef* refs, int n, size_t smem,
+                             cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid(n), block((8 + 1) * 32);
+    switch (prec) {
+        case PREC_FP32:
+            return launch_pdl_n(k_fdl_mac_batch<PREC_FP32, lpt_for<PREC_FP32>(), 8>, grid, block, smem, s, items, refs);
+        case PREC_FP16:
+            return launch_pdl_n(k_fdl_mac_batch<PREC_FP16, lpt_for<PREC_FP16>(), 8>, grid, block, smem, s, items, refs);
+        case PREC_BF16:
+            return launch_pdl_n(k_fdl_mac_batch<PREC_BF16, lpt_for<PREC_BF16>(), 8>, grid, block, smem, s, items, refs);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -121,6 +121,16 @@ struct OutArgs {
     size_t tile_elems;
 };
 
+// One CTA of a batched launch: which session's arguments (items[item]), and
+// the channel (pack/output) or the tile and split (MAC) it serves.
+struct BatchRef {
+    int item, idx, idx2;
+};
+
+// The batched MAC stages its arguments in the shared-memory header after the
+// mbarriers and the abort flag.
+constexpr int MAC_ARGS_OFFSET = 256;
+
 int fft_threads(int B);
 int out_threads(int B);
 size_t fft_smem_bytes(int B);
@@ -134,5 +144,8 @@ cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s);
 cudaError_t launch_tile_scales(int prec, const float* maxabs, float* sH, int n_dst, int R, int LT, cudaStream_t s);
 cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s);
 cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s);
+cudaError_t launch_pack_batch(int prec, const PackArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);
+cudaError_t launch_out_batch(int prec, const OutArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);
+cudaError_t launch_mac_batch(int prec, const MacArgs* items, const BatchRef* refs, int n, size_t smem, cudaStream_t s);
 
 }  // namespace gbconv

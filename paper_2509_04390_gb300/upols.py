@@ -127,6 +127,14 @@ def load():
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "conv_plan_check": (i, [i, i, i, i, ll, i, ctypes.POINTER(conv_tiling)]),
         "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
+        "conv_batch_create": (vp, [i]),
+        "conv_batch_add": (i, [vp, vp]),
+        "conv_batch_remove": (i, [vp, vp]),
+        "conv_batch_size": (i, [vp]),
+        "conv_batch_process_async": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]),
+        "conv_batch_synchronize": (i, [vp]),
+        "conv_batch_step_bytes": (ll, [vp]),
+        "conv_batch_destroy": (None, [vp]),
         "conv_destroy": (None, [vp]),
         "conv_last_error": (ctypes.c_char_p, []),
     }
@@ -284,6 +292,45 @@ def conv_fdl_mac_noalloc(d_H, d_X, block, n_in, n_out, K, slot0, d_y, stream=Non
     )
 
 
+def conv_batch_create(precision="fp32"):
+    b = load().conv_batch_create(int(PRECISIONS.get(precision, precision)))
+    if not b:
+        raise ConvError(CONV_E_INVAL, conv_last_error())
+    return b
+
+
+def conv_batch_add(b, h):
+    return _check(load().conv_batch_add(b, h))
+
+
+def conv_batch_remove(b, h):
+    return _check(load().conv_batch_remove(b, h))
+
+
+def conv_batch_size(b):
+    return int(load().conv_batch_size(b))
+
+
+def conv_batch_process_async(b, d_ins, d_outs, stream=None):
+    n = len(d_ins)
+    ins = (ctypes.c_void_p * n)(*[_dev_ptr(t).value for t in d_ins])
+    outs = (ctypes.c_void_p * n)(*[_dev_ptr(t).value for t in d_outs])
+    return _check(load().conv_batch_process_async(b, ins, outs, _stream_ptr(stream)))
+
+
+def conv_batch_synchronize(b):
+    return _check(load().conv_batch_synchronize(b))
+
+
+def conv_batch_step_bytes(b):
+    return int(load().conv_batch_step_bytes(b))
+
+
+def conv_batch_destroy(b):
+    if b:
+        load().conv_batch_destroy(b)
+
+
 def conv_destroy(h):
     if h:
         load().conv_destroy(h)
@@ -295,6 +342,42 @@ def _dims(h):
 
 
 # ------------------------------------------------------------ convenience
+
+
+class Batch:
+    """Owning wrapper of a conv_batch (sessions are Engine objects)."""
+
+    def __init__(self, precision="fp32"):
+        self.b = conv_batch_create(precision)
+        self.sessions = []
+
+    def add(self, eng):
+        conv_batch_add(self.b, eng.h)
+        self.sessions.append(eng)
+
+    def remove(self, eng):
+        conv_batch_remove(self.b, eng.h)
+        self.sessions.remove(eng)
+
+    def process_async(self, d_ins, d_outs, stream=None):
+        conv_batch_process_async(self.b, d_ins, d_outs, stream)
+
+    def synchronize(self):
+        conv_batch_synchronize(self.b)
+
+    def step_bytes(self):
+        return conv_batch_step_bytes(self.b)
+
+    def close(self):
+        if self.b:
+            conv_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Engine:
