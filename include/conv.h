@@ -220,15 +220,16 @@ int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int block, int n_in
  * sizes, channel counts, filter lengths and tilings.  Sessions keep their own
  * state; a session in a batch must not be processed on its own (add/remove
  * hand it over).  All sessions of a batch share the batch's precision and use
- * the TMA MAC with 8 consumer warps; batches run synthesis only. */
+ * the TMA MAC with 8 consumer warps.  Sessions with feedback paths run the
+ * canceller too (Sec. 5): their input is the microphone block. */
 typedef struct conv_batch conv_batch;
 
 /* Create an empty batch for sessions of the given precision on the current
  * device.  NULL on failure (conv_last_error()). */
 conv_batch* conv_batch_create(int precision);
 
-/* Add a session (filters set, no feedback paths).  Waits for the session's
- * own outstanding work and the batch's. */
+/* Add a session (filters set; feedback paths, if allocated, set too).  Waits
+ * for the session's own outstanding work and the batch's. */
 int conv_batch_add(conv_batch* b, conv_engine* e);
 
 /* Remove a session; it can be processed on its own again afterwards. */
@@ -245,10 +246,19 @@ int conv_batch_size(const conv_batch* b);
  * stream. */
 int conv_batch_process_async(conv_batch* b, const float* const* d_in, float* const* d_out, void* cuda_stream);
 
+/* One block of `count` of the sessions: idx[j] is the index (in add order) of
+ * the j-th session to process, d_in[j] / d_out[j] its buffers.  The others
+ * keep their state and can be processed in a later call (sessions with
+ * different block periods come due on different steps).  Same stream rules
+ * as conv_batch_process_async. */
+int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, const float* const* d_in,
+                                  float* const* d_out, void* cuda_stream);
+
 /* Wait for all of the batch's work; report a device-side error of any session. */
 int conv_batch_synchronize(conv_batch* b);
 
-/* Algorithmic bytes of one step's batched tail MAC (all sessions). */
+/* Algorithmic bytes of one step's batched tail MAC (all sessions, both
+ * convolutions of canceller sessions). */
 long long conv_batch_step_bytes(const conv_batch* b);
 
 /* Free the batch (its sessions are left intact and usable on their own).  NULL-safe. */

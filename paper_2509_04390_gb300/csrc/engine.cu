@@ -1062,6 +1062,7 @@ struct conv_batch {
     cudaStream_t stream = nullptr;
     cudaStream_t bg[2] = {nullptr, nullptr};
     cudaEvent_t ev_packed = nullptr, ev_tail[2] = {nullptr, nullptr}, ev_staged[2] = {nullptr, nullptr};
+    std::vector<int> all_idx;
     // descriptor tables, double-buffered by step parity: host staging (pinned) and device
     unsigned char* h_tab[2] = {nullptr, nullptr};
     unsigned char* d_tab[2] = {nullptr, nullptr};
@@ -1132,8 +1133,8 @@ int conv_batch_add(conv_batch* b, conv_engine* e) {
     if (e->prec != b->prec) return set_err(CONV_E_INVAL, "session precision differs from the batch's");
     if (e->dev != b->dev) return set_err(CONV_E_INVAL, "session lives on another device");
     if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
-    if (e->fb.allocated) return set_err(CONV_E_INVAL, "batches run synthesis only; this session has feedback paths");
-    if (e->syn.plan.direct || e->syn.plan.nw != 8)
+    if (e->fb.allocated && !e->fb.ready) return set_err(CONV_E_STATE, "feedback paths not set");
+    if (e->syn.plan.direct || e->syn.plan.nw != 8 || (e->fb.allocated && (e->fb.plan.direct || e->fb.plan.nw != 8)))
         return set_err(CONV_E_INVAL, "batched sessions use the TMA MAC with 8 consumer warps");
     for (conv_engine* x : b->sessions)
         if (x == e) return set_err(CONV_E_INVAL, "session already in the batch");
@@ -1158,35 +1159,59 @@ int conv_batch_remove(conv_batch* b, conv_engine* e) {
     b->sessions.erase(it);
     // its next block's tail partials are complete: mark them ready for its own streams
     CK(cudaEventRecord(e->syn.ev_tail[e->nblk & 1], e->stream));
+    if (e->fb.allocated) CK(cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream));
     return CONV_OK;
 }
 
 int conv_batch_size(const conv_batch* b) { return b ? (int)b->sessions.size() : 0; }
 
 int conv_batch_process_async(conv_batch* b, const float* const* d_in, float* const* d_out, void* cuda_stream) {
-    if (!b || !d_in || !d_out) return set_err(CONV_E_INVAL, "null argument");
+    if (!b) return set_err(CONV_E_INVAL, "null handle");
     const int n = (int)b->sessions.size();
-    if (n == 0) return CONV_OK;
+    b->all_idx.resize(n);
+    for (int i = 0; i < n; ++i) b->all_idx[i] = i;
+    return conv_batch_process_some_async(b, n, b->all_idx.data(), d_in, d_out, cuda_stream);
+}
+
+int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, const float* const* d_in,
+                                  float* const* d_out, void* cuda_stream) {
+    if (!b || (count > 0 && (!idx || !d_in || !d_out))) return set_err(CONV_E_INVAL, "null argument");
+    const int nses = (int)b->sessions.size();
+    if (count < 0 || count > nses) return set_err(CONV_E_INVAL, "count %d outside [0, %d]", count, nses);
+    if (count == 0) return CONV_OK;
+    std::vector<char> seen(nses, 0);
+    for (int j = 0; j < count; ++j) {
+        if (idx[j] < 0 || idx[j] >= nses || seen[idx[j]]) return set_err(CONV_E_INVAL, "bad session index %d", idx[j]);
+        seen[idx[j]] = 1;
+        if (!d_in[j] || !d_out[j]) return set_err(CONV_E_INVAL, "null buffer for session %d", idx[j]);
+    }
     DeviceGuard g(b->dev);
     cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : b->stream;
-    // count the CTAs of each launch
-    int n_pack = 0, n_out = 0, n_mac = 0, Bmax = 16;
+    // count the CTAs of each launch (synthesis, feedback canceller)
+    int n_pack = 0, n_out = 0, n_fpack = 0, n_fout = 0, n_mac = 0, n_afc = 0, Bmax = 16;
     size_t mac_smem = 0;
-    for (conv_engine* e : b->sessions) {
+    for (int j = 0; j < count; ++j) {
+        conv_engine* e = b->sessions[idx[j]];
         n_pack += e->syn.n_src;
         n_out += e->syn.n_dst;
         n_mac += e->syn.plan.S ? e->syn.plan.ctas : 0;
         Bmax = std::max(Bmax, e->B);
         if (e->syn.plan.S) mac_smem = std::max(mac_smem, e->syn.plan.smem);
+        if (e->fb.allocated) {
+            ++n_afc;
+            n_fpack += e->fb.n_src;
+            n_fout += e->fb.n_dst;
+            n_mac += e->fb.plan.S ? e->fb.plan.ctas : 0;
+            if (e->fb.plan.S) mac_smem = std::max(mac_smem, e->fb.plan.smem);
+        }
     }
-    for (int i = 0; i < n; ++i)
-        if (!d_in[i] || !d_out[i]) return set_err(CONV_E_INVAL, "null session buffer %d", i);
+    const int n_items = count + n_afc;  // synthesis items first, then the canceller's
     const size_t o_pack = 0;
-    const size_t o_out = align16(o_pack + (size_t)n * sizeof(PackArgs));
-    const size_t o_mac = align16(o_out + (size_t)n * sizeof(OutArgs));
-    const size_t o_rp = align16(o_mac + (size_t)n * sizeof(MacArgs));
-    const size_t o_ro = align16(o_rp + (size_t)n_pack * sizeof(BatchRef));
-    const size_t o_rm = align16(o_ro + (size_t)n_out * sizeof(BatchRef));
+    const size_t o_out = align16(o_pack + (size_t)n_items * sizeof(PackArgs));
+    const size_t o_mac = align16(o_out + (size_t)n_items * sizeof(OutArgs));
+    const size_t o_rp = align16(o_mac + (size_t)n_items * sizeof(MacArgs));
+    const size_t o_ro = align16(o_rp + (size_t)(n_pack + n_fpack) * sizeof(BatchRef));
+    const size_t o_rm = align16(o_ro + (size_t)(n_out + n_fout) * sizeof(BatchRef));
     const size_t bytes = align16(o_rm + (size_t)n_mac * sizeof(BatchRef));
     if (bytes > b->tab_cap) {
         int rc;
@@ -1209,18 +1234,32 @@ int conv_batch_process_async(conv_batch* b, const float* const* d_in, float* con
     BatchRef* rp = reinterpret_cast<BatchRef*>(h + o_rp);
     BatchRef* ro = reinterpret_cast<BatchRef*>(h + o_ro);
     BatchRef* rm = reinterpret_cast<BatchRef*>(h + o_rm);
-    int ip = 0, io = 0, im = 0;
-    for (int i = 0; i < n; ++i) {
-        conv_engine* e = b->sessions[i];
+    int ip = 0, io = 0, im = 0, ifp = n_pack, ifo = n_out, ia = count;
+    for (int j = 0; j < count; ++j) {
+        conv_engine* e = b->sessions[idx[j]];
         Part& P = e->syn;
         const long long blk = e->nblk;
-        pk[i] = pack_args(e, P, blk, d_in[i], e->B, nullptr, nullptr);
-        ot[i] = out_args(e, P, blk, d_out[i]);
-        mc[i] = tail_args(e, P, blk + 1);
-        for (int c = 0; c < P.n_src; ++c) rp[ip++] = BatchRef{i, c, 0};
-        for (int l = 0; l < P.n_dst; ++l) ro[io++] = BatchRef{i, l, 0};
+        const bool afc = e->fb.allocated;
+        // synthesis: e = mic - c_prev for canceller sessions (Sec. 5)
+        pk[j] = pack_args(e, P, blk, d_in[j], e->B, afc ? e->d_c : nullptr, nullptr);
+        ot[j] = out_args(e, P, blk, d_out[j]);
+        mc[j] = tail_args(e, P, blk + 1);
+        for (int c = 0; c < P.n_src; ++c) rp[ip++] = BatchRef{j, c, 0};
+        for (int l = 0; l < P.n_dst; ++l) ro[io++] = BatchRef{j, l, 0};
         if (P.plan.S)
-            for (int cta = 0; cta < P.plan.ctas; ++cta) rm[im++] = BatchRef{i, cta / P.plan.S, cta % P.plan.S};
+            for (int cta = 0; cta < P.plan.ctas; ++cta) rm[im++] = BatchRef{j, cta / P.plan.S, cta % P.plan.S};
+        if (afc) {
+            // canceller: c = F_hat * out, kept for the next block
+            Part& F = e->fb;
+            pk[ia] = pack_args(e, F, blk, d_out[j], e->B, nullptr, nullptr);
+            ot[ia] = out_args(e, F, blk, e->d_c);
+            mc[ia] = tail_args(e, F, blk + 1);
+            for (int c = 0; c < F.n_src; ++c) rp[ifp++] = BatchRef{ia, c, 0};
+            for (int l = 0; l < F.n_dst; ++l) ro[ifo++] = BatchRef{ia, l, 0};
+            if (F.plan.S)
+                for (int cta = 0; cta < F.plan.ctas; ++cta) rm[im++] = BatchRef{ia, cta / F.plan.S, cta % F.plan.S};
+            ++ia;
+        }
     }
     CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(b->ev_staged[par], s));
@@ -1230,17 +1269,26 @@ int conv_batch_process_async(conv_batch* b, const float* const* d_in, float* con
     const BatchRef* d_rp = reinterpret_cast<const BatchRef*>(d + o_rp);
     const BatchRef* d_ro = reinterpret_cast<const BatchRef*>(d + o_ro);
     const BatchRef* d_rm = reinterpret_cast<const BatchRef*>(d + o_rm);
-    // caller stream: pack all -> [packed] -> [wait tails of this step] -> outputs
+    // caller stream: pack all -> [wait outstanding tails] -> outputs; then the
+    // canceller's pack and outputs.  A session that skipped steps computed its
+    // tail in an earlier launch: waiting on both tail streams covers it.
     CK(launch_pack_batch(b->prec, d_pk, d_rp, n_pack, Bmax, s));
-    CK(cudaEventRecord(b->ev_packed, s));
-    CK(cudaStreamWaitEvent(s, b->ev_tail[par], 0));
+    if (!n_afc) CK(cudaEventRecord(b->ev_packed, s));
+    CK(cudaStreamWaitEvent(s, b->ev_tail[0], 0));
+    CK(cudaStreamWaitEvent(s, b->ev_tail[1], 0));
     CK(launch_out_batch(b->prec, d_ot, d_ro, n_out, Bmax, s));
-    // background: the next block's tails of every session, in one launch
+    if (n_afc) {
+        CK(launch_pack_batch(b->prec, d_pk, d_rp + n_pack, n_fpack, Bmax, s));
+        CK(cudaEventRecord(b->ev_packed, s));
+        CK(launch_out_batch(b->prec, d_ot, d_ro + n_out, n_fout, Bmax, s));
+    }
+    // background: the next block's tails of every processed session (both
+    // convolutions) in one launch
     cudaStream_t bg = b->bg[par ^ 1];
     CK(cudaStreamWaitEvent(bg, b->ev_packed, 0));
     CK(launch_mac_batch(b->prec, d_mc, d_rm, n_mac, mac_smem, bg));
     CK(cudaEventRecord(b->ev_tail[par ^ 1], bg));
-    for (conv_engine* e : b->sessions) ++e->nblk;
+    for (int j = 0; j < count; ++j) ++b->sessions[idx[j]]->nblk;
     ++b->step;
     return CONV_OK;
 }
@@ -1258,9 +1306,10 @@ int conv_batch_synchronize(conv_batch* b) {
 long long conv_batch_step_bytes(const conv_batch* b) {
     if (!b) return 0;
     long long t = 0;
+    auto tail = [](const MacPlan& p) { return (long long)(((size_t)p.n_dst + 1) * (size_t)(p.R - p.r_begin) * p.B * p.es); };
     for (conv_engine* e : b->sessions) {
-        const MacPlan& p = e->syn.plan;
-        t += (long long)(((size_t)p.n_dst + 1) * (size_t)(p.R - p.r_begin) * p.B * p.es);
+        t += tail(e->syn.plan);
+        if (e->fb.allocated) t += tail(e->fb.plan);
     }
     return t;
 }
@@ -1269,7 +1318,10 @@ void conv_batch_destroy(conv_batch* b) {
     if (!b) return;
     DeviceGuard g(b->dev);
     if (b->stream) batch_sync(b);
-    for (conv_engine* e : b->sessions) cudaEventRecord(e->syn.ev_tail[e->nblk & 1], e->stream);
+    for (conv_engine* e : b->sessions) {
+        cudaEventRecord(e->syn.ev_tail[e->nblk & 1], e->stream);
+        if (e->fb.allocated) cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream);
+    }
     batch_free_tables(b);
     if (b->ev_packed) cudaEventDestroy(b->ev_packed);
     for (int i = 0; i < 2; ++i) {

@@ -132,6 +132,7 @@ def load():
         "conv_batch_remove": (i, [vp, vp]),
         "conv_batch_size": (i, [vp]),
         "conv_batch_process_async": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]),
+        "conv_batch_process_some_async": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]),
         "conv_batch_synchronize": (i, [vp]),
         "conv_batch_step_bytes": (ll, [vp]),
         "conv_batch_destroy": (None, [vp]),
@@ -318,6 +319,14 @@ def conv_batch_process_async(b, d_ins, d_outs, stream=None):
     return _check(load().conv_batch_process_async(b, ins, outs, _stream_ptr(stream)))
 
 
+def conv_batch_process_some_async(b, idx, d_ins, d_outs, stream=None):
+    n = len(idx)
+    ids = (ctypes.c_int * n)(*[int(v) for v in idx])
+    ins = (ctypes.c_void_p * n)(*[_dev_ptr(t).value for t in d_ins])
+    outs = (ctypes.c_void_p * n)(*[_dev_ptr(t).value for t in d_outs])
+    return _check(load().conv_batch_process_some_async(b, n, ids, ins, outs, _stream_ptr(stream)))
+
+
 def conv_batch_synchronize(b):
     return _check(load().conv_batch_synchronize(b))
 
@@ -361,6 +370,9 @@ class Batch:
 
     def process_async(self, d_ins, d_outs, stream=None):
         conv_batch_process_async(self.b, d_ins, d_outs, stream)
+
+    def process_some_async(self, idx, d_ins, d_outs, stream=None):
+        conv_batch_process_some_async(self.b, idx, d_ins, d_outs, stream)
 
     def synchronize(self):
         conv_batch_synchronize(self.b)

@@ -134,3 +134,92 @@ def test_batch_rejects_mismatched_sessions():
             batch.add(en)  # no filters
         for e in (e16, ed, en):
             e.close()
+
+
+def test_sessions_due_on_different_ticks():
+    """Continuous batching: a 64-sample tick; a session of block B is due every
+    B / 64 ticks and is processed only then, alongside whatever else is due."""
+    torch = pytest.importorskip("torch")
+    shapes = [(2, 3, 1500, 64), (1, 4, 5000, 128), (3, 2, 9000, 256), (2, 6, 2000, 64)]
+    ws = [signals.random_case(700 + i, a, b, t, B, 16) for i, (a, b, t, B) in enumerate(shapes)]
+    engs = []
+    for w in ws:
+        e = U.Engine(w.fs, w.block, w.n_in, w.n_out, w.taps, "fp32", BATCH_TILING)
+        e.set_filters(w.h)
+        engs.append(e)
+    alone = [e.run(w.x[:, : 4 * w.block]) for e, w in zip(engs, ws)]
+    for e in engs:
+        e.reset()
+    got = [np.zeros_like(a) for a in alone]
+    done = [0] * len(ws)
+    d_y = [torch.zeros((w.n_out, w.block), dtype=torch.float32, device="cuda") for w in ws]
+    with U.Batch("fp32") as batch:
+        for e in engs:
+            batch.add(e)
+        for tick in range(16):
+            due = [i for i, w in enumerate(ws) if (tick * 64) % w.block == 0 and done[i] < 4]
+            if not due:
+                continue
+            ins = []
+            for i in due:
+                w, b = ws[i], done[i]
+                ins.append(torch.from_numpy(np.ascontiguousarray(w.x[:, b * w.block : (b + 1) * w.block])).cuda())
+            batch.process_some_async(due, ins, [d_y[i] for i in due])
+            batch.synchronize()
+            for i in due:
+                w, b = ws[i], done[i]
+                got[i][:, b * w.block : (b + 1) * w.block] = d_y[i].cpu().numpy()
+                done[i] += 1
+    assert done == [4] * len(ws)
+    for g, a in zip(got, alone):
+        np.testing.assert_array_equal(g, a)
+    for e in engs:
+        e.close()
+
+
+def test_canceller_session_in_a_batch():
+    torch = pytest.importorskip("torch")
+    w = signals.random_case(900, 2, 6, 4000, 128, 12)
+    rng = np.random.default_rng(901)
+    f = (rng.standard_normal((2, 6, 700)) * 0.02).astype(np.float32)
+    plain = signals.random_case(902, 3, 4, 2500, 256, 6)
+
+    def make():
+        e = U.Engine(w.fs, w.block, 2, 6, w.taps, "fp32", BATCH_TILING)
+        e.set_filters(w.h)
+        e.set_paths(f)
+        p = U.Engine(plain.fs, plain.block, 3, 4, plain.taps, "fp32", BATCH_TILING)
+        p.set_filters(plain.h)
+        return e, p
+
+    e, p = make()
+    alone_e = np.concatenate(
+        [e.process_afc(np.ascontiguousarray(w.x[:, b * 128 : (b + 1) * 128])).copy() for b in range(12)], axis=1
+    )
+    alone_p = p.run(plain.x)
+    e.close()
+    p.close()
+    e, p = make()
+    ye = np.zeros_like(alone_e)
+    yp = np.zeros_like(alone_p)
+    d_ye = torch.zeros((6, 128), dtype=torch.float32, device="cuda")
+    d_yp = torch.zeros((4, 256), dtype=torch.float32, device="cuda")
+    with U.Batch("fp32") as batch:
+        batch.add(e)
+        batch.add(p)
+        for tick in range(12):  # 128-sample ticks; the 256-block session every other tick
+            idx, ins, outs = [0], [torch.from_numpy(np.ascontiguousarray(w.x[:, tick * 128 : (tick + 1) * 128])).cuda()], [d_ye]
+            if tick % 2 == 0:
+                b = tick // 2
+                idx.append(1)
+                ins.append(torch.from_numpy(np.ascontiguousarray(plain.x[:, b * 256 : (b + 1) * 256])).cuda())
+                outs.append(d_yp)
+            batch.process_some_async(idx, ins, outs)
+            batch.synchronize()
+            ye[:, tick * 128 : (tick + 1) * 128] = d_ye.cpu().numpy()
+            if tick % 2 == 0:
+                yp[:, (tick // 2) * 256 : (tick // 2 + 1) * 256] = d_yp.cpu().numpy()
+    np.testing.assert_array_equal(ye, alone_e)
+    np.testing.assert_array_equal(yp, alone_p)
+    e.close()
+    p.close()
