@@ -155,3 +155,64 @@ def random_case(seed, n_in, n_out, taps, block, n_blocks, sigma=0.1, decay_s=Non
         h = rng.standard_normal((n_out, n_in, taps)) / np.sqrt(max(taps, 1))
     x = white_noise(rng, n_in, block * n_blocks, sigma)
     return Workload(f"rand_{n_in}x{n_out}_t{taps}_B{block}", FS, block, _f32(h), _f32(x))
+
+
+@dataclass
+class SessionSpec:
+    """Shape and seed of one auralization session; filters are drawn on demand."""
+
+    n_in: int
+    n_out: int
+    taps: int
+    block: int
+    seed: int
+    rt60: float
+    taps_fb: int = 0
+
+    def filters(self):
+        rng = np.random.default_rng(self.seed)
+        t = np.arange(self.taps, dtype=np.float32) / FS
+        env = np.exp(np.float32(-DECAY_60DB) * t / np.float32(self.rt60)).astype(np.float32)
+        h = rng.standard_normal((self.n_out, self.n_in, self.taps), dtype=np.float32)
+        h *= env
+        h *= np.float32(1.0 / np.sqrt(max(1.0, float(np.sum(env * env)))))
+        return h
+
+    def paths(self):
+        rng = np.random.default_rng(self.seed + 7919)
+        f = exp_decay_noise(rng, (self.n_in, self.n_out), self.taps_fb, FS, 0.3)
+        return _f32(normalise_l2(f, 0.1))
+
+    def signal(self, n_blocks, seed_offset=0):
+        rng = np.random.default_rng(self.seed + 104729 + seed_offset)
+        return rng.standard_normal((self.n_in, n_blocks * self.block), dtype=np.float32) * np.float32(0.1)
+
+    def tapch_per_block(self):
+        t = float(self.n_in) * self.n_out * self.taps
+        if self.taps_fb:
+            t += float(self.n_in) * self.n_out * self.taps_fb
+        return t * self.block
+
+
+def batch_sessions(count=64, seed=4):
+    """Heterogeneous sessions: inputs U{1..8}, outputs U{2..32}, filters
+    U(2, 12) s of exponentially decaying noise (RT60 = 3/4 of the length),
+    blocks from {64, 128, 256, 512, 1024}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        secs = float(rng.uniform(2.0, 12.0))
+        out.append(SessionSpec(
+            n_in=int(rng.integers(1, 9)), n_out=int(rng.integers(2, 33)), taps=int(secs * FS),
+            block=int(rng.choice([64, 128, 256, 512, 1024])), seed=seed * 100003 + i, rt60=0.75 * secs))
+    return out
+
+
+def serving_session(rng, seed):
+    """One arriving session of the serving workload: 1-8 inputs x 8-64 outputs,
+    1-15 s filters, block 128 or 256, half with a feedback canceller (0.5 s paths)."""
+    secs = float(rng.uniform(1.0, 15.0))
+    afc = bool(rng.integers(0, 2))
+    return SessionSpec(
+        n_in=int(rng.integers(1, 9)), n_out=int(rng.integers(8, 65)), taps=int(secs * FS),
+        block=int(rng.choice([128, 256])), seed=seed, rt60=0.75 * secs, taps_fb=24000 if afc else 0)
