@@ -213,6 +213,13 @@ int conv_plan_check(int precision, int block, int n_src, int n_dst, long long ta
 int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int block, int n_in, int n_out, long long K,
                          long long slot0, float* d_y, void* cuda_stream);
 
+/* Device bytes a handle with these sizes would hold (synthesis, plus the
+ * feedback canceller when taps_fb > 0), from the same planner the engine
+ * uses; host-only, allocates nothing.  For admission control.  -1 with
+ * conv_last_error() on invalid sizes. */
+long long conv_footprint(int precision, int block, int n_in, int n_out, long long taps, long long taps_fb,
+                         int num_sms);
+
 /* ---------------------------------------------------------------- batches
  * A batch processes one block of each of many independent sessions per step
  * with one launch per stage for all of them (batched pack + R2C, batched

@@ -1029,6 +1029,32 @@ int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches)
     return CONV_OK;
 }
 
+long long conv_footprint(int precision, int block, int n_in, int n_out, long long taps, long long taps_fb,
+                         int num_sms) {
+    if (precision < CONV_FP32 || precision > CONV_BF16 || block < 16 || block > 4096 || (block & (block - 1)) ||
+        n_in < 1 || n_out < 1 || taps < 1 || taps_fb < 0 || num_sms < 1) {
+        set_err(CONV_E_INVAL, "invalid footprint arguments");
+        return -1;
+    }
+    auto part = [&](int n_src, int n_dst, long long t) -> long long {
+        const long long K = (t + block - 1) / block;
+        if ((long long)n_src * K > 0x7fffffffLL / 2) return -1;
+        const MacPlan p = plan_mac(precision, block, n_src, n_dst, (int)K, num_sms, n_src);
+        // part buffers: spectra, ring, two partial buffers, window, scales
+        return (long long)part_bytes(p, precision) + (long long)p.partial_bytes;
+    };
+    long long b = part(n_in, n_out, taps);
+    if (b < 0) return set_err(CONV_E_INVAL, "too many partitions"), -1;
+    if (taps_fb > 0) {
+        const long long f = part(n_out, n_in, taps_fb);
+        if (f < 0) return set_err(CONV_E_INVAL, "too many partitions"), -1;
+        b += f + 2LL * n_in * block * (long long)sizeof(float);  // prediction and error buffers
+    }
+    // twiddles, staging, error word
+    b += 2LL * block * (long long)sizeof(float2) + (long long)(n_in + n_out) * block * (long long)sizeof(float);
+    return b;
+}
+
 int conv_plan_check(int precision, int block, int n_src, int n_dst, long long taps, int num_sms,
                     const conv_tiling* t) {
     if (precision < CONV_FP32 || precision > CONV_BF16 || block < 16 || block > 4096 || (block & (block - 1)) ||

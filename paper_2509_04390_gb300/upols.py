@@ -127,6 +127,7 @@ def load():
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "conv_plan_check": (i, [i, i, i, i, ll, i, ctypes.POINTER(conv_tiling)]),
         "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
+        "conv_footprint": (ll, [i, i, i, i, ll, ll, i]),
         "conv_batch_create": (vp, [i]),
         "conv_batch_add": (i, [vp, vp]),
         "conv_batch_remove": (i, [vp, vp]),
@@ -291,6 +292,16 @@ def conv_fdl_mac_noalloc(d_H, d_X, block, n_in, n_out, K, slot0, d_y, stream=Non
             _stream_ptr(stream),
         )
     )
+
+
+def conv_footprint(precision, block, n_in, n_out, taps, taps_fb=0, num_sms=152):
+    v = load().conv_footprint(
+        int(PRECISIONS.get(precision, precision)), int(block), int(n_in), int(n_out), int(taps), int(taps_fb),
+        int(num_sms),
+    )
+    if v < 0:
+        raise ConvError(CONV_E_INVAL, conv_last_error())
+    return int(v)
 
 
 def conv_batch_create(precision="fp32"):

@@ -1,0 +1,93 @@
+"""Serving: a session's output is the same alone and in the mix.
+
+A session is served on the 128-sample tick among other sessions that arrive
+and depart (blocks 128 and 256, some with a feedback canceller); its output
+must be bit-identical to the same session processed on its own, because every
+reduction in the engine has a fixed order whatever else is batched with it.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from paper_2509_04390_gb300 import build, serve, signals
+from paper_2509_04390_gb300 import upols as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def engine_lib():
+    if not os.path.exists(build.lib_path()):
+        build.build()
+    U.load()
+
+
+def small_spec(rng, seed, afc=False, block=None):
+    secs = float(rng.uniform(0.05, 0.3))
+    return signals.SessionSpec(
+        n_in=int(rng.integers(1, 4)), n_out=int(rng.integers(2, 9)), taps=int(secs * signals.FS),
+        block=block or int(rng.choice([128, 256])), seed=seed, rt60=0.75 * secs, taps_fb=2000 if afc else 0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("afc", [False, True])
+def test_alone_equals_in_the_mix(precision, afc):
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(41)
+    pool = serve.FilterPool(seed=3, n_out=8, n_in=4, taps=int(0.3 * signals.FS) + 1)
+    watched = small_spec(rng, 1000, afc=afc, block=256)
+    x = watched.signal(12)
+    h = pool.filters(watched)
+    f = watched.paths() if afc else None
+
+    # alone
+    e = U.Engine(signals.FS, 256, watched.n_in, watched.n_out, watched.taps, precision, serve.BATCH_TILING)
+    e.set_filters(h)
+    blocks = []
+    if afc:
+        e.set_paths(f)
+        for b in range(12):
+            blocks.append(e.process_afc(np.ascontiguousarray(x[:, b * 256 : (b + 1) * 256])).copy())
+    else:
+        for b in range(12):
+            blocks.append(e.process(np.ascontiguousarray(x[:, b * 256 : (b + 1) * 256])).copy())
+    alone = np.concatenate(blocks, axis=1)
+    e.close()
+
+    # in the mix: others arrive and depart around it
+    srv = serve.Server(precision, budget_bytes=2 << 30)
+    others = [srv.admit(sp, pool.filters(sp)) for sp in (small_spec(rng, 2000 + i, afc=(i % 2 == 1)) for i in range(3))]
+    srv.run_tick()
+    w = srv.admit(watched, h, paths=f, x=x, keep_outputs=True)
+    assert w is not None
+    tick = 0
+    while w.blocks < 12:
+        srv.run_tick()
+        tick += 1
+        if tick == 5:
+            srv.depart(others[0])
+        if tick == 9:
+            srv.admit(small_spec(rng, 3000, afc=True), pool.filters(small_spec(np.random.default_rng(7), 3000)))
+        assert tick < 100
+    mixed = np.concatenate(w.outputs, axis=1)
+    srv.close()
+    np.testing.assert_array_equal(mixed, alone)
+
+
+def test_admission_respects_the_memory_budget():
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    pool = serve.FilterPool(seed=3, n_out=8, n_in=4, taps=int(0.3 * signals.FS) + 1)
+    sp = small_spec(rng, 1)
+    fp = U.conv_footprint("fp32", sp.block, sp.n_in, sp.n_out, sp.taps, sp.taps_fb)
+    srv = serve.Server("fp32", budget_bytes=int(2.5 * fp))
+    assert srv.admit(sp, pool.filters(sp)) is not None
+    assert srv.admit(sp, pool.filters(sp)) is not None
+    assert srv.admit(sp, pool.filters(sp)) is None  # a third does not fit
+    assert srv.rejected == 1
+    assert srv.used <= srv.budget
+    srv.depart(srv.sessions[0])
+    assert srv.admit(sp, pool.filters(sp)) is not None  # room again after a departure
+    srv.close()
