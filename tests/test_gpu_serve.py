@@ -69,7 +69,8 @@ def test_alone_equals_in_the_mix(precision, afc):
         if tick == 5:
             srv.depart(others[0])
         if tick == 9:
-            srv.admit(small_spec(rng, 3000, afc=True), pool.filters(small_spec(np.random.default_rng(7), 3000)))
+            late = small_spec(rng, 3000, afc=True)
+            srv.admit(late, pool.filters(late))
         assert tick < 100
     mixed = np.concatenate(w.outputs, axis=1)
     srv.close()
