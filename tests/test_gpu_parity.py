@@ -299,3 +299,25 @@ def test_closed_loop_paper_scale(precision, bound):
     print(f"closed loop {precision}: e vs s {s_e:.1f} dB, output {s_y:.1f} dB")
     assert s_e >= bound
     assert s_y >= bound
+
+
+# ------------------------------------------- long closed-loop drift study
+
+
+@pytest.mark.parametrize("precision,bound", [("fp32", 110.0), ("fp16", 55.0), ("bf16", 38.0)])
+def test_closed_loop_does_not_drift(precision, bound):
+    """20 s of closed loop (2 mics x 8 loudspeakers, 1 s synthesis filters,
+    0.3 s paths at -20 dB, F_hat = F): the error signal must stay the dry
+    source, window after window; a drift would show as a falling SNR."""
+    rng = np.random.default_rng(77)
+    B, P, L = 256, 2, 8
+    h = signals.paper_filters(rng, L, P, 48000, rt60=0.8, reflections=5).astype(np.float32)
+    f = signals.feedback_paths(rng, P, L, 14400).astype(np.float32)
+    nb = 20 * 48000 // B
+    s = (rng.standard_normal((P, nb * B)) * 0.1).astype(np.float32)
+    y, e = run_gpu_closed_loop(h, f, f, s, B, precision)
+    win = 48000
+    snrs = [snr_db(e[:, i : i + win], s[:, i : i + win]) for i in range(0, nb * B - win + 1, win)]
+    print(f"drift {precision}: first {snrs[0]:.1f} dB, last {snrs[-1]:.1f} dB, min {min(snrs):.1f} dB")
+    assert min(snrs) >= bound
+    assert snrs[-1] >= snrs[0] - 3.0
