@@ -88,8 +88,9 @@ int conv_set_precision(conv_engine* e, int mode);
 /* FDL MAC kernels (conv_tiling.kernel) */
 #define CONV_KERNEL_AUTO 0    /* planner's choice                                        */
 #define CONV_KERNEL_TMA 1     /* producer warp streams 1-D bulk copies (TMA) into a ring */
-#define CONV_KERNEL_DIRECT1 2 /* direct 16-byte loads, 1 partition in flight, 3 CTAs/SM */
-#define CONV_KERNEL_DIRECT2 3 /* direct 16-byte loads, 2 partitions in flight, 2 CTAs/SM */
+#define CONV_KERNEL_DIRECT1 2 /* direct 16-byte loads, 1 partition in flight, 3 CTAs/SM (FP32 only;
+                                 reduced precision falls back to CONV_KERNEL_TMA) */
+#define CONV_KERNEL_DIRECT2 3 /* direct 16-byte loads, 2 partitions in flight, 2 CTAs/SM (FP32 only) */
 
 /* Tiling of the synthesis FDL MAC; every field 0 = the planner's choice.
  *   kernel     CONV_KERNEL_*

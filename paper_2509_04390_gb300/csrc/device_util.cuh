@@ -39,41 +39,55 @@ __device__ __forceinline__ void rmac2(float2& acc, float2 h, float2 x) {
 template <int PREC>
 struct Store;
 
+// Storage of a spectrum row of BT bins.  FP32 rows interleave (re, im);
+// FP16/BF16 rows are planar, [BT real parts][BT imaginary parts], so the MAC
+// can work on pairs of bins with packed FP32x2 FMAs.  `c` is the complex
+// element index (row start + kl), kl the bin within the row.
 template <>
 struct Store<PREC_FP32> {
     static constexpr int BYTES = 8;
     static constexpr int VEC = 2;
+    static constexpr bool PLANAR = false;
     __device__ __forceinline__ static void load16(const void* p, float2 (&v)[VEC]) {
         const float4 t = *reinterpret_cast<const float4*>(p);
         v[0] = make_float2(t.x, t.y);
         v[1] = make_float2(t.z, t.w);
     }
-    __device__ __forceinline__ static void store1(void* base, size_t idx, float2 v) {
-        reinterpret_cast<float2*>(base)[idx] = v;
+    __device__ __forceinline__ static void store1(void* base, size_t c, int kl, int BT, float2 v) {
+        (void)kl;
+        (void)BT;
+        reinterpret_cast<float2*>(base)[c] = v;
     }
-    __device__ __forceinline__ static float2 load1(const void* base, size_t idx) {
-        return reinterpret_cast<const float2*>(base)[idx];
+    __device__ __forceinline__ static float2 load1(const void* base, size_t c, int kl, int BT) {
+        (void)kl;
+        (void)BT;
+        return reinterpret_cast<const float2*>(base)[c];
     }
 };
+
+__device__ __forceinline__ float2 unpack_half2(uint32_t w) {
+    __half2 h2 = *reinterpret_cast<const __half2*>(&w);
+    return __half22float2(h2);
+}
+// bfloat16 -> float is exact: the bf16 bits are the top half of the float's
+__device__ __forceinline__ float2 unpack_bf162(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
 
 template <>
 struct Store<PREC_FP16> {
     static constexpr int BYTES = 4;
     static constexpr int VEC = 4;
-    __device__ __forceinline__ static void load16(const void* p, float2 (&v)[VEC]) {
-        const uint4 t = *reinterpret_cast<const uint4*>(p);
-        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __half2 h2 = *reinterpret_cast<const __half2*>(&w[i]);
-            v[i] = __half22float2(h2);
-        }
+    static constexpr bool PLANAR = true;
+    __device__ __forceinline__ static float2 unpack(uint32_t w) { return unpack_half2(w); }
+    __device__ __forceinline__ static void store1(void* base, size_t c, int kl, int BT, float2 v) {
+        __half* h = reinterpret_cast<__half*>(base) + 2 * (c - kl) + kl;
+        h[0] = __float2half_rn(v.x);
+        h[BT] = __float2half_rn(v.y);
     }
-    __device__ __forceinline__ static void store1(void* base, size_t idx, float2 v) {
-        reinterpret_cast<__half2*>(base)[idx] = __floats2half2_rn(v.x, v.y);
-    }
-    __device__ __forceinline__ static float2 load1(const void* base, size_t idx) {
-        return __half22float2(reinterpret_cast<const __half2*>(base)[idx]);
+    __device__ __forceinline__ static float2 load1(const void* base, size_t c, int kl, int BT) {
+        const __half* h = reinterpret_cast<const __half*>(base) + 2 * (c - kl) + kl;
+        return make_float2(__half2float(h[0]), __half2float(h[BT]));
     }
 };
 
@@ -81,22 +95,40 @@ template <>
 struct Store<PREC_BF16> {
     static constexpr int BYTES = 4;
     static constexpr int VEC = 4;
-    __device__ __forceinline__ static void load16(const void* p, float2 (&v)[VEC]) {
-        const uint4 t = *reinterpret_cast<const uint4*>(p);
-        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
-            v[i] = __bfloat1622float2(b2);
-        }
+    static constexpr bool PLANAR = true;
+    __device__ __forceinline__ static float2 unpack(uint32_t w) { return unpack_bf162(w); }
+    __device__ __forceinline__ static void store1(void* base, size_t c, int kl, int BT, float2 v) {
+        __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(base) + 2 * (c - kl) + kl;
+        h[0] = __float2bfloat16_rn(v.x);
+        h[BT] = __float2bfloat16_rn(v.y);
     }
-    __device__ __forceinline__ static void store1(void* base, size_t idx, float2 v) {
-        reinterpret_cast<__nv_bfloat162*>(base)[idx] = __floats2bfloat162_rn(v.x, v.y);
-    }
-    __device__ __forceinline__ static float2 load1(const void* base, size_t idx) {
-        return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(base)[idx]);
+    __device__ __forceinline__ static float2 load1(const void* base, size_t c, int kl, int BT) {
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(base) + 2 * (c - kl) + kl;
+        return make_float2(__bfloat162float(h[0]), __bfloat162float(h[BT]));
     }
 };
+
+// Four planar bins (8 bytes of real parts, 8 of imaginary parts) as floats.
+template <typename St>
+__device__ __forceinline__ void load_planar4(const unsigned char* row, int kv, int BT, float2 (&re)[2],
+                                             float2 (&im)[2]) {
+    const uint2 r = *reinterpret_cast<const uint2*>(row + (size_t)kv * 8);
+    const uint2 i = *reinterpret_cast<const uint2*>(row + (size_t)BT * 2 + (size_t)kv * 8);
+    re[0] = St::unpack(r.x);
+    re[1] = St::unpack(r.y);
+    im[0] = St::unpack(i.x);
+    im[1] = St::unpack(i.y);
+}
+
+// d = a * b + c on pairs of floats (one packed FP32x2 FMA)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+          "l"(*reinterpret_cast<unsigned long long*>(&c)));
+    return *reinterpret_cast<float2*>(&d);
+}
 
 // Power-of-two scale for a block of values with largest magnitude `maxabs`:
 // FP16 stores value/scale in [2^13, 2^14) at the top (well inside 65504),

@@ -126,7 +126,8 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     const int Rt = p.R - r_begin;
     p.es = prec == PREC_FP32 ? 8 : 4;
     p.VEC = 16 / p.es;
-    p.direct = o.kernel == CONV_KERNEL_DIRECT1 ? 1 : (o.kernel == CONV_KERNEL_DIRECT2 ? 2 : 0);
+    // the direct-load MAC reads interleaved FP32 rows only; reduced precision uses the TMA MAC
+    p.direct = prec != PREC_FP32 ? 0 : (o.kernel == CONV_KERNEL_DIRECT1 ? 1 : (o.kernel == CONV_KERNEL_DIRECT2 ? 2 : 0));
     p.LPT = (prec == PREC_FP32 && !p.direct) ? 8 : 4;
     p.nw = p.direct ? 8 : (o.warps ? o.warps : MAC_CONSUMER_WARPS);
     p.interleave = (!p.direct && o.order == CONV_ORDER_INTERLEAVED) ? 1 : 0;

@@ -71,16 +71,17 @@ __device__ float spectrum_max(const float2* Xs, int B, float* red) {
 // Writes the packed spectrum Xs[0..B) divided by `scale` (a power of two, so
 // exactly) in storage precision; `dst_index(k)` gives the element of bin k.
 template <int PREC, typename IndexFn>
-__device__ void store_scaled(const float2* Xs, int B, void* dst, IndexFn dst_index, float scale) {
+__device__ void store_scaled(const float2* Xs, int B, int BT, void* dst, IndexFn dst_index, float scale) {
     const float inv = 1.0f / scale;
-    for (int k = threadIdx.x; k < B; k += blockDim.x) Store<PREC>::store1(dst, dst_index(k), cscale(Xs[k], inv));
+    for (int k = threadIdx.x; k < B; k += blockDim.x)
+        Store<PREC>::store1(dst, dst_index(k), k % BT, BT, cscale(Xs[k], inv));
 }
 
 // Writes Xs with its own power-of-two scale (FP32: scale 1).  Returns the scale.
 template <int PREC, typename IndexFn>
-__device__ float store_spectrum(const float2* Xs, int B, void* dst, IndexFn dst_index, float* red) {
+__device__ float store_spectrum(const float2* Xs, int B, int BT, void* dst, IndexFn dst_index, float* red) {
     const float scale = PREC == PREC_FP32 ? 1.0f : block_scale<PREC>(spectrum_max(Xs, B, red));
-    store_scaled<PREC>(Xs, B, dst, dst_index, scale);
+    store_scaled<PREC>(Xs, B, BT, dst, dst_index, scale);
     return scale;
 }
 
@@ -127,7 +128,7 @@ __device__ __forceinline__ void pack_body(const PackArgs& a, const int c) {
     float2* Xs = (Z == bufA) ? bufB : bufA;
     for (int k = tid; k < B; k += nth) Xs[k] = r2c_post(Z, k, B, tws);
     __syncthreads();
-    const float scale = store_spectrum<PREC>(Xs, B, a.X, RingIndex{a.BT, a.n_ch, c, a.K, a.slot}, red);
+    const float scale = store_spectrum<PREC>(Xs, B, a.BT, a.X, RingIndex{a.BT, a.n_ch, c, a.K, a.slot}, red);
     if (PREC != PREC_FP32 && tid == 0) a.sX[(size_t)a.slot * a.n_ch + c] = scale;
 }
 
@@ -181,7 +182,7 @@ __global__ void k_filter_r2c(const FilterArgs a) {
     }
     const float scale = PREC == PREC_FP32 ? 1.0f : __ldg(a.sH + (size_t)(l / a.LT) * R + r);
     const int n_lt = (a.n_dst + a.LT - 1) / a.LT;
-    store_scaled<PREC>(Xs, B, a.H, FilterIndex{a.BT, n_lt, l / a.LT, r, LTt, ll, a.tile_elems}, scale);
+    store_scaled<PREC>(Xs, B, a.BT, a.H, FilterIndex{a.BT, n_lt, l / a.LT, r, LTt, ll, a.tile_elems}, scale);
 }
 
 // One power-of-two scale per (output tile, reduction index): from the largest
@@ -384,33 +385,80 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
             // the wrapped second run (ring rows 0..) lands after the first run's padded span
             sx2 = (((start + xrun + 3) & ~3) - (start & ~3)) - xrun;
         }
-        for (int j = rl; j < nr; j += a.NRL) {
-            float2 xv[VEC];
-            St::load16(sx + (size_t)j * hrow + (size_t)kv * 16, xv);
-            if (PREC != PREC_FP32) {
-                // both scales are per reduction index: fold them into x once
-                const float sc = (j < xrun ? ssx[sx0 + j] : ssx[sx2 + j]) * ssh[sh0 + j];
+        if constexpr (!St::PLANAR) {
+            for (int j = rl; j < nr; j += a.NRL) {
+                float2 xv[VEC];
+                St::load16(sx + (size_t)j * hrow + (size_t)kv * 16, xv);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) xv[v] = cscale(xv[v], sc);
+                for (int i = 0; i < LPT; ++i) {
+                    const int ll = lg + i * a.NLG;
+                    if (ll < LTt) {
+                        float2 hv[VEC];
+                        St::load16(sh + ((size_t)j * LTt + ll) * hrow + (size_t)kv * 16, hv);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            if (v == 0 && dc)
+                                rmac2(acc[i][v], hv[v], xv[v]);
+                            else
+                                cmac(acc[i][v], hv[v], xv[v]);
+                        }
+                    }
+                }
             }
+        } else {
+            // Planar rows, 4 bins per thread as two pairs; acc[i] = (re 0-1, re 2-3,
+            // im 0-1, im 2-3).  Per pair: re += hr*xr + hi*(-xi), im += hr*xi + hi*xr,
+            // four packed FP32x2 FMAs.  Both scales are per reduction index and are
+            // folded into x once.  The packed bin 0 (DC, Nyquist) needs re += hr*xr
+            // and im += hi*xi: its lane of the operand pairs is set up for that here,
+            // outside the output loop.
+            for (int j = rl; j < nr; j += a.NRL) {
+                float2 xr[2], xi[2];
+                load_planar4<St>(sx + (size_t)j * hrow, kv, a.BT, xr, xi);
+                const float sc = (j < xrun ? ssx[sx0 + j] : ssx[sx2 + j]) * ssh[sh0 + j];
+                xr[0] = cscale(xr[0], sc);
+                xr[1] = cscale(xr[1], sc);
+                xi[0] = cscale(xi[0], sc);
+                xi[1] = cscale(xi[1], sc);
+                float2 nxi0 = make_float2(-xi[0].x, -xi[0].y);
+                const float2 nxi1 = make_float2(-xi[1].x, -xi[1].y);
+                float2 xi0 = xi[0], xr0b = xr[0];
+                if (dc) {
+                    nxi0.x = 0.0f;
+                    xi0.x = 0.0f;
+                    xr0b.x = xi[0].x;
+                }
 #pragma unroll
-            for (int i = 0; i < LPT; ++i) {
-                const int ll = lg + i * a.NLG;
-                if (ll < LTt) {
-                    float2 hv[VEC];
-                    St::load16(sh + ((size_t)j * LTt + ll) * hrow + (size_t)kv * 16, hv);
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        if (v == 0 && dc)
-                            rmac2(acc[i][v], hv[v], xv[v]);
-                        else
-                            cmac(acc[i][v], hv[v], xv[v]);
+                for (int i = 0; i < LPT; ++i) {
+                    const int ll = lg + i * a.NLG;
+                    if (ll < LTt) {
+                        float2 hr[2], hi[2];
+                        load_planar4<St>(sh + ((size_t)j * LTt + ll) * hrow, kv, a.BT, hr, hi);
+                        acc[i][0] = ffma2(hr[0], xr[0], acc[i][0]);
+                        acc[i][0] = ffma2(hi[0], nxi0, acc[i][0]);
+                        acc[i][1] = ffma2(hr[1], xr[1], acc[i][1]);
+                        acc[i][1] = ffma2(hi[1], nxi1, acc[i][1]);
+                        acc[i][2] = ffma2(hr[0], xi0, acc[i][2]);
+                        acc[i][2] = ffma2(hi[0], xr0b, acc[i][2]);
+                        acc[i][3] = ffma2(hr[1], xi[1], acc[i][3]);
+                        acc[i][3] = ffma2(hi[1], xr[1], acc[i][3]);
                     }
                 }
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
+    }
+
+    if constexpr (St::PLANAR) {
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) {
+            const float2 re01 = acc[i][0], re23 = acc[i][1], im01 = acc[i][2], im23 = acc[i][3];
+            acc[i][0] = make_float2(re01.x, im01.x);
+            acc[i][1] = make_float2(re01.y, im01.y);
+            acc[i][2] = make_float2(re23.x, im23.x);
+            acc[i][3] = make_float2(re23.y, im23.y);
+        }
     }
 
     // combine r-lanes in a fixed order (stage memory is free: every stage has landed)
@@ -633,8 +681,8 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
             const size_t xbase = (((size_t)kt * a.K + a.slot0) * a.n_src) * a.BT + kl;
             float2 hd = make_float2(0.0f, 0.0f);
             for (int q = 0; q < a.n_src; ++q) {
-                const float2 h = St::load1(a.H, hbase + (size_t)q * LTt * a.BT);
-                const float2 x = St::load1(a.X, xbase + (size_t)q * a.BT);
+                const float2 h = St::load1(a.H, hbase + (size_t)q * LTt * a.BT, kl, a.BT);
+                const float2 x = St::load1(a.X, xbase + (size_t)q * a.BT, kl, a.BT);
                 float2 t = make_float2(0.0f, 0.0f);
                 if (k == 0)
                     rmac2(t, h, x);
@@ -764,11 +812,7 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR((k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>(), 16>), mac_smem)
     GB_ATTR((k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>(), 16>), mac_smem)
     GB_ATTR((k_fdl_mac_ldg<PREC_FP32, 4, 8, 1, 3>), mac_smem)
-    GB_ATTR((k_fdl_mac_ldg<PREC_FP16, 4, 8, 1, 3>), mac_smem)
-    GB_ATTR((k_fdl_mac_ldg<PREC_BF16, 4, 8, 1, 3>), mac_smem)
     GB_ATTR((k_fdl_mac_ldg<PREC_FP32, 4, 8, 2, 2>), mac_smem)
-    GB_ATTR((k_fdl_mac_ldg<PREC_FP16, 4, 8, 2, 2>), mac_smem)
-    GB_ATTR((k_fdl_mac_ldg<PREC_BF16, 4, 8, 2, 2>), mac_smem)
 #undef GB_ATTR
     return cudaSuccess;
 }
@@ -825,8 +869,6 @@ cudaError_t launch_fdl_mac_direct_u(int prec, const MacPlan& p, const MacArgs& a
     const dim3 grid(p.ctas), block(8 * 32);
     switch (prec) {
         case PREC_FP32: return launch_pdl(k_fdl_mac_ldg<PREC_FP32, 4, 8, U, MINB>, grid, block, p.smem, s, a);
-        case PREC_FP16: return launch_pdl(k_fdl_mac_ldg<PREC_FP16, 4, 8, U, MINB>, grid, block, p.smem, s, a);
-        case PREC_BF16: return launch_pdl(k_fdl_mac_ldg<PREC_BF16, 4, 8, U, MINB>, grid, block, p.smem, s, a);
         default: return cudaErrorInvalidValue;
     }
 }
