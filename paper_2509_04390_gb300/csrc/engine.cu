@@ -181,8 +181,9 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     p.sxoff = (unsigned)(p.soff + sh_part(p.RS));
     p.stage_bytes = (unsigned)stage_size(p.RS);
     const int fit = (int)std::max<size_t>(2, budget / p.stage_bytes);
-    // two large stages measured best; deeper rings only added bytes in flight
-    p.nstage = std::min(2, fit);
+    // measured on the back-to-back step: FP32 streams best with two large
+    // stages; FP16/BF16 (more consumer work per byte) with three
+    p.nstage = std::min(prec == PREC_FP32 ? 2 : 3, fit);
     if (o.stages) p.nstage = std::max(2, std::min(o.stages, fit));
     // scratch for combining r-lanes reuses (and if needed extends) the stage ring
     const size_t red = (size_t)(p.NRL - 1) * p.LT * p.BT * sizeof(float2);
