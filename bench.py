@@ -171,7 +171,8 @@ def make_workload(args):
 
 def workload_name(args):
     if args.afc:
-        return f"afc_4x16_{args.taps}taps_fb{args.taps_fb}_B{args.block}_{args.precision}"
+        nlms = "_nlms" if args.adapt > 0 else ""
+        return f"afc{nlms}_4x16_{args.taps}taps_fb{args.taps_fb}_B{args.block}_{args.precision}"
     return f"paper_4x16_{args.taps}taps_B{args.block}_{args.precision}"
 
 
@@ -317,6 +318,8 @@ def run_ours(args):
     eng.set_filters(w.h)
     if args.afc:
         eng.set_paths(w.f)
+        if args.adapt > 0:
+            eng.set_adaptation(args.adapt, 0.95, 1e-1)
     info = eng.info()
     nb = w.x.shape[1] // B
     d_x = torch.from_numpy(np.ascontiguousarray(w.x[:, : nb * B])).cuda()
@@ -669,6 +672,7 @@ def parse(argv=None):
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
     ap.add_argument("--afc", action="store_true", help="synthesis + feedback canceller (paths [4][16], 0.5 s)")
     ap.add_argument("--taps-fb", type=int, default=24000)
+    ap.add_argument("--adapt", type=float, default=0.0, help="with --afc: NLMS step size of the adaptive canceller")
     ap.add_argument("--e2e-steps", type=int, default=5000)
     ap.add_argument("--paced-blocks", type=int, default=1000)
     ap.add_argument("--cpu-budget", type=float, default=20.0)

@@ -69,6 +69,7 @@ typedef struct conv_info {
     long long mac_stage_bytes; /* bytes per MAC pipeline stage                    */
     long long mac_warps;      /* MAC consumer warps                               */
     long long mac_kernel;     /* CONV_KERNEL_TMA / _DIRECT1 / _DIRECT2            */
+    long long afc_adaptive;   /* 1 if the canceller adapts (afc_set_adaptation)   */
 } conv_info;
 
 /* Create an engine for n_in inputs, n_out outputs and filters of `taps` taps
@@ -153,6 +154,39 @@ int afc_process_block_async(conv_engine* e, const float* d_mic, float* d_out, fl
  * `max_rms` (> 0), the call returns CONV_E_UNSTABLE and resets the loop
  * state.  0 disables the guard (the default). */
 int afc_set_guard(conv_engine* e, double max_rms);
+
+/* Adaptive feedback canceller.  An extension beyond the paper, whose F_hat
+ * (Sec. 3.1, Sec. 5) is known in advance and static.  mu > 0 turns on a
+ * partitioned-block frequency-domain NLMS update of the canceller's
+ * sub-filter spectra; mu = 0 turns it off again (F_hat keeps its adapted value).
+ *
+ * Once per afc block n, after e_n = mic_n - c_{n-1} is formed and before l_n
+ * enters the canceller's delay line:
+ *   E_p    = R2C_2B([0_B | e_n,p])               (B zeros, then the error block)
+ *   pow[k] = lambda pow[k] + (1 - lambda) sum_l |U_l,0[k]|^2
+ *   F_hat[p][l][j][k] += mu E_p[k] conj(U_l,j[k]) / (K_fb pow[k] + delta)
+ * U_l,j: R2C of loudspeaker l's 2B-sample window of block n-1-j (the delay
+ * line that produced c_{n-1}).  The update is unconstrained: it does not
+ * project F_hat back onto B-tap sub-filters.  The packed bin 0 holds DC and
+ * Nyquist, and each is updated with its own power.  pow starts at 0, and
+ * conv_reset sets it back to 0.  conv_reset keeps the adapted F_hat.
+ * afc_set_paths restores a given estimate.  c_n is computed with the
+ * updated F_hat.
+ *
+ * mu in [0, 2), lambda in [0, 1), delta >= 0 finite (> 0 when mu > 0), else
+ * CONV_E_INVAL.  CONV_E_STATE without afc_set_paths, for FP16/BF16 engines
+ * (the update needs FP32 spectra), or while the session is in a batch.
+ * Waits for the engine's queued work.  Takes effect from the next block. */
+int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta);
+
+/* Copy the canceller's current sub-filter spectra to host memory f_spec, laid
+ * out [n_in (mic p)][n_out (loudspeaker l)][K_fb][block] complex values as
+ * (re, im) float pairs: 2 * n_in * n_out * K_fb * block floats, owned by the
+ * caller.  Bin 0 holds (DC, Nyquist).  The values are 2B-point R2C
+ * spectra of the zero-padded sub-filters, unscaled (Sec. 4 initialisation).
+ * Waits for the engine's queued work.  CONV_E_STATE without afc_set_paths or
+ * for FP16/BF16 engines. */
+int afc_get_path_spectra(conv_engine* e, float* f_spec);
 
 /* Zero the delay lines, sliding windows and the pending feedback prediction
  * (start of a new stream).  Filters are kept. */

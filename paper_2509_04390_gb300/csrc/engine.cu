@@ -36,6 +36,7 @@
 
 #include "conv.h"
 #include "kernels.h"
+#include "nlms.h"
 
 using namespace gbconv;
 
@@ -403,6 +404,14 @@ struct conv_engine {
     std::vector<cudaEvent_t> ev0, ev1;
     size_t ev_used = 0;
     size_t dev_bytes = 0;
+    // adaptive canceller (afc_set_adaptation)
+    bool adapt = false;
+    float mu = 0.0f, lam = 0.0f, delta = 0.0f;
+    cudaStream_t as = nullptr;   // high-priority stream of the update and the canceller's tail
+    cudaEvent_t ev_upd = nullptr;  // this block's update is done: the delay line may advance
+    float2* d_pow = nullptr;     // [2][B] packed power estimates, by block parity
+    float2* d_G = nullptr;       // [n_in][B] step-scaled error spectra
+    int in_batches = 0;          // batches holding this session
 };
 
 namespace {
@@ -691,10 +700,12 @@ int engine_reset(conv_engine* e) {
     int rc;
     CK(cudaStreamSynchronize(e->bg[0]));
     CK(cudaStreamSynchronize(e->bg[1]));
+    if (e->as) CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
     if ((rc = part_reset(e, e->syn))) return rc;
     if ((rc = part_reset(e, e->fb))) return rc;
     if (e->d_c) CK(cudaMemsetAsync(e->d_c, 0, (size_t)e->n_in * e->B * sizeof(float), e->stream));
+    if (e->d_pow) CK(cudaMemsetAsync(e->d_pow, 0, 2 * (size_t)e->B * sizeof(float2), e->stream));
     CK(cudaStreamSynchronize(e->stream));
     e->nblk = 0;
     return CONV_OK;
@@ -707,15 +718,93 @@ int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t 
     return CONV_OK;
 }
 
+// Adaptive canceller, block n (after e_n is known): NLMS update of F_hat with
+// the delay line as it is (loudspeaker spectra up to block n-1), then the
+// canceller's tail for block n with the updated spectra.  Runs on the
+// high-priority stream e->as beside the synthesis output.
+int enqueue_adapt(conv_engine* e, const float* d_err_block, cudaStream_t s) {
+    Part& F = e->fb;
+    const MacPlan& p = F.plan;
+    const long long n = e->nblk;
+    CK(cudaStreamWaitEvent(e->as, e->syn.ev_packed, 0));  // e_n is written; c_{n-1}'s head has read F_hat
+    NlmsPrepArgs a{};
+    a.e = d_err_block;
+    a.U = static_cast<const float2*>(F.X);
+    a.slot0 = slot0_for(n > 0 ? n - 1 : 0, F.K);
+    a.pow_in = e->d_pow + (size_t)(n & 1) * e->B;
+    a.pow_out = e->d_pow + (size_t)((n + 1) & 1) * e->B;
+    a.G = e->d_G;
+    a.B = e->B;
+    a.log2B = e->log2B;
+    a.BT = p.BT;
+    a.L = F.n_src;
+    a.K = F.K;
+    a.mu = e->mu;
+    a.lam = e->lam;
+    a.delta = e->delta;
+    a.tw = e->tw;
+    CK(launch_nlms_prep(a, F.n_dst, e->as));
+    NlmsUpdateArgs u{};
+    u.F = static_cast<float2*>(F.H);
+    u.U = a.U;
+    u.G = e->d_G;
+    u.B = e->B;
+    u.BT = p.BT;
+    u.n_kt = p.n_kt;
+    u.LT = p.LT;
+    u.n_lt = p.n_lt;
+    u.P = F.n_dst;
+    u.L = F.n_src;
+    u.K = F.K;
+    u.slot0 = a.slot0;
+    const long long rows = (long long)p.R * p.n_kt * p.n_lt;
+    u.rows_per_cta = (int)std::max<long long>(1, (rows + 4LL * e->num_sms - 1) / (4LL * e->num_sms));
+    u.tile_elems = p.tile_elems;
+    CK(launch_nlms_update(u, e->as));
+    CK(cudaEventRecord(e->ev_upd, e->as));
+    int rc = enqueue_tail(e, F, n, e->as, false);
+    if (rc) return rc;
+    CK(cudaEventRecord(F.ev_tail[n & 1], e->as));
+    (void)s;
+    return CONV_OK;
+}
+
 // Synthesis with feedback cancellation (Sec. 5): e = mic - c_prev, l = H^T * e
 // (first half), then c = F_hat * l, kept for the next block (second half).
 // The host-buffer call copies l and e out between the halves.
 int enqueue_afc_synthesis(conv_engine* e, const float* d_mic, float* d_out, float* d_e, cudaStream_t s) {
-    return enqueue_conv(e, e->syn, d_mic, e->d_c, d_e, d_out, s, true);
+    if (!e->adapt) return enqueue_conv(e, e->syn, d_mic, e->d_c, d_e, d_out, s, true);
+    float* eb = d_e ? d_e : e->d_e;
+    Part& P = e->syn;
+    const long long n = e->nblk;
+    int rc;
+    if ((rc = enqueue_pack(e, P, d_mic, e->B, e->d_c, eb, s))) return rc;
+    CK(cudaEventRecord(P.ev_packed, s));
+    if ((rc = enqueue_adapt(e, eb, s))) return rc;
+    CK(cudaStreamWaitEvent(s, P.ev_tail[n & 1], 0));
+    if ((rc = enqueue_out(e, P, n, d_out, s))) return rc;
+    cudaStream_t bg = e->bg[(n + 1) & 1];
+    CK(cudaStreamWaitEvent(bg, P.ev_packed, 0));
+    if (e->prof) CK(cudaStreamWaitEvent(bg, P.ev_tail[n & 1], 0));
+    if ((rc = enqueue_tail(e, P, n + 1, bg, true))) return rc;
+    CK(cudaEventRecord(P.ev_tail[(n + 1) & 1], bg));
+    return CONV_OK;
 }
 
 int enqueue_afc_prediction(conv_engine* e, const float* d_out, cudaStream_t s) {
-    int rc = enqueue_conv(e, e->fb, d_out, nullptr, nullptr, e->d_c, s, false);
+    int rc;
+    if (!e->adapt) {
+        rc = enqueue_conv(e, e->fb, d_out, nullptr, nullptr, e->d_c, s, false);
+    } else {
+        // the update read the delay-line slot this push overwrites; the tail
+        // of this block ran on e->as with the updated spectra
+        Part& F = e->fb;
+        const long long n = e->nblk;
+        CK(cudaStreamWaitEvent(s, e->ev_upd, 0));
+        if ((rc = enqueue_pack(e, F, d_out, e->B, nullptr, nullptr, s))) return rc;
+        CK(cudaStreamWaitEvent(s, F.ev_tail[n & 1], 0));
+        rc = enqueue_out(e, F, n, e->d_c, s);
+    }
     if (rc) return rc;
     ++e->nblk;
     return CONV_OK;
@@ -727,6 +816,7 @@ void engine_free(conv_engine* e) {
     if (e->stream) cudaStreamSynchronize(e->stream);
     for (int i = 0; i < 2; ++i)
         if (e->bg[i]) cudaStreamSynchronize(e->bg[i]);
+    if (e->as) cudaStreamSynchronize(e->as);
     for (Part* P : {&e->syn, &e->fb}) {
         if (P->ev_packed) cudaEventDestroy(P->ev_packed);
         for (int i = 0; i < 2; ++i)
@@ -739,6 +829,10 @@ void engine_free(conv_engine* e) {
     dev_free(e, &e->d_out, 0);
     dev_free(e, &e->d_e, 0);
     dev_free(e, &e->d_c, 0);
+    dev_free(e, &e->d_pow, 0);
+    dev_free(e, &e->d_G, 0);
+    if (e->ev_upd) cudaEventDestroy(e->ev_upd);
+    if (e->as) cudaStreamDestroy(e->as);
     if (e->h_in) cudaFreeHost(e->h_in);
     if (e->h_out) cudaFreeHost(e->h_out);
     if (e->h_e) cudaFreeHost(e->h_e);
@@ -947,6 +1041,76 @@ int afc_set_guard(conv_engine* e, double max_rms) {
     return CONV_OK;
 }
 
+int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    if (!(mu >= 0.0 && mu < 2.0)) return set_err(CONV_E_INVAL, "mu must be in [0, 2)");
+    if (!(lambda >= 0.0 && lambda < 1.0)) return set_err(CONV_E_INVAL, "lambda must be in [0, 1)");
+    if (!(delta >= 0.0) || !std::isfinite(delta)) return set_err(CONV_E_INVAL, "delta must be finite and >= 0");
+    if (mu > 0.0 && !(delta > 0.0)) return set_err(CONV_E_INVAL, "delta must be > 0 when mu > 0");
+    if (!e->fb.ready) return set_err(CONV_E_STATE, "feedback paths not set");
+    if (e->prec != CONV_FP32) return set_err(CONV_E_STATE, "the adaptive canceller needs FP32 spectra");
+    if (e->in_batches > 0) return set_err(CONV_E_STATE, "session is in a batch");
+    DeviceGuard g(e->dev);
+    int rc;
+    if (!e->as) {
+        int prio_low = 0, prio_high = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+        CK(cudaStreamCreateWithPriority(&e->as, cudaStreamNonBlocking, prio_high));
+        CK(cudaEventCreateWithFlags(&e->ev_upd, cudaEventDisableTiming));
+    }
+    if (!e->d_pow) {
+        if ((rc = dev_alloc(e, &e->d_pow, 2 * (size_t)e->B * sizeof(float2)))) return rc;
+        CK(cudaMemsetAsync(e->d_pow, 0, 2 * (size_t)e->B * sizeof(float2), e->stream));
+    }
+    if (!e->d_G && (rc = dev_alloc(e, &e->d_G, (size_t)e->n_in * e->B * sizeof(float2)))) return rc;
+    CK(cudaStreamSynchronize(e->bg[0]));
+    CK(cudaStreamSynchronize(e->bg[1]));
+    CK(cudaStreamSynchronize(e->as));
+    CK(cudaStreamSynchronize(e->stream));
+    const bool was = e->adapt;
+    e->adapt = mu > 0.0;
+    e->mu = (float)mu;
+    e->lam = (float)lambda;
+    e->delta = (float)delta;
+    if (was && !e->adapt) {
+        // the static schedule expects this block's canceller tail to be ready
+        if ((rc = enqueue_tail(e, e->fb, e->nblk, e->stream, false))) return rc;
+        CK(cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream));
+        CK(cudaStreamSynchronize(e->stream));
+    }
+    return CONV_OK;
+}
+
+int afc_get_path_spectra(conv_engine* e, float* f_spec) {
+    if (!e || !f_spec) return set_err(CONV_E_INVAL, "null argument");
+    if (!e->fb.ready) return set_err(CONV_E_STATE, "feedback paths not set");
+    if (e->prec != CONV_FP32) return set_err(CONV_E_STATE, "path spectra are read back from FP32 engines only");
+    DeviceGuard g(e->dev);
+    CK(cudaStreamSynchronize(e->bg[0]));
+    CK(cudaStreamSynchronize(e->bg[1]));
+    if (e->as) CK(cudaStreamSynchronize(e->as));
+    CK(cudaStreamSynchronize(e->stream));
+    const Part& F = e->fb;
+    const MacPlan& p = F.plan;
+    std::vector<float2> tiles(p.h_bytes / sizeof(float2));
+    CK(cudaMemcpy(tiles.data(), F.H, p.h_bytes, cudaMemcpyDeviceToHost));
+    // tiles (kt, lt) at (kt*n_lt + lt)*tile_elems, then [r][LTt][BT]; r = j*L + l
+    float2* out = reinterpret_cast<float2*>(f_spec);
+    const int P = F.n_dst, L = F.n_src, K = F.K, B = e->B;
+    for (int kt = 0; kt < p.n_kt; ++kt)
+        for (int lt = 0; lt < p.n_lt; ++lt) {
+            const int LTt = std::min(p.LT, P - lt * p.LT);
+            const float2* t = tiles.data() + ((size_t)kt * p.n_lt + lt) * p.tile_elems;
+            for (int r = 0; r < p.R; ++r)
+                for (int ll = 0; ll < LTt; ++ll)
+                    for (int kl = 0; kl < p.BT; ++kl) {
+                        const int pm = lt * p.LT + ll, l = r % L, j = r / L, k = kt * p.BT + kl;
+                        out[(((size_t)pm * L + l) * K + j) * B + k] = t[((size_t)r * LTt + ll) * p.BT + kl];
+                    }
+        }
+    return CONV_OK;
+}
+
 int conv_reset(conv_engine* e) {
     if (!e) return set_err(CONV_E_INVAL, "null handle");
     DeviceGuard g(e->dev);
@@ -958,6 +1122,7 @@ int conv_synchronize(conv_engine* e) {
     DeviceGuard g(e->dev);
     CK(cudaStreamSynchronize(e->bg[0]));
     CK(cudaStreamSynchronize(e->bg[1]));
+    if (e->as) CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
     CK(cudaDeviceSynchronize());
     return check_dev_err(e);
@@ -993,7 +1158,8 @@ int conv_get_info(const conv_engine* e, conv_info* out) {
     out->mac_kernel = p.direct == 0 ? CONV_KERNEL_TMA : (p.direct == 1 ? CONV_KERNEL_DIRECT1 : CONV_KERNEL_DIRECT2);
     out->device_bytes = (long long)e->dev_bytes;
     out->kernels_per_block = 3;
-    out->kernels_per_afc_block = 6;
+    out->kernels_per_afc_block = e->adapt ? 8 : 6;
+    out->afc_adaptive = e->adapt ? 1 : 0;
     return CONV_OK;
 }
 
@@ -1164,6 +1330,7 @@ int conv_batch_add(conv_batch* b, conv_engine* e) {
     if (e->fb.allocated && !e->fb.ready) return set_err(CONV_E_STATE, "feedback paths not set");
     if (e->syn.plan.direct || e->syn.plan.nw != 8 || (e->fb.allocated && (e->fb.plan.direct || e->fb.plan.nw != 8)))
         return set_err(CONV_E_INVAL, "batched sessions use the TMA MAC with 8 consumer warps");
+    if (e->adapt) return set_err(CONV_E_STATE, "sessions with an adaptive canceller are not batched");
     for (conv_engine* x : b->sessions)
         if (x == e) return set_err(CONV_E_INVAL, "session already in the batch");
     DeviceGuard g(b->dev);
@@ -1174,6 +1341,7 @@ int conv_batch_add(conv_batch* b, conv_engine* e) {
     CK(cudaStreamSynchronize(e->bg[1]));
     CK(cudaStreamSynchronize(e->stream));
     b->sessions.push_back(e);
+    ++e->in_batches;
     return CONV_OK;
 }
 
@@ -1185,6 +1353,7 @@ int conv_batch_remove(conv_batch* b, conv_engine* e) {
     int rc;
     if ((rc = batch_sync(b))) return rc;
     b->sessions.erase(it);
+    --e->in_batches;
     // its next block's tail partials are complete: mark them ready for its own streams
     CK(cudaEventRecord(e->syn.ev_tail[e->nblk & 1], e->stream));
     if (e->fb.allocated) CK(cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream));
@@ -1347,6 +1516,7 @@ void conv_batch_destroy(conv_batch* b) {
     DeviceGuard g(b->dev);
     if (b->stream) batch_sync(b);
     for (conv_engine* e : b->sessions) {
+        --e->in_batches;
         cudaEventRecord(e->syn.ev_tail[e->nblk & 1], e->stream);
         if (e->fb.allocated) cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream);
     }

@@ -82,6 +82,7 @@ class conv_info(ctypes.Structure):
             "mac_stage_bytes",
             "mac_warps",
             "mac_kernel",
+            "afc_adaptive",
         )
     ]
 
@@ -120,6 +121,8 @@ def load():
         "afc_process_block": (i, [vp, vp, vp, vp]),
         "afc_process_block_async": (i, [vp, vp, vp, vp, vp]),
         "afc_set_guard": (i, [vp, d]),
+        "afc_set_adaptation": (i, [vp, d, d, d]),
+        "afc_get_path_spectra": (i, [vp, vp]),
         "conv_reset": (i, [vp]),
         "conv_synchronize": (i, [vp]),
         "conv_get_info": (i, [vp, ctypes.POINTER(conv_info)]),
@@ -245,6 +248,19 @@ def afc_process_block_async(h, d_mic, d_out, d_e=None, stream=None):
 
 def afc_set_guard(h, max_rms: float):
     return _check(load().afc_set_guard(h, float(max_rms)))
+
+
+def afc_set_adaptation(h, mu: float, lam: float = 0.9, delta: float = 1e-6):
+    return _check(load().afc_set_adaptation(h, float(mu), float(lam), float(delta)))
+
+
+def afc_get_path_spectra(h) -> np.ndarray:
+    """The canceller's sub-filter spectra as complex64 [n_in][n_out][K_fb][block]
+    (bin 0 holds DC in its real part and Nyquist in its imaginary part)."""
+    info = conv_get_info(h)
+    out = np.empty((info["n_in"], info["n_out"], info["K_fb"], info["block"], 2), dtype=np.float32)
+    _check(load().afc_get_path_spectra(h, out.ctypes.data_as(ctypes.c_void_p)))
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def conv_reset(h):
@@ -423,6 +439,12 @@ class Engine:
 
     def set_paths(self, f: np.ndarray):
         afc_set_paths(self.h, np.ascontiguousarray(f, dtype=np.float32))
+
+    def set_adaptation(self, mu, lam=0.9, delta=1e-6):
+        afc_set_adaptation(self.h, mu, lam, delta)
+
+    def path_spectra(self) -> np.ndarray:
+        return afc_get_path_spectra(self.h)
 
     def process(self, x_block: np.ndarray, out: np.ndarray | None = None) -> np.ndarray:
         n_in, n_out, B = self.shape
