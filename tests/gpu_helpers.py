@@ -6,11 +6,18 @@ import numpy as np
 
 
 def snr_db(y, ref):
-    """Output SNR 10 log10(sum ref^2 / sum (y - ref)^2), pooled over everything."""
-    y = np.asarray(y, dtype=np.float64)
-    ref = np.asarray(ref, dtype=np.float64)
-    num = float(np.sum(ref * ref))
-    den = float(np.sum((y - ref) ** 2))
+    """Output SNR 10 log10(sum |ref|^2 / sum |y - ref|^2), pooled over
+    everything (real or complex arrays)."""
+    y = np.asarray(y)
+    ref = np.asarray(ref)
+    if np.iscomplexobj(y) or np.iscomplexobj(ref):
+        y = y.astype(np.complex128)
+        ref = ref.astype(np.complex128)
+    else:
+        y = y.astype(np.float64)
+        ref = ref.astype(np.float64)
+    num = float(np.sum(np.abs(ref) ** 2))
+    den = float(np.sum(np.abs(y - ref) ** 2))
     if den == 0.0:
         return float("inf")
     return 10.0 * np.log10(num / den)

@@ -99,7 +99,8 @@ def test_adaptive_closed_loop_against_oracle(B, f0_scale):
         w0 = start.path_spectra()
     finally:
         start.close()
-    assert snr_db(spec, w0) < 40.0
+    moved = np.sqrt(np.sum(np.abs(spec - w0) ** 2) / np.sum(np.abs(spec) ** 2))
+    assert moved > 0.01
 
 
 def test_path_spectra_are_the_subfilter_ffts():
