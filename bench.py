@@ -624,6 +624,139 @@ def run_batch(args):
     return 0
 
 
+def run_group(args):
+    """S sessions of the paper configuration sharing one filter set, in one
+    shared-filter group (tensor-core MAC): one step = one block of every
+    session.  Then the same sessions as S separate engines (one call each per
+    step) for comparison."""
+    import torch
+
+    from paper_2509_04390_gb300 import signals
+    from paper_2509_04390_gb300 import upols as U
+
+    rank, local_rank, world = env_rank()
+    torch.cuda.set_device(local_rank)
+    prec = args.precision if args.precision != "fp32" else "fp16"
+    S = args.group
+    w = signals.paper_4x16(block=args.block, seconds=min(args.seconds, 8.0), taps=args.taps)
+    B = w.block
+    nb = w.x.shape[1] // B
+    x = np.stack([np.roll(w.x[:, : nb * B], 4801 * s, axis=1) for s in range(S)]).astype(np.float32)
+    d_blocks = torch.from_numpy(x).cuda().reshape(S, w.n_in, nb, B).permute(2, 0, 1, 3).contiguous()
+    d_out = torch.empty((2, S, w.n_out, B), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    grp = U.Group(prec, B, w.n_in, w.n_out, w.taps, S)
+    grp.set_filters(w.h)
+    info = grp.info()
+    units = float(S) * w.n_in * w.n_out * w.taps * B
+
+    def step(i):
+        U.conv_group_process_async(grp.g, d_blocks[i % nb], d_out[i & 1], stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
+    time.sleep(0.5)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    U.conv_group_synchronize(grp.g)
+    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    # the MAC alone, CUDA events around each launch on its stream
+    k_p = min(args.steps, 4000)
+    U.conv_group_profile_enable(grp.g, k_p + 8)
+    for i in range(k_p):
+        step(i)
+    torch.cuda.synchronize()
+    mac_ms, mac_n = U.conv_group_profile_read(grp.g)
+    U.conv_group_profile_enable(grp.g, 0)
+    t_mac = mac_ms / 1e3 / max(1, mac_n)
+    # end to end through the host-buffer call
+    h_in = np.ascontiguousarray(x[:, :, :B])
+    h_out = np.empty((S, w.n_out, B), np.float32)
+    k_e = max(3, min(args.e2e_steps, 2000))
+    grp.reset()
+    for i in range(3):
+        U.conv_group_process(grp.g, h_in, h_out, (S, w.n_in, w.n_out, B))
+    t0 = time.perf_counter()
+    for i in range(k_e):
+        U.conv_group_process(grp.g, h_in, h_out, (S, w.n_in, w.n_out, B))
+    t_e2e = (time.perf_counter() - t0) / k_e
+    clocks.stop()
+    grp.close()
+    # the same sessions as separate engines (filters streamed once per session)
+    engs = []
+    for s in range(S):
+        e = U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, prec)
+        e.set_filters(w.h)
+        engs.append(e)
+    d_o1 = torch.empty((w.n_out, B), dtype=torch.float32, device="cuda")
+    k_u = max(3, min(args.steps, 500))
+    for i in range(3):
+        for s, e in enumerate(engs):
+            U.conv_process_block_async(e.h, d_blocks[i % nb][s], d_o1, stream)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(k_u):
+        for s, e in enumerate(engs):
+            U.conv_process_block_async(e.h, d_blocks[i % nb][s], d_o1, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_sep = ev0.elapsed_time(ev1) / 1e3 / k_u
+    for e in engs:
+        U.conv_synchronize(e.h)
+        e.close()
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    mac_bytes = info["mac_bytes"]
+    line = {
+        "metric": METRIC,
+        "value": units / t_step / 1e9,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": f"{prec} operands, f32 accumulation (tensor cores)",
+        "data": "synthetic: the paper-scale filter set shared by all sessions; each session a shifted pink-noise input",
+        "config": {
+            "workload": f"group_{S}_sessions_paper_4x16_{w.taps}taps_B{B}_{prec}",
+            "sessions": S, "n_in": w.n_in, "n_out": w.n_out, "taps": w.taps, "block": B, "precision": prec,
+            "l2": "inputs larger than L2: filter tiles and delay lines streamed every step exceed the 126 MB L2",
+        },
+        "roofline": {
+            "bound": "hbm", "kernel": "k_group_mac", "achieved": mac_bytes / t_mac / 1e9, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": mac_bytes / t_mac / 1e9 / peak, "traffic": None,
+            "algorithmic_bytes_per_launch": mac_bytes, "avg_launch_us": t_mac * 1e6, "launches_timed": mac_n,
+        },
+        "e2e": {
+            "value": units / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h_in.nbytes),
+            "d2h_bytes_per_step": int(h_out.nbytes), "steps": k_e, "ms_per_call": t_e2e * 1e3,
+        },
+        "separate_engines": {
+            "value": units / t_sep / 1e9, "ms_per_step": t_sep * 1e3, "steps": k_u,
+            "note": "the same sessions as separate engines, one call (3 launches) each per step",
+        },
+        "plan": {k: info[k] for k in ("groups", "splits", "stages", "stage_k_steps", "mac_ctas", "mac_smem",
+                                      "tmem_cols", "device_bytes")},
+        "gpu_launches": args.steps * info["kernels_per_block"],
+        "clocks": clocks.summary(tw0, tw1),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Serving loop: Poisson arrivals with admission by device memory and
     continuous batching (p50/p99 tick latency vs the tick period), and the
@@ -680,6 +813,7 @@ def parse(argv=None):
     ap.add_argument("--batch", type=int, default=0, help="time N heterogeneous sessions in one batch instead")
     ap.add_argument("--batch-seed", type=int, default=4)
     ap.add_argument("--serve", action="store_true", help="run the serving-loop simulation instead")
+    ap.add_argument("--group", type=int, default=0, help="time N sessions sharing one filter set (tensor-core MAC)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     return ap.parse_args(argv)
 
@@ -694,6 +828,8 @@ def main(argv=None):
         return run_batch(args)
     if args.serve:
         return run_serve(args)
+    if args.group:
+        return run_group(args)
     return run_ours(args)
 
 

@@ -306,6 +306,81 @@ long long conv_batch_step_bytes(const conv_batch* b);
 /* Free the batch (its sessions are left intact and usable on their own).  NULL-safe. */
 void conv_batch_destroy(conv_batch* b);
 
+/* ------------------------------------------------------ shared-filter groups
+ * A group runs `sessions` streams that use one filter set (same block, n_in,
+ * n_out, taps) in lock-step: one call processes block n of every session.
+ * For every bin k the FDL MAC of Sec. 4 (Eq. 6) over all sessions is then one
+ * complex GEMM, Y_k[l][s] = sum over (p, q) of H_k[l][q][p] X_k,s[q][(head - p) mod K],
+ * which runs on the tensor cores (FP16 or BF16 operands, FP32 accumulation)
+ * and reads every filter spectrum once per block for all sessions.  This is
+ * an extension beyond the paper, which runs one stream per engine.
+ *
+ * Limits (else CONV_E_INVAL): precision CONV_FP16 or CONV_BF16; n_out in
+ * {8, 16, 32}; n_in in {1, 2, 4, 8}; sessions a multiple of 8 with
+ * sessions * 128 / n_out <= 128; block a power of two in [16, 4096].
+ * Filter spectra carry a power-of-two scale per (bin, output); the delay line
+ * is stored unscaled, so FP16 groups saturate input spectra above 65504
+ * (inputs with |x| <= 1 never reach it: |X| <= 2 * block).  Output block n of
+ * every session is exactly samples [nB, (n+1)B) of its causal convolution,
+ * as for conv_process_block.  The whole MAC runs after the block's input
+ * arrives (no background tail): higher block latency than an engine, far
+ * higher throughput per GPU. */
+typedef struct conv_group conv_group;
+
+typedef struct conv_group_info {
+    long long block, n_in, n_out, taps, sessions, precision;
+    long long K;              /* partitions                                       */
+    long long ring_slots;     /* delay-line slots (K rounded up to a K-step)      */
+    long long bins_per_group; /* bins per tensor-core tile (128 / n_out)          */
+    long long groups;         /* bin groups (block / bins_per_group)              */
+    long long splits;         /* K-step splits per bin group                      */
+    long long k_steps;        /* K-steps of 16 reduction indices per block        */
+    long long stage_k_steps;  /* K-steps per pipeline stage                       */
+    long long stages;         /* pipeline depth                                   */
+    long long mac_ctas;       /* CTAs of one MAC launch                           */
+    long long mac_smem;       /* dynamic shared memory per MAC CTA, bytes         */
+    long long tmem_cols;      /* tensor-memory columns per MAC CTA                */
+    long long mac_bytes;      /* algorithmic bytes of one MAC launch: filters + delay lines, each read once */
+    long long device_bytes;   /* device memory held                               */
+    long long kernels_per_block; /* kernels one process call launches             */
+} conv_group_info;
+
+/* Create a group on the current device; NULL on failure (conv_last_error()). */
+conv_group* conv_group_create(int precision, int block, int n_in, int n_out, long long taps, int sessions);
+
+/* Host filters h[n_out][n_in][taps] (copied; caller keeps ownership), shared
+ * by all sessions.  Resets the sessions' state. */
+int conv_group_set_filters(conv_group* g, const float* h);
+
+/* One block of every session: d_in [sessions][n_in][block] and
+ * d_out [sessions][n_out][block], device pointers, enqueued on `cuda_stream`
+ * (NULL: the legacy default stream).  CONV_E_STATE before conv_group_set_filters. */
+int conv_group_process_async(conv_group* g, const float* d_in, float* d_out, void* cuda_stream);
+
+/* Same with host buffers; blocks until the outputs are in `out`.  Reports a
+ * device-side wait that gave up as CONV_E_TIMEOUT. */
+int conv_group_process(conv_group* g, const float* in, float* out);
+
+/* Zero every session's delay line and window (filters kept). */
+int conv_group_reset(conv_group* g);
+
+/* Wait for the group's work; CONV_E_TIMEOUT if a device-side wait gave up. */
+int conv_group_synchronize(conv_group* g);
+
+int conv_group_get_info(const conv_group* g, conv_group_info* out);
+
+/* Host-only: plans a group and replays every copy address of a block against
+ * the buffer and shared-memory sizes.  CONV_OK or CONV_E_INVAL with the reason. */
+int conv_group_plan_check(int precision, int block, int n_in, int n_out, long long taps, int sessions, int num_sms);
+
+/* CUDA-event timing of each MAC launch (enable > 1: number of event pairs),
+ * read and cleared by conv_group_profile_read (total ms, launches). */
+int conv_group_profile_enable(conv_group* g, int enable);
+int conv_group_profile_read(conv_group* g, double* total_ms, long long* launches);
+
+/* Free everything the group owns.  NULL-safe. */
+void conv_group_destroy(conv_group* g);
+
 /* Free everything the handle owns.  NULL-safe. */
 void conv_destroy(conv_engine* e);
 

@@ -1,0 +1,491 @@
+// group.cu - kernels of shared-filter session groups (see group.h): filter
+// tiles, pack + R2C into the duplicated-slot ring, the tcgen05 tensor-core
+// FDL MAC, and the split reduction + C2R.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "device_util.cuh"
+#include "group.h"
+
+namespace gbconv {
+
+namespace {
+
+constexpr uint64_t GRP_WAIT_NS = 1000000000ull;  // 1 s: far beyond any legitimate wait
+constexpr int TILE_BYTES = 8192;                 // one K-step of filter tiles: Hr 4 KiB + Hi 4 KiB
+
+// ------------------------------------------------------------ tcgen05 helpers
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension
+// byte offset (between core matrices along K), stride byte offset (between
+// 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// D[tmem] (+)= A * B, kind::f16, issued by one thread.
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// The mbarrier receives one arrival when every tcgen05 operation this thread
+// issued before has completed.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Eight consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int PREC>
+__device__ __forceinline__ uint16_t to16(float v) {
+    if (PREC == PREC_FP16) {
+        v = fminf(fmaxf(v, -65504.0f), 65504.0f);  // saturate instead of overflowing to inf
+        const __half h = __float2half_rn(v);
+        return *reinterpret_cast<const uint16_t*>(&h);
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const uint16_t*>(&h);
+}
+
+__device__ void report(int* err, volatile int* abort_flag, int code) {
+    *abort_flag = 1;
+    if (err) atomicExch(err, code);
+}
+
+// --------------------------------------------------------------- filter tiles
+// One CTA per (output l, input q, partition p < K).  Pass 0 records the
+// largest component per (bin, output); pass 1 stores the spectrum divided by
+// the row's power-of-two scale into the tile layout of group.h.
+template <int PREC>
+__global__ void k_group_filter(const GroupFilterArgs a) {
+    extern __shared__ float2 fsm[];
+    const int B = a.B, half = B >> 1, tid = threadIdx.x, nth = blockDim.x;
+    float2* bufA = fsm;
+    float2* bufB = fsm + B;
+    float2* tws = fsm + 2 * B;
+    const long long id = blockIdx.x;
+    const int p = (int)(id % a.K);
+    const long long rest = id / a.K;
+    const int q = (int)(rest % a.n_src);
+    const int l = (int)(rest / a.n_src);
+    load_twiddles(tws, a.tw, B);
+    const float* h = a.h + ((size_t)l * a.n_src + q) * (size_t)a.taps;
+    const long long t0 = (long long)p * B;
+    for (int n = tid; n < B; n += nth) {
+        float2 z = make_float2(0.0f, 0.0f);
+        if (n < half) {
+            const long long t = t0 + 2 * n;
+            if (t < a.taps) z.x = h[t];
+            if (t + 1 < a.taps) z.y = h[t + 1];
+        }
+        bufA[n] = z;
+    }
+    __syncthreads();
+    const float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, tws, a.log2B + 1, tid, nth);
+    for (int k = tid; k < B; k += nth) {
+        const float2 X = r2c_post(Z, k, B, tws);
+        unsigned* mb = a.maxbits + (size_t)k * a.n_dst + l;
+        if (a.pass == 0) {
+            atomicMax(mb, __float_as_uint(fmaxf(fabsf(X.x), fabsf(X.y))));  // non-negative floats order as integers
+            continue;
+        }
+        const float scale = block_scale<PREC>(__uint_as_float(*mb));
+        const int g = k / a.G, b = k - g * a.G;
+        const int row = b * a.n_dst + l;
+        if (q == 0 && p == 0) a.sH[(size_t)g * 128 + row] = scale;
+        const int c = p / a.KP;
+        const int kk = (p - c * a.KP) * a.n_src + q;
+        const size_t off = ((size_t)g * a.NKS + c) * TILE_BYTES + (size_t)(kk >> 3) * 2048 + (size_t)(row >> 3) * 128 +
+                           (size_t)(row & 7) * 16 + (size_t)(kk & 7) * 2;
+        unsigned char* H = static_cast<unsigned char*>(a.H);
+        const float inv = 1.0f / scale;
+        *reinterpret_cast<uint16_t*>(H + off) = to16<PREC>(X.x * inv);
+        *reinterpret_cast<uint16_t*>(H + off + 4096) = to16<PREC>(X.y * inv);
+    }
+}
+
+// ------------------------------------------------------------- pack + R2C
+// One CTA per (input q, session s): w = [previous block, this block], R2C,
+// then every bin's (re, im) goes to the D ring rows that hold this slot.
+template <int PREC>
+__global__ void k_group_pack(const GroupPackArgs a) {
+    extern __shared__ float2 fsm[];
+    const int B = a.B, half = B >> 1, tid = threadIdx.x, nth = blockDim.x;
+    float2* bufA = fsm;
+    float2* bufB = fsm + B;
+    float2* tws = fsm + 2 * B;
+    const int q = blockIdx.x, s = blockIdx.y;
+    load_twiddles(tws, a.tw, B);
+    const float* in = a.in + ((size_t)s * a.n_src + q) * B;
+    float* win = a.win + ((size_t)s * a.n_src + q) * B;
+    for (int n = tid; n < B; n += nth) {
+        bufA[n] = n < half ? make_float2(win[2 * n], win[2 * n + 1]) : make_float2(in[2 * n - B], in[2 * n - B + 1]);
+    }
+    __syncthreads();
+    for (int t = tid; t < B; t += nth) win[t] = in[t];
+    const float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, tws, a.log2B + 1, tid, nth);
+    unsigned char* X = static_cast<unsigned char*>(a.X);
+    const int rows_per_class = a.KR / a.D;
+    for (int k = tid; k < B; k += nth) {
+        const float2 v = r2c_post(Z, k, B, tws);
+        const int g = k / a.G, b = k - g * a.G;
+        const uint16_t re = to16<PREC>(v.x), im = to16<PREC>(v.y);
+        for (int u = 0; u < a.D; ++u) {
+            int t = a.slot - u;
+            if (t < 0) t += a.KR;
+            const size_t row = ((size_t)g * a.D + t % a.D) * rows_per_class + t / a.D;
+            unsigned char* base = X + row * a.RB + (size_t)s * 16 + (size_t)(u * a.n_src + q) * 2;
+            *reinterpret_cast<uint16_t*>(base + (size_t)b * a.S * 16) = re;
+            *reinterpret_cast<uint16_t*>(base + (size_t)(a.G + b) * a.S * 16) = im;
+        }
+    }
+}
+
+// ------------------------------------------------------------ tensor-core MAC
+// One CTA per (bin group g, split sp) over K-steps [c0, c1).
+//   warp 0     producer: bulk copies of filter tiles and ring rows into a ring
+//              of pipeline stages (mbarrier complete_tx)
+//   warp 1     allocates tensor memory; one lane issues two MMAs per K-step
+//              (D1 = Hr X into columns [0, N), D2 = Hi X into [N, 2N)) and
+//              commits each stage back to the producer
+//   warps 2-5  epilogue: each reads its TMEM lane quadrant (32 rows), keeps
+//              the diagonal blocks, forms the complex result and writes the
+//              split partials
+// Every wait is bounded; a timeout raises the abort flag and the error word.
+__global__ void __launch_bounds__(GRP_THREADS, 1) k_group_mac(const GroupMacArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + GRP_MAX_STAGES;
+    uint64_t* accb = empty + GRP_MAX_STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    unsigned char* stages = smem + GRP_HDR_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = blockIdx.x, sp = blockIdx.y;
+    const int c0 = (int)((long long)sp * a.NKS / a.SP);
+    const int c1 = (int)((long long)(sp + 1) * a.NKS / a.SP);
+    const int nfill = (c1 - c0 + a.NK - 1) / a.NK;
+
+    if (tid == 0) {
+        for (int i = 0; i < a.nstage; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, 1);
+        }
+        mbar_init(accb, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint64_t pol_h = policy_evict_first(), pol_x = policy_evict_last();
+            const int rows_per_class = a.KR / a.D;
+            const unsigned char* xb = static_cast<const unsigned char*>(a.X) +
+                                      ((size_t)g * a.D + a.slot0 % a.D) * rows_per_class * a.RB;
+            const unsigned char* hb = static_cast<const unsigned char*>(a.H) + (size_t)g * a.NKS * TILE_BYTES;
+            int i = 0;
+            for (; i < nfill; ++i) {
+                const int st = i % a.nstage;
+                if (i >= a.nstage &&
+                    !mbar_wait_bounded(empty + st, (uint32_t)((i / a.nstage) - 1) & 1u, abort_flag, GRP_WAIT_NS)) {
+                    report(a.err, abort_flag, DEVERR_TIMEOUT_PRODUCER);
+                    break;
+                }
+                const int c = c0 + i * a.NK;
+                const int nk = min(a.NK, c1 - c);
+                unsigned char* sA = stages + (size_t)st * a.stage_bytes;
+                unsigned char* sB = sA + (size_t)a.NK * TILE_BYTES;
+                mbar_arrive_expect_tx(full + st, (uint32_t)nk * (TILE_BYTES + 2u * a.RB));
+                bulk_g2s(sA, hb + (size_t)c * TILE_BYTES, (uint32_t)nk * TILE_BYTES, full + st, pol_h);
+                const int t0 = (a.slot0 + c * a.KP) % a.KR;
+                const int idx = t0 / a.D;
+                const int rows = 2 * nk;
+                const int first = min(rows, rows_per_class - idx);
+                bulk_g2s(sB, xb + (size_t)idx * a.RB, (uint32_t)(first * a.RB), full + st, pol_x);
+                if (first < rows)
+                    bulk_g2s(sB + (size_t)first * a.RB, xb, (uint32_t)((rows - first) * a.RB), full + st, pol_x);
+            }
+            // leave no copy in flight: wait (bounded) for the stages issued last
+            for (int j = max(0, i - a.nstage); j < i; ++j)
+                mbar_wait_bounded(full + j % a.nstage, (uint32_t)(j / a.nstage) & 1u, nullptr, GRP_WAIT_NS);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t sbase = smem_u32(stages);
+            for (int i = 0; i < nfill; ++i) {
+                const int st = i % a.nstage;
+                if (!mbar_wait_bounded(full + st, (uint32_t)(i / a.nstage) & 1u, abort_flag, GRP_WAIT_NS)) {
+                    report(a.err, abort_flag, DEVERR_TIMEOUT_CONSUMER);
+                    break;
+                }
+                tmem_fence_after();
+                const int nk = min(a.NK, c1 - (c0 + i * a.NK));
+                const uint32_t sA = sbase + (uint32_t)(st * a.stage_bytes);
+                const uint32_t sB = sA + (uint32_t)(a.NK * TILE_BYTES);
+                for (int j = 0; j < nk; ++j) {
+                    const uint64_t dAr = umma_desc(sA + (uint32_t)(j * TILE_BYTES), 2048, 128);
+                    const uint64_t dAi = umma_desc(sA + (uint32_t)(j * TILE_BYTES) + 4096, 2048, 128);
+                    const uint64_t dB = umma_desc(sB + (uint32_t)(j * 2 * a.RB), (uint32_t)a.RB, 128);
+                    const uint32_t acc = (i | j) ? 1u : 0u;
+                    umma_f16(tbase, dAr, dB, a.idesc, acc);
+                    umma_f16(tbase + (uint32_t)a.N, dAi, dB, a.idesc, acc);
+                }
+                umma_commit(empty + st);
+            }
+            umma_commit(accb);  // arrives once every MMA above has completed
+        }
+    } else {
+        const int quad = warp & 3;  // the TMEM lane quadrant this warp may access
+        const int row = quad * 32 + lane;
+        const int bq = 32 / a.n_dst;  // bins per quadrant
+        const int b_lo = quad * bq;
+        const int W = bq * a.S;  // columns of one range
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(accb, 0, abort_flag, GRP_WAIT_NS));
+        if (!ok && lane == 0) report(a.err, abort_flag, DEVERR_TIMEOUT_CONSUMER);
+        tmem_fence_after();
+        // stage the four column ranges (D1 re, D1 im, D2 re, D2 im) of this
+        // quadrant's bins: [range][column][lane], conflict-free both ways
+        float* stg = reinterpret_cast<float*>(stages) + (size_t)(warp - 2) * 4 * W * 32;
+        const int GS = a.G * a.S;
+        if (ok) {
+            for (int rg = 0; rg < 4; ++rg) {
+                const int colbase = ((rg >> 1) ? a.N : 0) + ((rg & 1) ? GS : 0) + b_lo * a.S;
+                for (int ch = 0; ch < W; ch += 8) {
+                    float v[8];
+                    tmem_ld8(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(colbase + ch), v);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) stg[((size_t)rg * W + ch + j) * 32 + lane] = v[j];
+                }
+            }
+        }
+        __syncwarp();
+        const int b = row / a.n_dst, l = row - b * a.n_dst;
+        const int k = g * a.G + b;
+        const int boff = (b - b_lo) * a.S;
+        const float scale = ok ? __ldg(a.sH + (size_t)g * 128 + row) : 0.0f;
+        for (int s = 0; s < a.S; ++s) {
+            float2 y = make_float2(0.0f, 0.0f);
+            if (ok) {
+                const float d1r = stg[((size_t)0 * W + boff + s) * 32 + lane];
+                const float d1i = stg[((size_t)1 * W + boff + s) * 32 + lane];
+                const float d2r = stg[((size_t)2 * W + boff + s) * 32 + lane];
+                const float d2i = stg[((size_t)3 * W + boff + s) * 32 + lane];
+                y = k == 0 ? make_float2(d1r, d2i) : make_float2(d1r - d2i, d1i + d2r);
+                y = cscale(y, scale);
+            }
+            a.partial[(((size_t)s * a.SP + sp) * a.n_dst + l) * a.B + k] = y;
+        }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    __syncwarp();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(a.tmem_cols) : "memory");
+}
+
+// --------------------------------------------------- split reduction + C2R
+// One CTA per (output l, session s): fixed-order sum of the SP split partials,
+// C2R, 1/B scaling, keep the last B samples (overlap-save).
+__global__ void k_group_out(const GroupOutArgs a) {
+    extern __shared__ float2 fsm[];
+    const int B = a.B, tid = threadIdx.x, nth = blockDim.x;
+    float2* P = fsm;
+    float2* W = fsm + B;
+    float2* tws = fsm + 2 * B;
+    const int l = blockIdx.x, s = blockIdx.y;
+    load_twiddles(tws, a.tw, B);
+    const size_t stride = (size_t)a.n_dst * B;
+    const float2* src0 = a.partial + ((size_t)s * a.SP * a.n_dst + l) * B;
+    for (int k = tid; k < B; k += nth) {
+        float2 tot = make_float2(0.0f, 0.0f);
+        for (int sp = 0; sp < a.SP; ++sp) tot = cadd(tot, src0[(size_t)sp * stride + k]);
+        P[k] = tot;
+    }
+    __syncthreads();
+    for (int k = tid; k < B; k += nth) W[k] = c2r_pre(P, k, B, tws);
+    __syncthreads();
+    const float2* z = fft_smem<true>(W, P, B, a.log2B, tws, a.log2B + 1, tid, nth);
+    const float invB = 1.0f / (float)B;
+    float* out = a.out + ((size_t)s * a.n_dst + l) * B;
+    for (int t = tid; t < B; t += nth) {
+        const int u = B + t, n = u >> 1;
+        out[t] = ((u & 1) ? z[n].y : z[n].x) * invB;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- planning
+
+const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, int S, int num_sms, GroupPlan* out) {
+    if (prec != PREC_FP16 && prec != PREC_BF16) return "session groups store FP16 or BF16 spectra";
+    if (B < 16 || B > 4096 || (B & (B - 1))) return "block must be a power of two in [16, 4096]";
+    if (n_dst != 8 && n_dst != 16 && n_dst != 32) return "session groups need n_out in {8, 16, 32}";
+    if (n_src != 1 && n_src != 2 && n_src != 4 && n_src != 8) return "session groups need n_in in {1, 2, 4, 8}";
+    if (S < 8 || S % 8) return "sessions must be a positive multiple of 8";
+    if (taps < 1) return "taps must be >= 1";
+    if (num_sms < 1) return "num_sms must be >= 1";
+    GroupPlan p{};
+    p.B = B;
+    p.n_src = n_src;
+    p.n_dst = n_dst;
+    p.S = S;
+    p.G = 128 / n_dst;
+    if (p.G * S > 128) return "sessions x (128 / n_out) must be <= 128";
+    const long long K = (taps + B - 1) / B;
+    p.D = 8 / n_src;
+    p.KP = 2 * p.D;
+    const long long KR = (K + p.KP - 1) / p.KP * p.KP;
+    if (KR > (1LL << 24)) return "too many partitions";
+    p.K = (int)K;
+    p.KR = (int)KR;
+    p.NKS = p.KR / p.KP;
+    p.NG = B / p.G;
+    p.N = 2 * p.G * S;
+    p.RB = 32 * p.G * S;
+    p.tmem_cols = 32;
+    while (p.tmem_cols < 2 * p.N) p.tmem_cols *= 2;
+    p.ctas_per_sm = p.tmem_cols <= 256 ? 2 : 1;
+    const int kb = TILE_BYTES + 2 * p.RB;
+    const int budget = (p.ctas_per_sm == 2 ? 112 * 1024 : 224 * 1024) - GRP_HDR_BYTES;
+    p.NK = std::max(1, std::min(4, (budget / 4) / kb));
+    p.nstage = std::min(GRP_MAX_STAGES, budget / (p.NK * kb));
+    if (p.nstage < 2) return "pipeline stages do not fit in shared memory";
+    p.stage_bytes = p.NK * kb;
+    const int W = (32 / n_dst) * S;
+    const int staging = 4 * 4 * W * 32 * (int)sizeof(float);
+    p.smem = GRP_HDR_BYTES + std::max(p.nstage * p.stage_bytes, staging);
+    if (p.smem - GRP_HDR_BYTES > budget) return "epilogue staging does not fit in shared memory";
+    const int want = p.ctas_per_sm * num_sms;
+    p.SP = std::max(1, std::min(p.NKS, want / p.NG));
+    p.ctas = p.NG * p.SP;
+    p.h_bytes = (size_t)p.NG * p.NKS * TILE_BYTES;
+    p.x_bytes = (size_t)p.NG * p.KR * p.RB;
+    p.partial_bytes = (size_t)S * p.SP * n_dst * B * sizeof(float2);
+    *out = p;
+    return nullptr;
+}
+
+const char* check_group_plan(const GroupPlan& p) {
+    static char msg[256];
+    if (p.G * p.n_dst != 128 || p.NG * p.G != p.B) return "group shape does not tile 128 rows / B bins";
+    if (p.N % 16 || p.N < 16 || p.N > 256) return "MMA N out of range";
+    if (2 * p.N > p.tmem_cols || p.tmem_cols > 512) return "tensor memory columns";
+    if (p.RB % 16 || p.stage_bytes % 16) return "copy sizes must be multiples of 16 bytes";
+    if ((size_t)p.smem > 227 * 1024) return "shared memory above the per-CTA limit";
+    if ((32 / p.n_dst) * p.S % 8) return "epilogue column ranges must be multiples of 8";
+    const int rows_per_class = p.KR / p.D;
+    for (int slot0 = 0; slot0 < std::min(p.KR, 2 * p.D + 1); ++slot0)
+        for (int sp = 0; sp < p.SP; ++sp) {
+            const int c0 = (int)((long long)sp * p.NKS / p.SP), c1 = (int)((long long)(sp + 1) * p.NKS / p.SP);
+            if (c1 <= c0) return "empty split";
+            for (int c = c0; c < c1; c += p.NK) {
+                const int nk = std::min(p.NK, c1 - c);
+                const size_t h_end = ((size_t)(p.NG - 1) * p.NKS + c + nk) * TILE_BYTES;
+                if (h_end > p.h_bytes) return "filter copy beyond the tiles";
+                const int t0 = (slot0 + c * p.KP) % p.KR;
+                if (t0 % p.D != slot0 % p.D) return "ring class changes within a block";
+                const int idx = t0 / p.D, rows = 2 * nk;
+                const int first = std::min(rows, rows_per_class - idx);
+                const size_t cls_base = ((size_t)(p.NG - 1) * p.D + (p.D - 1)) * rows_per_class;
+                if ((cls_base + idx + first) * p.RB > p.x_bytes) return "ring copy beyond the ring";
+                if (rows - first > rows_per_class) return "ring copy wraps twice";
+                // the rows of K-step c are t0 and t0 + D
+                for (int j = 0; j < nk; ++j) {
+                    const int ta = (slot0 + (c + j) * p.KP) % p.KR, tb = (ta + p.D) % p.KR;
+                    const int ia = (idx + 2 * j) % rows_per_class, ib = (idx + 2 * j + 1) % rows_per_class;
+                    if (ta / p.D != ia || tb / p.D != ib) {
+                        snprintf(msg, sizeof(msg), "ring row order: slot0 %d K-step %d", slot0, c + j);
+                        return msg;
+                    }
+                }
+            }
+        }
+    if ((size_t)p.stage_bytes * p.nstage + GRP_HDR_BYTES > (size_t)p.smem) return "stages beyond shared memory";
+    return nullptr;
+}
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t prepare_group_kernels() {
+    const int fft_max = (int)fft_smem_bytes(4096);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_group_filter<PREC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fft_max)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_group_filter<PREC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fft_max)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_group_pack<PREC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fft_max)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_group_pack<PREC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fft_max)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_group_out, cudaFuncAttributeMaxDynamicSharedMemorySize, fft_max))) return e;
+    return cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+cudaError_t launch_group_filter(int prec, const GroupFilterArgs& a, cudaStream_t s) {
+    const long long n = (long long)a.n_dst * a.n_src * a.K;
+    if (n <= 0 || n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const size_t sm = fft_smem_bytes(a.B);
+    if (prec == PREC_FP16)
+        k_group_filter<PREC_FP16><<<(unsigned)n, fft_threads(a.B), sm, s>>>(a);
+    else
+        k_group_filter<PREC_BF16><<<(unsigned)n, fft_threads(a.B), sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_pack(int prec, const GroupPackArgs& a, cudaStream_t s) {
+    const dim3 grid(a.n_src, a.S);
+    const size_t sm = fft_smem_bytes(a.B);
+    if (prec == PREC_FP16)
+        k_group_pack<PREC_FP16><<<grid, fft_threads(a.B), sm, s>>>(a);
+    else
+        k_group_pack<PREC_BF16><<<grid, fft_threads(a.B), sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_mac(const GroupPlan& p, const GroupMacArgs& a, cudaStream_t s) {
+    k_group_mac<<<dim3(p.NG, p.SP), GRP_THREADS, p.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_out(const GroupOutArgs& a, int S, cudaStream_t s) {
+    k_group_out<<<dim3(a.n_dst, S), out_threads(a.B), fft_smem_bytes(a.B), s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gbconv

@@ -1,0 +1,440 @@
+// group_engine.cu - the conv_group_* entry points of conv.h: shared-filter
+// session groups whose FDL MAC runs on the tensor cores (group.h).
+//
+// Per block, on the caller's stream: pack + R2C of every session's inputs
+// into the duplicated-slot ring, the tensor-core MAC over all partitions, and
+// the split reduction + C2R of every (session, output).  The whole MAC is on
+// the block's path (no split-phase tail): the group trades block latency for
+// throughput.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "conv.h"
+#include "group.h"
+#include "kernels.h"
+
+using namespace gbconv;
+
+struct conv_group {
+    int dev = 0;
+    int prec = CONV_FP16;
+    int B = 0, log2B = 0, n_in = 0, n_out = 0, S = 0;
+    long long taps = 0;
+    int num_sms = 0;
+    GroupPlan plan{};
+    uint32_t idesc = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_done = nullptr;
+    void* H = nullptr;
+    void* X = nullptr;
+    float* sH = nullptr;
+    float* win = nullptr;
+    float2* partial = nullptr;
+    float2* tw = nullptr;
+    float *d_in = nullptr, *d_out = nullptr, *h_in = nullptr, *h_out = nullptr;
+    int *h_err = nullptr, *d_err = nullptr;
+    long long nblk = 0;
+    bool ready = false;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev0, ev1;
+    size_t ev_used = 0;
+    size_t dev_bytes = 0;
+};
+
+namespace {
+
+int gset(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    set_last_error_message(buf);
+    return code;
+}
+
+#define GCK(call)                                                                                        \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return gset(CONV_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+struct GDev {
+    int prev = -1;
+    explicit GDev(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~GDev() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+int galloc(conv_group* g, T** p, size_t bytes) {
+    cudaError_t r = cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+    if (r != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return gset(r == cudaErrorMemoryAllocation ? CONV_E_NOMEM : CONV_E_CUDA, "cudaMalloc(%zu): %s", bytes,
+                    cudaGetErrorString(r));
+    }
+    g->dev_bytes += bytes ? bytes : 16;
+    return CONV_OK;
+}
+
+void group_free(conv_group* g) {
+    if (!g) return;
+    GDev d(g->dev);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (void* p : {g->H, g->X, (void*)g->sH, (void*)g->win, (void*)g->partial, (void*)g->tw, (void*)g->d_in,
+                    (void*)g->d_out})
+        if (p) cudaFree(p);
+    if (g->h_in) cudaFreeHost(g->h_in);
+    if (g->h_out) cudaFreeHost(g->h_out);
+    if (g->h_err) cudaFreeHost(g->h_err);
+    for (auto ev : g->ev0) cudaEventDestroy(ev);
+    for (auto ev : g->ev1) cudaEventDestroy(ev);
+    if (g->ev_done) cudaEventDestroy(g->ev_done);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+int to_prec(int precision) {
+    return precision == CONV_FP16 ? PREC_FP16 : (precision == CONV_BF16 ? PREC_BF16 : (precision == CONV_FP32 ? PREC_FP32 : -1));
+}
+
+int group_reset_impl(conv_group* g) {
+    GCK(cudaStreamSynchronize(g->stream));
+    const GroupPlan& p = g->plan;
+    GCK(cudaMemsetAsync(g->X, 0, p.x_bytes, g->stream));
+    GCK(cudaMemsetAsync(g->win, 0, (size_t)g->S * g->n_in * g->B * sizeof(float), g->stream));
+    GCK(cudaStreamSynchronize(g->stream));
+    g->nblk = 0;
+    return CONV_OK;
+}
+
+int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, long long taps, int sessions) {
+    const int prec = to_prec(precision);
+    if (prec < 0) return gset(CONV_E_INVAL, "unknown precision %d", precision);
+    GCK(cudaGetDevice(&g->dev));
+    cudaDeviceProp prop{};
+    GCK(cudaGetDeviceProperties(&prop, g->dev));
+    g->num_sms = prop.multiProcessorCount;
+    if (const char* why = plan_group(prec, block, n_in, n_out, taps, sessions, g->num_sms, &g->plan))
+        return gset(CONV_E_INVAL, "%s", why);
+    if (const char* why = check_group_plan(g->plan)) return gset(CONV_E_INVAL, "%s", why);
+    g->prec = precision;
+    g->B = block;
+    g->log2B = 0;
+    while ((1 << g->log2B) < block) ++g->log2B;
+    g->n_in = n_in;
+    g->n_out = n_out;
+    g->S = sessions;
+    g->taps = taps;
+    const GroupPlan& p = g->plan;
+    const uint32_t t = prec == PREC_BF16 ? 1u : 0u;
+    // kind::f16: D F32, A and B of the same 16-bit type, both K-major, N, M = 128
+    g->idesc = (1u << 4) | (t << 7) | (t << 10) | ((uint32_t)(p.N >> 3) << 17) | ((128u >> 4) << 24);
+    size_t free_b = 0, total_b = 0;
+    GCK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t need = p.h_bytes + p.x_bytes + p.partial_bytes + (size_t)p.NG * 128 * sizeof(float) +
+                        (size_t)sessions * (n_in + n_out) * block * sizeof(float) * 2;
+    if (need + (64ull << 20) > free_b)
+        return gset(CONV_E_NOMEM, "device footprint %zu bytes does not fit in %zu free bytes", need, free_b);
+    GCK(prepare_group_kernels());
+    int rc;
+    if ((rc = galloc(g, &g->H, p.h_bytes))) return rc;
+    if ((rc = galloc(g, &g->X, p.x_bytes))) return rc;
+    if ((rc = galloc(g, &g->sH, (size_t)p.NG * 128 * sizeof(float)))) return rc;
+    if ((rc = galloc(g, &g->win, (size_t)sessions * n_in * block * sizeof(float)))) return rc;
+    if ((rc = galloc(g, &g->partial, p.partial_bytes))) return rc;
+    if ((rc = galloc(g, &g->tw, 2 * (size_t)block * sizeof(float2)))) return rc;
+    if ((rc = galloc(g, &g->d_in, (size_t)sessions * n_in * block * sizeof(float)))) return rc;
+    if ((rc = galloc(g, &g->d_out, (size_t)sessions * n_out * block * sizeof(float)))) return rc;
+    GCK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_in), (size_t)sessions * n_in * block * sizeof(float),
+                      cudaHostAllocDefault));
+    GCK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_out), (size_t)sessions * n_out * block * sizeof(float),
+                      cudaHostAllocDefault));
+    GCK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_err), sizeof(int), cudaHostAllocMapped));
+    *g->h_err = 0;
+    GCK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&g->d_err), g->h_err, 0));
+    int lo = 0, hi = 0;
+    GCK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    GCK(cudaStreamCreateWithPriority(&g->stream, cudaStreamNonBlocking, hi));
+    GCK(cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming));
+    // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once
+    std::vector<float2> tw(2 * (size_t)block);
+    const double pi = 3.14159265358979323846264338327950288;
+    for (int j = 0; j < 2 * block; ++j) {
+        const double ang = -pi * (double)j / (double)block;
+        tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    GCK(cudaMemcpy(g->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    GCK(cudaMemset(g->H, 0, p.h_bytes));
+    GCK(cudaMemset(g->sH, 0, (size_t)p.NG * 128 * sizeof(float)));
+    return group_reset_impl(g);
+}
+
+int enqueue_group(conv_group* g, const float* d_in, float* d_out, cudaStream_t s) {
+    const GroupPlan& p = g->plan;
+    const int m = (int)(g->nblk % p.KR);
+    const int slot0 = m == 0 ? 0 : p.KR - m;  // slot of partition 0: (0 - n) mod KR
+    const int prec = to_prec(g->prec);
+    GroupPackArgs pk{};
+    pk.in = d_in;
+    pk.win = g->win;
+    pk.X = g->X;
+    pk.B = g->B;
+    pk.log2B = g->log2B;
+    pk.n_src = g->n_in;
+    pk.S = g->S;
+    pk.G = p.G;
+    pk.D = p.D;
+    pk.KR = p.KR;
+    pk.RB = p.RB;
+    pk.slot = slot0;
+    pk.tw = g->tw;
+    GCK(launch_group_pack(prec, pk, s));
+    GroupMacArgs a{};
+    a.H = g->H;
+    a.X = g->X;
+    a.sH = g->sH;
+    a.partial = g->partial;
+    a.B = g->B;
+    a.n_dst = g->n_out;
+    a.S = g->S;
+    a.G = p.G;
+    a.NG = p.NG;
+    a.D = p.D;
+    a.KP = p.KP;
+    a.KR = p.KR;
+    a.NKS = p.NKS;
+    a.N = p.N;
+    a.RB = p.RB;
+    a.SP = p.SP;
+    a.NK = p.NK;
+    a.nstage = p.nstage;
+    a.stage_bytes = p.stage_bytes;
+    a.slot0 = slot0;
+    a.tmem_cols = p.tmem_cols;
+    a.idesc = g->idesc;
+    a.err = g->d_err;
+    const bool rec = g->prof && g->ev_used < g->ev0.size();
+    if (rec) GCK(cudaEventRecord(g->ev0[g->ev_used], s));
+    GCK(launch_group_mac(p, a, s));
+    if (rec) {
+        GCK(cudaEventRecord(g->ev1[g->ev_used], s));
+        ++g->ev_used;
+    }
+    GroupOutArgs o{};
+    o.partial = g->partial;
+    o.out = d_out;
+    o.B = g->B;
+    o.log2B = g->log2B;
+    o.n_dst = g->n_out;
+    o.SP = p.SP;
+    o.tw = g->tw;
+    GCK(launch_group_out(o, g->S, s));
+    ++g->nblk;
+    return CONV_OK;
+}
+
+int check_err(conv_group* g) {
+    const int v = *(volatile int*)g->h_err;
+    if (v != 0) {
+        *(volatile int*)g->h_err = 0;
+        return gset(CONV_E_TIMEOUT, "device-side wait gave up (code %d); results of the block are invalid", v);
+    }
+    return CONV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+conv_group* conv_group_create(int precision, int block, int n_in, int n_out, long long taps, int sessions) {
+    conv_group* g = new (std::nothrow) conv_group();
+    if (!g) {
+        gset(CONV_E_NOMEM, "out of host memory");
+        return nullptr;
+    }
+    if (create_impl(g, precision, block, n_in, n_out, taps, sessions) != CONV_OK) {
+        const std::string msg = conv_last_error();
+        group_free(g);
+        set_last_error_message(msg.c_str());
+        return nullptr;
+    }
+    set_last_error_message("");
+    return g;
+}
+
+int conv_group_set_filters(conv_group* g, const float* h) {
+    if (!g || !h) return gset(CONV_E_INVAL, "null argument");
+    GDev d(g->dev);
+    const GroupPlan& p = g->plan;
+    const size_t bytes = (size_t)g->n_out * g->n_in * (size_t)g->taps * sizeof(float);
+    const size_t mbytes = (size_t)g->B * g->n_out * sizeof(unsigned);
+    float* d_h = nullptr;
+    unsigned* d_max = nullptr;
+    int rc;
+    if ((rc = galloc(g, &d_h, bytes))) return rc;
+    if ((rc = galloc(g, &d_max, mbytes))) {
+        cudaFree(d_h);
+        g->dev_bytes -= bytes;
+        return rc;
+    }
+    cudaError_t r = cudaMemcpyAsync(d_h, h, bytes, cudaMemcpyHostToDevice, g->stream);
+    if (r == cudaSuccess) r = cudaMemsetAsync(d_max, 0, mbytes, g->stream);
+    if (r == cudaSuccess) r = cudaMemsetAsync(g->H, 0, p.h_bytes, g->stream);
+    GroupFilterArgs a{};
+    a.h = d_h;
+    a.taps = g->taps;
+    a.n_dst = g->n_out;
+    a.n_src = g->n_in;
+    a.K = p.K;
+    a.B = g->B;
+    a.log2B = g->log2B;
+    a.G = p.G;
+    a.KP = p.KP;
+    a.NKS = p.NKS;
+    a.maxbits = d_max;
+    a.sH = g->sH;
+    a.H = g->H;
+    a.tw = g->tw;
+    const int prec = to_prec(g->prec);
+    for (int pass = 0; pass < 2 && r == cudaSuccess; ++pass) {
+        a.pass = pass;
+        r = launch_group_filter(prec, a, g->stream);
+    }
+    if (r == cudaSuccess) r = cudaStreamSynchronize(g->stream);
+    cudaFree(d_h);
+    cudaFree(d_max);
+    g->dev_bytes -= bytes + mbytes;
+    if (r != cudaSuccess) return gset(CONV_E_CUDA, "group filter tiles: %s", cudaGetErrorString(r));
+    g->ready = true;
+    return group_reset_impl(g);
+}
+
+int conv_group_process_async(conv_group* g, const float* d_in, float* d_out, void* cuda_stream) {
+    if (!g || !d_in || !d_out) return gset(CONV_E_INVAL, "null argument");
+    if (!g->ready) return gset(CONV_E_STATE, "filters not set");
+    GDev d(g->dev);
+    return enqueue_group(g, d_in, d_out, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int conv_group_process(conv_group* g, const float* in, float* out) {
+    if (!g || !in || !out) return gset(CONV_E_INVAL, "null argument");
+    if (!g->ready) return gset(CONV_E_STATE, "filters not set");
+    GDev d(g->dev);
+    const size_t ib = (size_t)g->S * g->n_in * g->B * sizeof(float);
+    const size_t ob = (size_t)g->S * g->n_out * g->B * sizeof(float);
+    std::memcpy(g->h_in, in, ib);
+    GCK(cudaMemcpyAsync(g->d_in, g->h_in, ib, cudaMemcpyHostToDevice, g->stream));
+    int rc = enqueue_group(g, g->d_in, g->d_out, g->stream);
+    if (rc) return rc;
+    GCK(cudaMemcpyAsync(g->h_out, g->d_out, ob, cudaMemcpyDeviceToHost, g->stream));
+    GCK(cudaEventRecord(g->ev_done, g->stream));
+    GCK(cudaEventSynchronize(g->ev_done));
+    if ((rc = check_err(g))) return rc;
+    std::memcpy(out, g->h_out, ob);
+    return CONV_OK;
+}
+
+int conv_group_reset(conv_group* g) {
+    if (!g) return gset(CONV_E_INVAL, "null handle");
+    GDev d(g->dev);
+    return group_reset_impl(g);
+}
+
+int conv_group_synchronize(conv_group* g) {
+    if (!g) return gset(CONV_E_INVAL, "null handle");
+    GDev d(g->dev);
+    GCK(cudaStreamSynchronize(g->stream));
+    GCK(cudaDeviceSynchronize());
+    return check_err(g);
+}
+
+int conv_group_get_info(const conv_group* g, conv_group_info* out) {
+    if (!g || !out) return gset(CONV_E_INVAL, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    const GroupPlan& p = g->plan;
+    out->block = g->B;
+    out->n_in = g->n_in;
+    out->n_out = g->n_out;
+    out->taps = g->taps;
+    out->sessions = g->S;
+    out->precision = g->prec;
+    out->K = p.K;
+    out->ring_slots = p.KR;
+    out->bins_per_group = p.G;
+    out->groups = p.NG;
+    out->splits = p.SP;
+    out->k_steps = p.NKS;
+    out->stage_k_steps = p.NK;
+    out->stages = p.nstage;
+    out->mac_ctas = p.ctas;
+    out->mac_smem = p.smem;
+    out->tmem_cols = p.tmem_cols;
+    // every filter tile and every delay-line slot of every session read once
+    out->mac_bytes = (long long)(g->n_out + g->S) * g->n_in * (long long)p.KR * g->B * 4;
+    out->device_bytes = (long long)g->dev_bytes;
+    out->kernels_per_block = 3;
+    return CONV_OK;
+}
+
+int conv_group_plan_check(int precision, int block, int n_in, int n_out, long long taps, int sessions, int num_sms) {
+    const int prec = to_prec(precision);
+    if (prec < 0) return gset(CONV_E_INVAL, "unknown precision %d", precision);
+    GroupPlan p{};
+    if (const char* why = plan_group(prec, block, n_in, n_out, taps, sessions, num_sms, &p))
+        return gset(CONV_E_INVAL, "%s", why);
+    if (const char* why = check_group_plan(p)) return gset(CONV_E_INVAL, "%s", why);
+    return CONV_OK;
+}
+
+int conv_group_profile_enable(conv_group* g, int enable) {
+    if (!g) return gset(CONV_E_INVAL, "null handle");
+    GDev d(g->dev);
+    g->prof = enable > 0;
+    if (g->prof) {
+        const size_t want = enable > 1 ? (size_t)enable : 4096;
+        while (g->ev0.size() < want) {
+            cudaEvent_t a, b;
+            GCK(cudaEventCreate(&a));
+            GCK(cudaEventCreate(&b));
+            g->ev0.push_back(a);
+            g->ev1.push_back(b);
+        }
+    }
+    g->ev_used = 0;
+    return CONV_OK;
+}
+
+int conv_group_profile_read(conv_group* g, double* total_ms, long long* launches) {
+    if (!g || !total_ms || !launches) return gset(CONV_E_INVAL, "null argument");
+    GDev d(g->dev);
+    GCK(cudaStreamSynchronize(g->stream));
+    double tot = 0.0;
+    for (size_t i = 0; i < g->ev_used; ++i) {
+        float ms = 0.0f;
+        GCK(cudaEventElapsedTime(&ms, g->ev0[i], g->ev1[i]));
+        tot += ms;
+    }
+    *total_ms = tot;
+    *launches = (long long)g->ev_used;
+    g->ev_used = 0;
+    return CONV_OK;
+}
+
+void conv_group_destroy(conv_group* g) { group_free(g); }
+
+}  // extern "C"

@@ -90,6 +90,20 @@ class conv_info(ctypes.Structure):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
+class conv_group_info(ctypes.Structure):
+    _fields_ = [
+        (name, ctypes.c_longlong)
+        for name in (
+            "block", "n_in", "n_out", "taps", "sessions", "precision", "K", "ring_slots", "bins_per_group", "groups",
+            "splits", "k_steps", "stage_k_steps", "stages", "mac_ctas", "mac_smem", "tmem_cols", "mac_bytes",
+            "device_bytes", "kernels_per_block",
+        )
+    ]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -140,6 +154,17 @@ def load():
         "conv_batch_synchronize": (i, [vp]),
         "conv_batch_step_bytes": (ll, [vp]),
         "conv_batch_destroy": (None, [vp]),
+        "conv_group_create": (vp, [i, i, i, i, ll, i]),
+        "conv_group_set_filters": (i, [vp, vp]),
+        "conv_group_process_async": (i, [vp, vp, vp, vp]),
+        "conv_group_process": (i, [vp, vp, vp]),
+        "conv_group_reset": (i, [vp]),
+        "conv_group_synchronize": (i, [vp]),
+        "conv_group_get_info": (i, [vp, ctypes.POINTER(conv_group_info)]),
+        "conv_group_plan_check": (i, [i, i, i, i, ll, i, i]),
+        "conv_group_profile_enable": (i, [vp, i]),
+        "conv_group_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+        "conv_group_destroy": (None, [vp]),
         "conv_destroy": (None, [vp]),
         "conv_last_error": (ctypes.c_char_p, []),
     }
@@ -367,6 +392,73 @@ def conv_batch_destroy(b):
         load().conv_batch_destroy(b)
 
 
+def conv_group_create(precision, block, n_in, n_out, taps, sessions):
+    g = load().conv_group_create(
+        int(PRECISIONS.get(precision, precision)), int(block), int(n_in), int(n_out), int(taps), int(sessions)
+    )
+    if not g:
+        raise ConvError(CONV_E_INVAL, conv_last_error())
+    return g
+
+
+def conv_group_get_info(g) -> dict:
+    info = conv_group_info()
+    _check(load().conv_group_get_info(g, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def conv_group_set_filters(g, filters: np.ndarray):
+    i = conv_group_get_info(g)
+    return _check(load().conv_group_set_filters(g, _host_ptr(filters, (i["n_out"], i["n_in"], i["taps"]))))
+
+
+def conv_group_process_async(g, d_in, d_out, stream=None):
+    return _check(load().conv_group_process_async(g, _dev_ptr(d_in), _dev_ptr(d_out), _stream_ptr(stream)))
+
+
+def conv_group_process(g, inp: np.ndarray, out: np.ndarray, _shape=None):
+    S, n_in, n_out, B = _shape if _shape else _gdims(g)
+    return _check(load().conv_group_process(g, _host_ptr(inp, (S, n_in, B)), _host_ptr(out, (S, n_out, B), True)))
+
+
+def conv_group_reset(g):
+    return _check(load().conv_group_reset(g))
+
+
+def conv_group_synchronize(g):
+    return _check(load().conv_group_synchronize(g))
+
+
+def conv_group_plan_check(precision, block, n_in, n_out, taps, sessions, num_sms=152):
+    return _check(
+        load().conv_group_plan_check(
+            int(PRECISIONS.get(precision, precision)), int(block), int(n_in), int(n_out), int(taps), int(sessions),
+            int(num_sms),
+        )
+    )
+
+
+def conv_group_profile_enable(g, enable: int):
+    return _check(load().conv_group_profile_enable(g, int(enable)))
+
+
+def conv_group_profile_read(g):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(load().conv_group_profile_read(g, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def conv_group_destroy(g):
+    if g:
+        load().conv_group_destroy(g)
+
+
+def _gdims(g):
+    i = conv_group_get_info(g)
+    return i["sessions"], i["n_in"], i["n_out"], i["block"]
+
+
 def conv_destroy(h):
     if h:
         load().conv_destroy(h)
@@ -417,6 +509,62 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Group:
+    """Owning wrapper of a conv_group: ``sessions`` lock-step streams sharing
+    one filter set."""
+
+    def __init__(self, precision, block, n_in, n_out, taps, sessions):
+        self.g = conv_group_create(precision, block, n_in, n_out, taps, sessions)
+        self.shape = (int(sessions), int(n_in), int(n_out), int(block))
+
+    def set_filters(self, h: np.ndarray):
+        conv_group_set_filters(self.g, np.ascontiguousarray(h, dtype=np.float32))
+
+    def process(self, x_blocks: np.ndarray, out: np.ndarray | None = None) -> np.ndarray:
+        S, n_in, n_out, B = self.shape
+        if out is None:
+            out = np.empty((S, n_out, B), dtype=np.float32)
+        conv_group_process(self.g, np.ascontiguousarray(x_blocks, dtype=np.float32), out, self.shape)
+        return out
+
+    def run(self, x: np.ndarray) -> np.ndarray:
+        """Stream whole signals x [sessions][n_in][T] (zero-extended to whole blocks)."""
+        S, n_in, n_out, B = self.shape
+        T = x.shape[2]
+        nb = -(-T // B)
+        xp = np.zeros((S, n_in, nb * B), dtype=np.float32)
+        xp[:, :, :T] = x
+        y = np.empty((S, n_out, nb * B), dtype=np.float32)
+        blk = np.empty((S, n_out, B), dtype=np.float32)
+        for b in range(nb):
+            self.process(np.ascontiguousarray(xp[:, :, b * B : (b + 1) * B]), blk)
+            y[:, :, b * B : (b + 1) * B] = blk
+        return y
+
+    def info(self):
+        return conv_group_get_info(self.g)
+
+    def reset(self):
+        conv_group_reset(self.g)
+
+    def close(self):
+        if self.g:
+            conv_group_destroy(self.g)
+            self.g = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Engine:

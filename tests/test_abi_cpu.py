@@ -123,3 +123,33 @@ def test_tiling_override_arguments_are_validated(lib):
         upols.conv_plan_check("fp32", 256, 4, 16, 384000, 152, 0, 24)  # bin tile not a power of two
     with pytest.raises(upols.ConvError):
         upols.conv_plan_check("fp32", 256, 4, 16, 384000, 152, 7)  # unknown kernel
+
+
+def test_group_plans_replay_clean_over_shapes(lib):
+    """Host replay of every copy address of a shared-filter group's block, over
+    the supported shapes, precisions and SM counts."""
+    from paper_2509_04390_gb300 import upols as U
+
+    n = 0
+    for prec in ("fp16", "bf16"):
+        for B in (16, 64, 256, 1024, 4096):
+            for n_in in (1, 2, 4, 8):
+                for n_out in (8, 16, 32):
+                    for S in (8, 16, 32):
+                        if (128 // n_out) * S > 128:
+                            continue
+                        for taps in (1, 257, 3000, 384000):
+                            for sms in (152, 20):
+                                U.conv_group_plan_check(prec, B, n_in, n_out, taps, S, sms)
+                                n += 1
+    assert n > 500
+
+
+def test_group_rejects_unsupported_shapes_on_the_host(lib):
+    from paper_2509_04390_gb300 import upols as U
+
+    for args in (("fp32", 64, 4, 16, 100, 8), ("fp16", 64, 3, 16, 100, 8), ("fp16", 64, 4, 12, 100, 8),
+                 ("fp16", 64, 4, 16, 100, 12), ("fp16", 64, 4, 8, 100, 16), ("fp16", 48, 4, 16, 100, 8)):
+        with pytest.raises(U.ConvError) as ei:
+            U.conv_group_plan_check(*args)
+        assert ei.value.code == U.CONV_E_INVAL
