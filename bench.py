@@ -749,7 +749,7 @@ def run_group(args):
             "note": "the same sessions as separate engines, one call (3 launches) each per step",
         },
         "plan": {k: info[k] for k in ("groups", "splits", "stages", "stage_k_steps", "mac_ctas", "mac_smem",
-                                      "tmem_cols", "device_bytes")},
+                                      "tmem_cols", "acc_buffers", "tail_streams", "device_bytes")},
         "gpu_launches": args.steps * info["kernels_per_block"],
         "clocks": clocks.summary(tw0, tw1),
     }

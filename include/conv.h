@@ -333,7 +333,7 @@ typedef struct conv_group_info {
     long long ring_slots;     /* delay-line slots (K rounded up to a K-step)      */
     long long bins_per_group; /* bins per tensor-core tile (128 / n_out)          */
     long long groups;         /* bin groups (block / bins_per_group)              */
-    long long splits;         /* K-step splits per bin group                      */
+    long long splits;         /* partial slots per bin group (most MAC CTAs sharing one group) */
     long long k_steps;        /* K-steps of 16 reduction indices per block        */
     long long stage_k_steps;  /* K-steps per pipeline stage                       */
     long long stages;         /* pipeline depth                                   */
@@ -343,10 +343,26 @@ typedef struct conv_group_info {
     long long mac_bytes;      /* algorithmic bytes of one MAC launch: filters + delay lines, each read once */
     long long device_bytes;   /* device memory held                               */
     long long kernels_per_block; /* kernels one process call launches             */
+    long long tail_streams;   /* background streams of the tails                  */
+    long long tail_ctas;      /* CTAs of one MAC launch (= mac_ctas)              */
+    long long acc_buffers;    /* TMEM accumulator buffers per MAC CTA             */
 } conv_group_info;
+
+/* Tiling of a group's tensor-core MAC (autotuner hook); 0 leaves a field to
+ * the planner.  ctas: MAC CTAs, at most one per SM (default: one per SM),
+ * each taking an equal run of (bin group, K-step) units; stage_k_steps: 1..4;
+ * stages: 2..8; tail_streams: 1 (tails of consecutive blocks in order on one
+ * stream) or 2 (alternating streams, consecutive tails may overlap). */
+typedef struct conv_group_tiling {
+    int ctas, stage_k_steps, stages, tail_streams;
+} conv_group_tiling;
 
 /* Create a group on the current device; NULL on failure (conv_last_error()). */
 conv_group* conv_group_create(int precision, int block, int n_in, int n_out, long long taps, int sessions);
+
+/* Same with a tiling (NULL: the planner's choice). */
+conv_group* conv_group_create_tiled(int precision, int block, int n_in, int n_out, long long taps, int sessions,
+                                    const conv_group_tiling* tiling);
 
 /* Host filters h[n_out][n_in][taps] (copied; caller keeps ownership), shared
  * by all sessions.  Resets the sessions' state. */
@@ -371,7 +387,8 @@ int conv_group_get_info(const conv_group* g, conv_group_info* out);
 
 /* Host-only: plans a group and replays every copy address of a block against
  * the buffer and shared-memory sizes.  CONV_OK or CONV_E_INVAL with the reason. */
-int conv_group_plan_check(int precision, int block, int n_in, int n_out, long long taps, int sessions, int num_sms);
+int conv_group_plan_check(int precision, int block, int n_in, int n_out, long long taps, int sessions, int num_sms,
+                          const conv_group_tiling* tiling);
 
 /* CUDA-event timing of each MAC launch (enable > 1: number of event pairs),
  * read and cleared by conv_group_profile_read (total ms, launches). */

@@ -167,36 +167,43 @@ __global__ void k_group_pack(const GroupPackArgs a) {
 }
 
 // ------------------------------------------------------------ tensor-core MAC
-// One CTA per (bin group g, split sp) over K-steps [c0, c1).
+// One CTA per run of (bin group, tail K-step) units (GroupTiling), at most
+// one CTA per SM.
 //   warp 0     producer: bulk copies of filter tiles and ring rows into a ring
 //              of pipeline stages (mbarrier complete_tx)
 //   warp 1     allocates tensor memory; one lane issues two MMAs per K-step
-//              (D1 = Hr X into columns [0, N), D2 = Hi X into [N, 2N)) and
-//              commits each stage back to the producer
+//              (D1 = Hr X into columns [0, N), D2 = Hi X into [N, 2N) of the
+//              segment's accumulator buffer) and commits each stage back to the
+//              producer and each finished segment to the epilogue
 //   warps 2-5  epilogue: each reads its TMEM lane quadrant (32 rows), keeps
-//              the diagonal blocks, forms the complex result and writes the
-//              split partials
+//              the diagonal blocks, forms the complex result, writes the
+//              segment's partial slot and hands the buffer back
 // Every wait is bounded; a timeout raises the abort flag and the error word.
 __global__ void __launch_bounds__(GRP_THREADS, 1) k_group_mac(const GroupMacArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + GRP_MAX_STAGES;
-    uint64_t* accb = empty + GRP_MAX_STAGES;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+    uint64_t* accb = empty + GRP_MAX_STAGES;  // [2] segment accumulated, by buffer
+    uint64_t* tfree = accb + 2;               // [2] buffer read out, by buffer
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     unsigned char* stages = smem + GRP_HDR_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = blockIdx.x, sp = blockIdx.y;
-    const int c0 = (int)((long long)sp * a.NKS / a.SP);
-    const int c1 = (int)((long long)(sp + 1) * a.NKS / a.SP);
-    const int nfill = (c1 - c0 + a.NK - 1) / a.NK;
+    const int cta = blockIdx.x;
+    const long long U = (long long)a.NG * a.T;
+    const long long lo = (long long)cta * U / a.C, hi = (long long)(cta + 1) * U / a.C;
+    const int rows_per_class = a.KR / a.D;
+    const int cl = a.slot0 % a.D;
 
     if (tid == 0) {
         for (int i = 0; i < a.nstage; ++i) {
             mbar_init(full + i, 1);
             mbar_init(empty + i, 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accb + b, 1);
+            mbar_init(tfree + b, 128);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -213,102 +220,131 @@ __global__ void __launch_bounds__(GRP_THREADS, 1) k_group_mac(const GroupMacArgs
 
     if (warp == 0) {
         if (lane == 0) {
-            const uint64_t pol_h = policy_evict_first(), pol_x = policy_evict_last();
-            const int rows_per_class = a.KR / a.D;
-            const unsigned char* xb = static_cast<const unsigned char*>(a.X) +
-                                      ((size_t)g * a.D + a.slot0 % a.D) * rows_per_class * a.RB;
-            const unsigned char* hb = static_cast<const unsigned char*>(a.H) + (size_t)g * a.NKS * TILE_BYTES;
-            int i = 0;
-            for (; i < nfill; ++i) {
-                const int st = i % a.nstage;
-                if (i >= a.nstage &&
-                    !mbar_wait_bounded(empty + st, (uint32_t)((i / a.nstage) - 1) & 1u, abort_flag, GRP_WAIT_NS)) {
-                    report(a.err, abort_flag, DEVERR_TIMEOUT_PRODUCER);
-                    break;
+            // a ring class is read again only two blocks later, after ~300 MB of
+            // other traffic: neither operand is kept in L2 (evict-last on the ring
+            // measured slower on GB300)
+            const uint64_t pol_h = policy_evict_first(), pol_x = policy_evict_first();
+            int f = 0;
+            bool ok = true;
+            for (long long u = lo; u < hi && ok;) {
+                const int g = (int)(u / a.T);
+                const long long se = min(hi, (long long)(g + 1) * a.T);
+                const unsigned char* xb =
+                    static_cast<const unsigned char*>(a.X) + ((size_t)g * a.D + cl) * rows_per_class * a.RB;
+                const unsigned char* hb = static_cast<const unsigned char*>(a.H) + (size_t)g * a.NKS * TILE_BYTES;
+                for (long long v = u; v < se; v += a.NK, ++f) {
+                    const int st = f % a.nstage;
+                    if (f >= a.nstage &&
+                        !mbar_wait_bounded(empty + st, (uint32_t)((f / a.nstage) - 1) & 1u, abort_flag, GRP_WAIT_NS)) {
+                        report(a.err, abort_flag, DEVERR_TIMEOUT_PRODUCER);
+                        ok = false;
+                        break;
+                    }
+                    const int nk = (int)min((long long)a.NK, se - v);
+                    const int c = 1 + (int)(v - (long long)g * a.T);
+                    unsigned char* sA = stages + (size_t)st * a.stage_bytes;
+                    unsigned char* sB = sA + (size_t)a.NK * TILE_BYTES;
+                    mbar_arrive_expect_tx(full + st, (uint32_t)nk * (TILE_BYTES + 2u * a.RB));
+                    bulk_g2s(sA, hb + (size_t)c * TILE_BYTES, (uint32_t)nk * TILE_BYTES, full + st, pol_h);
+                    const int idx = ((a.slot0 + c * a.KP) % a.KR) / a.D;
+                    const int rows = 2 * nk;
+                    const int first = min(rows, rows_per_class - idx);
+                    bulk_g2s(sB, xb + (size_t)idx * a.RB, (uint32_t)(first * a.RB), full + st, pol_x);
+                    if (first < rows)
+                        bulk_g2s(sB + (size_t)first * a.RB, xb, (uint32_t)((rows - first) * a.RB), full + st, pol_x);
                 }
-                const int c = c0 + i * a.NK;
-                const int nk = min(a.NK, c1 - c);
-                unsigned char* sA = stages + (size_t)st * a.stage_bytes;
-                unsigned char* sB = sA + (size_t)a.NK * TILE_BYTES;
-                mbar_arrive_expect_tx(full + st, (uint32_t)nk * (TILE_BYTES + 2u * a.RB));
-                bulk_g2s(sA, hb + (size_t)c * TILE_BYTES, (uint32_t)nk * TILE_BYTES, full + st, pol_h);
-                const int t0 = (a.slot0 + c * a.KP) % a.KR;
-                const int idx = t0 / a.D;
-                const int rows = 2 * nk;
-                const int first = min(rows, rows_per_class - idx);
-                bulk_g2s(sB, xb + (size_t)idx * a.RB, (uint32_t)(first * a.RB), full + st, pol_x);
-                if (first < rows)
-                    bulk_g2s(sB + (size_t)first * a.RB, xb, (uint32_t)((rows - first) * a.RB), full + st, pol_x);
+                u = se;
             }
             // leave no copy in flight: wait (bounded) for the stages issued last
-            for (int j = max(0, i - a.nstage); j < i; ++j)
+            for (int j = max(0, f - a.nstage); j < f; ++j)
                 mbar_wait_bounded(full + j % a.nstage, (uint32_t)(j / a.nstage) & 1u, nullptr, GRP_WAIT_NS);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t sbase = smem_u32(stages);
-            for (int i = 0; i < nfill; ++i) {
-                const int st = i % a.nstage;
-                if (!mbar_wait_bounded(full + st, (uint32_t)(i / a.nstage) & 1u, abort_flag, GRP_WAIT_NS)) {
+            int f = 0, seg = 0;
+            bool ok = true;
+            for (long long u = lo; u < hi && ok; ++seg) {
+                const int g = (int)(u / a.T);
+                const long long se = min(hi, (long long)(g + 1) * a.T);
+                const int b = seg % a.nbuf, m = seg / a.nbuf;
+                if (m > 0 && !mbar_wait_bounded(tfree + b, (uint32_t)(m - 1) & 1u, abort_flag, GRP_WAIT_NS)) {
                     report(a.err, abort_flag, DEVERR_TIMEOUT_CONSUMER);
                     break;
                 }
                 tmem_fence_after();
-                const int nk = min(a.NK, c1 - (c0 + i * a.NK));
-                const uint32_t sA = sbase + (uint32_t)(st * a.stage_bytes);
-                const uint32_t sB = sA + (uint32_t)(a.NK * TILE_BYTES);
-                for (int j = 0; j < nk; ++j) {
-                    const uint64_t dAr = umma_desc(sA + (uint32_t)(j * TILE_BYTES), 2048, 128);
-                    const uint64_t dAi = umma_desc(sA + (uint32_t)(j * TILE_BYTES) + 4096, 2048, 128);
-                    const uint64_t dB = umma_desc(sB + (uint32_t)(j * 2 * a.RB), (uint32_t)a.RB, 128);
-                    const uint32_t acc = (i | j) ? 1u : 0u;
-                    umma_f16(tbase, dAr, dB, a.idesc, acc);
-                    umma_f16(tbase + (uint32_t)a.N, dAi, dB, a.idesc, acc);
+                const uint32_t dacc = tbase + (uint32_t)(b * 2 * a.N);
+                uint32_t acc = 0u;
+                for (long long v = u; v < se; v += a.NK, ++f) {
+                    const int st = f % a.nstage;
+                    if (!mbar_wait_bounded(full + st, (uint32_t)(f / a.nstage) & 1u, abort_flag, GRP_WAIT_NS)) {
+                        report(a.err, abort_flag, DEVERR_TIMEOUT_CONSUMER);
+                        ok = false;
+                        break;
+                    }
+                    tmem_fence_after();
+                    const int nk = (int)min((long long)a.NK, se - v);
+                    const uint32_t sA = sbase + (uint32_t)(st * a.stage_bytes);
+                    const uint32_t sB = sA + (uint32_t)(a.NK * TILE_BYTES);
+                    for (int j = 0; j < nk; ++j) {
+                        const uint64_t dAr = umma_desc(sA + (uint32_t)(j * TILE_BYTES), 2048, 128);
+                        const uint64_t dAi = umma_desc(sA + (uint32_t)(j * TILE_BYTES) + 4096, 2048, 128);
+                        const uint64_t dB = umma_desc(sB + (uint32_t)(j * 2 * a.RB), (uint32_t)a.RB, 128);
+                        umma_f16(dacc, dAr, dB, a.idesc, acc);
+                        umma_f16(dacc + (uint32_t)a.N, dAi, dB, a.idesc, acc);
+                        acc = 1u;
+                    }
+                    umma_commit(empty + st);
                 }
-                umma_commit(empty + st);
+                umma_commit(accb + b);  // arrives once every MMA of the segment has completed
+                u = se;
             }
-            umma_commit(accb);  // arrives once every MMA above has completed
         }
     } else {
         const int quad = warp & 3;  // the TMEM lane quadrant this warp may access
         const int row = quad * 32 + lane;
         const int bq = 32 / a.n_dst;  // bins per quadrant
         const int b_lo = quad * bq;
-        const int W = bq * a.S;  // columns of one range
-        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(accb, 0, abort_flag, GRP_WAIT_NS));
-        if (!ok && lane == 0) report(a.err, abort_flag, DEVERR_TIMEOUT_CONSUMER);
-        tmem_fence_after();
-        // stage the four column ranges (D1 re, D1 im, D2 re, D2 im) of this
-        // quadrant's bins: [range][column][lane], conflict-free both ways
-        float* stg = reinterpret_cast<float*>(stages) + (size_t)(warp - 2) * 4 * W * 32;
+        const int mb = row / a.n_dst, l = row - mb * a.n_dst;  // this lane's bin (in the group) and output
         const int GS = a.G * a.S;
-        if (ok) {
-            for (int rg = 0; rg < 4; ++rg) {
-                const int colbase = ((rg >> 1) ? a.N : 0) + ((rg & 1) ? GS : 0) + b_lo * a.S;
-                for (int ch = 0; ch < W; ch += 8) {
-                    float v[8];
-                    tmem_ld8(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(colbase + ch), v);
+        int seg = 0;
+        for (long long u = lo; u < hi; ++seg) {
+            const int g = (int)(u / a.T);
+            const long long se = min(hi, (long long)(g + 1) * a.T);
+            const int b = seg % a.nbuf, m = seg / a.nbuf;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(accb + b, (uint32_t)m & 1u, abort_flag, GRP_WAIT_NS));
+            if (!ok && lane == 0) report(a.err, abort_flag, DEVERR_TIMEOUT_CONSUMER);
+            tmem_fence_after();
+            const int j = cta - group_cta_of_unit((long long)g * a.T, U, a.C);  // this CTA's slot in group g
+            const int k = g * a.G + mb;
+            const float scale = __ldg(a.sH + (size_t)g * 128 + row);
+            const uint32_t dl = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * a.N);
+            for (int ch = 0; ch < bq; ++ch) {
+                const int bin = b_lo + ch;
+                for (int sc = 0; sc < a.S; sc += 8) {
+                    float d1r[8], d1i[8], d2r[8], d2i[8];
+                    if (ok) {
+                        const uint32_t c_re = (uint32_t)(bin * a.S + sc), c_im = (uint32_t)(GS + bin * a.S + sc);
+                        tmem_ld8(dl + c_re, d1r);
+                        tmem_ld8(dl + c_im, d1i);
+                        tmem_ld8(dl + (uint32_t)a.N + c_re, d2r);
+                        tmem_ld8(dl + (uint32_t)a.N + c_im, d2i);
+                    }
+                    if (mb != bin) continue;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) stg[((size_t)rg * W + ch + j) * 32 + lane] = v[j];
+                    for (int e = 0; e < 8; ++e) {
+                        float2 y = make_float2(0.0f, 0.0f);
+                        if (ok) {
+                            y = k == 0 ? make_float2(d1r[e], d2i[e]) : make_float2(d1r[e] - d2i[e], d1i[e] + d2r[e]);
+                            y = cscale(y, scale);
+                        }
+                        a.partial[(((size_t)(sc + e) * a.SP + j) * a.n_dst + l) * a.B + k] = y;
+                    }
                 }
             }
-        }
-        __syncwarp();
-        const int b = row / a.n_dst, l = row - b * a.n_dst;
-        const int k = g * a.G + b;
-        const int boff = (b - b_lo) * a.S;
-        const float scale = ok ? __ldg(a.sH + (size_t)g * 128 + row) : 0.0f;
-        for (int s = 0; s < a.S; ++s) {
-            float2 y = make_float2(0.0f, 0.0f);
-            if (ok) {
-                const float d1r = stg[((size_t)0 * W + boff + s) * 32 + lane];
-                const float d1i = stg[((size_t)1 * W + boff + s) * 32 + lane];
-                const float d2r = stg[((size_t)2 * W + boff + s) * 32 + lane];
-                const float d2i = stg[((size_t)3 * W + boff + s) * 32 + lane];
-                y = k == 0 ? make_float2(d1r, d2i) : make_float2(d1r - d2i, d1i + d2r);
-                y = cscale(y, scale);
-            }
-            a.partial[(((size_t)s * a.SP + sp) * a.n_dst + l) * a.B + k] = y;
+            tmem_fence_before();
+            mbar_arrive(tfree + b);
+            u = se;
         }
     }
     tmem_fence_before();
@@ -318,9 +354,23 @@ __global__ void __launch_bounds__(GRP_THREADS, 1) k_group_mac(const GroupMacArgs
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(a.tmem_cols) : "memory");
 }
 
-// --------------------------------------------------- split reduction + C2R
-// One CTA per (output l, session s): fixed-order sum of the SP split partials,
-// C2R, 1/B scaling, keep the last B samples (overlap-save).
+template <int PREC>
+__device__ __forceinline__ void unpack8(const uint4 w, float (&v)[8]) {
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = PREC == PREC_FP16 ? unpack_half2(u[i]) : unpack_bf162(u[i]);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+
+// --------------------------------------------------- head + reduction + C2R
+// One CTA per (output l, session s): K-step 0 of this block (partitions
+// 0 .. KP-1, the only ones that need this block's spectrum) from the filter
+// tiles and ring rows, plus the fixed-order sum of the tail's SP split
+// partials; then C2R, 1/B scaling, keep the last B samples (overlap-save).
+template <int PREC>
 __global__ void k_group_out(const GroupOutArgs a) {
     extern __shared__ float2 fsm[];
     const int B = a.B, tid = threadIdx.x, nth = blockDim.x;
@@ -331,10 +381,43 @@ __global__ void k_group_out(const GroupOutArgs a) {
     load_twiddles(tws, a.tw, B);
     const size_t stride = (size_t)a.n_dst * B;
     const float2* src0 = a.partial + ((size_t)s * a.SP * a.n_dst + l) * B;
+    const long long U = (long long)(B / a.G) * a.T;
+    const int rows_per_class = a.KR / a.D;
+    const int cl = a.slot0 % a.D;
+    const int idx0 = a.slot0 / a.D, idx1 = (idx0 + 1) % rows_per_class;  // ring rows t0 = slot0, t1 = slot0 + D
+    const unsigned char* Hb = static_cast<const unsigned char*>(a.H);
+    const unsigned char* Xb = static_cast<const unsigned char*>(a.X);
     for (int k = tid; k < B; k += nth) {
+        const int g = k / a.G, b = k - g * a.G, row = b * a.n_dst + l;
+        // the tail CTAs that covered group g wrote slots 0 .. n-1, summed in that order
+        const int n = a.C ? group_cta_of_unit((long long)(g + 1) * a.T - 1, U, a.C) -
+                                group_cta_of_unit((long long)g * a.T, U, a.C) + 1
+                          : 0;
         float2 tot = make_float2(0.0f, 0.0f);
-        for (int sp = 0; sp < a.SP; ++sp) tot = cadd(tot, src0[(size_t)sp * stride + k]);
-        P[k] = tot;
+        for (int sp = 0; sp < n; ++sp) tot = cadd(tot, src0[(size_t)sp * stride + k]);
+        const unsigned char* ht = Hb + (size_t)g * a.NKS * TILE_BYTES + (size_t)(row >> 3) * 128 + (size_t)(row & 7) * 16;
+        const size_t cls = ((size_t)g * a.D + cl) * rows_per_class;
+        float2 hd = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc) {
+            const unsigned char* xr = Xb + (cls + (kc ? idx1 : idx0)) * a.RB + (size_t)s * 16;
+            float hr[8], hi[8], xre[8], xim[8];
+            unpack8<PREC>(*reinterpret_cast<const uint4*>(ht + kc * 2048), hr);
+            unpack8<PREC>(*reinterpret_cast<const uint4*>(ht + kc * 2048 + 4096), hi);
+            unpack8<PREC>(*reinterpret_cast<const uint4*>(xr + (size_t)b * a.S * 16), xre);
+            unpack8<PREC>(*reinterpret_cast<const uint4*>(xr + (size_t)(a.G + b) * a.S * 16), xim);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                if (k == 0) {  // packed DC and Nyquist: two real products
+                    hd.x = fmaf(hr[e], xre[e], hd.x);
+                    hd.y = fmaf(hi[e], xim[e], hd.y);
+                } else {
+                    hd.x = fmaf(hr[e], xre[e], fmaf(-hi[e], xim[e], hd.x));
+                    hd.y = fmaf(hr[e], xim[e], fmaf(hi[e], xre[e], hd.y));
+                }
+            }
+        }
+        P[k] = cadd(tot, cscale(hd, __ldg(a.sH + (size_t)g * 128 + row)));
     }
     __syncthreads();
     for (int k = tid; k < B; k += nth) W[k] = c2r_pre(P, k, B, tws);
@@ -352,7 +435,8 @@ __global__ void k_group_out(const GroupOutArgs a) {
 
 // ---------------------------------------------------------------- planning
 
-const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, int S, int num_sms, GroupPlan* out) {
+const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, int S, int num_sms, GroupPlan* out,
+                       const GroupTiling& t) {
     if (prec != PREC_FP16 && prec != PREC_BF16) return "session groups store FP16 or BF16 spectra";
     if (B < 16 || B > 4096 || (B & (B - 1))) return "block must be a power of two in [16, 4096]";
     if (n_dst != 8 && n_dst != 16 && n_dst != 32) return "session groups need n_out in {8, 16, 32}";
@@ -360,6 +444,10 @@ const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, in
     if (S < 8 || S % 8) return "sessions must be a positive multiple of 8";
     if (taps < 1) return "taps must be >= 1";
     if (num_sms < 1) return "num_sms must be >= 1";
+    if (t.ctas < 0) return "ctas must be >= 0";
+    if (t.stage_k_steps < 0 || t.stage_k_steps > 4) return "stage_k_steps must be in [0, 4]";
+    if (t.stages < 0 || t.stages == 1 || t.stages > GRP_MAX_STAGES) return "stages must be 0 or in [2, 8]";
+    if (t.tail_streams < 0 || t.tail_streams > 2) return "tail_streams must be 0, 1 or 2";
     GroupPlan p{};
     p.B = B;
     p.n_src = n_src;
@@ -378,22 +466,35 @@ const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, in
     p.NG = B / p.G;
     p.N = 2 * p.G * S;
     p.RB = 32 * p.G * S;
+    p.nbuf = 4 * p.N <= 512 ? 2 : 1;
     p.tmem_cols = 32;
-    while (p.tmem_cols < 2 * p.N) p.tmem_cols *= 2;
-    p.ctas_per_sm = p.tmem_cols <= 256 ? 2 : 1;
+    while (p.tmem_cols < p.nbuf * 2 * p.N) p.tmem_cols *= 2;
+    p.tail_streams = t.tail_streams ? t.tail_streams : 2;
     const int kb = TILE_BYTES + 2 * p.RB;
-    const int budget = (p.ctas_per_sm == 2 ? 112 * 1024 : 224 * 1024) - GRP_HDR_BYTES;
-    p.NK = std::max(1, std::min(4, (budget / 4) / kb));
-    p.nstage = std::min(GRP_MAX_STAGES, budget / (p.NK * kb));
-    if (p.nstage < 2) return "pipeline stages do not fit in shared memory";
+    // stages stay below ~180 KB so that the pack and output kernels of the
+    // next block fit beside a MAC CTA on every SM
+    const int budget = 180 * 1024 - GRP_HDR_BYTES;
+    // measured on GB300 (8 and 16 sessions of the 4x16 paper set): the largest
+    // stages that still give 3 in flight stream best; 1 K-step per stage starves
+    // the MMA
+    p.NK = t.stage_k_steps ? t.stage_k_steps : (3 * 4 * kb <= budget ? 4 : (3 * 3 * kb <= budget ? 3 : 2));
+    p.nstage = t.stages ? t.stages : std::min(6, budget / (p.NK * kb));
+    if (p.nstage < 2 || p.nstage * p.NK * kb > budget) return "pipeline stages do not fit in shared memory";
     p.stage_bytes = p.NK * kb;
-    const int W = (32 / n_dst) * S;
-    const int staging = 4 * 4 * W * 32 * (int)sizeof(float);
-    p.smem = GRP_HDR_BYTES + std::max(p.nstage * p.stage_bytes, staging);
-    if (p.smem - GRP_HDR_BYTES > budget) return "epilogue staging does not fit in shared memory";
-    const int want = p.ctas_per_sm * num_sms;
-    p.SP = std::max(1, std::min(p.NKS, want / p.NG));
-    p.ctas = p.NG * p.SP;
+    // at most one MAC CTA per SM: its tensor memory may be all of the SM's
+    p.smem = std::max(GRP_HDR_BYTES + p.nstage * p.stage_bytes, 116 * 1024);
+    p.T = p.NKS - 1;
+    const long long U = (long long)p.NG * p.T;
+    // default: all but 8 SMs, where the next block's pack and output kernels run
+    // at once (with a MAC CTA on every SM they wait for the tail to drain)
+    const int c_auto = std::max(1, num_sms > 16 ? num_sms - 8 : num_sms);
+    p.C = U > 0 ? (int)std::min<long long>(U, t.ctas ? std::min(t.ctas, num_sms) : c_auto) : 0;
+    p.SP = 0;
+    for (int g = 0; g < p.NG && p.C; ++g) {
+        const int n = group_cta_of_unit((long long)(g + 1) * p.T - 1, U, p.C) -
+                      group_cta_of_unit((long long)g * p.T, U, p.C) + 1;
+        p.SP = std::max(p.SP, n);
+    }
     p.h_bytes = (size_t)p.NG * p.NKS * TILE_BYTES;
     p.x_bytes = (size_t)p.NG * p.KR * p.RB;
     p.partial_bytes = (size_t)S * p.SP * n_dst * B * sizeof(float2);
@@ -402,41 +503,66 @@ const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, in
 }
 
 const char* check_group_plan(const GroupPlan& p) {
-    static char msg[256];
+    static thread_local char msg[256];
     if (p.G * p.n_dst != 128 || p.NG * p.G != p.B) return "group shape does not tile 128 rows / B bins";
     if (p.N % 16 || p.N < 16 || p.N > 256) return "MMA N out of range";
-    if (2 * p.N > p.tmem_cols || p.tmem_cols > 512) return "tensor memory columns";
+    if (p.nbuf < 1 || p.nbuf > 2 || p.nbuf * 2 * p.N > p.tmem_cols || p.tmem_cols > 512) return "tensor memory columns";
     if (p.RB % 16 || p.stage_bytes % 16) return "copy sizes must be multiples of 16 bytes";
     if ((size_t)p.smem > 227 * 1024) return "shared memory above the per-CTA limit";
+    if (p.smem <= 114 * 1024) return "shared memory small enough for two MAC CTAs on one SM";
     if ((32 / p.n_dst) * p.S % 8) return "epilogue column ranges must be multiples of 8";
+    if (p.nstage < 2 || p.nstage > GRP_MAX_STAGES) return "pipeline depth";
+    if ((size_t)p.stage_bytes * p.nstage + GRP_HDR_BYTES > (size_t)p.smem) return "stages beyond shared memory";
+    if (p.T != p.NKS - 1 || (p.T > 0) != (p.C > 0)) return "tail shape";
+    const long long U = (long long)p.NG * p.T;
+    if (p.C > U) return "more tail CTAs than units";
     const int rows_per_class = p.KR / p.D;
-    for (int slot0 = 0; slot0 < std::min(p.KR, 2 * p.D + 1); ++slot0)
-        for (int sp = 0; sp < p.SP; ++sp) {
-            const int c0 = (int)((long long)sp * p.NKS / p.SP), c1 = (int)((long long)(sp + 1) * p.NKS / p.SP);
-            if (c1 <= c0) return "empty split";
-            for (int c = c0; c < c1; c += p.NK) {
-                const int nk = std::min(p.NK, c1 - c);
-                const size_t h_end = ((size_t)(p.NG - 1) * p.NKS + c + nk) * TILE_BYTES;
-                if (h_end > p.h_bytes) return "filter copy beyond the tiles";
-                const int t0 = (slot0 + c * p.KP) % p.KR;
-                if (t0 % p.D != slot0 % p.D) return "ring class changes within a block";
-                const int idx = t0 / p.D, rows = 2 * nk;
-                const int first = std::min(rows, rows_per_class - idx);
-                const size_t cls_base = ((size_t)(p.NG - 1) * p.D + (p.D - 1)) * rows_per_class;
-                if ((cls_base + idx + first) * p.RB > p.x_bytes) return "ring copy beyond the ring";
-                if (rows - first > rows_per_class) return "ring copy wraps twice";
-                // the rows of K-step c are t0 and t0 + D
-                for (int j = 0; j < nk; ++j) {
-                    const int ta = (slot0 + (c + j) * p.KP) % p.KR, tb = (ta + p.D) % p.KR;
-                    const int ia = (idx + 2 * j) % rows_per_class, ib = (idx + 2 * j + 1) % rows_per_class;
-                    if (ta / p.D != ia || tb / p.D != ib) {
-                        snprintf(msg, sizeof(msg), "ring row order: slot0 %d K-step %d", slot0, c + j);
-                        return msg;
+    long long covered = 0;
+    for (int cta = 0; cta < p.C; ++cta) {
+        const long long lo = (long long)cta * U / p.C, hi = (long long)(cta + 1) * U / p.C;
+        if (hi <= lo) return "empty tail run";
+        covered += hi - lo;
+        for (long long u = lo; u < hi;) {
+            const int g = (int)(u / p.T);
+            const long long se = std::min(hi, (long long)(g + 1) * p.T);
+            const int j = cta - group_cta_of_unit((long long)g * p.T, U, p.C);
+            if (j < 0 || j >= p.SP) {
+                snprintf(msg, sizeof(msg), "partial slot %d of CTA %d in group %d outside [0, %d)", j, cta, g, p.SP);
+                return msg;
+            }
+            if (group_cta_of_unit(u, U, p.C) != cta) return "unit owner mismatch";
+            for (int slot0 = 0; slot0 < std::min(p.KR, 2 * p.D + 1); ++slot0)
+                for (long long v = u; v < se; v += p.NK) {
+                    const int nk = (int)std::min((long long)p.NK, se - v);
+                    const int c = 1 + (int)(v - (long long)g * p.T);
+                    if (c < 1 || c + nk > p.NKS) return "K-step outside the tail";
+                    if (((size_t)g * p.NKS + c + nk) * TILE_BYTES > p.h_bytes) return "filter copy beyond the tiles";
+                    const int t0 = (slot0 + c * p.KP) % p.KR;
+                    if (t0 % p.D != slot0 % p.D) return "ring class changes within a block";
+                    const int idx = t0 / p.D, rows = 2 * nk;
+                    const int first = std::min(rows, rows_per_class - idx);
+                    const size_t cls_base = ((size_t)g * p.D + slot0 % p.D) * rows_per_class;
+                    if ((cls_base + idx + first) * p.RB > p.x_bytes) return "ring copy beyond the ring";
+                    if (rows - first > rows_per_class) return "ring copy wraps twice";
+                    for (int jj = 0; jj < nk; ++jj) {  // the rows of K-step c are t0 and t0 + D
+                        const int ta = (slot0 + (c + jj) * p.KP) % p.KR, tb = (ta + p.D) % p.KR;
+                        const int ia = (idx + 2 * jj) % rows_per_class, ib = (idx + 2 * jj + 1) % rows_per_class;
+                        if (ta / p.D != ia || tb / p.D != ib) {
+                            snprintf(msg, sizeof(msg), "ring row order: slot0 %d K-step %d", slot0, c + jj);
+                            return msg;
+                        }
                     }
                 }
-            }
+            u = se;
         }
-    if ((size_t)p.stage_bytes * p.nstage + GRP_HDR_BYTES > (size_t)p.smem) return "stages beyond shared memory";
+    }
+    if (covered != U) return "tail runs do not cover every unit once";
+    for (int g = 0; g < p.NG && p.C; ++g) {
+        const int n = group_cta_of_unit((long long)(g + 1) * p.T - 1, U, p.C) -
+                      group_cta_of_unit((long long)g * p.T, U, p.C) + 1;
+        if (n < 1 || n > p.SP) return "group slot count";
+    }
+    if ((size_t)p.S * p.SP * p.n_dst * p.B * sizeof(float2) != p.partial_bytes) return "partial buffer size";
     return nullptr;
 }
 
@@ -453,7 +579,10 @@ cudaError_t prepare_group_kernels() {
         return e;
     if ((e = cudaFuncSetAttribute(k_group_pack<PREC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fft_max)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_group_out, cudaFuncAttributeMaxDynamicSharedMemorySize, fft_max))) return e;
+    if ((e = cudaFuncSetAttribute(k_group_out<PREC_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fft_max)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_group_out<PREC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fft_max)))
+        return e;
     return cudaFuncSetAttribute(k_group_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
@@ -479,12 +608,17 @@ cudaError_t launch_group_pack(int prec, const GroupPackArgs& a, cudaStream_t s) 
 }
 
 cudaError_t launch_group_mac(const GroupPlan& p, const GroupMacArgs& a, cudaStream_t s) {
-    k_group_mac<<<dim3(p.NG, p.SP), GRP_THREADS, p.smem, s>>>(a);
+    if (p.C == 0) return cudaSuccess;
+    k_group_mac<<<p.C, GRP_THREADS, p.smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_group_out(const GroupOutArgs& a, int S, cudaStream_t s) {
-    k_group_out<<<dim3(a.n_dst, S), out_threads(a.B), fft_smem_bytes(a.B), s>>>(a);
+cudaError_t launch_group_out(int prec, const GroupOutArgs& a, cudaStream_t s) {
+    const dim3 grid(a.n_dst, a.S);
+    if (prec == PREC_FP16)
+        k_group_out<PREC_FP16><<<grid, out_threads(a.B), fft_smem_bytes(a.B), s>>>(a);
+    else
+        k_group_out<PREC_BF16><<<grid, out_threads(a.B), fft_smem_bytes(a.B), s>>>(a);
     return cudaGetLastError();
 }
 

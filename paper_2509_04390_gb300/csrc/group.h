@@ -47,6 +47,25 @@ constexpr int GRP_HDR_BYTES = 1024;
 constexpr int GRP_MAX_STAGES = 8;
 constexpr int GRP_THREADS = 192;  // producer warp, MMA warp, 4 epilogue warps
 
+// Tiling fields a caller may fix (0 leaves a field to the planner).
+struct GroupTiling {
+    int ctas = 0;           // MAC CTAs (at most one per SM)
+    int stage_k_steps = 0;  // K-steps per pipeline stage (1..4)
+    int stages = 0;         // pipeline depth (2..8)
+    int tail_streams = 0;   // background streams the tails alternate over (1 or 2)
+};
+
+// Work split of the tail MAC: the NG * T units (bin group g, tail K-step c =
+// 1 + u - g*T) are cut into C equal runs, run i = [i*U/C, (i+1)*U/C), one per
+// CTA; a run that crosses a group boundary finishes one accumulator and starts
+// the next.  The CTAs that share a group write partials to consecutive slots.
+__host__ __device__ inline int group_cta_of_unit(long long u, long long U, int C) {
+    long long i = u * C / U;
+    while (i + 1 < C && (i + 1) * U / C <= u) ++i;
+    while (i > 0 && i * U / C > u) --i;
+    return (int)i;
+}
+
 struct GroupPlan {
     int B, n_src, n_dst, S, K;
     int G;         // bins per group = 128 / n_dst
@@ -57,14 +76,17 @@ struct GroupPlan {
     int NKS;       // K-steps per block = KR / KP
     int N;         // MMA N = 2 G S
     int RB;        // ring row bytes = 32 G S
-    int SP;        // splits of the K-steps per group
+    int T;         // tail K-steps per group, NKS - 1
+    int C;         // tail MAC CTAs (0: no tail)
+    int SP;        // partial slots per group: most CTAs that share one group
     int NK;        // K-steps per pipeline stage
     int nstage;
     int stage_bytes;  // NK * (8192 + 2 RB)
     int smem;         // dynamic shared memory per CTA
-    int ctas, ctas_per_sm;
-    int tmem_cols;    // power of two >= 2 N
-    size_t h_bytes, x_bytes, partial_bytes;
+    int nbuf;      // TMEM accumulator buffers (2: the next group's MMAs overlap the epilogue)
+    int tail_streams;
+    int tmem_cols;    // power of two >= nbuf * 2 N
+    size_t h_bytes, x_bytes, partial_bytes;  // partial_bytes: one block parity
 };
 
 struct GroupMacArgs {
@@ -72,7 +94,7 @@ struct GroupMacArgs {
     const void* X;       // ring
     const float* sH;     // [NG][128] row scales
     float2* partial;     // [S][SP][n_dst][B]
-    int B, n_dst, S, G, NG, D, KP, KR, NKS, N, RB, SP, NK, nstage, stage_bytes, slot0, tmem_cols;
+    int B, n_dst, S, G, NG, D, KP, KR, NKS, N, RB, T, C, SP, NK, nstage, stage_bytes, slot0, tmem_cols, nbuf;
     uint32_t idesc;
     int* err;
 };
@@ -98,12 +120,18 @@ struct GroupFilterArgs {
 struct GroupOutArgs {
     const float2* partial;
     float* out;  // [S][n_dst][B]
-    int B, log2B, n_dst, SP;
+    int B, log2B, n_dst, T, C, SP;
     const float2* tw;
+    // head: K-step 0 (partitions 0 .. KP-1) of this block, on CUDA cores
+    const void* H;
+    const void* X;
+    const float* sH;
+    int G, D, KR, NKS, RB, S, slot0;
 };
 
 // Plans a group; returns nullptr or a message naming the unsupported parameter.
-const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, int S, int num_sms, GroupPlan* p);
+const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, int S, int num_sms, GroupPlan* p,
+                       const GroupTiling& t = GroupTiling());
 // Replays every copy and store address of one block against the buffer and
 // shared-memory sizes (host only); nullptr or a message.
 const char* check_group_plan(const GroupPlan& p);
@@ -112,6 +140,6 @@ cudaError_t prepare_group_kernels();
 cudaError_t launch_group_filter(int prec, const GroupFilterArgs& a, cudaStream_t s);
 cudaError_t launch_group_pack(int prec, const GroupPackArgs& a, cudaStream_t s);
 cudaError_t launch_group_mac(const GroupPlan& p, const GroupMacArgs& a, cudaStream_t s);
-cudaError_t launch_group_out(const GroupOutArgs& a, int S, cudaStream_t s);
+cudaError_t launch_group_out(int prec, const GroupOutArgs& a, cudaStream_t s);
 
 }  // namespace gbconv

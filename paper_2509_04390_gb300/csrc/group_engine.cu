@@ -1,11 +1,19 @@
 // group_engine.cu - the conv_group_* entry points of conv.h: shared-filter
 // session groups whose FDL MAC runs on the tensor cores (group.h).
 //
-// Per block, on the caller's stream: pack + R2C of every session's inputs
-// into the duplicated-slot ring, the tensor-core MAC over all partitions, and
-// the split reduction + C2R of every (session, output).  The whole MAC is on
-// the block's path (no split-phase tail): the group trades block latency for
-// throughput.
+// Split-phase schedule, as for a single engine.  K-steps 1.. of block n+1
+// (partitions KP.., which need only spectra of blocks <= n+1-KP) are the
+// "tail": the tensor-core MAC runs them on a low-priority background stream
+// as soon as block n's spectra are in the ring, into split partials of block
+// n+1's parity.  When block n+1 arrives, the caller's stream runs the pack +
+// R2C of every session and one output kernel per (session, output) that adds
+// K-step 0 (the "head", on CUDA cores) to the tail's partials and transforms
+// back.  Tails alternate between two background streams:
+//   caller stream:      pack(n) -> [rec packed] -> [wait tail(n)] -> out(n)
+//   background n+1 & 1: [wait packed(n)] -> tail(n+1) -> [rec tail(n+1 & 1)]
+// pack(n+1) overwrites the slot of block n+1-KR, which only tail(n) read (and
+// out(n) waited for it); the ring rows pack(n+1) writes are never rows that
+// tail(n+1) reads (they hold slot0(n+1) at position 0 only in K-step 0's row).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,12 +39,15 @@ struct conv_group {
     GroupPlan plan{};
     uint32_t idesc = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t bg[2] = {nullptr, nullptr};
     cudaEvent_t ev_done = nullptr;
+    cudaEvent_t ev_packed = nullptr;
+    cudaEvent_t ev_tail[2] = {nullptr, nullptr};
     void* H = nullptr;
     void* X = nullptr;
     float* sH = nullptr;
     float* win = nullptr;
-    float2* partial = nullptr;
+    float2* partial[2] = {nullptr, nullptr};  // tail partials by block parity
     float2* tw = nullptr;
     float *d_in = nullptr, *d_out = nullptr, *h_in = nullptr, *h_out = nullptr;
     int *h_err = nullptr, *d_err = nullptr;
@@ -95,8 +106,10 @@ void group_free(conv_group* g) {
     if (!g) return;
     GDev d(g->dev);
     if (g->stream) cudaStreamSynchronize(g->stream);
-    for (void* p : {g->H, g->X, (void*)g->sH, (void*)g->win, (void*)g->partial, (void*)g->tw, (void*)g->d_in,
-                    (void*)g->d_out})
+    for (int i = 0; i < 2; ++i)
+        if (g->bg[i]) cudaStreamSynchronize(g->bg[i]);
+    for (void* p : {g->H, g->X, (void*)g->sH, (void*)g->win, (void*)g->partial[0], (void*)g->partial[1], (void*)g->tw,
+                    (void*)g->d_in, (void*)g->d_out})
         if (p) cudaFree(p);
     if (g->h_in) cudaFreeHost(g->h_in);
     if (g->h_out) cudaFreeHost(g->h_out);
@@ -104,6 +117,11 @@ void group_free(conv_group* g) {
     for (auto ev : g->ev0) cudaEventDestroy(ev);
     for (auto ev : g->ev1) cudaEventDestroy(ev);
     if (g->ev_done) cudaEventDestroy(g->ev_done);
+    if (g->ev_packed) cudaEventDestroy(g->ev_packed);
+    for (int i = 0; i < 2; ++i) {
+        if (g->ev_tail[i]) cudaEventDestroy(g->ev_tail[i]);
+        if (g->bg[i]) cudaStreamDestroy(g->bg[i]);
+    }
     if (g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -112,24 +130,47 @@ int to_prec(int precision) {
     return precision == CONV_FP16 ? PREC_FP16 : (precision == CONV_BF16 ? PREC_BF16 : (precision == CONV_FP32 ? PREC_FP32 : -1));
 }
 
-int group_reset_impl(conv_group* g) {
+int sync_all(conv_group* g) {
+    for (int i = 0; i < 2; ++i) GCK(cudaStreamSynchronize(g->bg[i]));
     GCK(cudaStreamSynchronize(g->stream));
+    return CONV_OK;
+}
+
+int group_reset_impl(conv_group* g) {
+    int rc;
+    if ((rc = sync_all(g))) return rc;
     const GroupPlan& p = g->plan;
     GCK(cudaMemsetAsync(g->X, 0, p.x_bytes, g->stream));
     GCK(cudaMemsetAsync(g->win, 0, (size_t)g->S * g->n_in * g->B * sizeof(float), g->stream));
+    for (int i = 0; i < 2; ++i) {
+        GCK(cudaMemsetAsync(g->partial[i], 0, p.partial_bytes, g->stream));
+        GCK(cudaEventRecord(g->ev_tail[i], g->stream));  // block 0's tail: zero partials
+    }
     GCK(cudaStreamSynchronize(g->stream));
     g->nblk = 0;
     return CONV_OK;
 }
 
-int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, long long taps, int sessions) {
+GroupTiling from_api(const conv_group_tiling* t) {
+    GroupTiling o;
+    if (t) {
+        o.ctas = t->ctas;
+        o.stage_k_steps = t->stage_k_steps;
+        o.stages = t->stages;
+        o.tail_streams = t->tail_streams;
+    }
+    return o;
+}
+
+int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, long long taps, int sessions,
+                const conv_group_tiling* tiling) {
     const int prec = to_prec(precision);
     if (prec < 0) return gset(CONV_E_INVAL, "unknown precision %d", precision);
     GCK(cudaGetDevice(&g->dev));
     cudaDeviceProp prop{};
     GCK(cudaGetDeviceProperties(&prop, g->dev));
     g->num_sms = prop.multiProcessorCount;
-    if (const char* why = plan_group(prec, block, n_in, n_out, taps, sessions, g->num_sms, &g->plan))
+    if (const char* why = plan_group(prec, block, n_in, n_out, taps, sessions, g->num_sms, &g->plan, from_api(tiling)))
         return gset(CONV_E_INVAL, "%s", why);
     if (const char* why = check_group_plan(g->plan)) return gset(CONV_E_INVAL, "%s", why);
     g->prec = precision;
@@ -146,7 +187,7 @@ int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, lo
     g->idesc = (1u << 4) | (t << 7) | (t << 10) | ((uint32_t)(p.N >> 3) << 17) | ((128u >> 4) << 24);
     size_t free_b = 0, total_b = 0;
     GCK(cudaMemGetInfo(&free_b, &total_b));
-    const size_t need = p.h_bytes + p.x_bytes + p.partial_bytes + (size_t)p.NG * 128 * sizeof(float) +
+    const size_t need = p.h_bytes + p.x_bytes + 2 * p.partial_bytes + (size_t)p.NG * 128 * sizeof(float) +
                         (size_t)sessions * (n_in + n_out) * block * sizeof(float) * 2;
     if (need + (64ull << 20) > free_b)
         return gset(CONV_E_NOMEM, "device footprint %zu bytes does not fit in %zu free bytes", need, free_b);
@@ -156,7 +197,8 @@ int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, lo
     if ((rc = galloc(g, &g->X, p.x_bytes))) return rc;
     if ((rc = galloc(g, &g->sH, (size_t)p.NG * 128 * sizeof(float)))) return rc;
     if ((rc = galloc(g, &g->win, (size_t)sessions * n_in * block * sizeof(float)))) return rc;
-    if ((rc = galloc(g, &g->partial, p.partial_bytes))) return rc;
+    if ((rc = galloc(g, &g->partial[0], p.partial_bytes))) return rc;
+    if ((rc = galloc(g, &g->partial[1], p.partial_bytes))) return rc;
     if ((rc = galloc(g, &g->tw, 2 * (size_t)block * sizeof(float2)))) return rc;
     if ((rc = galloc(g, &g->d_in, (size_t)sessions * n_in * block * sizeof(float)))) return rc;
     if ((rc = galloc(g, &g->d_out, (size_t)sessions * n_out * block * sizeof(float)))) return rc;
@@ -170,6 +212,11 @@ int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, lo
     int lo = 0, hi = 0;
     GCK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     GCK(cudaStreamCreateWithPriority(&g->stream, cudaStreamNonBlocking, hi));
+    for (int i = 0; i < 2; ++i) {
+        GCK(cudaStreamCreateWithPriority(&g->bg[i], cudaStreamNonBlocking, lo));
+        GCK(cudaEventCreateWithFlags(&g->ev_tail[i], cudaEventDisableTiming));
+    }
+    GCK(cudaEventCreateWithFlags(&g->ev_packed, cudaEventDisableTiming));
     GCK(cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming));
     // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once
     std::vector<float2> tw(2 * (size_t)block);
@@ -184,10 +231,56 @@ int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, lo
     return group_reset_impl(g);
 }
 
+inline int slot0_of(long long n, int KR) {
+    const int m = (int)(n % KR);
+    return m == 0 ? 0 : KR - m;  // slot of partition 0 at block n: (0 - n) mod KR
+}
+
+// Tail MAC of block `blk` (K-steps 1..NKS-1) into the partials of its parity.
+int enqueue_tail(conv_group* g, long long blk, cudaStream_t s) {
+    const GroupPlan& p = g->plan;
+    if (p.C == 0) return CONV_OK;
+    GroupMacArgs a{};
+    a.H = g->H;
+    a.X = g->X;
+    a.sH = g->sH;
+    a.partial = g->partial[blk & 1];
+    a.B = g->B;
+    a.n_dst = g->n_out;
+    a.S = g->S;
+    a.G = p.G;
+    a.NG = p.NG;
+    a.D = p.D;
+    a.KP = p.KP;
+    a.KR = p.KR;
+    a.NKS = p.NKS;
+    a.N = p.N;
+    a.RB = p.RB;
+    a.T = p.T;
+    a.C = p.C;
+    a.SP = p.SP;
+    a.nbuf = p.nbuf;
+    a.NK = p.NK;
+    a.nstage = p.nstage;
+    a.stage_bytes = p.stage_bytes;
+    a.slot0 = slot0_of(blk, p.KR);
+    a.tmem_cols = p.tmem_cols;
+    a.idesc = g->idesc;
+    a.err = g->d_err;
+    const bool rec = g->prof && g->ev_used < g->ev0.size();
+    if (rec) GCK(cudaEventRecord(g->ev0[g->ev_used], s));
+    GCK(launch_group_mac(p, a, s));
+    if (rec) {
+        GCK(cudaEventRecord(g->ev1[g->ev_used], s));
+        ++g->ev_used;
+    }
+    return CONV_OK;
+}
+
 int enqueue_group(conv_group* g, const float* d_in, float* d_out, cudaStream_t s) {
     const GroupPlan& p = g->plan;
-    const int m = (int)(g->nblk % p.KR);
-    const int slot0 = m == 0 ? 0 : p.KR - m;  // slot of partition 0: (0 - n) mod KR
+    const long long n = g->nblk;
+    const int slot0 = slot0_of(n, p.KR);
     const int prec = to_prec(g->prec);
     GroupPackArgs pk{};
     pk.in = d_in;
@@ -204,46 +297,36 @@ int enqueue_group(conv_group* g, const float* d_in, float* d_out, cudaStream_t s
     pk.slot = slot0;
     pk.tw = g->tw;
     GCK(launch_group_pack(prec, pk, s));
-    GroupMacArgs a{};
-    a.H = g->H;
-    a.X = g->X;
-    a.sH = g->sH;
-    a.partial = g->partial;
-    a.B = g->B;
-    a.n_dst = g->n_out;
-    a.S = g->S;
-    a.G = p.G;
-    a.NG = p.NG;
-    a.D = p.D;
-    a.KP = p.KP;
-    a.KR = p.KR;
-    a.NKS = p.NKS;
-    a.N = p.N;
-    a.RB = p.RB;
-    a.SP = p.SP;
-    a.NK = p.NK;
-    a.nstage = p.nstage;
-    a.stage_bytes = p.stage_bytes;
-    a.slot0 = slot0;
-    a.tmem_cols = p.tmem_cols;
-    a.idesc = g->idesc;
-    a.err = g->d_err;
-    const bool rec = g->prof && g->ev_used < g->ev0.size();
-    if (rec) GCK(cudaEventRecord(g->ev0[g->ev_used], s));
-    GCK(launch_group_mac(p, a, s));
-    if (rec) {
-        GCK(cudaEventRecord(g->ev1[g->ev_used], s));
-        ++g->ev_used;
-    }
+    GCK(cudaEventRecord(g->ev_packed, s));
+    GCK(cudaStreamWaitEvent(s, g->ev_tail[n & 1], 0));
     GroupOutArgs o{};
-    o.partial = g->partial;
+    o.partial = g->partial[n & 1];
     o.out = d_out;
     o.B = g->B;
     o.log2B = g->log2B;
     o.n_dst = g->n_out;
+    o.T = p.T;
+    o.C = p.C;
     o.SP = p.SP;
     o.tw = g->tw;
-    GCK(launch_group_out(o, g->S, s));
+    o.H = g->H;
+    o.X = g->X;
+    o.sH = g->sH;
+    o.G = p.G;
+    o.D = p.D;
+    o.KR = p.KR;
+    o.NKS = p.NKS;
+    o.RB = p.RB;
+    o.S = g->S;
+    o.slot0 = slot0;
+    GCK(launch_group_out(prec, o, s));
+    cudaStream_t bg = g->bg[p.tail_streams == 2 ? (n + 1) & 1 : 0];
+    GCK(cudaStreamWaitEvent(bg, g->ev_packed, 0));
+    // kernel timing needs each tail alone on the GPU: then tails run one after another
+    if (g->prof) GCK(cudaStreamWaitEvent(bg, g->ev_tail[n & 1], 0));
+    int rc = enqueue_tail(g, n + 1, bg);
+    if (rc) return rc;
+    GCK(cudaEventRecord(g->ev_tail[(n + 1) & 1], bg));
     ++g->nblk;
     return CONV_OK;
 }
@@ -262,12 +345,17 @@ int check_err(conv_group* g) {
 extern "C" {
 
 conv_group* conv_group_create(int precision, int block, int n_in, int n_out, long long taps, int sessions) {
+    return conv_group_create_tiled(precision, block, n_in, n_out, taps, sessions, nullptr);
+}
+
+conv_group* conv_group_create_tiled(int precision, int block, int n_in, int n_out, long long taps, int sessions,
+                                    const conv_group_tiling* tiling) {
     conv_group* g = new (std::nothrow) conv_group();
     if (!g) {
         gset(CONV_E_NOMEM, "out of host memory");
         return nullptr;
     }
-    if (create_impl(g, precision, block, n_in, n_out, taps, sessions) != CONV_OK) {
+    if (create_impl(g, precision, block, n_in, n_out, taps, sessions, tiling) != CONV_OK) {
         const std::string msg = conv_last_error();
         group_free(g);
         set_last_error_message(msg.c_str());
@@ -343,7 +431,7 @@ int conv_group_process(conv_group* g, const float* in, float* out) {
     if (rc) return rc;
     GCK(cudaMemcpyAsync(g->h_out, g->d_out, ob, cudaMemcpyDeviceToHost, g->stream));
     GCK(cudaEventRecord(g->ev_done, g->stream));
-    GCK(cudaEventSynchronize(g->ev_done));
+    GCK(cudaEventSynchronize(g->ev_done));  // the next block's tail keeps running
     if ((rc = check_err(g))) return rc;
     std::memcpy(out, g->h_out, ob);
     return CONV_OK;
@@ -358,7 +446,8 @@ int conv_group_reset(conv_group* g) {
 int conv_group_synchronize(conv_group* g) {
     if (!g) return gset(CONV_E_INVAL, "null handle");
     GDev d(g->dev);
-    GCK(cudaStreamSynchronize(g->stream));
+    int rc;
+    if ((rc = sync_all(g))) return rc;
     GCK(cudaDeviceSynchronize());
     return check_err(g);
 }
@@ -378,24 +467,29 @@ int conv_group_get_info(const conv_group* g, conv_group_info* out) {
     out->bins_per_group = p.G;
     out->groups = p.NG;
     out->splits = p.SP;
+    out->tail_ctas = p.C;
+    out->acc_buffers = p.nbuf;
     out->k_steps = p.NKS;
     out->stage_k_steps = p.NK;
     out->stages = p.nstage;
-    out->mac_ctas = p.ctas;
+    out->mac_ctas = p.C;
     out->mac_smem = p.smem;
     out->tmem_cols = p.tmem_cols;
-    // every filter tile and every delay-line slot of every session read once
-    out->mac_bytes = (long long)(g->n_out + g->S) * g->n_in * (long long)p.KR * g->B * 4;
+    // tail launch: every filter tile and every delay-line slot of every
+    // session of K-steps 1..NKS-1, read once
+    out->mac_bytes = (long long)(g->n_out + g->S) * g->n_in * (long long)(p.KR - p.KP) * g->B * 4;
     out->device_bytes = (long long)g->dev_bytes;
     out->kernels_per_block = 3;
+    out->tail_streams = p.tail_streams;
     return CONV_OK;
 }
 
-int conv_group_plan_check(int precision, int block, int n_in, int n_out, long long taps, int sessions, int num_sms) {
+int conv_group_plan_check(int precision, int block, int n_in, int n_out, long long taps, int sessions, int num_sms,
+                          const conv_group_tiling* tiling) {
     const int prec = to_prec(precision);
     if (prec < 0) return gset(CONV_E_INVAL, "unknown precision %d", precision);
     GroupPlan p{};
-    if (const char* why = plan_group(prec, block, n_in, n_out, taps, sessions, num_sms, &p))
+    if (const char* why = plan_group(prec, block, n_in, n_out, taps, sessions, num_sms, &p, from_api(tiling)))
         return gset(CONV_E_INVAL, "%s", why);
     if (const char* why = check_group_plan(p)) return gset(CONV_E_INVAL, "%s", why);
     return CONV_OK;
@@ -422,7 +516,8 @@ int conv_group_profile_enable(conv_group* g, int enable) {
 int conv_group_profile_read(conv_group* g, double* total_ms, long long* launches) {
     if (!g || !total_ms || !launches) return gset(CONV_E_INVAL, "null argument");
     GDev d(g->dev);
-    GCK(cudaStreamSynchronize(g->stream));
+    int rc;
+    if ((rc = sync_all(g))) return rc;
     double tot = 0.0;
     for (size_t i = 0; i < g->ev_used; ++i) {
         float ms = 0.0f;

@@ -96,12 +96,16 @@ class conv_group_info(ctypes.Structure):
         for name in (
             "block", "n_in", "n_out", "taps", "sessions", "precision", "K", "ring_slots", "bins_per_group", "groups",
             "splits", "k_steps", "stage_k_steps", "stages", "mac_ctas", "mac_smem", "tmem_cols", "mac_bytes",
-            "device_bytes", "kernels_per_block",
+            "device_bytes", "kernels_per_block", "tail_streams", "tail_ctas", "acc_buffers",
         )
     ]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class conv_group_tiling(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("ctas", "stage_k_steps", "stages", "tail_streams")]
 
 
 _lib = None
@@ -155,13 +159,14 @@ def load():
         "conv_batch_step_bytes": (ll, [vp]),
         "conv_batch_destroy": (None, [vp]),
         "conv_group_create": (vp, [i, i, i, i, ll, i]),
+        "conv_group_create_tiled": (vp, [i, i, i, i, ll, i, ctypes.POINTER(conv_group_tiling)]),
         "conv_group_set_filters": (i, [vp, vp]),
         "conv_group_process_async": (i, [vp, vp, vp, vp]),
         "conv_group_process": (i, [vp, vp, vp]),
         "conv_group_reset": (i, [vp]),
         "conv_group_synchronize": (i, [vp]),
         "conv_group_get_info": (i, [vp, ctypes.POINTER(conv_group_info)]),
-        "conv_group_plan_check": (i, [i, i, i, i, ll, i, i]),
+        "conv_group_plan_check": (i, [i, i, i, i, ll, i, i, ctypes.POINTER(conv_group_tiling)]),
         "conv_group_profile_enable": (i, [vp, i]),
         "conv_group_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "conv_group_destroy": (None, [vp]),
@@ -401,6 +406,17 @@ def conv_group_create(precision, block, n_in, n_out, taps, sessions):
     return g
 
 
+def conv_group_create_tiled(precision, block, n_in, n_out, taps, sessions, tiling=None):
+    t = conv_group_tiling(**(tiling or {}))
+    g = load().conv_group_create_tiled(
+        int(PRECISIONS.get(precision, precision)), int(block), int(n_in), int(n_out), int(taps), int(sessions),
+        ctypes.byref(t),
+    )
+    if not g:
+        raise ConvError(CONV_E_INVAL, conv_last_error())
+    return g
+
+
 def conv_group_get_info(g) -> dict:
     info = conv_group_info()
     _check(load().conv_group_get_info(g, ctypes.byref(info)))
@@ -429,11 +445,12 @@ def conv_group_synchronize(g):
     return _check(load().conv_group_synchronize(g))
 
 
-def conv_group_plan_check(precision, block, n_in, n_out, taps, sessions, num_sms=152):
+def conv_group_plan_check(precision, block, n_in, n_out, taps, sessions, num_sms=152, tiling=None):
+    t = conv_group_tiling(**(tiling or {}))
     return _check(
         load().conv_group_plan_check(
             int(PRECISIONS.get(precision, precision)), int(block), int(n_in), int(n_out), int(taps), int(sessions),
-            int(num_sms),
+            int(num_sms), ctypes.byref(t),
         )
     )
 
@@ -515,8 +532,8 @@ class Group:
     """Owning wrapper of a conv_group: ``sessions`` lock-step streams sharing
     one filter set."""
 
-    def __init__(self, precision, block, n_in, n_out, taps, sessions):
-        self.g = conv_group_create(precision, block, n_in, n_out, taps, sessions)
+    def __init__(self, precision, block, n_in, n_out, taps, sessions, tiling=None):
+        self.g = conv_group_create_tiled(precision, block, n_in, n_out, taps, sessions, tiling)
         self.shape = (int(sessions), int(n_in), int(n_out), int(block))
 
     def set_filters(self, h: np.ndarray):

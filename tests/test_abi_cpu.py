@@ -145,6 +145,19 @@ def test_group_plans_replay_clean_over_shapes(lib):
     assert n > 500
 
 
+def test_group_tilings_replay_clean(lib):
+    from paper_2509_04390_gb300 import upols as U
+
+    for tiling in ({"ctas": 1}, {"ctas": 7, "stage_k_steps": 1, "stages": 2}, {"ctas": 37, "stage_k_steps": 2, "stages": 4},
+                   {"ctas": 152, "stage_k_steps": 4, "stages": 2, "tail_streams": 1}, {"ctas": 100000}):
+        for B, taps in ((64, 2500), (256, 384000), (16, 1), (4096, 100000)):
+            U.conv_group_plan_check("fp16", B, 4, 16, taps, 8, 152, tiling)
+    for bad in ({"ctas": -1}, {"stage_k_steps": 5}, {"stages": 1}, {"stages": 9}, {"tail_streams": 3},
+                {"stage_k_steps": 4, "stages": 8}):
+        with pytest.raises(U.ConvError):
+            U.conv_group_plan_check("fp16", 256, 4, 16, 384000, 8, 152, bad)
+
+
 def test_group_rejects_unsupported_shapes_on_the_host(lib):
     from paper_2509_04390_gb300 import upols as U
 

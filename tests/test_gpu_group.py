@@ -60,6 +60,29 @@ def test_group_sessions_against_oracle(precision, S, n_in, n_out, taps, B, nb):
     assert worst >= BOUND[precision]
 
 
+@pytest.mark.parametrize(
+    "tiling",
+    [
+        {"ctas": 1},  # one CTA walks every (group, K-step) unit: many accumulator segments
+        {"ctas": 7, "stage_k_steps": 1, "stages": 2},
+        {"ctas": 37, "stage_k_steps": 3, "stages": 4, "tail_streams": 1},
+        {"ctas": 152, "stage_k_steps": 4, "stages": 2},
+    ],
+)
+def test_group_tilings_against_oracle(tiling):
+    """Work splits whose runs cross bin-group boundaries, shallow and deep
+    pipelines, one or two tail streams: same result bound."""
+    S, n_in, n_out, taps, B, nb = 8, 4, 16, 2500, 64, 45
+    h, x = group_case(300, S, n_in, n_out, taps, B, nb)
+    with U.Group("fp16", B, n_in, n_out, taps, S, tiling) as g:
+        g.set_filters(h)
+        y = g.run(x)
+        info = g.info()
+    worst = min(snr_db(y[s], upols(h, x[s], B)) for s in range(S))
+    print(f"group tiling {tiling}: worst session {worst:.1f} dB, ctas {info['tail_ctas']}, slots {info['splits']}")
+    assert worst >= BOUND["fp16"]
+
+
 def test_sessions_are_independent():
     """Session s's output must not depend on the other sessions' inputs."""
     S, n_in, n_out, taps, B, nb = 8, 4, 16, 2000, 64, 40
