@@ -70,6 +70,9 @@ typedef struct conv_info {
     long long mac_warps;      /* MAC consumer warps                               */
     long long mac_kernel;     /* CONV_KERNEL_TMA / _DIRECT1 / _DIRECT2            */
     long long afc_adaptive;   /* 1 if the canceller adapts (afc_set_adaptation)   */
+    long long far_block;      /* far block of non-uniform partitioning, 0 if none */
+    long long K_far;          /* partitions of the far part                       */
+    long long mac_far_bytes;  /* far tail MAC (once per far block), 0 if none    */
 } conv_info;
 
 /* Create an engine for n_in inputs, n_out outputs and filters of `taps` taps
@@ -121,6 +124,26 @@ int conv_set_tiling(conv_engine* e, const conv_tiling* t);
  * with `block` zeros and takes its 2*block-point R2C FFT on the device (Sec. 4,
  * initialisation).  Copied; the caller keeps ownership.  Resets the stream. */
 int conv_set_filters(conv_engine* e, const float* h);
+
+/* Non-uniform partitioning (an extension: the paper, Sec. 3.2, considers
+ * uniform partitions only).  far_block F (a power of two in (block, 4096])
+ * splits every filter: taps [0, F) stay in this engine's partitions of
+ * `block`; taps [F, taps) go to a second partitioned convolution of block F
+ * that runs once every F / block blocks on the last F input samples.  Its
+ * output over those samples, delayed by F, is added to the next F / block
+ * output blocks.  The result is the same causal convolution (no added
+ * latency).  The filter spectra streamed per output block drop from all
+ * partitions to F + (taps - F) * block / F taps' worth.  0 turns it off.
+ * Must come before conv_set_filters / afc_set_paths (CONV_E_STATE).  taps
+ * must exceed F (CONV_E_INVAL).  Not combined with afc_set_adaptation or
+ * batches (CONV_E_STATE).  With the feedback canceller, the far part filters
+ * the error signal e, like the near part. */
+int conv_set_far_block(conv_engine* e, int far_block);
+
+/* The far part's engine of a non-uniformly partitioned engine (NULL if none).
+ * Owned by `e`; use it only with conv_get_info and conv_profile_enable /
+ * conv_profile_read (timing of the far tail MAC). */
+conv_engine* conv_far_engine(conv_engine* e);
 
 /* Set the a-priori feedback-path estimates F_hat (Sec. 3.1, Eq. 3): host array
  * f[n_in][n_out][taps_fb] float32 (f[p][l] is loudspeaker l -> microphone p).

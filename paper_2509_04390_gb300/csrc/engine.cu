@@ -412,6 +412,16 @@ struct conv_engine {
     float2* d_pow = nullptr;     // [2][B] packed power estimates, by block parity
     float2* d_G = nullptr;       // [n_in][B] step-scaled error spectra
     int in_batches = 0;          // batches holding this session
+    // non-uniform partitioning (conv_set_far_block): taps [0, far_B) in this
+    // engine's own partitions of `block`, taps [far_B, taps) in a nested engine
+    // of block far_B driven once every far_B / block blocks
+    conv_engine* far = nullptr;
+    int far_B = 0;
+    long long taps_total = 0;
+    float* d_acc = nullptr;             // [n_in][far_B] input of the far engine's next block
+    float* d_far_out[2] = {nullptr, nullptr};  // [n_out][far_B] far outputs, by far-block parity
+    const float* addend = nullptr;      // added by this block's output kernel, or null
+    int addend_stride = 0;
 };
 
 namespace {
@@ -638,6 +648,10 @@ OutArgs out_args(conv_engine* e, Part& P, long long blk, float* out) {
     a.LT = p.LT;
     a.slot0 = slot0_for(blk, P.K);
     a.tile_elems = p.tile_elems;
+    if (&P == &e->syn && e->addend) {
+        a.extra = e->addend;
+        a.extra_stride = e->addend_stride;
+    }
     return a;
 }
 
@@ -688,6 +702,10 @@ int enqueue_conv(conv_engine* e, Part& P, const float* src, const float* sub, fl
 }
 
 int check_dev_err(conv_engine* e) {
+    if (e->far) {
+        const int rc = check_dev_err(e->far);
+        if (rc) return rc;
+    }
     const int v = *(volatile int*)e->h_err;
     if (v != DEVERR_NONE) {
         *(volatile int*)e->h_err = DEVERR_NONE;
@@ -706,13 +724,52 @@ int engine_reset(conv_engine* e) {
     if ((rc = part_reset(e, e->fb))) return rc;
     if (e->d_c) CK(cudaMemsetAsync(e->d_c, 0, (size_t)e->n_in * e->B * sizeof(float), e->stream));
     if (e->d_pow) CK(cudaMemsetAsync(e->d_pow, 0, 2 * (size_t)e->B * sizeof(float2), e->stream));
+    if (e->far) {
+        if ((rc = engine_reset(e->far))) return rc;
+        CK(cudaMemsetAsync(e->d_acc, 0, (size_t)e->n_in * e->far_B * sizeof(float), e->stream));
+        for (int i = 0; i < 2; ++i)
+            CK(cudaMemsetAsync(e->d_far_out[i], 0, (size_t)e->n_out * e->far_B * sizeof(float), e->stream));
+    }
     CK(cudaStreamSynchronize(e->stream));
     e->nblk = 0;
     return CONV_OK;
 }
 
+int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t s);
+
+// Non-uniform partitioning around block n of the near part.  Far block k
+// (input samples [k F, (k+1) F), F = far block) convolved with h[F:] lands on
+// samples [(k+1) F, (k+2) F), i.e. on near blocks (k+1) m .. (k+2) m - 1
+// (m = F / B): near block n adds slice n mod m of far block n / m - 1, which
+// the far engine finished at the end of near block (n / m) m - 1.  Then this
+// block's input (the error signal when the canceller runs) is appended to the
+// far engine's next input, and after the m-th block the far engine runs.
+void far_before(conv_engine* e) {
+    if (!e->far) return;
+    const int m = e->far_B / e->B;
+    const long long k = e->nblk / m;
+    const int j = (int)(e->nblk % m);
+    e->addend = e->d_far_out[(k + 1) & 1] + (size_t)j * e->B;  // far block k - 1 (zeros before the first)
+    e->addend_stride = e->far_B;
+}
+
+int far_after(conv_engine* e, const float* src, cudaStream_t s) {
+    if (!e->far) return CONV_OK;
+    e->addend = nullptr;
+    const int m = e->far_B / e->B;
+    const long long k = e->nblk / m;
+    const int j = (int)(e->nblk % m);
+    CK(cudaMemcpy2DAsync(e->d_acc + (size_t)j * e->B, (size_t)e->far_B * sizeof(float), src,
+                         (size_t)e->B * sizeof(float), (size_t)e->B * sizeof(float), (size_t)e->n_in,
+                         cudaMemcpyDeviceToDevice, s));
+    if (j == m - 1) return enqueue_block(e->far, e->d_acc, e->d_far_out[k & 1], s);
+    return CONV_OK;
+}
+
 int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t s) {
+    far_before(e);
     int rc = enqueue_conv(e, e->syn, d_in, nullptr, nullptr, d_out, s, true);
+    if (!rc) rc = far_after(e, d_in, s);
     if (rc) return rc;
     ++e->nblk;
     return CONV_OK;
@@ -773,7 +830,13 @@ int enqueue_adapt(conv_engine* e, const float* d_err_block, cudaStream_t s) {
 // (first half), then c = F_hat * l, kept for the next block (second half).
 // The host-buffer call copies l and e out between the halves.
 int enqueue_afc_synthesis(conv_engine* e, const float* d_mic, float* d_out, float* d_e, cudaStream_t s) {
-    if (!e->adapt) return enqueue_conv(e, e->syn, d_mic, e->d_c, d_e, d_out, s, true);
+    if (!e->adapt) {
+        float* eb = (d_e || !e->far) ? d_e : e->d_e;  // the far engine's input is the error signal
+        far_before(e);
+        int rc = enqueue_conv(e, e->syn, d_mic, e->d_c, eb, d_out, s, true);
+        if (!rc) rc = far_after(e, eb, s);
+        return rc;
+    }
     float* eb = d_e ? d_e : e->d_e;
     Part& P = e->syn;
     const long long n = e->nblk;
@@ -813,6 +876,13 @@ int enqueue_afc_prediction(conv_engine* e, const float* d_out, cudaStream_t s) {
 void engine_free(conv_engine* e) {
     if (!e) return;
     DeviceGuard g(e->dev);
+    if (e->far) {
+        engine_free(e->far);
+        e->far = nullptr;
+    }
+    dev_free(e, &e->d_acc, 0);
+    dev_free(e, &e->d_far_out[0], 0);
+    dev_free(e, &e->d_far_out[1], 0);
     if (e->stream) cudaStreamSynchronize(e->stream);
     for (int i = 0; i < 2; ++i)
         if (e->bg[i]) cudaStreamSynchronize(e->bg[i]);
@@ -859,6 +929,7 @@ int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long 
     e->n_in = n_in;
     e->n_out = n_out;
     e->taps = taps;
+    e->taps_total = taps;
     CK(cudaGetDevice(&e->dev));
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, e->dev));
@@ -921,8 +992,10 @@ int conv_set_precision(conv_engine* e, int mode) {
         return set_err(CONV_E_STATE, "precision must be set before conv_set_filters / afc_set_paths");
     if (mode == e->prec) return CONV_OK;
     DeviceGuard g(e->dev);
+    int rc;
+    if (e->far && (rc = conv_set_precision(e->far, mode))) return rc;
     e->prec = mode;
-    int rc = part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling);
+    rc = part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling);
     if (rc) return rc;
     return engine_reset(e);
 }
@@ -950,10 +1023,67 @@ int conv_set_tiling(conv_engine* e, const conv_tiling* t) {
 int conv_set_filters(conv_engine* e, const float* h) {
     if (!e || !h) return set_err(CONV_E_INVAL, "null argument");
     DeviceGuard g(e->dev);
-    int rc = part_set_filters(e, e->syn, h);
-    if (rc) return rc;
+    int rc;
+    if (!e->far) {
+        if ((rc = part_set_filters(e, e->syn, h))) return rc;
+        return engine_reset(e);
+    }
+    // h[l][q][0 .. far_B) to this engine, h[l][q][far_B .. taps) to the far engine
+    const size_t pairs = (size_t)e->n_out * e->n_in, T = (size_t)e->taps_total, F = (size_t)e->far_B;
+    std::vector<float> near(pairs * F), farh(pairs * (T - F));
+    for (size_t i = 0; i < pairs; ++i) {
+        std::memcpy(near.data() + i * F, h + i * T, F * sizeof(float));
+        std::memcpy(farh.data() + i * (T - F), h + i * T + F, (T - F) * sizeof(float));
+    }
+    if ((rc = part_set_filters(e, e->syn, near.data()))) return rc;
+    if ((rc = conv_set_filters(e->far, farh.data()))) return rc;
     return engine_reset(e);
 }
+
+int conv_set_far_block(conv_engine* e, int far_block) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    if (e->syn.ready || e->fb.allocated)
+        return set_err(CONV_E_STATE, "the far block must be set before conv_set_filters / afc_set_paths");
+    if (e->in_batches > 0) return set_err(CONV_E_STATE, "session is in a batch");
+    if (far_block != 0) {
+        if (far_block <= e->B || far_block > 4096 || (far_block & (far_block - 1)))
+            return set_err(CONV_E_INVAL, "far block %d must be 0 or a power of two in (block, 4096]", far_block);
+        if (e->taps_total <= far_block)
+            return set_err(CONV_E_INVAL, "taps %lld must exceed the far block %d", e->taps_total, far_block);
+    }
+    DeviceGuard g(e->dev);
+    if (e->far) {
+        engine_free(e->far);
+        e->far = nullptr;
+    }
+    dev_free(e, &e->d_acc, (size_t)e->n_in * e->far_B * sizeof(float));
+    for (int i = 0; i < 2; ++i) dev_free(e, &e->d_far_out[i], (size_t)e->n_out * e->far_B * sizeof(float));
+    e->far_B = 0;
+    e->taps = e->taps_total;
+    int rc;
+    if (far_block != 0) {
+        conv_engine* f = new (std::nothrow) conv_engine();
+        if (!f) return set_err(CONV_E_NOMEM, "out of host memory");
+        if ((rc = create_impl(f, e->fs, far_block, e->n_in, e->n_out, e->taps_total - far_block)) ||
+            (rc = conv_set_precision(f, e->prec))) {
+            const std::string msg = g_err;
+            engine_free(f);
+            g_err = msg;
+            part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling);
+            return rc;
+        }
+        e->far = f;
+        e->far_B = far_block;
+        e->taps = far_block;
+        if ((rc = dev_alloc(e, &e->d_acc, (size_t)e->n_in * far_block * sizeof(float)))) return rc;
+        for (int i = 0; i < 2; ++i)
+            if ((rc = dev_alloc(e, &e->d_far_out[i], (size_t)e->n_out * far_block * sizeof(float)))) return rc;
+    }
+    if ((rc = part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling))) return rc;
+    return engine_reset(e);
+}
+
+conv_engine* conv_far_engine(conv_engine* e) { return e ? e->far : nullptr; }
 
 int afc_set_paths(conv_engine* e, const float* f, long long taps_fb) {
     if (!e || !f) return set_err(CONV_E_INVAL, "null argument");
@@ -1049,6 +1179,7 @@ int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta) {
     if (mu > 0.0 && !(delta > 0.0)) return set_err(CONV_E_INVAL, "delta must be > 0 when mu > 0");
     if (!e->fb.ready) return set_err(CONV_E_STATE, "feedback paths not set");
     if (e->prec != CONV_FP32) return set_err(CONV_E_STATE, "the adaptive canceller needs FP32 spectra");
+    if (e->far) return set_err(CONV_E_STATE, "the adaptive canceller is not combined with a far block");
     if (e->in_batches > 0) return set_err(CONV_E_STATE, "session is in a batch");
     DeviceGuard g(e->dev);
     int rc;
@@ -1120,6 +1251,10 @@ int conv_reset(conv_engine* e) {
 int conv_synchronize(conv_engine* e) {
     if (!e) return set_err(CONV_E_INVAL, "null handle");
     DeviceGuard g(e->dev);
+    if (e->far) {
+        const int rc = conv_synchronize(e->far);
+        if (rc) return rc;
+    }
     CK(cudaStreamSynchronize(e->bg[0]));
     CK(cudaStreamSynchronize(e->bg[1]));
     if (e->as) CK(cudaStreamSynchronize(e->as));
@@ -1135,7 +1270,7 @@ int conv_get_info(const conv_engine* e, conv_info* out) {
     out->block = e->B;
     out->n_in = e->n_in;
     out->n_out = e->n_out;
-    out->taps = e->taps;
+    out->taps = e->taps_total;
     out->K = e->syn.K;
     out->taps_fb = e->fb.allocated ? e->fb.taps : 0;
     out->K_fb = e->fb.allocated ? e->fb.K : 0;
@@ -1160,6 +1295,9 @@ int conv_get_info(const conv_engine* e, conv_info* out) {
     out->kernels_per_block = 3;
     out->kernels_per_afc_block = e->adapt ? 8 : 6;
     out->afc_adaptive = e->adapt ? 1 : 0;
+    out->far_block = e->far_B;
+    out->K_far = e->far ? e->far->syn.K : 0;
+    out->mac_far_bytes = e->far ? tail_bytes(e->far->syn.plan) : 0;
     return CONV_OK;
 }
 
@@ -1331,6 +1469,7 @@ int conv_batch_add(conv_batch* b, conv_engine* e) {
     if (e->syn.plan.direct || e->syn.plan.nw != 8 || (e->fb.allocated && (e->fb.plan.direct || e->fb.plan.nw != 8)))
         return set_err(CONV_E_INVAL, "batched sessions use the TMA MAC with 8 consumer warps");
     if (e->adapt) return set_err(CONV_E_STATE, "sessions with an adaptive canceller are not batched");
+    if (e->far) return set_err(CONV_E_STATE, "sessions with a far block are not batched");
     for (conv_engine* x : b->sessions)
         if (x == e) return set_err(CONV_E_INVAL, "session already in the batch");
     DeviceGuard g(b->dev);

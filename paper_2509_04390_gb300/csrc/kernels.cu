@@ -704,9 +704,11 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
     const float2* z = fft_smem<true>(W, P, B, a.log2B, tws, a.log2B + 1, tid, nth);
     const float invB = 1.0f / (float)B;
     float* out = a.out + (size_t)l * a.out_stride;
+    const float* extra = a.extra ? a.extra + (size_t)l * a.extra_stride : nullptr;
     for (int t = tid; t < B; t += nth) {
         const int u = B + t, n = u >> 1;
-        out[t] = ((u & 1) ? z[n].y : z[n].x) * invB;
+        const float v = ((u & 1) ? z[n].y : z[n].x) * invB;
+        out[t] = extra ? v + extra[t] : v;
     }
 }
 

@@ -119,6 +119,9 @@ struct OutArgs {
     const float* sX;
     int n_src, K, R, BT, LT, slot0;
     size_t tile_elems;
+    // added to the output after the overlap-save discard ([n_dst][extra_stride]), or null
+    const float* extra;
+    int extra_stride;
 };
 
 // One CTA of a batched launch: which session's arguments (items[item]), and

@@ -83,6 +83,9 @@ class conv_info(ctypes.Structure):
             "mac_warps",
             "mac_kernel",
             "afc_adaptive",
+            "far_block",
+            "K_far",
+            "mac_far_bytes",
         )
     ]
 
@@ -140,6 +143,8 @@ def load():
         "afc_process_block_async": (i, [vp, vp, vp, vp, vp]),
         "afc_set_guard": (i, [vp, d]),
         "afc_set_adaptation": (i, [vp, d, d, d]),
+        "conv_set_far_block": (i, [vp, i]),
+        "conv_far_engine": (vp, [vp]),
         "afc_get_path_spectra": (i, [vp, vp]),
         "conv_reset": (i, [vp]),
         "conv_synchronize": (i, [vp]),
@@ -235,6 +240,15 @@ def conv_create(fs: float, block: int, n_in: int, n_out: int, taps: int):
 def conv_set_precision(h, mode):
     mode = PRECISIONS.get(mode, mode)
     return _check(load().conv_set_precision(h, int(mode)))
+
+
+def conv_set_far_block(h, far_block: int):
+    return _check(load().conv_set_far_block(h, int(far_block)))
+
+
+def conv_far_engine(h):
+    """Handle of the far part's engine (owned by h; for conv_get_info and profiling), or None."""
+    return load().conv_far_engine(h) or None
 
 
 def conv_set_tiling(h, kernel=0, bin_tile=0, stages=0, stage_kib=0, splits=0, warps=0, order=0):
@@ -587,7 +601,7 @@ class Group:
 class Engine:
     """Owning wrapper: ``with Engine(fs, block, n_in, n_out, taps) as e: ...``."""
 
-    def __init__(self, fs, block, n_in, n_out, taps, precision="fp32", tiling=None):
+    def __init__(self, fs, block, n_in, n_out, taps, precision="fp32", tiling=None, far_block=0):
         self.h = conv_create(fs, block, n_in, n_out, taps)
         self.shape = (int(n_in), int(n_out), int(block))
         try:
@@ -595,6 +609,8 @@ class Engine:
                 conv_set_precision(self.h, precision)
             if tiling:
                 conv_set_tiling(self.h, **tiling)
+            if far_block:
+                conv_set_far_block(self.h, far_block)
         except Exception:
             conv_destroy(self.h)
             raise
