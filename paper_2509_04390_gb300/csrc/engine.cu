@@ -422,6 +422,7 @@ struct conv_engine {
     float* d_far_out[2] = {nullptr, nullptr};  // [n_out][far_B] far outputs, by far-block parity
     const float* addend = nullptr;      // added by this block's output kernel, or null
     int addend_stride = 0;
+    int e_stride = 0;                   // row pitch of the pack's e_out for this block (0: block)
 };
 
 namespace {
@@ -578,6 +579,7 @@ PackArgs pack_args(conv_engine* e, Part& P, long long blk, const float* src, int
     a.in_stride = stride;
     a.sub = sub;
     a.e_out = e_out;
+    a.e_stride = e_out && &P == &e->syn ? e->e_stride : 0;
     a.win = P.win;
     a.X = P.X;
     a.sX = P.sX;
@@ -759,17 +761,24 @@ int far_after(conv_engine* e, const float* src, cudaStream_t s) {
     const int m = e->far_B / e->B;
     const long long k = e->nblk / m;
     const int j = (int)(e->nblk % m);
-    CK(cudaMemcpy2DAsync(e->d_acc + (size_t)j * e->B, (size_t)e->far_B * sizeof(float), src,
-                         (size_t)e->B * sizeof(float), (size_t)e->B * sizeof(float), (size_t)e->n_in,
-                         cudaMemcpyDeviceToDevice, s));
+    if (src)  // else the pack wrote the block into the far input already
+        CK(cudaMemcpy2DAsync(e->d_acc + (size_t)j * e->B, (size_t)e->far_B * sizeof(float), src,
+                             (size_t)e->B * sizeof(float), (size_t)e->B * sizeof(float), (size_t)e->n_in,
+                             cudaMemcpyDeviceToDevice, s));
     if (j == m - 1) return enqueue_block(e->far, e->d_acc, e->d_far_out[k & 1], s);
     return CONV_OK;
 }
 
 int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t s) {
     far_before(e);
-    int rc = enqueue_conv(e, e->syn, d_in, nullptr, nullptr, d_out, s, true);
-    if (!rc) rc = far_after(e, d_in, s);
+    float* acc = nullptr;
+    if (e->far) {  // the pack appends the input block to the far engine's next input directly
+        acc = e->d_acc + (size_t)(e->nblk % (e->far_B / e->B)) * e->B;
+        e->e_stride = e->far_B;
+    }
+    int rc = enqueue_conv(e, e->syn, d_in, nullptr, acc, d_out, s, true);
+    e->e_stride = 0;
+    if (!rc) rc = far_after(e, nullptr, s);
     if (rc) return rc;
     ++e->nblk;
     return CONV_OK;

@@ -119,10 +119,11 @@ __device__ __forceinline__ void pack_body(const PackArgs& a, const int c) {
         bufA[n] = z;
     }
     __syncthreads();
+    float* e_out = a.e_out ? a.e_out + (size_t)c * (a.e_stride ? a.e_stride : B) : nullptr;
     for (int t = tid; t < B; t += nth) {
         const float v = sub ? in[t] - sub[t] : in[t];
         win[t] = v;
-        if (a.e_out) a.e_out[(size_t)c * B + t] = v;
+        if (e_out) e_out[t] = v;
     }
     float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, tws, a.log2B + 1, tid, nth);
     float2* Xs = (Z == bufA) ? bufB : bufA;

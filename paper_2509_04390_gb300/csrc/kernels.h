@@ -85,7 +85,8 @@ struct PackArgs {
     const float* in;  // [n_ch][in_stride], first B samples of each row used
     int in_stride;
     const float* sub;  // [n_ch][B] subtracted from `in` (feedback prediction), or null
-    float* e_out;      // [n_ch][B] receives in - sub, or null
+    float* e_out;      // [n_ch][e_stride] receives in - sub, or null
+    int e_stride;      // row pitch of e_out (0: B)
     float* win;        // [n_ch][B] previous block (sliding-window state)
     void* X;           // FDL ring [n_kt][K][n_ch][BT] (storage type)
     float* sX;         // [K][n_ch] slot scales (reduced precision), else null
