@@ -339,8 +339,10 @@ void conv_batch_destroy(conv_batch* b);
  * an extension beyond the paper, which runs one stream per engine.
  *
  * Limits (else CONV_E_INVAL): precision CONV_FP16 or CONV_BF16; n_out in
- * {8, 16, 32}; n_in in {1, 2, 4, 8}; sessions a multiple of 8 with
- * sessions * 128 / n_out <= 128; block a power of two in [16, 4096].
+ * {8, 16, 32}; n_in in {1, 2, 4, 8}; sessions 1, 2, 4 or a multiple of 8,
+ * with sessions * 128 / n_out in [8, 128]; block a power of two in
+ * [16, 4096].  A group of one session is a single stream whose MAC runs on
+ * the tensor cores.
  * Filter spectra carry a power-of-two scale per (bin, output); the delay line
  * is stored unscaled, so FP16 groups saturate input spectra above 65504
  * (inputs with |x| <= 1 never reach it: |X| <= 2 * block).  Output block n of

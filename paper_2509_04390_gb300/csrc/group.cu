@@ -319,27 +319,27 @@ __global__ void __launch_bounds__(GRP_THREADS, 1) k_group_mac(const GroupMacArgs
             const int k = g * a.G + mb;
             const float scale = __ldg(a.sH + (size_t)g * 128 + row);
             const uint32_t dl = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 2 * a.N);
-            for (int ch = 0; ch < bq; ++ch) {
-                const int bin = b_lo + ch;
-                for (int sc = 0; sc < a.S; sc += 8) {
-                    float d1r[8], d1i[8], d2r[8], d2i[8];
-                    if (ok) {
-                        const uint32_t c_re = (uint32_t)(bin * a.S + sc), c_im = (uint32_t)(GS + bin * a.S + sc);
-                        tmem_ld8(dl + c_re, d1r);
-                        tmem_ld8(dl + c_im, d1i);
-                        tmem_ld8(dl + (uint32_t)a.N + c_re, d2r);
-                        tmem_ld8(dl + (uint32_t)a.N + c_im, d2i);
-                    }
-                    if (mb != bin) continue;
+            // the quadrant's bins own columns [b_lo S, (b_lo + bq) S) of each part; read them
+            // in aligned runs of 8 and let each lane keep the columns of its own bin
+            const int c_lo = (b_lo * a.S) & ~7, c_hi = ((b_lo + bq) * a.S + 7) & ~7;
+            for (int c = c_lo; c < c_hi; c += 8) {
+                float d1r[8], d1i[8], d2r[8], d2i[8];
+                if (ok) {
+                    tmem_ld8(dl + (uint32_t)c, d1r);
+                    tmem_ld8(dl + (uint32_t)(GS + c), d1i);
+                    tmem_ld8(dl + (uint32_t)(a.N + c), d2r);
+                    tmem_ld8(dl + (uint32_t)(a.N + GS + c), d2i);
+                }
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        float2 y = make_float2(0.0f, 0.0f);
-                        if (ok) {
-                            y = k == 0 ? make_float2(d1r[e], d2i[e]) : make_float2(d1r[e] - d2i[e], d1i[e] + d2r[e]);
-                            y = cscale(y, scale);
-                        }
-                        a.partial[(((size_t)(sc + e) * a.SP + j) * a.n_dst + l) * a.B + k] = y;
+                for (int e = 0; e < 8; ++e) {
+                    const int col = c + e, bin = col / a.S, sess = col - bin * a.S;
+                    if (bin != mb) continue;
+                    float2 y = make_float2(0.0f, 0.0f);
+                    if (ok) {
+                        y = k == 0 ? make_float2(d1r[e], d2i[e]) : make_float2(d1r[e] - d2i[e], d1i[e] + d2r[e]);
+                        y = cscale(y, scale);
                     }
+                    a.partial[(((size_t)sess * a.SP + j) * a.n_dst + l) * a.B + k] = y;
                 }
             }
             tmem_fence_before();
@@ -441,7 +441,7 @@ const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, in
     if (B < 16 || B > 4096 || (B & (B - 1))) return "block must be a power of two in [16, 4096]";
     if (n_dst != 8 && n_dst != 16 && n_dst != 32) return "session groups need n_out in {8, 16, 32}";
     if (n_src != 1 && n_src != 2 && n_src != 4 && n_src != 8) return "session groups need n_in in {1, 2, 4, 8}";
-    if (S < 8 || S % 8) return "sessions must be a positive multiple of 8";
+    if (!(S == 1 || S == 2 || S == 4 || (S >= 8 && S % 8 == 0))) return "sessions must be 1, 2, 4 or a multiple of 8";
     if (taps < 1) return "taps must be >= 1";
     if (num_sms < 1) return "num_sms must be >= 1";
     if (t.ctas < 0) return "ctas must be >= 0";
@@ -455,6 +455,7 @@ const char* plan_group(int prec, int B, int n_src, int n_dst, long long taps, in
     p.S = S;
     p.G = 128 / n_dst;
     if (p.G * S > 128) return "sessions x (128 / n_out) must be <= 128";
+    if (p.G * S < 8) return "sessions x (128 / n_out) must be >= 8 (MMA N >= 16)";
     const long long K = (taps + B - 1) / B;
     p.D = 8 / n_src;
     p.KP = 2 * p.D;
@@ -510,7 +511,7 @@ const char* check_group_plan(const GroupPlan& p) {
     if (p.RB % 16 || p.stage_bytes % 16) return "copy sizes must be multiples of 16 bytes";
     if ((size_t)p.smem > 227 * 1024) return "shared memory above the per-CTA limit";
     if (p.smem <= 114 * 1024) return "shared memory small enough for two MAC CTAs on one SM";
-    if ((32 / p.n_dst) * p.S % 8) return "epilogue column ranges must be multiples of 8";
+    if ((p.G * p.S) % 8) return "columns of a part must be a multiple of 8";
     if (p.nstage < 2 || p.nstage > GRP_MAX_STAGES) return "pipeline depth";
     if ((size_t)p.stage_bytes * p.nstage + GRP_HDR_BYTES > (size_t)p.smem) return "stages beyond shared memory";
     if (p.T != p.NKS - 1 || (p.T > 0) != (p.C > 0)) return "tail shape";

@@ -135,8 +135,8 @@ def test_group_plans_replay_clean_over_shapes(lib):
         for B in (16, 64, 256, 1024, 4096):
             for n_in in (1, 2, 4, 8):
                 for n_out in (8, 16, 32):
-                    for S in (8, 16, 32):
-                        if (128 // n_out) * S > 128:
+                    for S in (1, 2, 4, 8, 16, 32):
+                        if not 8 <= (128 // n_out) * S <= 128:
                             continue
                         for taps in (1, 257, 3000, 384000):
                             for sms in (152, 20):
@@ -162,7 +162,8 @@ def test_group_rejects_unsupported_shapes_on_the_host(lib):
     from paper_2509_04390_gb300 import upols as U
 
     for args in (("fp32", 64, 4, 16, 100, 8), ("fp16", 64, 3, 16, 100, 8), ("fp16", 64, 4, 12, 100, 8),
-                 ("fp16", 64, 4, 16, 100, 12), ("fp16", 64, 4, 8, 100, 16), ("fp16", 48, 4, 16, 100, 8)):
+                 ("fp16", 64, 4, 16, 100, 12), ("fp16", 64, 4, 8, 100, 16), ("fp16", 48, 4, 16, 100, 8),
+                 ("fp16", 64, 4, 32, 100, 1), ("fp16", 64, 4, 16, 100, 3)):
         with pytest.raises(U.ConvError) as ei:
             U.conv_group_plan_check(*args)
         assert ei.value.code == U.CONV_E_INVAL

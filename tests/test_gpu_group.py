@@ -46,6 +46,10 @@ def group_case(seed, S, n_in, n_out, taps, B, nb):
         ("fp16", 8, 1, 32, 900, 128, 20),  # 4 bins per tile, 8 slots per ring row
         ("fp16", 32, 2, 32, 1000, 64, 30),  # 32 sessions, 4 slots per ring row
         ("fp16", 8, 4, 16, 1, 64, 6),  # one tap: K = 1, ring of 4 slots
+        ("fp16", 1, 4, 16, 3000, 64, 60),  # one session: N = 16
+        ("bf16", 2, 2, 16, 2000, 32, 80),
+        ("fp16", 4, 8, 8, 1200, 16, 90),  # 16 bins x 4 sessions
+        ("fp16", 2, 1, 32, 5000, 128, 50),  # 4 bins x 2 sessions: N = 16
     ],
 )
 def test_group_sessions_against_oracle(precision, S, n_in, n_out, taps, B, nb):
@@ -150,7 +154,8 @@ def test_group_paper_scale_sampled():
 
 def test_unsupported_shapes_are_rejected():
     for args in (("fp32", 64, 4, 16, 100, 8), ("fp16", 64, 3, 16, 100, 8), ("fp16", 64, 4, 12, 100, 8),
-                 ("fp16", 64, 4, 16, 100, 12), ("fp16", 64, 4, 8, 100, 16), ("fp16", 48, 4, 16, 100, 8)):
+                 ("fp16", 64, 4, 16, 100, 12), ("fp16", 64, 4, 8, 100, 16), ("fp16", 48, 4, 16, 100, 8),
+                 ("fp16", 64, 4, 32, 100, 1), ("fp16", 64, 4, 16, 100, 3)):
         with pytest.raises(U.ConvError) as ei:
             U.Group(*args)
         assert ei.value.code == U.CONV_E_INVAL
