@@ -156,6 +156,15 @@ int afc_set_paths(conv_engine* e, const float* f, long long taps_fb);
  * when out is written.  Needs conv_set_filters (CONV_E_STATE otherwise). */
 int conv_process_block(conv_engine* e, const float* in, float* out);
 
+/* n_blocks consecutive blocks from host buffers in one call (offline
+ * rendering): in[n_in][n_blocks * block] and out[n_out][n_blocks * block],
+ * row-major with row pitch n_blocks * block, owned by the caller.  The same
+ * result as n_blocks calls of conv_process_block; the blocks run back to back
+ * on the device in chunks of up to 256 blocks, with one strided copy in and
+ * out per chunk (the chunk buffers are allocated on first use and kept).
+ * Blocks until `out` is filled. */
+int conv_process_blocks(conv_engine* e, const float* in, float* out, long long n_blocks);
+
 /* Same as conv_process_block with device pointers d_in[n_in][block] and
  * d_out[n_out][block], enqueued on `cuda_stream` (a cudaStream_t; NULL = the
  * legacy default stream).  Returns once the work is enqueued. */

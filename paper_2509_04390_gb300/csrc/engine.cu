@@ -423,6 +423,10 @@ struct conv_engine {
     const float* addend = nullptr;      // added by this block's output kernel, or null
     int addend_stride = 0;
     int e_stride = 0;                   // row pitch of the pack's e_out for this block (0: block)
+    // conv_process_blocks: row pitches of the synthesis input and output (0: block)
+    int io_in_stride = 0, io_out_stride = 0;
+    float *d_cin = nullptr, *d_cout = nullptr;  // its device chunk buffers
+    long long chunk_cap = 0;                    // blocks they hold
 };
 
 namespace {
@@ -637,7 +641,7 @@ OutArgs out_args(conv_engine* e, Part& P, long long blk, float* out) {
     a.log2B = e->log2B;
     a.tw = e->tw;
     a.out = out;
-    a.out_stride = e->B;
+    a.out_stride = (&P == &e->syn && e->io_out_stride) ? e->io_out_stride : e->B;
     a.head = 1;
     a.H = P.H;
     a.X = P.X;
@@ -690,7 +694,8 @@ int enqueue_conv(conv_engine* e, Part& P, const float* src, const float* sub, fl
                  cudaStream_t s, bool timed) {
     int rc;
     const long long n = e->nblk;
-    if ((rc = enqueue_pack(e, P, src, e->B, sub, e_out, s))) return rc;
+    const int in_stride = (&P == &e->syn && e->io_in_stride) ? e->io_in_stride : e->B;
+    if ((rc = enqueue_pack(e, P, src, in_stride, sub, e_out, s))) return rc;
     CK(cudaEventRecord(P.ev_packed, s));
     CK(cudaStreamWaitEvent(s, P.ev_tail[n & 1], 0));
     if ((rc = enqueue_out(e, P, n, out, s))) return rc;
@@ -889,6 +894,8 @@ void engine_free(conv_engine* e) {
         engine_free(e->far);
         e->far = nullptr;
     }
+    dev_free(e, &e->d_cin, 0);
+    dev_free(e, &e->d_cout, 0);
     dev_free(e, &e->d_acc, 0);
     dev_free(e, &e->d_far_out[0], 0);
     dev_free(e, &e->d_far_out[1], 0);
@@ -1128,6 +1135,42 @@ int conv_process_block(conv_engine* e, const float* in, float* out) {
     if ((rc = check_dev_err(e))) return rc;
     std::memcpy(out, e->h_out, ob);
     return CONV_OK;
+}
+
+int conv_process_blocks(conv_engine* e, const float* in, float* out, long long n_blocks) {
+    if (!e || !in || !out) return set_err(CONV_E_INVAL, "null argument");
+    if (n_blocks < 1) return set_err(CONV_E_INVAL, "n_blocks must be >= 1");
+    if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
+    DeviceGuard g(e->dev);
+    const long long C = std::min<long long>(n_blocks, 256);  // blocks per chunk
+    int rc = CONV_OK;
+    if (C > e->chunk_cap) {
+        CK(cudaStreamSynchronize(e->stream));
+        dev_free(e, &e->d_cin, (size_t)e->n_in * e->chunk_cap * e->B * sizeof(float));
+        dev_free(e, &e->d_cout, (size_t)e->n_out * e->chunk_cap * e->B * sizeof(float));
+        e->chunk_cap = 0;
+        if ((rc = dev_alloc(e, &e->d_cin, (size_t)e->n_in * C * e->B * sizeof(float)))) return rc;
+        if ((rc = dev_alloc(e, &e->d_cout, (size_t)e->n_out * C * e->B * sizeof(float)))) return rc;
+        e->chunk_cap = C;
+    }
+    const size_t T = (size_t)n_blocks * e->B, fs = sizeof(float);
+    for (long long b0 = 0; b0 < n_blocks; b0 += C) {
+        const long long nb = std::min(C, n_blocks - b0);
+        const size_t w = (size_t)nb * e->B;
+        CK(cudaMemcpy2DAsync(e->d_cin, (size_t)C * e->B * fs, in + (size_t)b0 * e->B, T * fs, w * fs, e->n_in,
+                             cudaMemcpyHostToDevice, e->stream));
+        e->io_in_stride = (int)(C * e->B);
+        e->io_out_stride = (int)(C * e->B);
+        for (long long b = 0; b < nb && !rc; ++b)
+            rc = enqueue_block(e, e->d_cin + (size_t)b * e->B, e->d_cout + (size_t)b * e->B, e->stream);
+        e->io_in_stride = e->io_out_stride = 0;
+        if (rc) return rc;
+        CK(cudaMemcpy2DAsync(out + (size_t)b0 * e->B, T * fs, e->d_cout, (size_t)C * e->B * fs, w * fs, e->n_out,
+                             cudaMemcpyDeviceToHost, e->stream));
+    }
+    CK(cudaEventRecord(e->ev_done, e->stream));
+    CK(cudaEventSynchronize(e->ev_done));
+    return check_dev_err(e);
 }
 
 int afc_process_block_async(conv_engine* e, const float* d_mic, float* d_out, float* d_e, void* cuda_stream) {

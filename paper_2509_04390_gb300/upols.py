@@ -139,6 +139,7 @@ def load():
         "afc_set_paths": (i, [vp, vp, ll]),
         "conv_process_block": (i, [vp, vp, vp]),
         "conv_process_block_async": (i, [vp, vp, vp, vp]),
+        "conv_process_blocks": (i, [vp, vp, vp, ll]),
         "afc_process_block": (i, [vp, vp, vp, vp]),
         "afc_process_block_async": (i, [vp, vp, vp, vp, vp]),
         "afc_set_guard": (i, [vp, d]),
@@ -272,6 +273,17 @@ def afc_set_paths(h, paths: np.ndarray):
 def conv_process_block(h, inp: np.ndarray, out: np.ndarray, _shape=None):
     n_in, n_out, B = _shape if _shape else _dims(h)
     return _check(load().conv_process_block(h, _host_ptr(inp, (n_in, B)), _host_ptr(out, (n_out, B), True)))
+
+
+def conv_process_blocks(h, inp: np.ndarray, out: np.ndarray, _shape=None):
+    """inp [n_in][n_blocks * block], out [n_out][n_blocks * block] (float32, C-contiguous)."""
+    n_in, n_out, B = _shape if _shape else _dims(h)
+    T = inp.shape[1] if inp.ndim == 2 else -1
+    if T <= 0 or T % B:
+        raise ValueError("input length must be a positive multiple of the block size")
+    return _check(
+        load().conv_process_blocks(h, _host_ptr(inp, (n_in, T)), _host_ptr(out, (n_out, T), True), T // B)
+    )
 
 
 def conv_process_block_async(h, d_in, d_out, stream=None):
@@ -642,7 +654,7 @@ class Engine:
         return out
 
     def run(self, x: np.ndarray) -> np.ndarray:
-        """Stream a whole [n_in][T] signal (zero-extended to whole blocks)."""
+        """Stream a whole [n_in][T] signal block by block (zero-extended to whole blocks)."""
         n_in, n_out, B = self.shape
         T = x.shape[1]
         nb = -(-T // B)
@@ -653,6 +665,17 @@ class Engine:
         for b in range(nb):
             self.process(np.ascontiguousarray(xp[:, b * B : (b + 1) * B]), blk)
             y[:, b * B : (b + 1) * B] = blk
+        return y
+
+    def render(self, x: np.ndarray) -> np.ndarray:
+        """Stream a whole [n_in][T] signal in one multi-block call (zero-extended)."""
+        n_in, n_out, B = self.shape
+        T = x.shape[1]
+        nb = -(-T // B)
+        xp = np.zeros((n_in, nb * B), dtype=np.float32)
+        xp[:, :T] = x
+        y = np.empty((n_out, nb * B), dtype=np.float32)
+        conv_process_blocks(self.h, xp, y, self.shape)
         return y
 
     def info(self):
