@@ -411,6 +411,13 @@ int conv_group_process_async(conv_group* g, const float* d_in, float* d_out, voi
  * device-side wait that gave up as CONV_E_TIMEOUT. */
 int conv_group_process(conv_group* g, const float* in, float* out);
 
+/* n_blocks consecutive blocks of every session from host buffers in one call:
+ * in [sessions][n_in][n_blocks * block], out [sessions][n_out][n_blocks * block]
+ * (row pitch n_blocks * block), owned by the caller.  The same result as
+ * n_blocks calls of conv_group_process; chunks of up to 256 blocks run back to
+ * back on the device, one strided copy in and out per chunk. */
+int conv_group_process_blocks(conv_group* g, const float* in, float* out, long long n_blocks);
+
 /* Zero every session's delay line and window (filters kept). */
 int conv_group_reset(conv_group* g);
 

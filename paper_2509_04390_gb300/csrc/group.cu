@@ -141,7 +141,7 @@ __global__ void k_group_pack(const GroupPackArgs a) {
     float2* tws = fsm + 2 * B;
     const int q = blockIdx.x, s = blockIdx.y;
     load_twiddles(tws, a.tw, B);
-    const float* in = a.in + ((size_t)s * a.n_src + q) * B;
+    const float* in = a.in + ((size_t)s * a.n_src + q) * a.in_stride;
     float* win = a.win + ((size_t)s * a.n_src + q) * B;
     for (int n = tid; n < B; n += nth) {
         bufA[n] = n < half ? make_float2(win[2 * n], win[2 * n + 1]) : make_float2(in[2 * n - B], in[2 * n - B + 1]);
@@ -424,7 +424,7 @@ __global__ void k_group_out(const GroupOutArgs a) {
     __syncthreads();
     const float2* z = fft_smem<true>(W, P, B, a.log2B, tws, a.log2B + 1, tid, nth);
     const float invB = 1.0f / (float)B;
-    float* out = a.out + ((size_t)s * a.n_dst + l) * B;
+    float* out = a.out + ((size_t)s * a.n_dst + l) * a.out_stride;
     for (int t = tid; t < B; t += nth) {
         const int u = B + t, n = u >> 1;
         out[t] = ((u & 1) ? z[n].y : z[n].x) * invB;

@@ -100,7 +100,8 @@ struct GroupMacArgs {
 };
 
 struct GroupPackArgs {
-    const float* in;  // [S][n_src][B]
+    const float* in;  // [S][n_src][in_stride], first B samples of each row used
+    int in_stride;
     float* win;       // [S][n_src][B]
     void* X;
     int B, log2B, n_src, S, G, D, KR, RB, slot;
@@ -119,7 +120,8 @@ struct GroupFilterArgs {
 
 struct GroupOutArgs {
     const float2* partial;
-    float* out;  // [S][n_dst][B]
+    float* out;  // [S][n_dst][out_stride], first B samples of each row written
+    int out_stride;
     int B, log2B, n_dst, T, C, SP;
     const float2* tw;
     // head: K-step 0 (partitions 0 .. KP-1) of this block, on CUDA cores

@@ -16,6 +16,7 @@
 // tail(n+1) reads (they hold slot0(n+1) at position 0 only in K-step 0's row).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -50,6 +51,9 @@ struct conv_group {
     float2* partial[2] = {nullptr, nullptr};  // tail partials by block parity
     float2* tw = nullptr;
     float *d_in = nullptr, *d_out = nullptr, *h_in = nullptr, *h_out = nullptr;
+    float *d_cin = nullptr, *d_cout = nullptr;  // conv_group_process_blocks chunk buffers
+    long long chunk_cap = 0;
+    int io_stride = 0;  // row pitch of the input and output of the block being enqueued (0: block)
     int *h_err = nullptr, *d_err = nullptr;
     long long nblk = 0;
     bool ready = false;
@@ -109,7 +113,7 @@ void group_free(conv_group* g) {
     for (int i = 0; i < 2; ++i)
         if (g->bg[i]) cudaStreamSynchronize(g->bg[i]);
     for (void* p : {g->H, g->X, (void*)g->sH, (void*)g->win, (void*)g->partial[0], (void*)g->partial[1], (void*)g->tw,
-                    (void*)g->d_in, (void*)g->d_out})
+                    (void*)g->d_in, (void*)g->d_out, (void*)g->d_cin, (void*)g->d_cout})
         if (p) cudaFree(p);
     if (g->h_in) cudaFreeHost(g->h_in);
     if (g->h_out) cudaFreeHost(g->h_out);
@@ -284,6 +288,7 @@ int enqueue_group(conv_group* g, const float* d_in, float* d_out, cudaStream_t s
     const int prec = to_prec(g->prec);
     GroupPackArgs pk{};
     pk.in = d_in;
+    pk.in_stride = g->io_stride ? g->io_stride : g->B;
     pk.win = g->win;
     pk.X = g->X;
     pk.B = g->B;
@@ -302,6 +307,7 @@ int enqueue_group(conv_group* g, const float* d_in, float* d_out, cudaStream_t s
     GroupOutArgs o{};
     o.partial = g->partial[n & 1];
     o.out = d_out;
+    o.out_stride = g->io_stride ? g->io_stride : g->B;
     o.B = g->B;
     o.log2B = g->log2B;
     o.n_dst = g->n_out;
@@ -435,6 +441,46 @@ int conv_group_process(conv_group* g, const float* in, float* out) {
     if ((rc = check_err(g))) return rc;
     std::memcpy(out, g->h_out, ob);
     return CONV_OK;
+}
+
+int conv_group_process_blocks(conv_group* g, const float* in, float* out, long long n_blocks) {
+    if (!g || !in || !out) return gset(CONV_E_INVAL, "null argument");
+    if (n_blocks < 1) return gset(CONV_E_INVAL, "n_blocks must be >= 1");
+    if (!g->ready) return gset(CONV_E_STATE, "filters not set");
+    GDev d(g->dev);
+    const long long C = std::min<long long>(n_blocks, 256);  // blocks per chunk
+    const size_t rows_in = (size_t)g->S * g->n_in, rows_out = (size_t)g->S * g->n_out, fs = sizeof(float);
+    int rc = CONV_OK;
+    if (C > g->chunk_cap) {
+        if ((rc = sync_all(g))) return rc;
+        for (float** p : {&g->d_cin, &g->d_cout})
+            if (*p) {
+                cudaFree(*p);
+                *p = nullptr;
+            }
+        g->dev_bytes -= (rows_in + rows_out) * (size_t)g->chunk_cap * g->B * fs;
+        g->chunk_cap = 0;
+        if ((rc = galloc(g, &g->d_cin, rows_in * (size_t)C * g->B * fs))) return rc;
+        if ((rc = galloc(g, &g->d_cout, rows_out * (size_t)C * g->B * fs))) return rc;
+        g->chunk_cap = C;
+    }
+    const size_t T = (size_t)n_blocks * g->B;
+    for (long long b0 = 0; b0 < n_blocks; b0 += C) {
+        const long long nb = std::min(C, n_blocks - b0);
+        const size_t w = (size_t)nb * g->B;
+        GCK(cudaMemcpy2DAsync(g->d_cin, (size_t)C * g->B * fs, in + (size_t)b0 * g->B, T * fs, w * fs, rows_in,
+                              cudaMemcpyHostToDevice, g->stream));
+        g->io_stride = (int)(C * g->B);
+        for (long long b = 0; b < nb && !rc; ++b)
+            rc = enqueue_group(g, g->d_cin + (size_t)b * g->B, g->d_cout + (size_t)b * g->B, g->stream);
+        g->io_stride = 0;
+        if (rc) return rc;
+        GCK(cudaMemcpy2DAsync(out + (size_t)b0 * g->B, T * fs, g->d_cout, (size_t)C * g->B * fs, w * fs, rows_out,
+                              cudaMemcpyDeviceToHost, g->stream));
+    }
+    GCK(cudaEventRecord(g->ev_done, g->stream));
+    GCK(cudaEventSynchronize(g->ev_done));
+    return check_err(g);
 }
 
 int conv_group_reset(conv_group* g) {

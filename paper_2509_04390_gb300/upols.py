@@ -169,6 +169,7 @@ def load():
         "conv_group_set_filters": (i, [vp, vp]),
         "conv_group_process_async": (i, [vp, vp, vp, vp]),
         "conv_group_process": (i, [vp, vp, vp]),
+        "conv_group_process_blocks": (i, [vp, vp, vp, ll]),
         "conv_group_reset": (i, [vp]),
         "conv_group_synchronize": (i, [vp]),
         "conv_group_get_info": (i, [vp, ctypes.POINTER(conv_group_info)]),
@@ -463,6 +464,17 @@ def conv_group_process(g, inp: np.ndarray, out: np.ndarray, _shape=None):
     return _check(load().conv_group_process(g, _host_ptr(inp, (S, n_in, B)), _host_ptr(out, (S, n_out, B), True)))
 
 
+def conv_group_process_blocks(g, inp: np.ndarray, out: np.ndarray, _shape=None):
+    """inp [sessions][n_in][n_blocks * block], out [sessions][n_out][n_blocks * block]."""
+    S, n_in, n_out, B = _shape if _shape else _gdims(g)
+    T = inp.shape[2] if inp.ndim == 3 else -1
+    if T <= 0 or T % B:
+        raise ValueError("input length must be a positive multiple of the block size")
+    return _check(
+        load().conv_group_process_blocks(g, _host_ptr(inp, (S, n_in, T)), _host_ptr(out, (S, n_out, T), True), T // B)
+    )
+
+
 def conv_group_reset(g):
     return _check(load().conv_group_reset(g))
 
@@ -584,6 +596,17 @@ class Group:
         for b in range(nb):
             self.process(np.ascontiguousarray(xp[:, :, b * B : (b + 1) * B]), blk)
             y[:, :, b * B : (b + 1) * B] = blk
+        return y
+
+    def render(self, x: np.ndarray) -> np.ndarray:
+        """Whole signals x [sessions][n_in][T] in one multi-block call (zero-extended)."""
+        S, n_in, n_out, B = self.shape
+        T = x.shape[2]
+        nb = -(-T // B)
+        xp = np.zeros((S, n_in, nb * B), dtype=np.float32)
+        xp[:, :, :T] = x
+        y = np.empty((S, n_out, nb * B), dtype=np.float32)
+        conv_group_process_blocks(self.g, xp, y, self.shape)
         return y
 
     def info(self):

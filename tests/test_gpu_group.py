@@ -112,6 +112,19 @@ def test_reset_repeats_bit_exact():
     assert np.array_equal(y0, y1)
 
 
+def test_render_equals_block_calls():
+    """conv_group_process_blocks over a chunk boundary (300 blocks) is the
+    block-by-block stream, bit for bit."""
+    S, n_in, n_out, taps, B, nb = 8, 4, 16, 700, 16, 300
+    h, x = group_case(11, S, n_in, n_out, taps, B, nb)
+    with U.Group("fp16", B, n_in, n_out, taps, S) as g:
+        g.set_filters(h)
+        y_blocks = g.run(x)
+        g.reset()
+        y_render = g.render(x)
+    assert np.array_equal(y_blocks, y_render)
+
+
 def test_device_path_matches_host_path():
     torch = pytest.importorskip("torch")
     S, n_in, n_out, taps, B, nb = 8, 4, 16, 1200, 64, 30
