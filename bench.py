@@ -78,7 +78,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("kernels.cu", "device_util.cuh", "kernels.h"):
+    for name in ("kernels.cu", "device_util.cuh", "kernels.h", "engine.cu"):
         with open(os.path.join(ROOT, "paper_2509_04390_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
