@@ -77,10 +77,19 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """sha256 (first 16 hex digits) of the MAC's sources: kernels.cu,
+    device_util.cuh, kernels.h and the planner function plan_mac of engine.cu
+    (it fixes the launch configuration)."""
     h = hashlib.sha256()
-    for name in ("kernels.cu", "device_util.cuh", "kernels.h", "engine.cu"):
-        with open(os.path.join(ROOT, "paper_2509_04390_gb300", "csrc", name), "rb") as f:
+    csrc = os.path.join(ROOT, "paper_2509_04390_gb300", "csrc")
+    for name in ("kernels.cu", "device_util.cuh", "kernels.h"):
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
+    with open(os.path.join(csrc, "engine.cu"), "rb") as f:
+        eng = f.read()
+    start = eng.find(b"MacPlan plan_mac(")
+    end = eng.find(b"\n}\n", start)
+    h.update(eng[start:end] if start >= 0 and end > start else eng)
     return h.hexdigest()[:16]
 
 

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "conv.h"
+#include "host_util.h"
 #include "kernels.h"
 #include "nlms.h"
 
@@ -54,12 +55,7 @@ int set_err(int code, const char* fmt, ...) {
     return code;
 }
 
-#define CK(call)                                                                                          \
-    do {                                                                                                  \
-        cudaError_t e_ = (call);                                                                          \
-        if (e_ != cudaSuccess) return set_err(CONV_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
-                                              __FILE__, __LINE__);                                        \
-    } while (0)
+#define CK(call) GB_CK(call)
 
 inline int ilog2(int v) {
     int r = 0;
@@ -368,17 +364,6 @@ size_t part_bytes(const MacPlan& p, int prec) {
     if (prec != PREC_FP32) b += ((size_t)p.n_lt * p.R + (size_t)p.R + 8) * sizeof(float);
     return b;
 }
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 }  // namespace
 

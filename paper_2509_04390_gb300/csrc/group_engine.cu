@@ -27,6 +27,7 @@
 
 #include "conv.h"
 #include "group.h"
+#include "host_util.h"
 #include "kernels.h"
 
 using namespace gbconv;
@@ -65,41 +66,13 @@ struct conv_group {
 
 namespace {
 
-int gset(int code, const char* fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
-    va_end(ap);
-    set_last_error_message(buf);
-    return code;
-}
-
-#define GCK(call)                                                                                        \
-    do {                                                                                                 \
-        cudaError_t e_ = (call);                                                                         \
-        if (e_ != cudaSuccess)                                                                           \
-            return gset(CONV_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)
-
-struct GDev {
-    int prev = -1;
-    explicit GDev(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
-    }
-    ~GDev() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
 template <typename T>
 int galloc(conv_group* g, T** p, size_t bytes) {
     cudaError_t r = cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
     if (r != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
-        return gset(r == cudaErrorMemoryAllocation ? CONV_E_NOMEM : CONV_E_CUDA, "cudaMalloc(%zu): %s", bytes,
+        return fail(r == cudaErrorMemoryAllocation ? CONV_E_NOMEM : CONV_E_CUDA, "cudaMalloc(%zu): %s", bytes,
                     cudaGetErrorString(r));
     }
     g->dev_bytes += bytes ? bytes : 16;
@@ -108,7 +81,7 @@ int galloc(conv_group* g, T** p, size_t bytes) {
 
 void group_free(conv_group* g) {
     if (!g) return;
-    GDev d(g->dev);
+    DeviceGuard d(g->dev);
     if (g->stream) cudaStreamSynchronize(g->stream);
     for (int i = 0; i < 2; ++i)
         if (g->bg[i]) cudaStreamSynchronize(g->bg[i]);
@@ -135,8 +108,8 @@ int to_prec(int precision) {
 }
 
 int sync_all(conv_group* g) {
-    for (int i = 0; i < 2; ++i) GCK(cudaStreamSynchronize(g->bg[i]));
-    GCK(cudaStreamSynchronize(g->stream));
+    for (int i = 0; i < 2; ++i) GB_CK(cudaStreamSynchronize(g->bg[i]));
+    GB_CK(cudaStreamSynchronize(g->stream));
     return CONV_OK;
 }
 
@@ -144,13 +117,13 @@ int group_reset_impl(conv_group* g) {
     int rc;
     if ((rc = sync_all(g))) return rc;
     const GroupPlan& p = g->plan;
-    GCK(cudaMemsetAsync(g->X, 0, p.x_bytes, g->stream));
-    GCK(cudaMemsetAsync(g->win, 0, (size_t)g->S * g->n_in * g->B * sizeof(float), g->stream));
+    GB_CK(cudaMemsetAsync(g->X, 0, p.x_bytes, g->stream));
+    GB_CK(cudaMemsetAsync(g->win, 0, (size_t)g->S * g->n_in * g->B * sizeof(float), g->stream));
     for (int i = 0; i < 2; ++i) {
-        GCK(cudaMemsetAsync(g->partial[i], 0, p.partial_bytes, g->stream));
-        GCK(cudaEventRecord(g->ev_tail[i], g->stream));  // block 0's tail: zero partials
+        GB_CK(cudaMemsetAsync(g->partial[i], 0, p.partial_bytes, g->stream));
+        GB_CK(cudaEventRecord(g->ev_tail[i], g->stream));  // block 0's tail: zero partials
     }
-    GCK(cudaStreamSynchronize(g->stream));
+    GB_CK(cudaStreamSynchronize(g->stream));
     g->nblk = 0;
     return CONV_OK;
 }
@@ -169,14 +142,14 @@ GroupTiling from_api(const conv_group_tiling* t) {
 int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, long long taps, int sessions,
                 const conv_group_tiling* tiling) {
     const int prec = to_prec(precision);
-    if (prec < 0) return gset(CONV_E_INVAL, "unknown precision %d", precision);
-    GCK(cudaGetDevice(&g->dev));
+    if (prec < 0) return fail(CONV_E_INVAL, "unknown precision %d", precision);
+    GB_CK(cudaGetDevice(&g->dev));
     cudaDeviceProp prop{};
-    GCK(cudaGetDeviceProperties(&prop, g->dev));
+    GB_CK(cudaGetDeviceProperties(&prop, g->dev));
     g->num_sms = prop.multiProcessorCount;
     if (const char* why = plan_group(prec, block, n_in, n_out, taps, sessions, g->num_sms, &g->plan, from_api(tiling)))
-        return gset(CONV_E_INVAL, "%s", why);
-    if (const char* why = check_group_plan(g->plan)) return gset(CONV_E_INVAL, "%s", why);
+        return fail(CONV_E_INVAL, "%s", why);
+    if (const char* why = check_group_plan(g->plan)) return fail(CONV_E_INVAL, "%s", why);
     g->prec = precision;
     g->B = block;
     g->log2B = 0;
@@ -190,12 +163,12 @@ int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, lo
     // kind::f16: D F32, A and B of the same 16-bit type, both K-major, N, M = 128
     g->idesc = (1u << 4) | (t << 7) | (t << 10) | ((uint32_t)(p.N >> 3) << 17) | ((128u >> 4) << 24);
     size_t free_b = 0, total_b = 0;
-    GCK(cudaMemGetInfo(&free_b, &total_b));
+    GB_CK(cudaMemGetInfo(&free_b, &total_b));
     const size_t need = p.h_bytes + p.x_bytes + 2 * p.partial_bytes + (size_t)p.NG * 128 * sizeof(float) +
                         (size_t)sessions * (n_in + n_out) * block * sizeof(float) * 2;
     if (need + (64ull << 20) > free_b)
-        return gset(CONV_E_NOMEM, "device footprint %zu bytes does not fit in %zu free bytes", need, free_b);
-    GCK(prepare_group_kernels());
+        return fail(CONV_E_NOMEM, "device footprint %zu bytes does not fit in %zu free bytes", need, free_b);
+    GB_CK(prepare_group_kernels());
     int rc;
     if ((rc = galloc(g, &g->H, p.h_bytes))) return rc;
     if ((rc = galloc(g, &g->X, p.x_bytes))) return rc;
@@ -206,22 +179,22 @@ int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, lo
     if ((rc = galloc(g, &g->tw, 2 * (size_t)block * sizeof(float2)))) return rc;
     if ((rc = galloc(g, &g->d_in, (size_t)sessions * n_in * block * sizeof(float)))) return rc;
     if ((rc = galloc(g, &g->d_out, (size_t)sessions * n_out * block * sizeof(float)))) return rc;
-    GCK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_in), (size_t)sessions * n_in * block * sizeof(float),
+    GB_CK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_in), (size_t)sessions * n_in * block * sizeof(float),
                       cudaHostAllocDefault));
-    GCK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_out), (size_t)sessions * n_out * block * sizeof(float),
+    GB_CK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_out), (size_t)sessions * n_out * block * sizeof(float),
                       cudaHostAllocDefault));
-    GCK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_err), sizeof(int), cudaHostAllocMapped));
+    GB_CK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_err), sizeof(int), cudaHostAllocMapped));
     *g->h_err = 0;
-    GCK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&g->d_err), g->h_err, 0));
+    GB_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&g->d_err), g->h_err, 0));
     int lo = 0, hi = 0;
-    GCK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    GCK(cudaStreamCreateWithPriority(&g->stream, cudaStreamNonBlocking, hi));
+    GB_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    GB_CK(cudaStreamCreateWithPriority(&g->stream, cudaStreamNonBlocking, hi));
     for (int i = 0; i < 2; ++i) {
-        GCK(cudaStreamCreateWithPriority(&g->bg[i], cudaStreamNonBlocking, lo));
-        GCK(cudaEventCreateWithFlags(&g->ev_tail[i], cudaEventDisableTiming));
+        GB_CK(cudaStreamCreateWithPriority(&g->bg[i], cudaStreamNonBlocking, lo));
+        GB_CK(cudaEventCreateWithFlags(&g->ev_tail[i], cudaEventDisableTiming));
     }
-    GCK(cudaEventCreateWithFlags(&g->ev_packed, cudaEventDisableTiming));
-    GCK(cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming));
+    GB_CK(cudaEventCreateWithFlags(&g->ev_packed, cudaEventDisableTiming));
+    GB_CK(cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming));
     // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once
     std::vector<float2> tw(2 * (size_t)block);
     const double pi = 3.14159265358979323846264338327950288;
@@ -229,9 +202,9 @@ int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, lo
         const double ang = -pi * (double)j / (double)block;
         tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
-    GCK(cudaMemcpy(g->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
-    GCK(cudaMemset(g->H, 0, p.h_bytes));
-    GCK(cudaMemset(g->sH, 0, (size_t)p.NG * 128 * sizeof(float)));
+    GB_CK(cudaMemcpy(g->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    GB_CK(cudaMemset(g->H, 0, p.h_bytes));
+    GB_CK(cudaMemset(g->sH, 0, (size_t)p.NG * 128 * sizeof(float)));
     return group_reset_impl(g);
 }
 
@@ -272,10 +245,10 @@ int enqueue_tail(conv_group* g, long long blk, cudaStream_t s) {
     a.idesc = g->idesc;
     a.err = g->d_err;
     const bool rec = g->prof && g->ev_used < g->ev0.size();
-    if (rec) GCK(cudaEventRecord(g->ev0[g->ev_used], s));
-    GCK(launch_group_mac(p, a, s));
+    if (rec) GB_CK(cudaEventRecord(g->ev0[g->ev_used], s));
+    GB_CK(launch_group_mac(p, a, s));
     if (rec) {
-        GCK(cudaEventRecord(g->ev1[g->ev_used], s));
+        GB_CK(cudaEventRecord(g->ev1[g->ev_used], s));
         ++g->ev_used;
     }
     return CONV_OK;
@@ -301,9 +274,9 @@ int enqueue_group(conv_group* g, const float* d_in, float* d_out, cudaStream_t s
     pk.RB = p.RB;
     pk.slot = slot0;
     pk.tw = g->tw;
-    GCK(launch_group_pack(prec, pk, s));
-    GCK(cudaEventRecord(g->ev_packed, s));
-    GCK(cudaStreamWaitEvent(s, g->ev_tail[n & 1], 0));
+    GB_CK(launch_group_pack(prec, pk, s));
+    GB_CK(cudaEventRecord(g->ev_packed, s));
+    GB_CK(cudaStreamWaitEvent(s, g->ev_tail[n & 1], 0));
     GroupOutArgs o{};
     o.partial = g->partial[n & 1];
     o.out = d_out;
@@ -325,14 +298,14 @@ int enqueue_group(conv_group* g, const float* d_in, float* d_out, cudaStream_t s
     o.RB = p.RB;
     o.S = g->S;
     o.slot0 = slot0;
-    GCK(launch_group_out(prec, o, s));
+    GB_CK(launch_group_out(prec, o, s));
     cudaStream_t bg = g->bg[p.tail_streams == 2 ? (n + 1) & 1 : 0];
-    GCK(cudaStreamWaitEvent(bg, g->ev_packed, 0));
+    GB_CK(cudaStreamWaitEvent(bg, g->ev_packed, 0));
     // kernel timing needs each tail alone on the GPU: then tails run one after another
-    if (g->prof) GCK(cudaStreamWaitEvent(bg, g->ev_tail[n & 1], 0));
+    if (g->prof) GB_CK(cudaStreamWaitEvent(bg, g->ev_tail[n & 1], 0));
     int rc = enqueue_tail(g, n + 1, bg);
     if (rc) return rc;
-    GCK(cudaEventRecord(g->ev_tail[(n + 1) & 1], bg));
+    GB_CK(cudaEventRecord(g->ev_tail[(n + 1) & 1], bg));
     ++g->nblk;
     return CONV_OK;
 }
@@ -341,7 +314,7 @@ int check_err(conv_group* g) {
     const int v = *(volatile int*)g->h_err;
     if (v != 0) {
         *(volatile int*)g->h_err = 0;
-        return gset(CONV_E_TIMEOUT, "device-side wait gave up (code %d); results of the block are invalid", v);
+        return fail(CONV_E_TIMEOUT, "device-side wait gave up (code %d); results of the block are invalid", v);
     }
     return CONV_OK;
 }
@@ -358,7 +331,7 @@ conv_group* conv_group_create_tiled(int precision, int block, int n_in, int n_ou
                                     const conv_group_tiling* tiling) {
     conv_group* g = new (std::nothrow) conv_group();
     if (!g) {
-        gset(CONV_E_NOMEM, "out of host memory");
+        fail(CONV_E_NOMEM, "out of host memory");
         return nullptr;
     }
     if (create_impl(g, precision, block, n_in, n_out, taps, sessions, tiling) != CONV_OK) {
@@ -372,8 +345,8 @@ conv_group* conv_group_create_tiled(int precision, int block, int n_in, int n_ou
 }
 
 int conv_group_set_filters(conv_group* g, const float* h) {
-    if (!g || !h) return gset(CONV_E_INVAL, "null argument");
-    GDev d(g->dev);
+    if (!g || !h) return fail(CONV_E_INVAL, "null argument");
+    DeviceGuard d(g->dev);
     const GroupPlan& p = g->plan;
     const size_t bytes = (size_t)g->n_out * g->n_in * (size_t)g->taps * sizeof(float);
     const size_t mbytes = (size_t)g->B * g->n_out * sizeof(unsigned);
@@ -413,41 +386,41 @@ int conv_group_set_filters(conv_group* g, const float* h) {
     cudaFree(d_h);
     cudaFree(d_max);
     g->dev_bytes -= bytes + mbytes;
-    if (r != cudaSuccess) return gset(CONV_E_CUDA, "group filter tiles: %s", cudaGetErrorString(r));
+    if (r != cudaSuccess) return fail(CONV_E_CUDA, "group filter tiles: %s", cudaGetErrorString(r));
     g->ready = true;
     return group_reset_impl(g);
 }
 
 int conv_group_process_async(conv_group* g, const float* d_in, float* d_out, void* cuda_stream) {
-    if (!g || !d_in || !d_out) return gset(CONV_E_INVAL, "null argument");
-    if (!g->ready) return gset(CONV_E_STATE, "filters not set");
-    GDev d(g->dev);
+    if (!g || !d_in || !d_out) return fail(CONV_E_INVAL, "null argument");
+    if (!g->ready) return fail(CONV_E_STATE, "filters not set");
+    DeviceGuard d(g->dev);
     return enqueue_group(g, d_in, d_out, static_cast<cudaStream_t>(cuda_stream));
 }
 
 int conv_group_process(conv_group* g, const float* in, float* out) {
-    if (!g || !in || !out) return gset(CONV_E_INVAL, "null argument");
-    if (!g->ready) return gset(CONV_E_STATE, "filters not set");
-    GDev d(g->dev);
+    if (!g || !in || !out) return fail(CONV_E_INVAL, "null argument");
+    if (!g->ready) return fail(CONV_E_STATE, "filters not set");
+    DeviceGuard d(g->dev);
     const size_t ib = (size_t)g->S * g->n_in * g->B * sizeof(float);
     const size_t ob = (size_t)g->S * g->n_out * g->B * sizeof(float);
     std::memcpy(g->h_in, in, ib);
-    GCK(cudaMemcpyAsync(g->d_in, g->h_in, ib, cudaMemcpyHostToDevice, g->stream));
+    GB_CK(cudaMemcpyAsync(g->d_in, g->h_in, ib, cudaMemcpyHostToDevice, g->stream));
     int rc = enqueue_group(g, g->d_in, g->d_out, g->stream);
     if (rc) return rc;
-    GCK(cudaMemcpyAsync(g->h_out, g->d_out, ob, cudaMemcpyDeviceToHost, g->stream));
-    GCK(cudaEventRecord(g->ev_done, g->stream));
-    GCK(cudaEventSynchronize(g->ev_done));  // the next block's tail keeps running
+    GB_CK(cudaMemcpyAsync(g->h_out, g->d_out, ob, cudaMemcpyDeviceToHost, g->stream));
+    GB_CK(cudaEventRecord(g->ev_done, g->stream));
+    GB_CK(cudaEventSynchronize(g->ev_done));  // the next block's tail keeps running
     if ((rc = check_err(g))) return rc;
     std::memcpy(out, g->h_out, ob);
     return CONV_OK;
 }
 
 int conv_group_process_blocks(conv_group* g, const float* in, float* out, long long n_blocks) {
-    if (!g || !in || !out) return gset(CONV_E_INVAL, "null argument");
-    if (n_blocks < 1) return gset(CONV_E_INVAL, "n_blocks must be >= 1");
-    if (!g->ready) return gset(CONV_E_STATE, "filters not set");
-    GDev d(g->dev);
+    if (!g || !in || !out) return fail(CONV_E_INVAL, "null argument");
+    if (n_blocks < 1) return fail(CONV_E_INVAL, "n_blocks must be >= 1");
+    if (!g->ready) return fail(CONV_E_STATE, "filters not set");
+    DeviceGuard d(g->dev);
     const long long C = std::min<long long>(n_blocks, 256);  // blocks per chunk
     const size_t rows_in = (size_t)g->S * g->n_in, rows_out = (size_t)g->S * g->n_out, fs = sizeof(float);
     int rc = CONV_OK;
@@ -468,38 +441,38 @@ int conv_group_process_blocks(conv_group* g, const float* in, float* out, long l
     for (long long b0 = 0; b0 < n_blocks; b0 += C) {
         const long long nb = std::min(C, n_blocks - b0);
         const size_t w = (size_t)nb * g->B;
-        GCK(cudaMemcpy2DAsync(g->d_cin, (size_t)C * g->B * fs, in + (size_t)b0 * g->B, T * fs, w * fs, rows_in,
+        GB_CK(cudaMemcpy2DAsync(g->d_cin, (size_t)C * g->B * fs, in + (size_t)b0 * g->B, T * fs, w * fs, rows_in,
                               cudaMemcpyHostToDevice, g->stream));
         g->io_stride = (int)(C * g->B);
         for (long long b = 0; b < nb && !rc; ++b)
             rc = enqueue_group(g, g->d_cin + (size_t)b * g->B, g->d_cout + (size_t)b * g->B, g->stream);
         g->io_stride = 0;
         if (rc) return rc;
-        GCK(cudaMemcpy2DAsync(out + (size_t)b0 * g->B, T * fs, g->d_cout, (size_t)C * g->B * fs, w * fs, rows_out,
+        GB_CK(cudaMemcpy2DAsync(out + (size_t)b0 * g->B, T * fs, g->d_cout, (size_t)C * g->B * fs, w * fs, rows_out,
                               cudaMemcpyDeviceToHost, g->stream));
     }
-    GCK(cudaEventRecord(g->ev_done, g->stream));
-    GCK(cudaEventSynchronize(g->ev_done));
+    GB_CK(cudaEventRecord(g->ev_done, g->stream));
+    GB_CK(cudaEventSynchronize(g->ev_done));
     return check_err(g);
 }
 
 int conv_group_reset(conv_group* g) {
-    if (!g) return gset(CONV_E_INVAL, "null handle");
-    GDev d(g->dev);
+    if (!g) return fail(CONV_E_INVAL, "null handle");
+    DeviceGuard d(g->dev);
     return group_reset_impl(g);
 }
 
 int conv_group_synchronize(conv_group* g) {
-    if (!g) return gset(CONV_E_INVAL, "null handle");
-    GDev d(g->dev);
+    if (!g) return fail(CONV_E_INVAL, "null handle");
+    DeviceGuard d(g->dev);
     int rc;
     if ((rc = sync_all(g))) return rc;
-    GCK(cudaDeviceSynchronize());
+    GB_CK(cudaDeviceSynchronize());
     return check_err(g);
 }
 
 int conv_group_get_info(const conv_group* g, conv_group_info* out) {
-    if (!g || !out) return gset(CONV_E_INVAL, "null argument");
+    if (!g || !out) return fail(CONV_E_INVAL, "null argument");
     std::memset(out, 0, sizeof(*out));
     const GroupPlan& p = g->plan;
     out->block = g->B;
@@ -533,24 +506,24 @@ int conv_group_get_info(const conv_group* g, conv_group_info* out) {
 int conv_group_plan_check(int precision, int block, int n_in, int n_out, long long taps, int sessions, int num_sms,
                           const conv_group_tiling* tiling) {
     const int prec = to_prec(precision);
-    if (prec < 0) return gset(CONV_E_INVAL, "unknown precision %d", precision);
+    if (prec < 0) return fail(CONV_E_INVAL, "unknown precision %d", precision);
     GroupPlan p{};
     if (const char* why = plan_group(prec, block, n_in, n_out, taps, sessions, num_sms, &p, from_api(tiling)))
-        return gset(CONV_E_INVAL, "%s", why);
-    if (const char* why = check_group_plan(p)) return gset(CONV_E_INVAL, "%s", why);
+        return fail(CONV_E_INVAL, "%s", why);
+    if (const char* why = check_group_plan(p)) return fail(CONV_E_INVAL, "%s", why);
     return CONV_OK;
 }
 
 int conv_group_profile_enable(conv_group* g, int enable) {
-    if (!g) return gset(CONV_E_INVAL, "null handle");
-    GDev d(g->dev);
+    if (!g) return fail(CONV_E_INVAL, "null handle");
+    DeviceGuard d(g->dev);
     g->prof = enable > 0;
     if (g->prof) {
         const size_t want = enable > 1 ? (size_t)enable : 4096;
         while (g->ev0.size() < want) {
             cudaEvent_t a, b;
-            GCK(cudaEventCreate(&a));
-            GCK(cudaEventCreate(&b));
+            GB_CK(cudaEventCreate(&a));
+            GB_CK(cudaEventCreate(&b));
             g->ev0.push_back(a);
             g->ev1.push_back(b);
         }
@@ -560,14 +533,14 @@ int conv_group_profile_enable(conv_group* g, int enable) {
 }
 
 int conv_group_profile_read(conv_group* g, double* total_ms, long long* launches) {
-    if (!g || !total_ms || !launches) return gset(CONV_E_INVAL, "null argument");
-    GDev d(g->dev);
+    if (!g || !total_ms || !launches) return fail(CONV_E_INVAL, "null argument");
+    DeviceGuard d(g->dev);
     int rc;
     if ((rc = sync_all(g))) return rc;
     double tot = 0.0;
     for (size_t i = 0; i < g->ev_used; ++i) {
         float ms = 0.0f;
-        GCK(cudaEventElapsedTime(&ms, g->ev0[i], g->ev1[i]));
+        GB_CK(cudaEventElapsedTime(&ms, g->ev0[i], g->ev1[i]));
         tot += ms;
     }
     *total_ms = tot;
