@@ -51,7 +51,8 @@ struct conv_group {
     float* win = nullptr;
     float2* partial[2] = {nullptr, nullptr};  // tail partials by block parity
     float2* tw = nullptr;
-    float *d_in = nullptr, *d_out = nullptr, *h_in = nullptr, *h_out = nullptr;
+    float *h_in = nullptr, *h_out = nullptr;  // mapped pinned host staging of conv_group_process
+    float *m_in = nullptr, *m_out = nullptr;  // their device addresses
     float *d_cin = nullptr, *d_cout = nullptr;  // conv_group_process_blocks chunk buffers
     long long chunk_cap = 0;
     int io_stride = 0;  // row pitch of the input and output of the block being enqueued (0: block)
@@ -86,7 +87,7 @@ void group_free(conv_group* g) {
     for (int i = 0; i < 2; ++i)
         if (g->bg[i]) cudaStreamSynchronize(g->bg[i]);
     for (void* p : {g->H, g->X, (void*)g->sH, (void*)g->win, (void*)g->partial[0], (void*)g->partial[1], (void*)g->tw,
-                    (void*)g->d_in, (void*)g->d_out, (void*)g->d_cin, (void*)g->d_cout})
+                    (void*)g->d_cin, (void*)g->d_cout})
         if (p) cudaFree(p);
     if (g->h_in) cudaFreeHost(g->h_in);
     if (g->h_out) cudaFreeHost(g->h_out);
@@ -177,12 +178,12 @@ int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, lo
     if ((rc = galloc(g, &g->partial[0], p.partial_bytes))) return rc;
     if ((rc = galloc(g, &g->partial[1], p.partial_bytes))) return rc;
     if ((rc = galloc(g, &g->tw, 2 * (size_t)block * sizeof(float2)))) return rc;
-    if ((rc = galloc(g, &g->d_in, (size_t)sessions * n_in * block * sizeof(float)))) return rc;
-    if ((rc = galloc(g, &g->d_out, (size_t)sessions * n_out * block * sizeof(float)))) return rc;
     GB_CK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_in), (size_t)sessions * n_in * block * sizeof(float),
-                      cudaHostAllocDefault));
+                        cudaHostAllocMapped));
     GB_CK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_out), (size_t)sessions * n_out * block * sizeof(float),
-                      cudaHostAllocDefault));
+                        cudaHostAllocMapped));
+    GB_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&g->m_in), g->h_in, 0));
+    GB_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&g->m_out), g->h_out, 0));
     GB_CK(cudaHostAlloc(reinterpret_cast<void**>(&g->h_err), sizeof(int), cudaHostAllocMapped));
     *g->h_err = 0;
     GB_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&g->d_err), g->h_err, 0));
@@ -405,10 +406,9 @@ int conv_group_process(conv_group* g, const float* in, float* out) {
     const size_t ib = (size_t)g->S * g->n_in * g->B * sizeof(float);
     const size_t ob = (size_t)g->S * g->n_out * g->B * sizeof(float);
     std::memcpy(g->h_in, in, ib);
-    GB_CK(cudaMemcpyAsync(g->d_in, g->h_in, ib, cudaMemcpyHostToDevice, g->stream));
-    int rc = enqueue_group(g, g->d_in, g->d_out, g->stream);
+    // blocks in and out through mapped pinned host memory: no copy launches per block
+    int rc = enqueue_group(g, g->m_in, g->m_out, g->stream);
     if (rc) return rc;
-    GB_CK(cudaMemcpyAsync(g->h_out, g->d_out, ob, cudaMemcpyDeviceToHost, g->stream));
     GB_CK(cudaEventRecord(g->ev_done, g->stream));
     GB_CK(cudaEventSynchronize(g->ev_done));  // the next block's tail keeps running
     if ((rc = check_err(g))) return rc;
