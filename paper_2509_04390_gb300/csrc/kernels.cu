@@ -658,11 +658,13 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
     float2* tws = fsm + 2 * B;
     griddep_launch_dependents();
     load_twiddles(tws, a.tw, B);
-    griddep_wait();
     const size_t stride = (size_t)a.n_dst * B;
     const int S = a.S;
     const int l0 = a.head ? (l / a.LT) * a.LT : 0;
     const int LTt = a.head ? min(a.LT, a.n_dst - l0) : 0, ll = l - l0;
+    // The tail's split partials come from another stream (an event the launch
+    // already waited for), not from the previous kernel: sum them while the
+    // pack kernel may still be running, then wait for it before the head.
     for (int k = tid; k < B; k += nth) {
         const float2* src = a.partial + (size_t)l * B + k;
         float2 tot = make_float2(0.0f, 0.0f);
@@ -675,6 +677,11 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
             tot = cadd(tot, g);
         }
         for (; s < S; ++s) tot = cadd(tot, src[(size_t)s * stride]);
+        P[k] = tot;
+    }
+    griddep_wait();
+    for (int k = tid; k < B; k += nth) {
+        float2 tot = P[k];
         if (a.head) {
             const int kt = k / a.BT, kl = k - kt * a.BT;
             const int n_lt = (a.n_dst + a.LT - 1) / a.LT;
