@@ -834,7 +834,11 @@ def run_serve(args):
     rank, local_rank, world = env_rank()
     torch.cuda.set_device(local_rank)
     pool = serve.FilterPool()
+    peaks, _ = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     sims = [serve.simulate_poisson(p, duration_s=args.serve_seconds, pool=pool) for p in ("fp16", "fp32")]
+    # FP32 with admission by HBM load as well as memory: no deadline misses by construction of the budget
+    sims.append(serve.simulate_poisson("fp32", duration_s=args.serve_seconds, pool=pool, load_frac=0.6, hbm_gbs=hbm))
     caps = [
         serve.capacity("fp16", True, pool=pool),
         serve.capacity("fp32", True, pool=pool),

@@ -3,6 +3,10 @@
 * Admission by device-memory footprint (``conv_footprint``, host-only): a
   session is admitted when its spectra, delay lines and buffers fit in the
   budget; its state then stays resident on the device until it departs.
+* Admission by HBM load (optional): the tail MAC streams every filter
+  spectrum once per block, so a session adds ``tick_bytes`` to every tick;
+  with a load fraction set, a session is admitted only while the sum stays
+  below that fraction of the HBM bandwidth times the tick period.
 * Continuous batching on a fixed tick (128 samples): each tick, the sessions
   whose next block is due (block 128: every tick, block 256: every other
   tick) are processed together, one batched launch per stage.  Sessions that
@@ -26,6 +30,21 @@ from . import signals
 from . import upols as U
 
 BATCH_TILING = {"kernel": "tma", "warps": 8}
+DEFAULT_HBM_GBS = 6704.5  # measured copy bandwidth of the GB300s this was tuned on
+
+
+def tick_bytes(spec, precision, tick=128):
+    """Algorithmic HBM bytes a session adds to each tick on average: every
+    filter spectrum plus the delay-line rows of one output tile, per block
+    ((n_out + 1) n_in K B s, s = bytes per complex value), and the same for
+    the canceller, divided by the ticks per block."""
+    s = 8 if precision in ("fp32", U.CONV_FP32) else 4
+    K = -(-spec.taps // spec.block)
+    per_block = (spec.n_out + 1) * spec.n_in * K * spec.block * s
+    if spec.taps_fb:
+        K_fb = -(-spec.taps_fb // spec.block)
+        per_block += (spec.n_in + 1) * spec.n_out * K_fb * spec.block * s
+    return per_block * tick / spec.block
 
 
 @dataclass
@@ -41,6 +60,7 @@ class Session:
     blocks: int = 0
     outputs: list = field(default_factory=list)
     keep_outputs: bool = False
+    tick_bytes: float = 0.0
 
 
 class FilterPool:
@@ -59,7 +79,8 @@ class FilterPool:
 
 
 class Server:
-    def __init__(self, precision="fp16", budget_bytes=None, tick=128, fs=signals.FS):
+    def __init__(self, precision="fp16", budget_bytes=None, tick=128, fs=signals.FS, load_frac=None,
+                 hbm_gbs=DEFAULT_HBM_GBS):
         import torch
 
         self.torch = torch
@@ -71,6 +92,10 @@ class Server:
             budget_bytes = int(free * 0.85)
         self.budget = int(budget_bytes)
         self.used = 0
+        # HBM load admission: bytes per tick against load_frac of the bandwidth
+        self.load_cap = None if load_frac is None else load_frac * hbm_gbs * 1e9 * tick / fs
+        self.load = 0.0
+        self.rejected_load = 0
         self.batch = U.Batch(precision)
         self.sessions: list[Session] = []  # batch order
         self.tick_index = 0
@@ -89,6 +114,10 @@ class Server:
         if self.used + fp > self.budget:
             self.rejected += 1
             return None
+        tb = tick_bytes(spec, self.precision, self.tick)
+        if self.load_cap is not None and self.load + tb > self.load_cap:
+            self.rejected_load += 1
+            return None
         eng = U.Engine(self.fs, spec.block, spec.n_in, spec.n_out, spec.taps, self.precision, BATCH_TILING)
         eng.set_filters(filters)
         if spec.taps_fb:
@@ -105,6 +134,8 @@ class Server:
         self.batch.add(eng)
         self.sessions.append(s)
         self.used += fp
+        self.load += tb
+        s.tick_bytes = tb
         return s
 
     def depart(self, s):
@@ -112,6 +143,7 @@ class Server:
         self.sessions.remove(s)
         s.eng.close()
         self.used -= s.footprint
+        self.load -= s.tick_bytes
 
     def close(self):
         for s in list(self.sessions):
@@ -201,13 +233,13 @@ def percentiles(lat_s):
 
 
 def simulate_poisson(precision="fp16", duration_s=20.0, rate=4.0, life=(5.0, 60.0), seed=5, budget_bytes=None,
-                     pool=None):
+                     pool=None, load_frac=None, hbm_gbs=DEFAULT_HBM_GBS):
     """Poisson arrivals of serving sessions; ticks run back to back (simulated
     time advances one tick per iteration).  Set-up time of arriving sessions is
     kept out of the tick latencies."""
     rng = np.random.default_rng(seed)
     pool = pool or FilterPool()
-    srv = Server(precision, budget_bytes)
+    srv = Server(precision, budget_bytes, load_frac=load_frac, hbm_gbs=hbm_gbs)
     period = srv.tick / srv.fs
     n_ticks = int(duration_s / period)
     t_next = rng.exponential(1.0 / rate)
@@ -245,6 +277,8 @@ def simulate_poisson(precision="fp16", duration_s=20.0, rate=4.0, life=(5.0, 60.
         "arrivals": k,
         "admitted": srv.next_sid,
         "rejected_by_memory": srv.rejected,
+        "rejected_by_load": srv.rejected_load,
+        "load_frac": load_frac,
         "active_sessions": {"mean": float(np.mean(active)), "max": int(np.max(active))},
         "budget_gb": srv.budget / 1e9,
         "throughput_gtapch_s": work / busy / 1e9 if busy else None,
