@@ -321,3 +321,23 @@ def test_closed_loop_does_not_drift(precision, bound):
     print(f"drift {precision}: first {snrs[0]:.1f} dB, last {snrs[-1]:.1f} dB, min {min(snrs):.1f} dB")
     assert min(snrs) >= bound
     assert snrs[-1] >= snrs[0] - 3.0
+
+
+# ------------------------------------------------------------ channel extremes
+
+
+@pytest.mark.parametrize(
+    "n_in,n_out,taps,B,nb,precision,bound",
+    [
+        (2, 1024, 300, 64, 12, "fp32", FP32_DB),  # the largest output count: 64 output tiles
+        (1024, 2, 300, 64, 12, "fp32", FP32_DB),  # the largest input count: 1024 pack CTAs, R = 5120
+        (3, 5, 20000, 4096, 8, "fp16", FP16_DB),  # the largest block with several partitions
+    ],
+)
+def test_channel_and_block_extremes(n_in, n_out, taps, B, nb, precision, bound):
+    w = signals.random_case(60 + n_in + n_out, n_in, n_out, taps, B, nb)
+    y = run_gpu(w, precision)
+    ref = oracle_out(w)
+    s = snr_db(y, ref)
+    print(f"extremes {n_in}x{n_out} taps={taps} B={B} {precision}: {s:.1f} dB")
+    assert s >= bound
