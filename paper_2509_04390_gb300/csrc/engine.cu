@@ -782,7 +782,7 @@ int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t 
 // the delay line as it is (loudspeaker spectra up to block n-1), then the
 // canceller's tail for block n with the updated spectra.  Runs on the
 // high-priority stream e->as beside the synthesis output.
-int enqueue_adapt(conv_engine* e, const float* d_err_block, cudaStream_t s) {
+int enqueue_adapt(conv_engine* e, const float* d_err_block) {
     Part& F = e->fb;
     const MacPlan& p = F.plan;
     const long long n = e->nblk;
@@ -825,7 +825,6 @@ int enqueue_adapt(conv_engine* e, const float* d_err_block, cudaStream_t s) {
     int rc = enqueue_tail(e, F, n, e->as, false);
     if (rc) return rc;
     CK(cudaEventRecord(F.ev_tail[n & 1], e->as));
-    (void)s;
     return CONV_OK;
 }
 
@@ -846,7 +845,7 @@ int enqueue_afc_synthesis(conv_engine* e, const float* d_mic, float* d_out, floa
     int rc;
     if ((rc = enqueue_pack(e, P, d_mic, e->B, e->d_c, eb, s))) return rc;
     CK(cudaEventRecord(P.ev_packed, s));
-    if ((rc = enqueue_adapt(e, eb, s))) return rc;
+    if ((rc = enqueue_adapt(e, eb))) return rc;
     CK(cudaStreamWaitEvent(s, P.ev_tail[n & 1], 0));
     if ((rc = enqueue_out(e, P, n, d_out, s))) return rc;
     cudaStream_t bg = e->bg[(n + 1) & 1];
