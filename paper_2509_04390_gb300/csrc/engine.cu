@@ -377,7 +377,10 @@ struct conv_engine {
     int prec = CONV_FP32;
     int num_sms = 0;
     cudaStream_t stream = nullptr;     // the engine's own stream for host-buffer calls
-    cudaStream_t bg[2] = {nullptr, nullptr};  // low-priority streams for the tail MACs, by block parity
+    // low-priority streams for the tail MACs, by block parity: [0], [1] the
+    // synthesis, [2], [3] the canceller (so a canceller tail never queues
+    // behind the much longer synthesis tail of the same block)
+    cudaStream_t bg[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_done = nullptr;     // output of the current host-buffer call is on the host
     float2* tw = nullptr;
     float *d_e = nullptr, *d_c = nullptr;
@@ -688,7 +691,7 @@ int enqueue_conv(conv_engine* e, Part& P, const float* src, const float* sub, fl
     CK(cudaEventRecord(P.ev_packed, s));
     CK(cudaStreamWaitEvent(s, P.ev_tail[n & 1], 0));
     if ((rc = enqueue_out(e, P, n, out, s))) return rc;
-    cudaStream_t bg = e->bg[(n + 1) & 1];
+    cudaStream_t bg = e->bg[(&P == &e->fb ? 2 : 0) + ((n + 1) & 1)];
     CK(cudaStreamWaitEvent(bg, P.ev_packed, 0));
     // kernel timing needs each tail alone on the GPU: then tails run one after another
     if (timed && e->prof) CK(cudaStreamWaitEvent(bg, P.ev_tail[n & 1], 0));
@@ -712,8 +715,7 @@ int check_dev_err(conv_engine* e) {
 
 int engine_reset(conv_engine* e) {
     int rc;
-    CK(cudaStreamSynchronize(e->bg[0]));
-    CK(cudaStreamSynchronize(e->bg[1]));
+    for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
     if (e->as) CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
     if ((rc = part_reset(e, e->syn))) return rc;
@@ -888,7 +890,7 @@ void engine_free(conv_engine* e) {
     dev_free(e, &e->d_far_out[0], 0);
     dev_free(e, &e->d_far_out[1], 0);
     if (e->stream) cudaStreamSynchronize(e->stream);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
         if (e->bg[i]) cudaStreamSynchronize(e->bg[i]);
     if (e->as) cudaStreamSynchronize(e->as);
     for (Part* P : {&e->syn, &e->fb}) {
@@ -912,7 +914,7 @@ void engine_free(conv_engine* e) {
     for (auto ev : e->ev0) cudaEventDestroy(ev);
     for (auto ev : e->ev1) cudaEventDestroy(ev);
     if (e->ev_done) cudaEventDestroy(e->ev_done);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
         if (e->bg[i]) cudaStreamDestroy(e->bg[i]);
     if (e->stream) cudaStreamDestroy(e->stream);
     delete e;
@@ -940,7 +942,7 @@ int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long 
     int prio_low = 0, prio_high = 0;
     CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
     CK(cudaStreamCreateWithPriority(&e->stream, cudaStreamNonBlocking, prio_high));
-    for (int i = 0; i < 2; ++i) CK(cudaStreamCreateWithPriority(&e->bg[i], cudaStreamNonBlocking, prio_low));
+    for (int i = 0; i < 4; ++i) CK(cudaStreamCreateWithPriority(&e->bg[i], cudaStreamNonBlocking, prio_low));
     // spin-wait on completion: a blocking wait would add the host's wake-up latency to every block
     CK(cudaEventCreateWithFlags(&e->ev_done, cudaEventDisableTiming));
     // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once to FP32
@@ -1231,8 +1233,7 @@ int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta) {
         CK(cudaMemsetAsync(e->d_pow, 0, 2 * (size_t)e->B * sizeof(float2), e->stream));
     }
     if (!e->d_G && (rc = dev_alloc(e, &e->d_G, (size_t)e->n_in * e->B * sizeof(float2)))) return rc;
-    CK(cudaStreamSynchronize(e->bg[0]));
-    CK(cudaStreamSynchronize(e->bg[1]));
+    for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
     CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
     const bool was = e->adapt;
@@ -1254,8 +1255,7 @@ int afc_get_path_spectra(conv_engine* e, float* f_spec) {
     if (!e->fb.ready) return set_err(CONV_E_STATE, "feedback paths not set");
     if (e->prec != CONV_FP32) return set_err(CONV_E_STATE, "path spectra are read back from FP32 engines only");
     DeviceGuard g(e->dev);
-    CK(cudaStreamSynchronize(e->bg[0]));
-    CK(cudaStreamSynchronize(e->bg[1]));
+    for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
     if (e->as) CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
     const Part& F = e->fb;
@@ -1292,8 +1292,7 @@ int conv_synchronize(conv_engine* e) {
         const int rc = conv_synchronize(e->far);
         if (rc) return rc;
     }
-    CK(cudaStreamSynchronize(e->bg[0]));
-    CK(cudaStreamSynchronize(e->bg[1]));
+    for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
     if (e->as) CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
     CK(cudaDeviceSynchronize());
@@ -1513,8 +1512,7 @@ int conv_batch_add(conv_batch* b, conv_engine* e) {
     int rc;
     if ((rc = batch_sync(b))) return rc;
     // the session's own streams may still run its last tail: let it finish
-    CK(cudaStreamSynchronize(e->bg[0]));
-    CK(cudaStreamSynchronize(e->bg[1]));
+    for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
     CK(cudaStreamSynchronize(e->stream));
     b->sessions.push_back(e);
     ++e->in_batches;
