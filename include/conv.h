@@ -40,8 +40,9 @@ extern "C" {
 
 /* storage precision of the filter and delay-line spectra (conv_set_precision) */
 #define CONV_FP32 0 /* complex float32                                             */
-#define CONV_FP16 1 /* complex float16, power-of-two scale per partition, FP32 MAC */
-#define CONV_BF16 2 /* complex bfloat16, same scaling, FP32 MAC                    */
+#define CONV_FP16 1 /* complex float16 with power-of-two scales per (output tile,
+                       partition) and per delay-line slot; FP32 FFTs and MAC     */
+#define CONV_BF16 2 /* complex bfloat16, same scaling, FP32 FFTs and MAC           */
 
 typedef struct conv_engine conv_engine; /* opaque; owns all device state */
 
@@ -52,11 +53,13 @@ typedef struct conv_info {
     long long n_in;           /* inputs (microphones)                             */
     long long n_out;          /* outputs (loudspeakers)                           */
     long long taps;           /* n_h of the synthesis filters                     */
-    long long K;              /* synthesis partitions, ceil(taps / block)         */
+    long long K;              /* synthesis partitions of `block` taps: ceil(taps / block),
+                                 or far_block / block with a far block          */
     long long taps_fb;        /* feedback-path length, 0 if none                  */
     long long K_fb;           /* feedback partitions, 0 if none                   */
     long long precision;      /* CONV_FP32 / CONV_FP16 / CONV_BF16                */
-    long long mac_bytes;      /* synthesis FDL MAC: filters + delay line + partials */
+    long long mac_bytes;      /* synthesis tail MAC (partitions 1..K-1): filter
+                                 spectra + delay-line rows, each read once      */
     long long mac_fb_bytes;   /* feedback FDL MAC, 0 if none                      */
     long long mac_ctas;       /* CTAs of one synthesis MAC launch                 */
     long long mac_splits;     /* partition splits per output tile                 */
@@ -152,8 +155,10 @@ conv_engine* conv_far_engine(conv_engine* e);
 int afc_set_paths(conv_engine* e, const float* f, long long taps_fb);
 
 /* Process one block, host buffers: in[n_in][block] -> out[n_out][block].
- * Copies in, runs the path on the engine's stream, copies out, and returns
- * when out is written.  Needs conv_set_filters (CONV_E_STATE otherwise). */
+ * The block goes through the engine's mapped pinned host buffers, which the
+ * pack kernel reads and the output kernel writes directly (no copy launches);
+ * returns when out is written.  The next block's tail MAC keeps running in
+ * the background.  Needs conv_set_filters (CONV_E_STATE otherwise). */
 int conv_process_block(conv_engine* e, const float* in, float* out);
 
 /* n_blocks consecutive blocks from host buffers in one call (offline
