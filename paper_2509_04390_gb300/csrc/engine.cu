@@ -650,6 +650,7 @@ OutArgs out_args(conv_engine* e, Part& P, long long blk, float* out) {
         a.extra = e->addend;
         a.extra_stride = e->addend_stride;
     }
+    a.early_partials = 1;  // every schedule waits for the tail's event before the output launch
     return a;
 }
 
@@ -661,12 +662,12 @@ int enqueue_pack(conv_engine* e, Part& P, const float* src, int stride, const fl
 
 // Tail MAC for block `blk`: partitions 1..K-1, into the partial buffer of the
 // block's parity.
-int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool timed) {
+int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool timed, bool pdl = true) {
     const MacPlan& p = P.plan;
     if (p.S == 0) return CONV_OK;  // K = 1: no tail
     const bool rec = timed && e->prof && e->ev_used < e->ev0.size();
     if (rec) CK(cudaEventRecord(e->ev0[e->ev_used], s));
-    CK(launch_fdl_mac(e->prec, p, tail_args(e, P, blk), s));
+    CK(launch_fdl_mac(e->prec, p, tail_args(e, P, blk), s, pdl));
     if (rec) {
         CK(cudaEventRecord(e->ev1[e->ev_used], s));
         ++e->ev_used;
@@ -824,7 +825,8 @@ int enqueue_adapt(conv_engine* e, const float* d_err_block) {
     u.tile_elems = p.tile_elems;
     CK(launch_nlms_update(u, e->as));
     CK(cudaEventRecord(e->ev_upd, e->as));
-    int rc = enqueue_tail(e, F, n, e->as, false);
+    // no early start: the MAC would stream the spectra the update is writing
+    int rc = enqueue_tail(e, F, n, e->as, false, false);
     if (rc) return rc;
     CK(cudaEventRecord(F.ev_tail[n & 1], e->as));
     return CONV_OK;

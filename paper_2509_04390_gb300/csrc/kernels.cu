@@ -662,9 +662,10 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
     const int S = a.S;
     const int l0 = a.head ? (l / a.LT) * a.LT : 0;
     const int LTt = a.head ? min(a.LT, a.n_dst - l0) : 0, ll = l - l0;
-    // The tail's split partials come from another stream (an event the launch
-    // already waited for), not from the previous kernel: sum them while the
-    // pack kernel may still be running, then wait for it before the head.
+    // The engine's tail partials come from another stream (an event the
+    // launch already waited for), not from the previous kernel: sum them while
+    // the pack kernel may still be running, then wait for it before the head.
+    if (!a.early_partials) griddep_wait();
     for (int k = tid; k < B; k += nth) {
         const float2* src = a.partial + (size_t)l * B + k;
         float2 tot = make_float2(0.0f, 0.0f);
@@ -775,7 +776,8 @@ namespace {
 // the previous kernel in the stream finishes; it orders itself with
 // griddepcontrol.wait before touching anything that kernel produces.
 template <typename Kern, typename Arg>
-cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const Arg& arg) {
+cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const Arg& arg,
+                       bool pdl = true) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -783,7 +785,7 @@ cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, arg);
@@ -864,34 +866,38 @@ cudaError_t launch_tile_scales(int prec, const float* maxabs, float* sH, int n_d
 }
 
 template <int NW>
-cudaError_t launch_fdl_mac_nw(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
+cudaError_t launch_fdl_mac_nw(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s, bool pdl) {
     const dim3 grid(p.ctas), block((NW + 1) * 32);
     switch (prec) {
-        case PREC_FP32: return launch_pdl(k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>(), NW>, grid, block, p.smem, s, a);
-        case PREC_FP16: return launch_pdl(k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>(), NW>, grid, block, p.smem, s, a);
-        case PREC_BF16: return launch_pdl(k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>(), NW>, grid, block, p.smem, s, a);
+        case PREC_FP32:
+            return launch_pdl(k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>(), NW>, grid, block, p.smem, s, a, pdl);
+        case PREC_FP16:
+            return launch_pdl(k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>(), NW>, grid, block, p.smem, s, a, pdl);
+        case PREC_BF16:
+            return launch_pdl(k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>(), NW>, grid, block, p.smem, s, a, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int U, int MINB>
-cudaError_t launch_fdl_mac_direct_u(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
+cudaError_t launch_fdl_mac_direct_u(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s, bool pdl) {
     const dim3 grid(p.ctas), block(8 * 32);
     switch (prec) {
-        case PREC_FP32: return launch_pdl(k_fdl_mac_ldg<PREC_FP32, 4, 8, U, MINB>, grid, block, p.smem, s, a);
+        case PREC_FP32: return launch_pdl(k_fdl_mac_ldg<PREC_FP32, 4, 8, U, MINB>, grid, block, p.smem, s, a, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_fdl_mac_direct(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
-    return p.direct == 1 ? launch_fdl_mac_direct_u<1, 3>(prec, p, a, s) : launch_fdl_mac_direct_u<2, 2>(prec, p, a, s);
+cudaError_t launch_fdl_mac_direct(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s, bool pdl) {
+    return p.direct == 1 ? launch_fdl_mac_direct_u<1, 3>(prec, p, a, s, pdl)
+                         : launch_fdl_mac_direct_u<2, 2>(prec, p, a, s, pdl);
 }
 
-cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s) {
-    if (p.direct) return launch_fdl_mac_direct(prec, p, a, s);
+cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s, bool pdl) {
+    if (p.direct) return launch_fdl_mac_direct(prec, p, a, s, pdl);
     switch (p.nw) {
-        case 8: return launch_fdl_mac_nw<8>(prec, p, a, s);
-        case 16: return launch_fdl_mac_nw<16>(prec, p, a, s);
+        case 8: return launch_fdl_mac_nw<8>(prec, p, a, s, pdl);
+        case 16: return launch_fdl_mac_nw<16>(prec, p, a, s, pdl);
         default: return cudaErrorInvalidValue;
     }
 }

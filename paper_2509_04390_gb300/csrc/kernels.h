@@ -123,6 +123,10 @@ struct OutArgs {
     // added to the output after the overlap-save discard ([n_dst][extra_stride]), or null
     const float* extra;
     int extra_stride;
+    // 1: the partials come from another stream, complete before this launch, so
+    // they are summed before waiting for the previous kernel in the stream;
+    // 0: the previous kernel may be writing them
+    int early_partials;
 };
 
 // One CTA of a batched launch: which session's arguments (items[item]), and
@@ -146,7 +150,10 @@ cudaError_t prepare_kernels(size_t mac_smem);
 cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s);
 cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s);
 cudaError_t launch_tile_scales(int prec, const float* maxabs, float* sH, int n_dst, int R, int LT, cudaStream_t s);
-cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s);
+// pdl: programmatic dependent launch after the previous kernel in the stream.
+// The MAC streams its first filter stages before waiting for that kernel, so
+// pass false when the previous kernel writes the filter spectra.
+cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s, bool pdl = true);
 cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s);
 cudaError_t launch_pack_batch(int prec, const PackArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);
 cudaError_t launch_out_batch(int prec, const OutArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);

@@ -187,7 +187,8 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     a.xoff = p.xoff;
     a.tile_elems = p.tile_elems;
     a.err = nullptr;
-    e = launch_fdl_mac(PREC_FP32, p, a, s);
+    // no early start: the caller's previous kernel may be writing d_H
+    e = launch_fdl_mac(PREC_FP32, p, a, s, false);
     if (e != cudaSuccess) return fail(CONV_E_CUDA, "MAC launch", e);
 
     int log2B = 0;
