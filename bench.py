@@ -232,6 +232,52 @@ def time_oracle(w, budget_s: float, max_blocks: int | None = None, n_sub: int | 
     return value, per_block, b, n_sub
 
 
+def _oracle_worker(args):
+    """One process of the all-cores oracle timing: UPOLS of one output slice."""
+    h, x, B, n_blocks = args
+    from oracle import UpolsOracle
+
+    eng = UpolsOracle(h, B)
+    nb_avail = x.shape[1] // B
+    eng.process_block(x[:, :B])  # warm-up
+    times = []
+    for b in range(1, n_blocks + 1):
+        xb = x[:, (b % nb_avail) * B : (b % nb_avail + 1) * B]
+        t0 = time.perf_counter()
+        eng.process_block(xb)
+        times.append(time.perf_counter() - t0)
+    return statistics.median(times)
+
+
+def time_oracle_all_cores(w, budget_s: float, per_block_1: float):
+    """The same oracle on every host core: the outputs split into one slice per
+    process (spawned, so nothing inherits the CUDA context), all processes
+    running the same blocks at once; the block time is the slowest slice's."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    workers = max(1, min(cores, w.n_out))
+    bounds = [round(i * w.n_out / workers) for i in range(workers + 1)]
+    slices = [np.ascontiguousarray(w.h[bounds[i] : bounds[i + 1]]) for i in range(workers)]
+    x = np.ascontiguousarray(w.x[:, : min(w.x.shape[1], 64 * w.block)])
+    # blocks per process: the single-thread time per output scaled to the slice, within the budget
+    per_out = per_block_1 / w.n_out
+    n_blocks = int(max(3, min(200, budget_s / max(per_out * (bounds[1] - bounds[0]), 1e-6))))
+    env_before = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            per = pool.map(_oracle_worker, [(h, x, w.block, n_blocks) for h in slices])
+    finally:
+        if env_before is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = env_before
+    per_block = max(per)
+    value = float(w.n_in) * w.n_out * w.taps * w.block / per_block / 1e9
+    return value, per_block, n_blocks, workers
+
+
 # ------------------------------------------------------------------- arms
 
 
@@ -478,6 +524,16 @@ def run_ours(args):
             "sample": f"{nblk} blocks of {B} on all {n_sub} outputs, FP64 numpy oracle, single thread "
                       f"(median {per_block * 1e3:.1f} ms per block)",
         }
+        if args.cpu_all_cores:
+            av, apb, anb, aw = time_oracle_all_cores(w, args.cpu_budget / 2, per_block)
+            cpu["all_cores"] = {
+                "value": av,
+                "unit": UNIT,
+                "cores": aw,
+                "kind": "oracle",
+                "sample": f"{anb} blocks of {B}, the 16 outputs split over {aw} spawned processes, same FP64 "
+                          f"oracle (slowest slice {apb * 1e3:.1f} ms per block)",
+            }
 
     clk = clocks.summary(tw0, tw1)
     if rank == 0:
@@ -882,6 +938,8 @@ def parse(argv=None):
     ap.add_argument("--e2e-chunk", type=int, default=64, help="blocks per conv_process_blocks call in the e2e figure")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-all-cores", type=int, default=1,
+                    help="also time the oracle on all host cores (one output slice per process); 0 to skip")
     ap.add_argument("--batch", type=int, default=0, help="time N heterogeneous sessions in one batch instead")
     ap.add_argument("--batch-seed", type=int, default=4)
     ap.add_argument("--serve", action="store_true", help="run the serving-loop simulation instead")
