@@ -172,7 +172,9 @@ int conv_process_blocks(conv_engine* e, const float* in, float* out, long long n
 
 /* Same as conv_process_block with device pointers d_in[n_in][block] and
  * d_out[n_out][block], enqueued on `cuda_stream` (a cudaStream_t; NULL = the
- * legacy default stream).  Returns once the work is enqueued. */
+ * legacy default stream).  Returns once the work is enqueued.  Blocks of one
+ * engine form a chain: a block enqueued on another stream than the previous
+ * block (or after a host-buffer call) first waits for that stream's work. */
 int conv_process_block_async(conv_engine* e, const float* d_in, float* d_out, void* cuda_stream);
 
 /* One block of synthesis with feedback cancellation, host buffers:

@@ -382,6 +382,9 @@ struct conv_engine {
     // behind the much longer synthesis tail of the same block)
     cudaStream_t bg[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_done = nullptr;     // output of the current host-buffer call is on the host
+    cudaEvent_t ev_handoff = nullptr;  // orders a block after the previous one enqueued on another stream
+    cudaStream_t last_stream = nullptr;
+    bool has_last = false;
     float2* tw = nullptr;
     float *d_e = nullptr, *d_c = nullptr;
     float *h_in = nullptr, *h_out = nullptr, *h_e = nullptr;
@@ -716,6 +719,7 @@ int check_dev_err(conv_engine* e) {
 
 int engine_reset(conv_engine* e) {
     int rc;
+    if (e->has_last) CK(cudaStreamSynchronize(e->last_stream));  // blocks enqueued on a caller's stream
     for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
     if (e->as) CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
@@ -731,6 +735,7 @@ int engine_reset(conv_engine* e) {
     }
     CK(cudaStreamSynchronize(e->stream));
     e->nblk = 0;
+    e->has_last = false;
     return CONV_OK;
 }
 
@@ -766,7 +771,21 @@ int far_after(conv_engine* e, const float* src, cudaStream_t s) {
     return CONV_OK;
 }
 
+// Blocks of one engine are a chain (window, ring, partials): a block enqueued on
+// another stream than the previous one first waits for everything the
+// previous stream holds.
+int stream_handoff(conv_engine* e, cudaStream_t s) {
+    if (e->has_last && s != e->last_stream) {
+        CK(cudaEventRecord(e->ev_handoff, e->last_stream));
+        CK(cudaStreamWaitEvent(s, e->ev_handoff, 0));
+    }
+    e->last_stream = s;
+    e->has_last = true;
+    return CONV_OK;
+}
+
 int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t s) {
+    if (int rc = stream_handoff(e, s)) return rc;
     far_before(e);
     float* acc = nullptr;
     if (e->far) {  // the pack appends the input block to the far engine's next input directly
@@ -836,6 +855,7 @@ int enqueue_adapt(conv_engine* e, const float* d_err_block) {
 // (first half), then c = F_hat * l, kept for the next block (second half).
 // The host-buffer call copies l and e out between the halves.
 int enqueue_afc_synthesis(conv_engine* e, const float* d_mic, float* d_out, float* d_e, cudaStream_t s) {
+    if (int rc = stream_handoff(e, s)) return rc;
     if (!e->adapt) {
         float* eb = (d_e || !e->far) ? d_e : e->d_e;  // the far engine's input is the error signal
         far_before(e);
@@ -916,6 +936,7 @@ void engine_free(conv_engine* e) {
     for (auto ev : e->ev0) cudaEventDestroy(ev);
     for (auto ev : e->ev1) cudaEventDestroy(ev);
     if (e->ev_done) cudaEventDestroy(e->ev_done);
+    if (e->ev_handoff) cudaEventDestroy(e->ev_handoff);
     for (int i = 0; i < 4; ++i)
         if (e->bg[i]) cudaStreamDestroy(e->bg[i]);
     if (e->stream) cudaStreamDestroy(e->stream);
@@ -947,6 +968,7 @@ int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long 
     for (int i = 0; i < 4; ++i) CK(cudaStreamCreateWithPriority(&e->bg[i], cudaStreamNonBlocking, prio_low));
     // spin-wait on completion: a blocking wait would add the host's wake-up latency to every block
     CK(cudaEventCreateWithFlags(&e->ev_done, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&e->ev_handoff, cudaEventDisableTiming));
     // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once to FP32
     std::vector<float2> tw(2 * (size_t)block);
     const double pi = 3.14159265358979323846264338327950288;

@@ -44,6 +44,9 @@ struct conv_group {
     cudaStream_t bg[2] = {nullptr, nullptr};
     cudaEvent_t ev_done = nullptr;
     cudaEvent_t ev_packed = nullptr;
+    cudaEvent_t ev_handoff = nullptr;  // orders a block after the previous one enqueued on another stream
+    cudaStream_t last_stream = nullptr;
+    bool has_last = false;
     cudaEvent_t ev_tail[2] = {nullptr, nullptr};
     void* H = nullptr;
     void* X = nullptr;
@@ -96,6 +99,7 @@ void group_free(conv_group* g) {
     for (auto ev : g->ev1) cudaEventDestroy(ev);
     if (g->ev_done) cudaEventDestroy(g->ev_done);
     if (g->ev_packed) cudaEventDestroy(g->ev_packed);
+    if (g->ev_handoff) cudaEventDestroy(g->ev_handoff);
     for (int i = 0; i < 2; ++i) {
         if (g->ev_tail[i]) cudaEventDestroy(g->ev_tail[i]);
         if (g->bg[i]) cudaStreamDestroy(g->bg[i]);
@@ -116,6 +120,7 @@ int sync_all(conv_group* g) {
 
 int group_reset_impl(conv_group* g) {
     int rc;
+    if (g->has_last) GB_CK(cudaStreamSynchronize(g->last_stream));  // blocks enqueued on a caller's stream
     if ((rc = sync_all(g))) return rc;
     const GroupPlan& p = g->plan;
     GB_CK(cudaMemsetAsync(g->X, 0, p.x_bytes, g->stream));
@@ -126,6 +131,7 @@ int group_reset_impl(conv_group* g) {
     }
     GB_CK(cudaStreamSynchronize(g->stream));
     g->nblk = 0;
+    g->has_last = false;
     return CONV_OK;
 }
 
@@ -195,6 +201,7 @@ int create_impl(conv_group* g, int precision, int block, int n_in, int n_out, lo
         GB_CK(cudaEventCreateWithFlags(&g->ev_tail[i], cudaEventDisableTiming));
     }
     GB_CK(cudaEventCreateWithFlags(&g->ev_packed, cudaEventDisableTiming));
+    GB_CK(cudaEventCreateWithFlags(&g->ev_handoff, cudaEventDisableTiming));
     GB_CK(cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming));
     // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once
     std::vector<float2> tw(2 * (size_t)block);
@@ -256,6 +263,14 @@ int enqueue_tail(conv_group* g, long long blk, cudaStream_t s) {
 }
 
 int enqueue_group(conv_group* g, const float* d_in, float* d_out, cudaStream_t s) {
+    // blocks of a group are a chain: a block on another stream than the
+    // previous one first waits for that stream
+    if (g->has_last && s != g->last_stream) {
+        GB_CK(cudaEventRecord(g->ev_handoff, g->last_stream));
+        GB_CK(cudaStreamWaitEvent(s, g->ev_handoff, 0));
+    }
+    g->last_stream = s;
+    g->has_last = true;
     const GroupPlan& p = g->plan;
     const long long n = g->nblk;
     const int slot0 = slot0_of(n, p.KR);

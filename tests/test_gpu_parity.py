@@ -341,3 +341,32 @@ def test_channel_and_block_extremes(n_in, n_out, taps, B, nb, precision, bound):
     s = snr_db(y, ref)
     print(f"extremes {n_in}x{n_out} taps={taps} B={B} {precision}: {s:.1f} dB")
     assert s >= bound
+
+
+def test_blocks_on_alternating_streams_keep_the_chain():
+    """Blocks enqueued on two caller streams in turn, with host-buffer calls in
+    between, give exactly the single-stream result (each block waits for the
+    stream of the block before)."""
+    torch = pytest.importorskip("torch")
+    w = signals.random_case(88, 3, 5, 4000, 64, 36)
+    B, nb = w.block, w.x.shape[1] // w.block
+    ref = run_gpu(w)
+    d_blocks = torch.from_numpy(w.x).cuda().reshape(w.n_in, nb, B).permute(1, 0, 2).contiguous()
+    d_y = torch.zeros((nb, w.n_out, B), dtype=torch.float32, device="cuda")
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    y = np.empty((w.n_out, nb * B), np.float32)
+    with U.Engine(w.fs, B, w.n_in, w.n_out, w.taps) as e:
+        e.set_filters(w.h)
+        for b in range(nb):
+            if b % 3 == 2:
+                y[:, b * B : (b + 1) * B] = e.process(np.ascontiguousarray(w.x[:, b * B : (b + 1) * B]))
+            else:
+                U.conv_process_block_async(e.h, d_blocks[b], d_y[b], streams[b % 2])
+        U.conv_synchronize(e.h)
+        torch.cuda.synchronize()
+    dev = d_y.cpu().numpy()
+    for b in range(nb):
+        if b % 3 != 2:
+            y[:, b * B : (b + 1) * B] = dev[b]
+    assert np.array_equal(y, ref)
