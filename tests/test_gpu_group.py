@@ -176,3 +176,19 @@ def test_unsupported_shapes_are_rejected():
         with pytest.raises(U.ConvError) as ei:
             g.process(np.zeros((8, 4, 64), np.float32))
         assert ei.value.code == U.CONV_E_STATE
+
+
+def test_fp16_group_saturates_instead_of_overflowing():
+    """Input spectra beyond the FP16 range saturate (the delay line is stored
+    unscaled): outputs stay finite, and BF16 handles the same input."""
+    S, n_in, n_out, taps, B, nb = 8, 4, 16, 500, 256, 6
+    h, x = group_case(12, S, n_in, n_out, taps, B, nb)
+    x = (x * 1.0e4).astype(np.float32)  # |X| up to ~2e5 > 65504
+    with U.Group("fp16", B, n_in, n_out, taps, S) as g:
+        g.set_filters(h)
+        y = g.run(x)
+    assert np.all(np.isfinite(y))
+    with U.Group("bf16", B, n_in, n_out, taps, S) as g:
+        g.set_filters(h)
+        yb = g.run(x)
+    assert min(snr_db(yb[s], upols(h, x[s], B)) for s in range(S)) >= BOUND["bf16"]

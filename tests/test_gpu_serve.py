@@ -92,3 +92,38 @@ def test_admission_respects_the_memory_budget():
     srv.depart(srv.sessions[0])
     assert srv.admit(sp, pool.filters(sp)) is not None  # room again after a departure
     srv.close()
+
+
+@pytest.mark.parametrize(
+    "precision,block,n_in,n_out,taps,taps_fb",
+    [("fp32", 128, 4, 16, 48000, 0), ("fp16", 256, 2, 8, 100000, 24000), ("bf16", 64, 1, 33, 5000, 700)],
+)
+def test_footprint_matches_what_an_engine_holds(precision, block, n_in, n_out, taps, taps_fb):
+    """conv_footprint (host-only, the admission figure) against the device bytes
+    a created engine reports, within the host-side staging it leaves out."""
+    fp = U.conv_footprint(precision, block, n_in, n_out, taps, taps_fb)
+    with U.Engine(48000, block, n_in, n_out, taps, precision) as e:
+        if taps_fb:
+            e.set_paths(np.zeros((n_in, n_out, taps_fb), np.float32))
+        held = e.info()["device_bytes"]
+    print(f"footprint {fp} vs held {held}")
+    assert abs(fp - held) <= max(4096, 0.02 * held)
+
+
+def test_admission_by_hbm_load():
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(6)
+    pool = serve.FilterPool(seed=4, n_out=8, n_in=4, taps=int(0.3 * signals.FS) + 1)
+    sp = small_spec(rng, 2)
+    tb = serve.tick_bytes(sp, "fp16")
+    # a load budget of 2.5 sessions' bytes per tick, expressed as a fraction of the bandwidth
+    frac = 2.5 * tb / (serve.DEFAULT_HBM_GBS * 1e9 * 128 / signals.FS)
+    srv = serve.Server("fp16", load_frac=frac)
+    assert srv.admit(sp, pool.filters(sp)) is not None
+    assert srv.admit(sp, pool.filters(sp)) is not None
+    assert srv.admit(sp, pool.filters(sp)) is None
+    assert srv.rejected_load == 1 and srv.rejected == 0
+    srv.depart(srv.sessions[0])
+    assert abs(srv.load - tb) < 1e-6 * tb
+    assert srv.admit(sp, pool.filters(sp)) is not None
+    srv.close()
