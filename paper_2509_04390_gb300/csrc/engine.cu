@@ -839,8 +839,10 @@ int enqueue_adapt(conv_engine* e, const float* d_err_block) {
     u.L = F.n_src;
     u.K = F.K;
     u.slot0 = a.slot0;
+    // few rows per CTA: every thread's read-modify-writes of F_hat are in flight at once
     const long long rows = (long long)p.R * p.n_kt * p.n_lt;
-    u.rows_per_cta = (int)std::max<long long>(1, (rows + 4LL * e->num_sms - 1) / (4LL * e->num_sms));
+    u.rows_per_cta = (int)std::max<long long>(1, std::min<long long>(4, (rows + 16LL * e->num_sms - 1) /
+                                                                             (16LL * e->num_sms)));
     u.tile_elems = p.tile_elems;
     CK(launch_nlms_update(u, e->as));
     CK(cudaEventRecord(e->ev_upd, e->as));

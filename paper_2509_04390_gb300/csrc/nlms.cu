@@ -36,8 +36,24 @@ __global__ void k_nlms_prep(const NlmsPrepArgs a) {
         const int kt = k / a.BT, kl = k - kt * a.BT;
         const float2* u = a.U + ((size_t)kt * a.K + a.slot0) * a.L * a.BT + kl;
         float px = 0.0f, py = 0.0f;
-        for (int l = 0; l < a.L; ++l) {
-            const float2 v = u[(size_t)l * a.BT];
+        // eight loudspeaker rows per batch of independent loads, summed in order
+        int l = 0;
+        for (; l + 8 <= a.L; l += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = __ldg(u + (size_t)(l + i) * a.BT);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (k == 0) {
+                    px = fmaf(v[i].x, v[i].x, px);
+                    py = fmaf(v[i].y, v[i].y, py);
+                } else {
+                    px = fmaf(v[i].x, v[i].x, fmaf(v[i].y, v[i].y, px));
+                }
+            }
+        }
+        for (; l < a.L; ++l) {
+            const float2 v = __ldg(u + (size_t)l * a.BT);
             if (k == 0) {
                 px = fmaf(v.x, v.x, px);
                 py = fmaf(v.y, v.y, py);
@@ -111,7 +127,9 @@ cudaError_t launch_nlms_prep(const NlmsPrepArgs& a, int P, cudaStream_t s) {
         cudaError_t e = cudaFuncSetAttribute(k_nlms_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_nlms_prep<<<P, fft_threads(a.B), sm, s>>>(a);
+    // one thread per bin (up to 256): the power sums are latency-bound loads
+    const int threads = a.B < 256 ? (a.B < 64 ? 64 : a.B) : 256;
+    k_nlms_prep<<<P, threads, sm, s>>>(a);
     return cudaGetLastError();
 }
 
