@@ -21,6 +21,7 @@ Prints ONE JSON line (rank 0):
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -388,11 +389,20 @@ def run_ours(args):
     d_out = torch.empty((2, w.n_out, B), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # device addresses resolved once: the timed loop is the C-ABI call and the
+    # engine's own launches, not Python tensor indexing
+    lib = U.load()
+    p_blocks = [d_blocks[i].data_ptr() for i in range(nb)]
+    p_out = [d_out[0].data_ptr(), d_out[1].data_ptr()]
+    p_stream = stream.cuda_stream
+
     def step(i):
         if args.afc:
-            U.afc_process_block_async(eng.h, d_blocks[i % nb], d_out[i & 1], None, stream)
+            rc = lib.afc_process_block_async(eng.h, p_blocks[i % nb], p_out[i & 1], None, p_stream)
         else:
-            U.conv_process_block_async(eng.h, d_blocks[i % nb], d_out[i & 1], stream)
+            rc = lib.conv_process_block_async(eng.h, p_blocks[i % nb], p_out[i & 1], p_stream)
+        if rc:
+            raise U.ConvError(rc, U.conv_last_error())
 
     def host_call(h_in, h_out):
         if args.afc:
@@ -648,8 +658,24 @@ def run_batch(args):
     for e in engs:
         batch.add(e)
 
+    lib = U.load()
+    p_stream = stream.cuda_stream
+    n_s = len(specs)
+    p_ins = [(ctypes.c_void_p * n_s)(*[x[k].data_ptr() for x in d_x]) for k in range(nbuf)]
+    p_outs = (ctypes.c_void_p * n_s)(*[y.data_ptr() for y in d_y])
+    p_x = [[x[k].data_ptr() for k in range(nbuf)] for x in d_x]
+    p_y = [y.data_ptr() for y in d_y]
+
     def bstep(i):
-        batch.process_async([x[i % nbuf] for x in d_x], d_y, stream)
+        rc = lib.conv_batch_process_async(batch.b, p_ins[i % nbuf], p_outs, p_stream)
+        if rc:
+            raise U.ConvError(rc, U.conv_last_error())
+
+    def ustep(i):
+        for j, e in enumerate(engs):
+            rc = lib.conv_process_block_async(e.h, p_x[j][i % nbuf], p_y[j], p_stream)
+            if rc:
+                raise U.ConvError(rc, U.conv_last_error())
 
     for i in range(args.warmup):
         bstep(i)
@@ -672,13 +698,11 @@ def run_batch(args):
     # unbatched: one engine call per session per step
     k_u = max(3, min(args.steps, 200))
     for i in range(3):
-        for j, e in enumerate(engs):
-            U.conv_process_block_async(e.h, d_x[j][i % nbuf], d_y[j], stream)
+        ustep(i)
     torch.cuda.synchronize()
     ev0.record(stream)
     for i in range(k_u):
-        for j, e in enumerate(engs):
-            U.conv_process_block_async(e.h, d_x[j][i % nbuf], d_y[j], stream)
+        ustep(i)
     ev1.record(stream)
     torch.cuda.synchronize()
     for e in engs:
@@ -755,8 +779,15 @@ def run_group(args):
     info = grp.info()
     units = float(S) * w.n_in * w.n_out * w.taps * B
 
+    lib = U.load()
+    p_blocks = [d_blocks[i].data_ptr() for i in range(nb)]
+    p_out = [d_out[0].data_ptr(), d_out[1].data_ptr()]
+    p_stream = stream.cuda_stream
+
     def step(i):
-        U.conv_group_process_async(grp.g, d_blocks[i % nb], d_out[i & 1], stream)
+        rc = lib.conv_group_process_async(grp.g, p_blocks[i % nb], p_out[i & 1], p_stream)
+        if rc:
+            raise U.ConvError(rc, U.conv_last_error())
 
     for i in range(args.warmup):
         step(i)
@@ -818,14 +849,21 @@ def run_group(args):
         engs.append(e)
     d_o1 = torch.empty((w.n_out, B), dtype=torch.float32, device="cuda")
     k_u = max(3, min(args.steps, 500))
-    for i in range(3):
+    p_sess = [[d_blocks[i][s].data_ptr() for s in range(S)] for i in range(min(nb, k_u + 3))]
+    p_o1 = d_o1.data_ptr()
+
+    def sep_step(i):
         for s, e in enumerate(engs):
-            U.conv_process_block_async(e.h, d_blocks[i % nb][s], d_o1, stream)
+            rc = lib.conv_process_block_async(e.h, p_sess[i % len(p_sess)][s], p_o1, p_stream)
+            if rc:
+                raise U.ConvError(rc, U.conv_last_error())
+
+    for i in range(3):
+        sep_step(i)
     torch.cuda.synchronize()
     ev0.record(stream)
     for i in range(k_u):
-        for s, e in enumerate(engs):
-            U.conv_process_block_async(e.h, d_blocks[i % nb][s], d_o1, stream)
+        sep_step(i)
     ev1.record(stream)
     torch.cuda.synchronize()
     t_sep = ev0.elapsed_time(ev1) / 1e3 / k_u

@@ -402,10 +402,14 @@ struct conv_engine {
     // adaptive canceller (afc_set_adaptation)
     bool adapt = false;
     float mu = 0.0f, lam = 0.0f, delta = 0.0f;
-    cudaStream_t as = nullptr;   // high-priority stream of the update and the canceller's tail
-    cudaEvent_t ev_upd = nullptr;  // this block's update is done: the delay line may advance
+    cudaStream_t as = nullptr;     // high-priority stream of the NLMS step (critical path)
+    cudaEvent_t ev_prep = nullptr;    // this block's step G is ready (the power sum has read the ring)
+    cudaEvent_t ev_corr = nullptr;    // the next block's correlation chunks are written
     float2* d_pow = nullptr;     // [2][B] packed power estimates, by block parity
-    float2* d_G = nullptr;       // [n_in][B] step-scaled error spectra
+    float2* d_G = nullptr;       // [3][n_in][B] step-scaled error spectra, by block mod 3
+    float2* d_A = nullptr;       // [2][2][8][B] correlation chunks (block parity, lag one/two)
+    float2* d_side = nullptr;    // [2][n_kt][n_out][BT] ring slots the pushes overwrote, by block parity
+    bool upd_pending = false;    // the previous block's step is not yet in the tail partitions
     int in_batches = 0;          // batches holding this session
     // non-uniform partitioning (conv_set_far_block): taps [0, far_B) in this
     // engine's own partitions of `block`, taps [far_B, taps) in a nested engine
@@ -727,6 +731,12 @@ int engine_reset(conv_engine* e) {
     if ((rc = part_reset(e, e->fb))) return rc;
     if (e->d_c) CK(cudaMemsetAsync(e->d_c, 0, (size_t)e->n_in * e->B * sizeof(float), e->stream));
     if (e->d_pow) CK(cudaMemsetAsync(e->d_pow, 0, 2 * (size_t)e->B * sizeof(float2), e->stream));
+    if (e->d_G) {  // zero ring: no step pending, correlations and saved entries zero
+        CK(cudaMemsetAsync(e->d_G, 0, 3 * (size_t)e->n_in * e->B * sizeof(float2), e->stream));
+        CK(cudaMemsetAsync(e->d_A, 0, 32 * (size_t)e->B * sizeof(float2), e->stream));
+        CK(cudaMemsetAsync(e->d_side, 0, 2 * (size_t)e->n_out * e->B * sizeof(float2), e->stream));
+    }
+    e->upd_pending = false;
     if (e->far) {
         if ((rc = engine_reset(e->far))) return rc;
         CK(cudaMemsetAsync(e->d_acc, 0, (size_t)e->n_in * e->far_B * sizeof(float), e->stream));
@@ -800,22 +810,36 @@ int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t 
     return CONV_OK;
 }
 
-// Adaptive canceller, block n (after e_n is known): NLMS update of F_hat with
-// the delay line as it is (loudspeaker spectra up to block n-1), then the
-// canceller's tail for block n with the updated spectra.  Runs on the
-// high-priority stream e->as beside the synthesis output.
-int enqueue_adapt(conv_engine* e, const float* d_err_block) {
+// Ring slot of block m's spectra (m may be negative: zeros before the first block).
+inline int slot_of(long long m, int K) {
+    const int r = (int)((-m) % K);
+    return r < 0 ? r + K : r;
+}
+
+// Three step buffers: block m+2's step kernel may run while block m's step is
+// still being applied to the tail partitions.
+float2* G_of(conv_engine* e, long long m) { return e->d_G + (size_t)(((m % 3) + 3) % 3) * e->n_in * e->B; }
+float2* side_of(conv_engine* e, long long m) { return e->d_side + (size_t)(m & 1) * e->n_out * e->B; }
+float2* A_of(conv_engine* e, long long m, int lag) {
+    return e->d_A + ((size_t)(m & 1) * 2 + (lag - 1)) * 8 * e->B;
+}
+
+// Adaptive canceller (deferred update, see nlms.h), block n.
+// On the high-priority stream e->as once e_n is written: the step G_n
+// (nlms_prep: R2C of e_n, the power recursion over the newest delay-line
+// entry, block n-1) and its application to partition 0.
+int enqueue_nlms_prep(conv_engine* e, const float* d_err_block) {
     Part& F = e->fb;
     const MacPlan& p = F.plan;
     const long long n = e->nblk;
-    CK(cudaStreamWaitEvent(e->as, e->syn.ev_packed, 0));  // e_n is written; c_{n-1}'s head has read F_hat
+    CK(cudaStreamWaitEvent(e->as, e->syn.ev_packed, 0));  // e_n is written
     NlmsPrepArgs a{};
     a.e = d_err_block;
     a.U = static_cast<const float2*>(F.X);
-    a.slot0 = slot0_for(n > 0 ? n - 1 : 0, F.K);
+    a.slot0 = slot_of(n - 1, F.K);
     a.pow_in = e->d_pow + (size_t)(n & 1) * e->B;
     a.pow_out = e->d_pow + (size_t)((n + 1) & 1) * e->B;
-    a.G = e->d_G;
+    a.G = G_of(e, n);
     a.B = e->B;
     a.log2B = e->log2B;
     a.BT = p.BT;
@@ -825,11 +849,25 @@ int enqueue_adapt(conv_engine* e, const float* d_err_block) {
     a.lam = e->lam;
     a.delta = e->delta;
     a.tw = e->tw;
+    a.F = static_cast<float2*>(F.H);
+    a.LT = p.LT;
+    a.n_lt = p.n_lt;
+    a.tile_elems = p.tile_elems;
     CK(launch_nlms_prep(a, F.n_dst, e->as));
+    CK(cudaEventRecord(e->ev_prep, e->as));
+    return CONV_OK;
+}
+
+// Arguments of block m's step on the tail partitions (entries j = 1..K-1,
+// blocks m-2 .. m-1-K).  after_push: block m+1's push is done, so blocks m-K
+// and m+1-K come from the saved slots; else only block m-K.
+NlmsUpdateArgs update_args(conv_engine* e, long long m, bool after_push) {
+    Part& F = e->fb;
+    const MacPlan& p = F.plan;
     NlmsUpdateArgs u{};
     u.F = static_cast<float2*>(F.H);
-    u.U = a.U;
-    u.G = e->d_G;
+    u.U = static_cast<const float2*>(F.X);
+    u.G = G_of(e, m);
     u.B = e->B;
     u.BT = p.BT;
     u.n_kt = p.n_kt;
@@ -838,65 +876,144 @@ int enqueue_adapt(conv_engine* e, const float* d_err_block) {
     u.P = F.n_dst;
     u.L = F.n_src;
     u.K = F.K;
-    u.slot0 = a.slot0;
+    u.slot0 = slot_of(m - 1, F.K);  // entry 0 = block m-1
+    u.r_begin = F.n_src;
     // few rows per CTA: every thread's read-modify-writes of F_hat are in flight at once
-    const long long rows = (long long)p.R * p.n_kt * p.n_lt;
+    const long long rows = (long long)(p.R - u.r_begin) * p.n_kt * p.n_lt;
     u.rows_per_cta = (int)std::max<long long>(1, std::min<long long>(4, (rows + 16LL * e->num_sms - 1) /
                                                                              (16LL * e->num_sms)));
     u.tile_elems = p.tile_elems;
-    CK(launch_nlms_update(u, e->as));
-    CK(cudaEventRecord(e->ev_upd, e->as));
-    // no early start: the MAC would stream the spectra the update is writing
-    int rc = enqueue_tail(e, F, n, e->as, false, false);
+    u.U_old[0] = side_of(e, m);
+    u.U_old[1] = after_push ? side_of(e, m + 1) : nullptr;
+    return u;
+}
+
+// Block m's step on the tail partitions on its own (before block m+1's push).
+int enqueue_nlms_update(conv_engine* e, long long m, cudaStream_t s) {
+    if (m < 0 || e->fb.K < 2) return CONV_OK;
+    CK(launch_nlms_update(update_args(e, m, false), s));
+    return CONV_OK;
+}
+
+// After block m+1's push: block m's step on the tail partitions (if `step`)
+// in one pass with the tail MAC of block m+2 (which needs F_m).
+int enqueue_nlms_update_mac(conv_engine* e, long long m, bool step, cudaStream_t s) {
+    Part& F = e->fb;
+    if (F.K < 2 || F.plan.S == 0) return CONV_OK;
+    NlmsUpdateMacArgs a{};
+    a.u = update_args(e, m, true);
+    if (!step || m < 0) a.u.G = nullptr;
+    a.partial = static_cast<float2*>(F.partial[(m + 2) & 1]);
+    a.S = F.plan.S;
+    a.mac_slot0 = slot_of(m + 2, F.K);
+    CK(launch_nlms_update_mac(a, s));
+    return CONV_OK;
+}
+
+// Correlation chunks for block m+1 from the delay line after block m's push.
+int enqueue_nlms_corr(conv_engine* e, long long m, cudaStream_t s) {
+    Part& F = e->fb;
+    NlmsCorrArgs c{};
+    c.C = nlms_corr_chunks(F.K);
+    if (c.C == 0) return CONV_OK;
+    c.U = static_cast<const float2*>(F.X);
+    c.oldest = side_of(e, m);
+    c.A1 = A_of(e, m + 1, 1);
+    c.A2 = A_of(e, m + 1, 2);
+    c.B = e->B;
+    c.BT = F.plan.BT;
+    c.L = F.n_src;
+    c.K = F.K;
+    c.slot_m = slot_of(m, F.K);
+    CK(launch_nlms_corr(c, s));
+    return CONV_OK;
+}
+
+// Applies a pending step now, before the next push (reading the spectra back,
+// or leaving the adaptive schedule).
+int flush_nlms_update(conv_engine* e) {
+    if (!e->upd_pending) return CONV_OK;
+    e->upd_pending = false;
+    int rc = enqueue_nlms_update(e, e->nblk - 1, e->stream);
     if (rc) return rc;
-    CK(cudaEventRecord(F.ev_tail[n & 1], e->as));
+    CK(cudaStreamSynchronize(e->stream));
     return CONV_OK;
 }
 
 // Synthesis with feedback cancellation (Sec. 5): e = mic - c_prev, l = H^T * e
 // (first half), then c = F_hat * l, kept for the next block (second half).
-// The host-buffer call copies l and e out between the halves.
+// The synthesis output kernel also pushes l_n into the canceller's delay line
+// (one kernel less on the block's critical path).  The host-buffer call
+// copies l and e out between the halves.
 int enqueue_afc_synthesis(conv_engine* e, const float* d_mic, float* d_out, float* d_e, cudaStream_t s) {
     if (int rc = stream_handoff(e, s)) return rc;
-    if (!e->adapt) {
-        float* eb = (d_e || !e->far) ? d_e : e->d_e;  // the far engine's input is the error signal
-        far_before(e);
-        int rc = enqueue_conv(e, e->syn, d_mic, e->d_c, eb, d_out, s, true);
-        if (!rc) rc = far_after(e, eb, s);
-        return rc;
-    }
-    float* eb = d_e ? d_e : e->d_e;
     Part& P = e->syn;
+    Part& F = e->fb;
     const long long n = e->nblk;
+    // the far engine's input and the NLMS step's input are the error signal
+    float* eb = d_e ? d_e : ((e->far || e->adapt) ? e->d_e : nullptr);
     int rc;
+    far_before(e);
     if ((rc = enqueue_pack(e, P, d_mic, e->B, e->d_c, eb, s))) return rc;
     CK(cudaEventRecord(P.ev_packed, s));
-    if ((rc = enqueue_adapt(e, eb))) return rc;
+    if (e->adapt && (rc = enqueue_nlms_prep(e, eb))) return rc;
     CK(cudaStreamWaitEvent(s, P.ev_tail[n & 1], 0));
-    if ((rc = enqueue_out(e, P, n, d_out, s))) return rc;
+    PackArgs pa = pack_args(e, F, n, d_out, e->B, nullptr, nullptr);
+    if (e->adapt) {
+        // The push keeps the entry it overwrites (block n-K) for the deferred
+        // step; the previous block's background work has read the slots
+        // involved; with K = 1 the step kernel reads the overwritten slot.
+        pa.save_old = side_of(e, n);
+        CK(cudaStreamWaitEvent(s, F.ev_tail[n & 1], 0));
+        CK(cudaStreamWaitEvent(s, e->ev_corr, 0));
+        if (F.K == 1) CK(cudaStreamWaitEvent(s, e->ev_prep, 0));
+    }
+    CK(launch_out_push(e->prec, out_args(e, P, n, d_out), pa, s));
+    CK(cudaEventRecord(F.ev_packed, s));
     cudaStream_t bg = e->bg[(n + 1) & 1];
     CK(cudaStreamWaitEvent(bg, P.ev_packed, 0));
     if (e->prof) CK(cudaStreamWaitEvent(bg, P.ev_tail[n & 1], 0));
     if ((rc = enqueue_tail(e, P, n + 1, bg, true))) return rc;
     CK(cudaEventRecord(P.ev_tail[(n + 1) & 1], bg));
-    return CONV_OK;
+    return far_after(e, eb, s);
 }
 
-int enqueue_afc_prediction(conv_engine* e, const float* d_out, cudaStream_t s) {
+int enqueue_afc_prediction(conv_engine* e, cudaStream_t s) {
+    Part& F = e->fb;
+    const long long n = e->nblk;
     int rc;
-    if (!e->adapt) {
-        rc = enqueue_conv(e, e->fb, d_out, nullptr, nullptr, e->d_c, s, false);
-    } else {
-        // the update read the delay-line slot this push overwrites; the tail
-        // of this block ran on e->as with the updated spectra
-        Part& F = e->fb;
-        const long long n = e->nblk;
-        CK(cudaStreamWaitEvent(s, e->ev_upd, 0));
-        if ((rc = enqueue_pack(e, F, d_out, e->B, nullptr, nullptr, s))) return rc;
-        CK(cudaStreamWaitEvent(s, F.ev_tail[n & 1], 0));
-        rc = enqueue_out(e, F, n, e->d_c, s);
+    CK(cudaStreamWaitEvent(s, F.ev_tail[n & 1], 0));
+    OutArgs oa = out_args(e, F, n, e->d_c);
+    if (e->adapt) {
+        // G_n and the step on partition 0 are done; the tail of this block
+        // holds F_{n-2}: add the two steps it lacks
+        CK(cudaStreamWaitEvent(s, e->ev_prep, 0));
+        oa.corr_G = G_of(e, n);
+        oa.corr_G2 = G_of(e, n - 1);
+        oa.corr_A = A_of(e, n, 1);
+        oa.corr_A2 = A_of(e, n, 2);
+        oa.corr_C = nlms_corr_chunks(F.K);
     }
-    if (rc) return rc;
+    CK(launch_out_c2r(e->prec, oa, s));
+    if (!e->adapt) {
+        cudaStream_t bg = e->bg[2 + ((n + 1) & 1)];
+        CK(cudaStreamWaitEvent(bg, F.ev_packed, 0));
+        if ((rc = enqueue_tail(e, F, n + 1, bg, false))) return rc;
+        CK(cudaEventRecord(F.ev_tail[(n + 1) & 1], bg));
+    } else {
+        // background, a block ahead: the correlations of block n+1, and
+        // block n-1's step on the tail partitions fused with block n+1's tail
+        // (in order on one stream: each pass follows the one that read the
+        // spectra before it)
+        cudaStream_t bg = e->bg[2], bc = e->bg[3];
+        CK(cudaStreamWaitEvent(bc, F.ev_packed, 0));
+        if ((rc = enqueue_nlms_corr(e, n, bc))) return rc;
+        CK(cudaEventRecord(e->ev_corr, bc));
+        CK(cudaStreamWaitEvent(bg, F.ev_packed, 0));
+        if ((rc = enqueue_nlms_update_mac(e, n - 1, e->upd_pending, bg))) return rc;
+        e->upd_pending = true;
+        CK(cudaEventRecord(F.ev_tail[(n + 1) & 1], bg));
+    }
     ++e->nblk;
     return CONV_OK;
 }
@@ -929,7 +1046,10 @@ void engine_free(conv_engine* e) {
     dev_free(e, &e->d_c, 0);
     dev_free(e, &e->d_pow, 0);
     dev_free(e, &e->d_G, 0);
-    if (e->ev_upd) cudaEventDestroy(e->ev_upd);
+    dev_free(e, &e->d_A, 0);
+    dev_free(e, &e->d_side, 0);
+    if (e->ev_prep) cudaEventDestroy(e->ev_prep);
+    if (e->ev_corr) cudaEventDestroy(e->ev_corr);
     if (e->as) cudaStreamDestroy(e->as);
     if (e->h_in) cudaFreeHost(e->h_in);
     if (e->h_out) cudaFreeHost(e->h_out);
@@ -1194,7 +1314,7 @@ int afc_process_block_async(conv_engine* e, const float* d_mic, float* d_out, fl
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     int rc = enqueue_afc_synthesis(e, d_mic, d_out, d_e, s);
     if (rc) return rc;
-    return enqueue_afc_prediction(e, d_out, s);
+    return enqueue_afc_prediction(e, s);
 }
 
 int afc_process_block(conv_engine* e, const float* mic, float* out, float* e_or_null) {
@@ -1210,7 +1330,7 @@ int afc_process_block(conv_engine* e, const float* mic, float* out, float* e_or_
     if (want_e) CK(cudaMemcpyAsync(e->h_e, e->d_e, ib, cudaMemcpyDeviceToHost, e->stream));
     CK(cudaEventRecord(e->ev_done, e->stream));
     // the prediction for the next block runs while this block's output is read on the host
-    if ((rc = enqueue_afc_prediction(e, e->m_out, e->stream))) return rc;
+    if ((rc = enqueue_afc_prediction(e, e->stream))) return rc;
     CK(cudaEventSynchronize(e->ev_done));
     if ((rc = check_dev_err(e))) return rc;
     if (e->guard > 0.0) {
@@ -1252,27 +1372,44 @@ int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta) {
         int prio_low = 0, prio_high = 0;
         CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
         CK(cudaStreamCreateWithPriority(&e->as, cudaStreamNonBlocking, prio_high));
-        CK(cudaEventCreateWithFlags(&e->ev_upd, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&e->ev_prep, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&e->ev_corr, cudaEventDisableTiming));
     }
     if (!e->d_pow) {
         if ((rc = dev_alloc(e, &e->d_pow, 2 * (size_t)e->B * sizeof(float2)))) return rc;
         CK(cudaMemsetAsync(e->d_pow, 0, 2 * (size_t)e->B * sizeof(float2), e->stream));
     }
-    if (!e->d_G && (rc = dev_alloc(e, &e->d_G, (size_t)e->n_in * e->B * sizeof(float2)))) return rc;
+    if (!e->d_G && (rc = dev_alloc(e, &e->d_G, 3 * (size_t)e->n_in * e->B * sizeof(float2)))) return rc;
+    if (!e->d_A && (rc = dev_alloc(e, &e->d_A, 32 * (size_t)e->B * sizeof(float2)))) return rc;
+    if (!e->d_side && (rc = dev_alloc(e, &e->d_side, 2 * (size_t)e->n_out * e->B * sizeof(float2)))) return rc;
+    if (e->has_last) CK(cudaStreamSynchronize(e->last_stream));
     for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
     CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
     const bool was = e->adapt;
-    e->adapt = mu > 0.0;
+    const bool now = mu > 0.0;
+    if (was && !now) {
+        // the static schedule expects the stored spectra complete and this
+        // block's tail computed with them
+        if ((rc = flush_nlms_update(e))) return rc;
+        if ((rc = enqueue_tail(e, e->fb, e->nblk, e->stream, false))) return rc;
+        CK(cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream));
+    }
+    if (!was && now) {
+        // the static tail of this block holds the current spectra; no step
+        // before this block (G of the previous block zero), and this block's
+        // correlations from the delay line as it is
+        CK(cudaMemsetAsync(e->d_G, 0, 3 * (size_t)e->n_in * e->B * sizeof(float2), e->stream));
+        CK(cudaMemsetAsync(e->d_A, 0, 32 * (size_t)e->B * sizeof(float2), e->stream));
+        CK(cudaMemsetAsync(e->d_side, 0, 2 * (size_t)e->n_out * e->B * sizeof(float2), e->stream));
+        if (e->nblk > 0 && (rc = enqueue_nlms_corr(e, e->nblk - 1, e->stream))) return rc;
+        e->upd_pending = false;
+    }
+    CK(cudaStreamSynchronize(e->stream));
+    e->adapt = now;
     e->mu = (float)mu;
     e->lam = (float)lambda;
     e->delta = (float)delta;
-    if (was && !e->adapt) {
-        // the static schedule expects this block's canceller tail to be ready
-        if ((rc = enqueue_tail(e, e->fb, e->nblk, e->stream, false))) return rc;
-        CK(cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream));
-        CK(cudaStreamSynchronize(e->stream));
-    }
     return CONV_OK;
 }
 
@@ -1281,9 +1418,12 @@ int afc_get_path_spectra(conv_engine* e, float* f_spec) {
     if (!e->fb.ready) return set_err(CONV_E_STATE, "feedback paths not set");
     if (e->prec != CONV_FP32) return set_err(CONV_E_STATE, "path spectra are read back from FP32 engines only");
     DeviceGuard g(e->dev);
+    if (e->has_last) CK(cudaStreamSynchronize(e->last_stream));
     for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
     if (e->as) CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
+    int rc;
+    if ((rc = flush_nlms_update(e))) return rc;  // the last block's step on the tail partitions
     const Part& F = e->fb;
     const MacPlan& p = F.plan;
     std::vector<float2> tiles(p.h_bytes / sizeof(float2));
@@ -1355,7 +1495,10 @@ int conv_get_info(const conv_engine* e, conv_info* out) {
     out->mac_kernel = p.direct == 0 ? CONV_KERNEL_TMA : (p.direct == 1 ? CONV_KERNEL_DIRECT1 : CONV_KERNEL_DIRECT2);
     out->device_bytes = (long long)e->dev_bytes;
     out->kernels_per_block = 3;
-    out->kernels_per_afc_block = e->adapt ? 8 : 6;
+    // pack, output (+ the canceller's push) and tail of the synthesis, output
+    // and tail of the canceller; adaptive: NLMS step, update and the
+    // correlation chunks (K_fb >= 2)
+    out->kernels_per_afc_block = 5 + (e->adapt ? 2 + (e->fb.K >= 2 ? 1 : 0) : 0);
     out->afc_adaptive = e->adapt ? 1 : 0;
     out->far_block = e->far_B;
     out->K_far = e->far ? e->far->syn.K : 0;

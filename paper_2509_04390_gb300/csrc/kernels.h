@@ -92,6 +92,9 @@ struct PackArgs {
     float* sX;         // [K][n_ch] slot scales (reduced precision), else null
     int B, log2B, BT, n_ch, K, slot;
     const float2* tw;  // W_2B^j = exp(-i pi j / B), j in [0, 2B)
+    // FP32 rings only: receives the slot's previous spectra, [n_kt][n_ch][BT],
+    // before the push overwrites them (null: not kept)
+    float2* save_old;
 };
 
 struct FilterArgs {
@@ -127,6 +130,14 @@ struct OutArgs {
     // they are summed before waiting for the previous kernel in the stream;
     // 0: the previous kernel may be writing them
     int early_partials;
+    // FP32 only (corr_G null: none).  Adds corr_G[l][k] * sum_c corr_A[c][k] +
+    // corr_G2[l][k] * sum_c corr_A2[c][k] to bin k: the effect of the two
+    // NLMS steps that the tail's filter spectra do not hold yet (see nlms.h)
+    const float2* corr_G;   // [n_dst][B] this block's step
+    const float2* corr_G2;  // [n_dst][B] the previous block's step
+    const float2* corr_A;   // [corr_C][B] lag-one correlation chunks
+    const float2* corr_A2;  // [corr_C][B] lag-two correlation chunks
+    int corr_C;
 };
 
 // One CTA of a batched launch: which session's arguments (items[item]), and
@@ -155,6 +166,9 @@ cudaError_t launch_tile_scales(int prec, const float* maxabs, float* sH, int n_d
 // pass false when the previous kernel writes the filter spectra.
 cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s, bool pdl = true);
 cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s);
+// Output (a) fused with the push of each output channel into another ring (b,
+// b.in = a.out, b.n_ch = a.n_dst).
+cudaError_t launch_out_push(int prec, const OutArgs& a, const PackArgs& b, cudaStream_t s);
 cudaError_t launch_pack_batch(int prec, const PackArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);
 cudaError_t launch_out_batch(int prec, const OutArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);
 cudaError_t launch_mac_batch(int prec, const MacArgs* items, const BatchRef* refs, int n, size_t smem, cudaStream_t s);

@@ -3,10 +3,13 @@
 //
 //   nlms_prep    one CTA per microphone: R2C of [0_B | e_p] (shared-memory
 //                FFT), the per-bin power recursion over the loudspeakers'
-//                newest spectra, and G_p = mu E_p / (K pow + delta)
-//   nlms_update  F_hat[p][l][j][k] += G_p[k] conj(U_l,j[k]) over every filter
-//                tile; streams F_hat once (read + write), the delay line and
-//                G come from L2
+//                newest spectra, G_p = mu E_p / (K pow + delta), and the step
+//                on partition 0
+//   nlms_update  F_hat[p][l][j][k] += G_p[k] conj(U_l,j[k]) over the tail
+//                partitions of every filter tile; streams them once (read +
+//                write), the delay line and G come from L2
+//   nlms_corr    chunks of the lag-one and lag-two correlations of the delay
+//                line (the deferred update's correction terms)
 #include <cuda_runtime.h>
 
 #include "device_util.cuh"
@@ -61,7 +64,7 @@ __global__ void k_nlms_prep(const NlmsPrepArgs a) {
                 px = fmaf(v.x, v.x, fmaf(v.y, v.y, px));
             }
         }
-        const float2 old = a.pow_in[k];
+        const float2 old = a.pow_in[k];  // (the ring loads below repeat from L1/L2)
         float2 pw;
         pw.x = a.lam * old.x + (1.0f - a.lam) * px;
         pw.y = k == 0 ? a.lam * old.y + (1.0f - a.lam) * py : 0.0f;
@@ -75,6 +78,33 @@ __global__ void k_nlms_prep(const NlmsPrepArgs a) {
             g = cscale(E, st);
         }
         a.G[(size_t)p * B + k] = g;
+        // partition 0: F[p][l][0][k] += g conj(U_l,0[k])
+        const int lt = p / a.LT, ll = p - lt * a.LT;
+        const int LTt = min(a.LT, (int)gridDim.x - lt * a.LT);
+        float2* f = a.F + (size_t)(kt * a.n_lt + lt) * a.tile_elems + (size_t)ll * a.BT + kl;
+        const size_t fr = (size_t)LTt * a.BT;  // row pitch
+        for (int l0 = 0; l0 < a.L; l0 += 8) {
+            const int nl = min(8, a.L - l0);
+            float2 v[8], w[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < nl) {
+                    v[i] = __ldg(u + (size_t)(l0 + i) * a.BT);
+                    w[i] = f[(size_t)(l0 + i) * fr];
+                }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < nl) {
+                    if (k == 0) {
+                        w[i].x = fmaf(g.x, v[i].x, w[i].x);
+                        w[i].y = fmaf(g.y, v[i].y, w[i].y);
+                    } else {
+                        w[i].x = fmaf(g.x, v[i].x, fmaf(g.y, v[i].y, w[i].x));
+                        w[i].y = fmaf(g.y, v[i].x, fmaf(-g.x, v[i].y, w[i].y));
+                    }
+                    f[(size_t)(l0 + i) * fr] = w[i];
+                }
+        }
     }
 }
 
@@ -83,7 +113,7 @@ __global__ void __launch_bounds__(256) k_nlms_update(const NlmsUpdateArgs a) {
     const int kt = tile / a.n_lt, lt = tile - kt * a.n_lt;
     const int LTt = min(a.LT, a.P - lt * a.LT);
     const int R = a.L * a.K;
-    const int r0 = blockIdx.x * a.rows_per_cta;
+    const int r0 = a.r_begin + blockIdx.x * a.rows_per_cta;
     const int r1 = min(R, r0 + a.rows_per_cta);
     if (r0 >= r1) return;
     const int row = LTt * a.BT;
@@ -94,12 +124,18 @@ __global__ void __launch_bounds__(256) k_nlms_update(const NlmsUpdateArgs a) {
         const int ll = e / a.BT, kl = e - ll * a.BT;
         const int p = lt * a.LT + ll, k = kt * a.BT + kl;
         const float2 g = G[(size_t)p * a.B + k];
-        int l = r0 % a.L;
-        int slot = a.slot0 + r0 / a.L;
+        int l = r0 % a.L, j = r0 / a.L;
+        int slot = a.slot0 + j;
         if (slot >= a.K) slot -= a.K;
 #pragma unroll 4
         for (int r = r0; r < r1; ++r) {
-            const float2 u = U[((size_t)(kt * a.K + slot) * a.L + l) * a.BT + kl];
+            float2 u;
+            if (j == a.K - 1 && a.U_old[0])
+                u = a.U_old[0][((size_t)kt * a.L + l) * a.BT + kl];
+            else if (j == a.K - 2 && a.U_old[1])
+                u = a.U_old[1][((size_t)kt * a.L + l) * a.BT + kl];
+            else
+                u = U[((size_t)(kt * a.K + slot) * a.L + l) * a.BT + kl];
             float2* f = Ft + (size_t)r * row + e;
             float2 v = *f;
             if (k == 0) {  // packed DC and Nyquist: two real products
@@ -112,13 +148,170 @@ __global__ void __launch_bounds__(256) k_nlms_update(const NlmsUpdateArgs a) {
             *f = v;
             if (++l == a.L) {
                 l = 0;
+                ++j;
                 if (++slot == a.K) slot = 0;
             }
         }
     }
 }
 
+// CTA (split, filter tile); thread (element of the tile row, row lane).  Each
+// lane walks every NRL-th row of the split: read F, take the step, write F
+// back, accumulate F x (MAC entry); the lanes' sums are combined in shared
+// memory in a fixed order into the split's partial.
+__global__ void __launch_bounds__(512) k_nlms_update_mac(const NlmsUpdateMacArgs a) {
+    extern __shared__ float2 lanes[];  // [NRL][row]
+    const NlmsUpdateArgs& u = a.u;
+    const int tile = blockIdx.y, split = blockIdx.x;
+    const int kt = tile / u.n_lt, lt = tile - kt * u.n_lt;
+    const int LTt = min(u.LT, u.P - lt * u.LT);
+    const int R = u.L * u.K, Rt = R - u.r_begin;
+    const int r0 = u.r_begin + (int)((long long)split * Rt / a.S);
+    const int r1 = u.r_begin + (int)((long long)(split + 1) * Rt / a.S);
+    const int row = LTt * u.BT;
+    const int ET = blockDim.x, NRL = blockDim.y, ly = threadIdx.y;
+    float2* __restrict__ Ft = u.F + (size_t)tile * u.tile_elems;
+    for (int e = threadIdx.x; e < row; e += ET) {
+        const int ll = e / u.BT, kl = e - ll * u.BT;
+        const int p = lt * u.LT + ll, k = kt * u.BT + kl;
+        const float2 g = u.G ? u.G[(size_t)p * u.B + k] : make_float2(0.0f, 0.0f);
+        float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll 4
+        for (int r = r0 + ly; r < r1; r += NRL) {
+            const int j = r / u.L, l = r - j * u.L;
+            float2* f = Ft + (size_t)r * row + e;
+            float2 v = *f;
+            if (u.G) {
+                float2 w;
+                if (j == u.K - 1 && u.U_old[0]) {
+                    w = u.U_old[0][((size_t)kt * u.L + l) * u.BT + kl];
+                } else if (j == u.K - 2 && u.U_old[1]) {
+                    w = u.U_old[1][((size_t)kt * u.L + l) * u.BT + kl];
+                } else {
+                    int sl = u.slot0 + j;
+                    if (sl >= u.K) sl -= u.K;
+                    w = u.U[((size_t)(kt * u.K + sl) * u.L + l) * u.BT + kl];
+                }
+                if (k == 0) {
+                    v.x = fmaf(g.x, w.x, v.x);
+                    v.y = fmaf(g.y, w.y, v.y);
+                } else {  // v += g * conj(w)
+                    v.x = fmaf(g.x, w.x, fmaf(g.y, w.y, v.x));
+                    v.y = fmaf(g.y, w.x, fmaf(-g.x, w.y, v.y));
+                }
+                *f = v;
+            }
+            int sm = a.mac_slot0 + j;
+            if (sm >= u.K) sm -= u.K;
+            const float2 x = u.U[((size_t)(kt * u.K + sm) * u.L + l) * u.BT + kl];
+            if (k == 0) {
+                acc.x = fmaf(v.x, x.x, acc.x);
+                acc.y = fmaf(v.y, x.y, acc.y);
+            } else {
+                acc.x = fmaf(v.x, x.x, fmaf(-v.y, x.y, acc.x));
+                acc.y = fmaf(v.x, x.y, fmaf(v.y, x.x, acc.y));
+            }
+        }
+        lanes[(size_t)ly * row + e] = acc;
+    }
+    __syncthreads();
+    if (ly != 0) return;
+    for (int e = threadIdx.x; e < row; e += ET) {
+        const int ll = e / u.BT, kl = e - ll * u.BT;
+        const int p = lt * u.LT + ll, k = kt * u.BT + kl;
+        float2 t = lanes[e];
+        for (int y = 1; y < NRL; ++y) t = cadd(t, lanes[(size_t)y * row + e]);
+        a.partial[((size_t)split * u.P + p) * u.B + k] = t;
+    }
+}
+
+// CTA (bin chunk, j chunk); thread (l, bin).  A window of three consecutive
+// delay-line entries slides over the chunk, so each thread loads every entry
+// once; the sums over loudspeakers run in shared memory in a fixed order.
+__device__ __forceinline__ void conj_mac(float2& acc, float2 o, float2 n, bool packed0) {
+    if (packed0) {  // DC and Nyquist: real products
+        acc.x = fmaf(o.x, n.x, acc.x);
+        acc.y = fmaf(o.y, n.y, acc.y);
+    } else {  // acc += conj(o) n
+        acc.x = fmaf(o.x, n.x, fmaf(o.y, n.y, acc.x));
+        acc.y = fmaf(o.x, n.y, fmaf(-o.y, n.x, acc.y));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_nlms_corr(const NlmsCorrArgs a, const int BA) {
+    extern __shared__ float2 red[];  // [2][L][BA]
+    const int c = blockIdx.y, J = a.K - 1;
+    const int j0 = 1 + (int)((long long)c * J / a.C), j1 = 1 + (int)((long long)(c + 1) * J / a.C);
+    const size_t ss = (size_t)a.L * a.BT;  // slot pitch
+    const int LB = a.L * BA;
+    for (int e = threadIdx.x; e < LB; e += blockDim.x) {
+        const int l = e / BA, kb = e - l * BA;
+        const int k = blockIdx.x * BA + kb;
+        const int kt = k / a.BT, kl = k - kt * a.BT;
+        const float2* base = a.U + (size_t)kt * a.K * ss + (size_t)l * a.BT + kl;
+        const float2 oldest = j1 == a.K ? __ldg(a.oldest + ((size_t)kt * a.L + l) * a.BT + kl) : make_float2(0.0f, 0.0f);
+        int s = (a.slot_m + j0 - 1) % a.K;  // entry j0 - 1 (block m+1-j0)
+        float2 nv = __ldg(base + s * ss);
+        if (++s == a.K) s = 0;
+        float2 o1 = __ldg(base + s * ss);  // entry j0
+        float2 acc1 = make_float2(0.0f, 0.0f), acc2 = make_float2(0.0f, 0.0f);
+#pragma unroll 4
+        for (int j = j0; j < j1; ++j) {
+            if (++s == a.K) s = 0;
+            const float2 o2 = j + 1 == a.K ? oldest : __ldg(base + s * ss);  // entry j + 1
+            conj_mac(acc1, o1, nv, k == 0);
+            conj_mac(acc2, o2, nv, k == 0);
+            nv = o1;
+            o1 = o2;
+        }
+        red[e] = acc1;
+        red[LB + e] = acc2;
+    }
+    __syncthreads();
+    for (int kb = threadIdx.x; kb < BA; kb += blockDim.x) {
+        float2 t1 = make_float2(0.0f, 0.0f), t2 = make_float2(0.0f, 0.0f);
+        for (int l = 0; l < a.L; ++l) {
+            t1 = cadd(t1, red[l * BA + kb]);
+            t2 = cadd(t2, red[LB + l * BA + kb]);
+        }
+        a.A1[(size_t)c * a.B + blockIdx.x * BA + kb] = t1;
+        a.A2[(size_t)c * a.B + blockIdx.x * BA + kb] = t2;
+    }
+}
+
 }  // namespace
+
+int nlms_corr_chunks(int K) { return K < 2 ? 0 : (K - 1 < 8 ? K - 1 : 8); }
+
+cudaError_t launch_nlms_corr(const NlmsCorrArgs& a, cudaStream_t s) {
+    if (a.K < 2 || a.C < 1 || a.C > a.K - 1 || a.L < 1 || a.L > 1024 || a.B < 16 || (a.B & (a.B - 1)))
+        return cudaErrorInvalidValue;
+    // small CTAs (<= 256 threads) that fit beside a MAC CTA on its SM
+    int BA = 1;
+    while (BA * 2 * a.L <= 256 && BA * 2 <= a.B) BA *= 2;
+    int threads = ((a.L * BA + 31) / 32) * 32;
+    if (threads > 256) threads = 256;
+    const dim3 grid((unsigned)(a.B / BA), (unsigned)a.C);
+    k_nlms_corr<<<grid, threads, 2 * (size_t)a.L * BA * sizeof(float2), s>>>(a, BA);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nlms_update_mac(const NlmsUpdateMacArgs& a, cudaStream_t s) {
+    const NlmsUpdateArgs& u = a.u;
+    if (a.S < 1 || u.r_begin < 0 || u.L * u.K - u.r_begin < 1) return cudaErrorInvalidValue;
+    const int row = u.LT * u.BT;
+    const int ET = row < 256 ? ((row + 31) / 32) * 32 : 256;
+    int NRL = 512 / ET;
+    if (NRL > 4) NRL = 4;
+    while (NRL > 1 && (size_t)NRL * row * sizeof(float2) > 48 * 1024) --NRL;
+    const size_t smem = (size_t)NRL * row * sizeof(float2);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_nlms_update_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_nlms_update_mac<<<dim3((unsigned)a.S, (unsigned)(u.n_kt * u.n_lt)), dim3(ET, NRL), smem, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_nlms_prep(const NlmsPrepArgs& a, int P, cudaStream_t s) {
     static_assert(sizeof(float2) == 8, "packed spectra are float pairs");
@@ -134,8 +327,8 @@ cudaError_t launch_nlms_prep(const NlmsPrepArgs& a, int P, cudaStream_t s) {
 }
 
 cudaError_t launch_nlms_update(const NlmsUpdateArgs& a, cudaStream_t s) {
-    const int R = a.L * a.K;
-    if (a.rows_per_cta < 1 || R < 1) return cudaErrorInvalidValue;
+    const int R = a.L * a.K - a.r_begin;  // rows that take the step
+    if (a.rows_per_cta < 1 || a.r_begin < 0 || R < 1) return cudaErrorInvalidValue;
     const int row = a.LT * a.BT;
     int threads = ((row + 31) / 32) * 32;
     if (threads > 256) threads = 256;

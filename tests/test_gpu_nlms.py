@@ -12,7 +12,8 @@ import numpy as np
 import pytest
 
 from gpu_helpers import RoomPlant, snr_db
-from oracle.nlms_oracle import afc_closed_loop_nlms
+from oracle.nlms_oracle import NlmsCanceller, afc_closed_loop_nlms
+from oracle.upols_oracle import UpolsOracle
 from paper_2509_04390_gb300 import build, signals
 from paper_2509_04390_gb300 import upols as U
 
@@ -103,6 +104,72 @@ def test_adaptive_closed_loop_against_oracle(B, f0_scale):
     assert moved > 0.01
 
 
+@pytest.mark.parametrize("B,n_t", [(64, 64), (64, 100), (32, 300), (16, 257)])
+def test_adaptive_partition_counts_against_oracle(B, n_t):
+    """K_fb = 1 (the delay line is one entry: the update and the correction
+    read the copy the push saved), K_fb = 2, and longer rings with a ragged
+    last partition."""
+    h, f, s = small_case(seed=60 + n_t, B=B, n_t=n_t, nb=50)
+    fh0 = (0.25 * f).astype(np.float32)
+    # mu = 0.1: with one or two partitions the unconstrained update at larger
+    # steps makes the closed loop diverge in the FP64 oracle as well
+    mu, lam, delta = 0.1, 0.8, 1e-2
+    y, e, spec = run_adaptive(h, f, fh0, s, B, mu, lam, delta)
+    ref_l, ref_e, can = afc_closed_loop_nlms(h, f, fh0, s, B, mu, lam, delta)
+    s_l, s_e, s_w = snr_db(y, ref_l), snr_db(e, ref_e), snr_db(spec, packed(can.W))
+    print(f"adaptive B={B} n_t={n_t} (K_fb {can.K}): l {s_l:.1f} dB, e {s_e:.1f} dB, F_hat {s_w:.1f} dB")
+    assert min(s_l, s_e, s_w) >= ADAPT_DB
+
+
+def test_switching_adaptation_on_mid_stream_against_oracle():
+    """Static canceller for 20 blocks, then adaptive: the oracle's loop skips
+    the NLMS step (and the power recursion) until the same block."""
+    h, f, s = small_case(seed=57, nb=50)
+    P, L, B = 2, 3, 64
+    n0, nb = 20, 50
+    fh0 = (0.5 * f).astype(np.float32)
+    mu, lam, delta = 0.3, 0.9, 1e-2
+    with U.Engine(48000, B, P, L, h.shape[2]) as e:
+        e.set_filters(h)
+        e.set_paths(fh0)
+        y0, e0, _ = run_adaptive(h, f, None, s[:, : n0 * B], B, None, None, None, engine=e)
+        fb_state = RoomPlant(f, B)
+        # the room's state at block n0 comes from the loudspeaker blocks so far
+        fb = np.zeros((P, B))
+        for b in range(n0):
+            fb = fb_state.step(y0[:, b * B : (b + 1) * B])
+        e.set_adaptation(mu, lam, delta)
+        y1 = np.zeros((L, (nb - n0) * B), np.float32)
+        e1 = np.zeros((P, (nb - n0) * B), np.float32)
+        l_n = np.empty((L, B), np.float32)
+        e_n = np.empty((P, B), np.float32)
+        for b in range(n0, nb):
+            m_n = (s[:, b * B : (b + 1) * B].astype(np.float64) + fb).astype(np.float32)
+            e.process_afc(m_n, l_n, e_n)
+            y1[:, (b - n0) * B : (b - n0 + 1) * B] = l_n
+            e1[:, (b - n0) * B : (b - n0 + 1) * B] = e_n
+            fb = fb_state.step(l_n)
+        spec = e.path_spectra()
+    y = np.concatenate([y0, y1], axis=1)
+    err = np.concatenate([e0, e1], axis=1)
+    synth, room = UpolsOracle(h, B), UpolsOracle(f, B)
+    can = NlmsCanceller(fh0, B, mu, lam, delta)
+    ref_l, ref_e = np.zeros((L, nb * B)), np.zeros((P, nb * B))
+    fb_prev, c_prev = np.zeros((P, B)), np.zeros((P, B))
+    for b in range(nb):
+        sl = slice(b * B, (b + 1) * B)
+        e_b = s[:, sl].astype(np.float64) + fb_prev - c_prev
+        if b >= n0:
+            can.adapt(e_b)
+        l_b = synth.process_block(e_b)
+        c_prev = can.predict(l_b)
+        fb_prev = room.process_block(l_b)
+        ref_l[:, sl], ref_e[:, sl] = l_b, e_b
+    s_l, s_e, s_w = snr_db(y, ref_l), snr_db(err, ref_e), snr_db(spec, packed(can.W))
+    print(f"adaptation switched on at block {n0}: l {s_l:.1f} dB, e {s_e:.1f} dB, F_hat {s_w:.1f} dB")
+    assert min(s_l, s_e, s_w) >= ADAPT_DB
+
+
 def test_path_spectra_are_the_subfilter_ffts():
     rng = np.random.default_rng(5)
     P, L, B, n_t = 3, 5, 32, 150
@@ -119,17 +186,20 @@ def test_path_spectra_are_the_subfilter_ffts():
     assert snr_db(got, ref) >= 120.0
 
 
-def test_vanishing_step_reproduces_the_static_schedule_bit_exact():
-    """delta far above the signal power makes every update round away, so the
-    adaptive schedule (update, then the canceller's tail on its own stream)
-    must give exactly the static schedule's outputs."""
+def test_vanishing_step_reproduces_the_static_schedule():
+    """delta far above the signal power makes every step round away, so the
+    adaptive schedule (step on partition 0, deferred step fused with the
+    canceller's tail, correlation terms) must leave the spectra exactly as
+    they were and give the static schedule's outputs up to the rounding of
+    its own tail summation order."""
     h, f, s = small_case(seed=52, nb=40)
     fh0 = (0.5 * f).astype(np.float32)
     y0, e0, w0 = run_adaptive(h, f, fh0, s, 64, 0.0, 0.5, 0.0)
     y1, e1, w1 = run_adaptive(h, f, fh0, s, 64, 1e-3, 0.5, 1e30)
     assert np.array_equal(w0, w1)
-    assert np.array_equal(y0, y1)
-    assert np.array_equal(e0, e1)
+    print(f"vanishing step vs static: l {snr_db(y1, y0):.1f} dB, e {snr_db(e1, e0):.1f} dB")
+    assert snr_db(y1, y0) >= 125.0
+    assert snr_db(e1, e0) >= 125.0
 
 
 def test_reset_and_paths_repeat_bit_exact():
