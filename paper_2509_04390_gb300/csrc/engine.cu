@@ -24,6 +24,14 @@
 // waited for by out(n)) was the last to read; tail(n+1) never reads it.
 // tail(n+2) reuses the partials out(n) read; it waits for pack(n+1), which
 // the caller stream runs after out(n).
+//
+// With the feedback canceller the caller stream runs three kernels per block:
+// the microphone pack (e = m - c), the synthesis output fused with the push
+// of l_n into the canceller's ring, and the canceller's output (c_n).  The
+// canceller's tails alternate over a second pair of background streams.  The
+// adaptive canceller adds the NLMS step on a high-priority stream beside the
+// synthesis output and a deferred step fused into the canceller's tail (see
+// nlms.h and enqueue_afc_synthesis / enqueue_afc_prediction).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -407,7 +415,8 @@ struct conv_engine {
     cudaEvent_t ev_corr = nullptr;    // the next block's correlation chunks are written
     float2* d_pow = nullptr;     // [2][B] packed power estimates, by block parity
     float2* d_G = nullptr;       // [3][n_in][B] step-scaled error spectra, by block mod 3
-    float2* d_A = nullptr;       // [2][2][8][B] correlation chunks (block parity, lag one/two)
+    float2* d_A = nullptr;       // [2][2][9][B] correlation chunks + their sum (block parity, lag one/two)
+    unsigned* d_ticket = nullptr;  // [B] completion counters of the correlation kernel
     float2* d_side = nullptr;    // [2][n_kt][n_out][BT] ring slots the pushes overwrote, by block parity
     bool upd_pending = false;    // the previous block's step is not yet in the tail partitions
     int in_batches = 0;          // batches holding this session
@@ -733,7 +742,7 @@ int engine_reset(conv_engine* e) {
     if (e->d_pow) CK(cudaMemsetAsync(e->d_pow, 0, 2 * (size_t)e->B * sizeof(float2), e->stream));
     if (e->d_G) {  // zero ring: no step pending, correlations and saved entries zero
         CK(cudaMemsetAsync(e->d_G, 0, 3 * (size_t)e->n_in * e->B * sizeof(float2), e->stream));
-        CK(cudaMemsetAsync(e->d_A, 0, 32 * (size_t)e->B * sizeof(float2), e->stream));
+        CK(cudaMemsetAsync(e->d_A, 0, 36 * (size_t)e->B * sizeof(float2), e->stream));
         CK(cudaMemsetAsync(e->d_side, 0, 2 * (size_t)e->n_out * e->B * sizeof(float2), e->stream));
     }
     e->upd_pending = false;
@@ -820,8 +829,9 @@ inline int slot_of(long long m, int K) {
 // still being applied to the tail partitions.
 float2* G_of(conv_engine* e, long long m) { return e->d_G + (size_t)(((m % 3) + 3) % 3) * e->n_in * e->B; }
 float2* side_of(conv_engine* e, long long m) { return e->d_side + (size_t)(m & 1) * e->n_out * e->B; }
-float2* A_of(conv_engine* e, long long m, int lag) {
-    return e->d_A + ((size_t)(m & 1) * 2 + (lag - 1)) * 8 * e->B;
+// Correlation chunks of block m (index 0..7) and their sum (index 8).
+float2* A_of(conv_engine* e, long long m, int lag, int idx = 0) {
+    return e->d_A + (((size_t)(m & 1) * 2 + (lag - 1)) * 9 + idx) * e->B;
 }
 
 // Adaptive canceller (deferred update, see nlms.h), block n.
@@ -920,6 +930,9 @@ int enqueue_nlms_corr(conv_engine* e, long long m, cudaStream_t s) {
     c.oldest = side_of(e, m);
     c.A1 = A_of(e, m + 1, 1);
     c.A2 = A_of(e, m + 1, 2);
+    c.A1f = A_of(e, m + 1, 1, 8);
+    c.A2f = A_of(e, m + 1, 2, 8);
+    c.ticket = e->d_ticket;
     c.B = e->B;
     c.BT = F.plan.BT;
     c.L = F.n_src;
@@ -990,9 +1003,9 @@ int enqueue_afc_prediction(conv_engine* e, cudaStream_t s) {
         CK(cudaStreamWaitEvent(s, e->ev_prep, 0));
         oa.corr_G = G_of(e, n);
         oa.corr_G2 = G_of(e, n - 1);
-        oa.corr_A = A_of(e, n, 1);
-        oa.corr_A2 = A_of(e, n, 2);
-        oa.corr_C = nlms_corr_chunks(F.K);
+        oa.corr_A = A_of(e, n, 1, 8);
+        oa.corr_A2 = A_of(e, n, 2, 8);
+        oa.corr_C = F.K >= 2 ? 1 : 0;
     }
     CK(launch_out_c2r(e->prec, oa, s));
     if (!e->adapt) {
@@ -1047,6 +1060,7 @@ void engine_free(conv_engine* e) {
     dev_free(e, &e->d_pow, 0);
     dev_free(e, &e->d_G, 0);
     dev_free(e, &e->d_A, 0);
+    dev_free(e, &e->d_ticket, 0);
     dev_free(e, &e->d_side, 0);
     if (e->ev_prep) cudaEventDestroy(e->ev_prep);
     if (e->ev_corr) cudaEventDestroy(e->ev_corr);
@@ -1380,7 +1394,11 @@ int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta) {
         CK(cudaMemsetAsync(e->d_pow, 0, 2 * (size_t)e->B * sizeof(float2), e->stream));
     }
     if (!e->d_G && (rc = dev_alloc(e, &e->d_G, 3 * (size_t)e->n_in * e->B * sizeof(float2)))) return rc;
-    if (!e->d_A && (rc = dev_alloc(e, &e->d_A, 32 * (size_t)e->B * sizeof(float2)))) return rc;
+    if (!e->d_A && (rc = dev_alloc(e, &e->d_A, 36 * (size_t)e->B * sizeof(float2)))) return rc;
+    if (!e->d_ticket) {
+        if ((rc = dev_alloc(e, &e->d_ticket, (size_t)e->B * sizeof(unsigned)))) return rc;
+        CK(cudaMemsetAsync(e->d_ticket, 0, (size_t)e->B * sizeof(unsigned), e->stream));
+    }
     if (!e->d_side && (rc = dev_alloc(e, &e->d_side, 2 * (size_t)e->n_out * e->B * sizeof(float2)))) return rc;
     if (e->has_last) CK(cudaStreamSynchronize(e->last_stream));
     for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
@@ -1400,7 +1418,7 @@ int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta) {
         // before this block (G of the previous block zero), and this block's
         // correlations from the delay line as it is
         CK(cudaMemsetAsync(e->d_G, 0, 3 * (size_t)e->n_in * e->B * sizeof(float2), e->stream));
-        CK(cudaMemsetAsync(e->d_A, 0, 32 * (size_t)e->B * sizeof(float2), e->stream));
+        CK(cudaMemsetAsync(e->d_A, 0, 36 * (size_t)e->B * sizeof(float2), e->stream));
         CK(cudaMemsetAsync(e->d_side, 0, 2 * (size_t)e->n_out * e->B * sizeof(float2), e->stream));
         if (e->nblk > 0 && (rc = enqueue_nlms_corr(e, e->nblk - 1, e->stream))) return rc;
         e->upd_pending = false;

@@ -174,42 +174,59 @@ __global__ void __launch_bounds__(512) k_nlms_update_mac(const NlmsUpdateMacArgs
     for (int e = threadIdx.x; e < row; e += ET) {
         const int ll = e / u.BT, kl = e - ll * u.BT;
         const int p = lt * u.LT + ll, k = kt * u.BT + kl;
-        const float2 g = u.G ? u.G[(size_t)p * u.B + k] : make_float2(0.0f, 0.0f);
+        const bool step = u.G != nullptr;
+        const float2 g = step ? u.G[(size_t)p * u.B + k] : make_float2(0.0f, 0.0f);
         float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll 4
-        for (int r = r0 + ly; r < r1; r += NRL) {
-            const int j = r / u.L, l = r - j * u.L;
-            float2* f = Ft + (size_t)r * row + e;
-            float2 v = *f;
-            if (u.G) {
-                float2 w;
-                if (j == u.K - 1 && u.U_old[0]) {
-                    w = u.U_old[0][((size_t)kt * u.L + l) * u.BT + kl];
-                } else if (j == u.K - 2 && u.U_old[1]) {
-                    w = u.U_old[1][((size_t)kt * u.L + l) * u.BT + kl];
-                } else {
-                    int sl = u.slot0 + j;
-                    if (sl >= u.K) sl -= u.K;
-                    w = u.U[((size_t)(kt * u.K + sl) * u.L + l) * u.BT + kl];
+        // eight rows per trip: all their loads are issued before any store
+        for (int rb = r0 + ly; rb < r1; rb += 8 * NRL) {
+            float2 fv[8], wv[8], xv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = rb + i * NRL;
+                if (r < r1) {
+                    const int j = r / u.L, l = r - j * u.L;
+                    fv[i] = Ft[(size_t)r * row + e];
+                    int sm = a.mac_slot0 + j;
+                    if (sm >= u.K) sm -= u.K;
+                    xv[i] = u.U[((size_t)(kt * u.K + sm) * u.L + l) * u.BT + kl];
+                    if (step) {
+                        if (j == u.K - 1 && u.U_old[0]) {
+                            wv[i] = u.U_old[0][((size_t)kt * u.L + l) * u.BT + kl];
+                        } else if (j == u.K - 2 && u.U_old[1]) {
+                            wv[i] = u.U_old[1][((size_t)kt * u.L + l) * u.BT + kl];
+                        } else {
+                            int sl = u.slot0 + j;
+                            if (sl >= u.K) sl -= u.K;
+                            wv[i] = u.U[((size_t)(kt * u.K + sl) * u.L + l) * u.BT + kl];
+                        }
+                    }
                 }
-                if (k == 0) {
-                    v.x = fmaf(g.x, w.x, v.x);
-                    v.y = fmaf(g.y, w.y, v.y);
-                } else {  // v += g * conj(w)
-                    v.x = fmaf(g.x, w.x, fmaf(g.y, w.y, v.x));
-                    v.y = fmaf(g.y, w.x, fmaf(-g.x, w.y, v.y));
-                }
-                *f = v;
             }
-            int sm = a.mac_slot0 + j;
-            if (sm >= u.K) sm -= u.K;
-            const float2 x = u.U[((size_t)(kt * u.K + sm) * u.L + l) * u.BT + kl];
-            if (k == 0) {
-                acc.x = fmaf(v.x, x.x, acc.x);
-                acc.y = fmaf(v.y, x.y, acc.y);
-            } else {
-                acc.x = fmaf(v.x, x.x, fmaf(-v.y, x.y, acc.x));
-                acc.y = fmaf(v.x, x.y, fmaf(v.y, x.x, acc.y));
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = rb + i * NRL;
+                if (r < r1) {
+                    float2 v = fv[i];
+                    if (step) {
+                        const float2 w = wv[i];
+                        if (k == 0) {
+                            v.x = fmaf(g.x, w.x, v.x);
+                            v.y = fmaf(g.y, w.y, v.y);
+                        } else {  // v += g * conj(w)
+                            v.x = fmaf(g.x, w.x, fmaf(g.y, w.y, v.x));
+                            v.y = fmaf(g.y, w.x, fmaf(-g.x, w.y, v.y));
+                        }
+                        Ft[(size_t)r * row + e] = v;
+                    }
+                    const float2 x = xv[i];
+                    if (k == 0) {
+                        acc.x = fmaf(v.x, x.x, acc.x);
+                        acc.y = fmaf(v.y, x.y, acc.y);
+                    } else {
+                        acc.x = fmaf(v.x, x.x, fmaf(-v.y, x.y, acc.x));
+                        acc.y = fmaf(v.x, x.y, fmaf(v.y, x.x, acc.y));
+                    }
+                }
             }
         }
         lanes[(size_t)ly * row + e] = acc;
@@ -277,6 +294,27 @@ __global__ void __launch_bounds__(256) k_nlms_corr(const NlmsCorrArgs a, const i
         a.A1[(size_t)c * a.B + blockIdx.x * BA + kb] = t1;
         a.A2[(size_t)c * a.B + blockIdx.x * BA + kb] = t2;
     }
+    // the last of the range's C CTAs adds the chunks in order
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(a.ticket + blockIdx.x, 1u) == (unsigned)(a.C - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int kb = threadIdx.x; kb < BA; kb += blockDim.x) {
+        const size_t k = (size_t)blockIdx.x * BA + kb;
+        float2 t1 = make_float2(0.0f, 0.0f), t2 = make_float2(0.0f, 0.0f);
+        for (int cc = 0; cc < a.C; ++cc) {
+            t1 = cadd(t1, __ldcg(a.A1 + (size_t)cc * a.B + k));
+            t2 = cadd(t2, __ldcg(a.A2 + (size_t)cc * a.B + k));
+        }
+        a.A1f[k] = t1;
+        a.A2f[k] = t2;
+    }
+    if (threadIdx.x == 0) a.ticket[blockIdx.x] = 0u;
 }
 
 }  // namespace

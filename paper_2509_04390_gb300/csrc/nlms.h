@@ -86,15 +86,20 @@ struct NlmsUpdateMacArgs {
 // over j = 1..K-1 split into C chunks.  U_{m-i} sits at ring slot
 // (slot_m + i) mod K for i < K; U_{m-K} (the last A2 term) in `oldest`.
 // Packed bin 0: (DC, Nyquist) products.  K >= 2.
+// The CTA that completes a bin range last (a ticket counter per range, reset
+// by that CTA) sums the range's C chunks in order into A1f / A2f.
 struct NlmsCorrArgs {
     const float2* U;       // ring [n_kt][K][L][BT]
     const float2* oldest;  // [n_kt][L][BT] block m-K
     float2* A1;            // [C][B]
     float2* A2;            // [C][B]
+    float2* A1f;           // [B] sum of the chunks
+    float2* A2f;           // [B]
+    unsigned* ticket;      // [B] zero-initialised counters (one per bin range used)
     int B, BT, L, K, slot_m, C;
 };
 
-// Chunks of the correlations (at most 8: the output kernel sums them).
+// Chunks of the correlations (at most 8).
 int nlms_corr_chunks(int K);
 
 cudaError_t launch_nlms_prep(const NlmsPrepArgs& a, int P, cudaStream_t s);

@@ -286,3 +286,66 @@ def test_adaptive_paper_scale_canceller_against_oracle():
     s_l, s_e, s_w = snr_db(y, ref_l), snr_db(e, ref_e), snr_db(spec, packed(can.W))
     print(f"adaptive paper-scale canceller: l {s_l:.1f} dB, e {s_e:.1f} dB, F_hat {s_w:.1f} dB")
     assert min(s_l, s_e, s_w) >= ADAPT_DB
+
+
+def open_loop_adaptive(e, s, B, read_at=(), stream_plan=None):
+    """Drive an adaptive engine with microphone blocks s (no room): host calls,
+    or device calls on the streams that stream_plan(b) names (None: host)."""
+    torch = pytest.importorskip("torch")
+    P = s.shape[0]
+    L = e.info()["n_out"]
+    nb = s.shape[1] // B
+    y = np.zeros((L, nb * B), np.float32)
+    err = np.zeros((P, nb * B), np.float32)
+    d_m = torch.from_numpy(s).cuda().reshape(P, nb, B).permute(1, 0, 2).contiguous()
+    d_y = torch.zeros((nb, L, B), dtype=torch.float32, device="cuda")
+    d_e = torch.zeros((nb, P, B), dtype=torch.float32, device="cuda")
+    on_dev = []
+    l_n = np.empty((L, B), np.float32)
+    e_n = np.empty((P, B), np.float32)
+    torch.cuda.synchronize()
+    for b in range(nb):
+        st = stream_plan(b) if stream_plan else None
+        if st is None:
+            e.process_afc(np.ascontiguousarray(s[:, b * B : (b + 1) * B]), l_n, e_n)
+            y[:, b * B : (b + 1) * B] = l_n
+            err[:, b * B : (b + 1) * B] = e_n
+        else:
+            U.afc_process_block_async(e.h, d_m[b], d_y[b], d_e[b], st)
+            on_dev.append(b)
+        if b in read_at:
+            e.path_spectra()
+    U.conv_synchronize(e.h)
+    torch.cuda.synchronize()
+    dy, de = d_y.cpu().numpy(), d_e.cpu().numpy()
+    for b in on_dev:
+        y[:, b * B : (b + 1) * B] = dy[b]
+        err[:, b * B : (b + 1) * B] = de[b]
+    return y, err, e.path_spectra()
+
+
+def test_adaptive_device_streams_and_spectra_reads_are_bit_exact():
+    """The adaptive schedule through device calls on two alternating caller
+    streams (with host calls in between), and with the spectra read back
+    mid-stream (which applies the pending deferred step early), gives exactly
+    the host-call result."""
+    torch = pytest.importorskip("torch")
+    h, f, s = small_case(seed=58, nb=40)
+    P, L, B = 2, 3, 64
+
+    def engine():
+        e = U.Engine(48000, B, P, L, h.shape[2])
+        e.set_filters(h)
+        e.set_paths((0.3 * f).astype(np.float32))
+        e.set_adaptation(0.3, 0.9, 1e-2)
+        return e
+
+    with engine() as e:
+        y0, e0, w0 = open_loop_adaptive(e, s, B)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    with engine() as e:
+        y1, e1, w1 = open_loop_adaptive(e, s, B, stream_plan=lambda b: None if b % 3 == 2 else streams[b % 2])
+    with engine() as e:
+        y2, e2, w2 = open_loop_adaptive(e, s, B, read_at=(0, 17, 29))
+    assert np.array_equal(y0, y1) and np.array_equal(e0, e1) and np.array_equal(w0, w1)
+    assert np.array_equal(y0, y2) and np.array_equal(e0, e2) and np.array_equal(w0, w2)
