@@ -667,6 +667,7 @@ OutArgs out_args(conv_engine* e, Part& P, long long blk, float* out) {
         a.extra_stride = e->addend_stride;
     }
     a.early_partials = 1;  // every schedule waits for the tail's event before the output launch
+    a.head_pre = out_head_smem(P.n_src, e->B) > 0 ? 1 : 0;
     return a;
 }
 
@@ -1801,6 +1802,7 @@ int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, cons
         // synthesis: e = mic - c_prev for canceller sessions (Sec. 5)
         pk[j] = pack_args(e, P, blk, d_in[j], e->B, afc ? e->d_c : nullptr, nullptr);
         ot[j] = out_args(e, P, blk, d_out[j]);
+        ot[j].head_pre = 0;
         mc[j] = tail_args(e, P, blk + 1);
         for (int c = 0; c < P.n_src; ++c) rp[ip++] = BatchRef{j, c, 0};
         for (int l = 0; l < P.n_dst; ++l) ro[io++] = BatchRef{j, l, 0};
@@ -1811,6 +1813,7 @@ int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, cons
             Part& F = e->fb;
             pk[ia] = pack_args(e, F, blk, d_out[j], e->B, nullptr, nullptr);
             ot[ia] = out_args(e, F, blk, e->d_c);
+            ot[ia].head_pre = 0;
             mc[ia] = tail_args(e, F, blk + 1);
             for (int c = 0; c < F.n_src; ++c) rp[ifp++] = BatchRef{ia, c, 0};
             for (int l = 0; l < F.n_dst; ++l) ro[ifo++] = BatchRef{ia, l, 0};

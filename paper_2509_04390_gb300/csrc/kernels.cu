@@ -670,9 +670,14 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
     const int S = a.S;
     const int l0 = a.head ? (l / a.LT) * a.LT : 0;
     const int LTt = a.head ? min(a.LT, a.n_dst - l0) : 0, ll = l - l0;
-    // The engine's tail partials come from another stream (an event the
-    // launch already waited for), not from the previous kernel: sum them while
-    // the pack kernel may still be running, then wait for it before the head.
+    // The engine's tail partials (and the adaptive canceller's correction
+    // terms) come from other streams (events the launch already waited for),
+    // not from the previous kernel: sum them, and load the head's constant
+    // filter spectra, while the pack kernel may still be running; then wait
+    // for it before the head's delay-line row.
+    const bool corr = PREC == PREC_FP32 && a.corr_G != nullptr;
+    const int n_lt = (a.n_dst + a.LT - 1) / a.LT;
+    float2* hs = fsm + 4 * B;  // [n_src][B] when head_pre
     if (!a.early_partials) griddep_wait();
     for (int k = tid; k < B; k += nth) {
         const float2* src = a.partial + (size_t)l * B + k;
@@ -686,19 +691,38 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
             tot = cadd(tot, g);
         }
         for (; s < S; ++s) tot = cadd(tot, src[(size_t)s * stride]);
+        if (corr) {
+            float2 c1 = make_float2(0.0f, 0.0f), c2 = make_float2(0.0f, 0.0f);
+            for (int c = 0; c < a.corr_C; ++c) {
+                c1 = cadd(c1, a.corr_A[(size_t)c * B + k]);
+                c2 = cadd(c2, a.corr_A2[(size_t)c * B + k]);
+            }
+            const float2 g1 = a.corr_G[(size_t)l * B + k], g2 = a.corr_G2[(size_t)l * B + k];
+            if (k == 0) {  // DC and Nyquist: real products
+                rmac2(tot, g1, c1);
+                rmac2(tot, g2, c2);
+            } else {
+                cmac(tot, g1, c1);
+                cmac(tot, g2, c2);
+            }
+        }
         P[k] = tot;
+        if (a.head && a.head_pre) {  // the same thread reads these back below
+            const int kt = k / a.BT, kl = k - kt * a.BT;
+            const size_t hbase = ((size_t)kt * n_lt + l / a.LT) * a.tile_elems + (size_t)ll * a.BT + kl;
+            for (int q = 0; q < a.n_src; ++q) hs[(size_t)q * B + k] = St::load1(a.H, hbase + (size_t)q * LTt * a.BT, kl, a.BT);
+        }
     }
     griddep_wait();
     for (int k = tid; k < B; k += nth) {
         float2 tot = P[k];
         if (a.head) {
             const int kt = k / a.BT, kl = k - kt * a.BT;
-            const int n_lt = (a.n_dst + a.LT - 1) / a.LT;
             const size_t hbase = ((size_t)kt * n_lt + l / a.LT) * a.tile_elems + (size_t)ll * a.BT + kl;
             const size_t xbase = (((size_t)kt * a.K + a.slot0) * a.n_src) * a.BT + kl;
             float2 hd = make_float2(0.0f, 0.0f);
             for (int q = 0; q < a.n_src; ++q) {
-                const float2 h = St::load1(a.H, hbase + (size_t)q * LTt * a.BT, kl, a.BT);
+                const float2 h = a.head_pre ? hs[(size_t)q * B + k] : St::load1(a.H, hbase + (size_t)q * LTt * a.BT, kl, a.BT);
                 const float2 x = St::load1(a.X, xbase + (size_t)q * a.BT, kl, a.BT);
                 float2 t = make_float2(0.0f, 0.0f);
                 if (k == 0)
@@ -712,21 +736,6 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
                 hd.y = fmaf(sc, t.y, hd.y);
             }
             tot = cadd(tot, hd);
-            if (PREC == PREC_FP32 && a.corr_G) {
-                float2 c1 = make_float2(0.0f, 0.0f), c2 = make_float2(0.0f, 0.0f);
-                for (int c = 0; c < a.corr_C; ++c) {
-                    c1 = cadd(c1, a.corr_A[(size_t)c * B + k]);
-                    c2 = cadd(c2, a.corr_A2[(size_t)c * B + k]);
-                }
-                const float2 g1 = a.corr_G[(size_t)l * B + k], g2 = a.corr_G2[(size_t)l * B + k];
-                if (k == 0) {  // DC and Nyquist: real products
-                    rmac2(tot, g1, c1);
-                    rmac2(tot, g2, c2);
-                } else {
-                    cmac(tot, g1, c1);
-                    cmac(tot, g2, c2);
-                }
-            }
         }
         P[k] = tot;
     }
@@ -775,7 +784,10 @@ template <int PREC>
 __global__ void k_out_batch(const OutArgs* __restrict__ items, const BatchRef* __restrict__ refs) {
     __shared__ OutArgs sa;
     const BatchRef r = refs[blockIdx.x];
-    if (threadIdx.x == 0) sa = items[r.item];
+    if (threadIdx.x == 0) {
+        sa = items[r.item];
+        sa.head_pre = 0;  // batched launches carry no head prefetch space
+    }
     __syncthreads();
     out_body<PREC>(sa, r.idx);
 }
@@ -941,9 +953,15 @@ cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStr
     }
 }
 
+size_t out_head_smem(int n_src, int B) {
+    // keep the output CTA small enough to share an SM with a tail MAC CTA
+    const size_t extra = (size_t)n_src * B * sizeof(float2);
+    return fft_smem_bytes(B) + extra <= 64 * 1024 ? extra : 0;
+}
+
 cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s) {
     const dim3 grid(a.n_dst), block(out_threads(a.B));
-    const size_t sm = fft_smem_bytes(a.B);
+    const size_t sm = fft_smem_bytes(a.B) + (a.head && a.head_pre ? (size_t)a.n_src * a.B * sizeof(float2) : 0);
     switch (prec) {
         case PREC_FP32: return launch_pdl(k_out_c2r<PREC_FP32>, grid, block, sm, s, a);
         case PREC_FP16: return launch_pdl(k_out_c2r<PREC_FP16>, grid, block, sm, s, a);
@@ -970,7 +988,7 @@ cudaError_t launch_pdl_n(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStre
 cudaError_t launch_out_push(int prec, const OutArgs& a, const PackArgs& b, cudaStream_t s) {
     if (a.n_dst != b.n_ch || a.B != b.B) return cudaErrorInvalidValue;
     const dim3 grid(a.n_dst), block(out_threads(a.B));
-    const size_t sm = fft_smem_bytes(a.B);
+    const size_t sm = fft_smem_bytes(a.B) + (a.head && a.head_pre ? (size_t)a.n_src * a.B * sizeof(float2) : 0);
     switch (prec) {
         case PREC_FP32: return launch_pdl_n(k_out_push<PREC_FP32>, grid, block, sm, s, a, b);
         case PREC_FP16: return launch_pdl_n(k_out_push<PREC_FP16>, grid, block, sm, s, a, b);

@@ -138,7 +138,15 @@ struct OutArgs {
     const float2* corr_A;   // [corr_C][B] lag-one correlation chunks
     const float2* corr_A2;  // [corr_C][B] lag-two correlation chunks
     int corr_C;
+    // 1: the launch adds n_src*B float2 of shared memory in which the head's
+    // filter spectra (constant) are loaded before waiting for the previous
+    // kernel (out_head_smem)
+    int head_pre;
 };
+
+// Extra shared memory of an output launch that prefetches its head spectra
+// (0 when n_src x B is too large to keep the CTA small).
+size_t out_head_smem(int n_src, int B);
 
 // One CTA of a batched launch: which session's arguments (items[item]), and
 // the channel (pack/output) or the tile and split (MAC) it serves.
