@@ -394,7 +394,30 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
             // the wrapped second run (ring rows 0..) lands after the first run's padded span
             sx2 = (((start + xrun + 3) & ~3) - (start & ~3)) - xrun;
         }
+        // Whole output tile for this thread (every LPT output exists): a loop
+        // without per-output branches, so the loads of all outputs of a row are
+        // issued before their FMAs
+        const bool full = lg + (LPT - 1) * a.NLG < LTt;
         if constexpr (!St::PLANAR) {
+            if (full) {
+                for (int j = rl; j < nr; j += a.NRL) {
+                    float2 xv[VEC];
+                    St::load16(sx + (size_t)j * hrow + (size_t)kv * 16, xv);
+                    float2 hv[LPT][VEC];
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i)
+                        St::load16(sh + ((size_t)j * LTt + lg + i * a.NLG) * hrow + (size_t)kv * 16, hv[i]);
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            if (v == 0 && dc)
+                                rmac2(acc[i][v], hv[i][v], xv[v]);
+                            else
+                                cmac(acc[i][v], hv[i][v], xv[v]);
+                        }
+                }
+            } else {
             for (int j = rl; j < nr; j += a.NRL) {
                 float2 xv[VEC];
                 St::load16(sx + (size_t)j * hrow + (size_t)kv * 16, xv);
@@ -413,6 +436,7 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
                         }
                     }
                 }
+            }
             }
         } else {
             // Planar rows, 4 bins per thread as two pairs; acc[i] = (re 0-1, re 2-3,
@@ -437,6 +461,26 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
                     xi0.x = 0.0f;
                     xr0b.x = xi[0].x;
                 }
+                if (full) {
+                    float2 hr[LPT][2], hi[LPT][2];
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i)
+                        load_planar4<St>(sh + ((size_t)j * LTt + lg + i * a.NLG) * hrow, kv, a.BT, hr[i], hi[i]);
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i) {
+                        acc[i][0] = ffma2(hr[i][0], xr[0], acc[i][0]);
+                        acc[i][1] = ffma2(hr[i][1], xr[1], acc[i][1]);
+                        acc[i][2] = ffma2(hr[i][0], xi0, acc[i][2]);
+                        acc[i][3] = ffma2(hr[i][1], xi[1], acc[i][3]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i) {
+                        acc[i][0] = ffma2(hi[i][0], nxi0, acc[i][0]);
+                        acc[i][1] = ffma2(hi[i][1], nxi1, acc[i][1]);
+                        acc[i][2] = ffma2(hi[i][0], xr0b, acc[i][2]);
+                        acc[i][3] = ffma2(hi[i][1], xr[1], acc[i][3]);
+                    }
+                } else {
 #pragma unroll
                 for (int i = 0; i < LPT; ++i) {
                     const int ll = lg + i * a.NLG;
@@ -452,6 +496,7 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
                         acc[i][3] = ffma2(hr[1], xi[1], acc[i][3]);
                         acc[i][3] = ffma2(hi[1], xr[1], acc[i][3]);
                     }
+                }
                 }
             }
         }
