@@ -184,6 +184,8 @@ def workload_name(args):
         nlms = "_nlms" if args.adapt > 0 else ""
         return f"afc{nlms}_4x16_{args.taps}taps_fb{args.taps_fb}_B{args.block}_{args.precision}"
     far = f"_far{args.far_block}" if args.far_block else ""
+    if args.far_block and args.far_block2:
+        far += f"_far{args.far_block2}"
     return f"paper_4x16_{args.taps}taps_B{args.block}{far}_{args.precision}"
 
 
@@ -349,6 +351,7 @@ def config_dict(args, w):
         "global_batch": 1,
         "parallelism": "replicas",
         "far_block": args.far_block or None,
+        "far_block2": (args.far_block2 or None) if args.far_block else None,
         "l2": ("inputs larger than L2: the far part's spectra, streamed once per far block, exceed the 126 MB L2; "
                "the near part (block-size partitions up to the far block) stays L2-resident, as in real-time use")
         if args.far_block else "inputs larger than L2: the filter spectra streamed every step exceed the 126 MB L2",
@@ -375,8 +378,10 @@ def run_ours(args):
     B = w.block
     prec = args.precision
     eng = U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, prec, far_block=args.far_block)
-    eng.set_filters(w.h)
     far_h = U.conv_far_engine(eng.h) if args.far_block else None
+    if far_h and args.far_block2:  # a third partition size: the far part's own far block
+        U.conv_set_far_block(far_h, args.far_block2)
+    eng.set_filters(w.h)
     if args.afc:
         eng.set_paths(w.f)
         if args.adapt > 0:
@@ -613,7 +618,8 @@ def run_ours(args):
             },
             "cpu_baseline": cpu,
             "gpu_launches": args.steps * (info["kernels_per_afc_block"] if args.afc else info["kernels_per_block"])
-            + (args.steps // (args.far_block // B)) * 3 if args.far_block else
+            + (args.steps // (args.far_block // B)) * 3
+            + ((args.steps // (args.far_block2 // B)) * 3 if args.far_block2 else 0) if args.far_block else
             args.steps * (info["kernels_per_afc_block"] if args.afc else info["kernels_per_block"]),
             "clocks": clk,
             "plan": {k: info[k] for k in ("K", "mac_ctas", "mac_splits", "mac_smem", "device_bytes")},
@@ -971,6 +977,8 @@ def parse(argv=None):
     ap.add_argument("--adapt", type=float, default=0.0, help="with --afc: NLMS step size of the adaptive canceller")
     ap.add_argument("--far-block", type=int, default=0,
                     help="non-uniform partitioning: taps beyond this many samples in partitions of this size")
+    ap.add_argument("--far-block2", type=int, default=0,
+                    help="with --far-block: taps beyond far-block + far-block2 in partitions of far-block2")
     ap.add_argument("--e2e-steps", type=int, default=5000)
     ap.add_argument("--paced-blocks", type=int, default=1000)
     ap.add_argument("--e2e-chunk", type=int, default=64, help="blocks per conv_process_blocks call in the e2e figure")

@@ -160,3 +160,25 @@ def test_far_block_errors():
         with pytest.raises(U.ConvError) as ei:
             e.set_adaptation(0.3)
         assert ei.value.code == U.CONV_E_STATE
+
+
+@pytest.mark.parametrize("B,F,F2,taps,nb,precision", [(64, 256, 1024, 9000, 160, "fp32"), (32, 128, 2048, 12000, 420, "fp32"),
+                                                       (64, 256, 1024, 9000, 160, "fp16")])
+def test_nested_far_blocks_against_oracle(B, F, F2, taps, nb, precision):
+    """Three partition sizes: the far part's engine gets a far block of its own
+    (conv_set_far_block on conv_far_engine), so taps [0, F) run in partitions
+    of B, [F, F + F2) in partitions of F and the rest in partitions of F2; the
+    output is still the causal convolution."""
+    w = signals.random_case(900 + F2, 2, 3, taps, B, nb, decay_s=0.1)
+    with U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, precision, far_block=F) as e:
+        far = U.conv_far_engine(e.h)
+        U.conv_set_far_block(far, F2)
+        e.set_filters(w.h)
+        y = e.run(w.x)
+        e.reset()
+        y2 = e.run(w.x)
+    ref = upols(w.h.astype(np.float64), w.x.astype(np.float64), B)
+    s = snr_db(y, ref)
+    print(f"nested far blocks {precision} B={B} F={F} F2={F2}: {s:.1f} dB")
+    assert s >= BOUND[precision]
+    assert np.array_equal(y, y2)
