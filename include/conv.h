@@ -144,8 +144,10 @@ int conv_set_filters(conv_engine* e, const float* h);
 int conv_set_far_block(conv_engine* e, int far_block);
 
 /* The far part's engine of a non-uniformly partitioned engine (NULL if none).
- * Owned by `e`; use it only with conv_get_info and conv_profile_enable /
- * conv_profile_read (timing of the far tail MAC). */
+ * Owned by `e`; use it only with conv_get_info, conv_profile_enable /
+ * conv_profile_read (timing of the far tail MAC), and conv_set_far_block
+ * before conv_set_filters on `e`: the far part then splits again (a third
+ * partition size F2 > F for taps [F + F2, taps)), with the same result. */
 conv_engine* conv_far_engine(conv_engine* e);
 
 /* Set the a-priori feedback-path estimates F_hat (Sec. 3.1, Eq. 3): host array
@@ -210,7 +212,10 @@ int afc_set_guard(conv_engine* e, double max_rms);
  * Nyquist, and each is updated with its own power.  pow starts at 0, and
  * conv_reset sets it back to 0.  conv_reset keeps the adapted F_hat.
  * afc_set_paths restores a given estimate.  c_n is computed with the
- * updated F_hat.
+ * updated F_hat.  (Internally, partition 0 takes each step at once and the
+ * other partitions two blocks later, with correction terms that give the same
+ * c_n; afc_get_path_spectra and turning adaptation off first apply what is
+ * pending.)
  *
  * mu in [0, 2), lambda in [0, 1), delta >= 0 finite (> 0 when mu > 0), else
  * CONV_E_INVAL.  CONV_E_STATE without afc_set_paths, for FP16/BF16 engines

@@ -731,12 +731,16 @@ int check_dev_err(conv_engine* e) {
     return CONV_OK;
 }
 
+int flush_nlms_update(conv_engine* e);
+
 int engine_reset(conv_engine* e) {
     int rc;
     if (e->has_last) CK(cudaStreamSynchronize(e->last_stream));  // blocks enqueued on a caller's stream
     for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
     if (e->as) CK(cudaStreamSynchronize(e->as));
     CK(cudaStreamSynchronize(e->stream));
+    // the adapted spectra are kept: apply the step still pending on them
+    if ((rc = flush_nlms_update(e))) return rc;
     if ((rc = part_reset(e, e->syn))) return rc;
     if ((rc = part_reset(e, e->fb))) return rc;
     if (e->d_c) CK(cudaMemsetAsync(e->d_c, 0, (size_t)e->n_in * e->B * sizeof(float), e->stream));
@@ -1254,6 +1258,7 @@ int afc_set_paths(conv_engine* e, const float* f, long long taps_fb) {
     if (taps_fb < 1) return set_err(CONV_E_INVAL, "taps_fb must be >= 1");
     DeviceGuard g(e->dev);
     int rc;
+    e->upd_pending = false;  // the estimate is replaced: a pending step of the old one is dropped
     if ((rc = part_alloc(e, e->fb, e->n_out, e->n_in, taps_fb))) return rc;
     if (!e->d_c && (rc = dev_alloc(e, &e->d_c, (size_t)e->n_in * e->B * sizeof(float)))) return rc;
     if (!e->d_e && (rc = dev_alloc(e, &e->d_e, (size_t)e->n_in * e->B * sizeof(float)))) return rc;

@@ -349,3 +349,30 @@ def test_adaptive_device_streams_and_spectra_reads_are_bit_exact():
         y2, e2, w2 = open_loop_adaptive(e, s, B, read_at=(0, 17, 29))
     assert np.array_equal(y0, y1) and np.array_equal(e0, e1) and np.array_equal(w0, w1)
     assert np.array_equal(y0, y2) and np.array_equal(e0, e2) and np.array_equal(w0, w2)
+
+
+def test_reset_keeps_the_adapted_estimate():
+    """conv_reset restarts the stream but keeps F_hat as adapted so far,
+    including the step the deferred schedule has not applied to the tail
+    partitions yet."""
+    h, f, s = small_case(seed=59, nb=30)
+    P, L, B = 2, 3, 64
+
+    def engine():
+        e = U.Engine(48000, B, P, L, h.shape[2])
+        e.set_filters(h)
+        e.set_paths((0.3 * f).astype(np.float32))
+        e.set_adaptation(0.3, 0.9, 1e-2)
+        return e
+
+    with engine() as e:
+        open_loop_adaptive(e, s, B)
+        w0 = e.path_spectra()
+    with engine() as e:
+        l_n = np.empty((L, B), np.float32)
+        for b in range(s.shape[1] // B):
+            e.process_afc(np.ascontiguousarray(s[:, b * B : (b + 1) * B]), l_n)
+        e.reset()
+        w1 = e.path_spectra()
+        assert e.info()["afc_adaptive"] == 1
+    assert np.array_equal(w0, w1)
