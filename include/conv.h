@@ -220,7 +220,9 @@ int afc_set_guard(conv_engine* e, double max_rms);
  * mu in [0, 2), lambda in [0, 1), delta >= 0 finite (> 0 when mu > 0), else
  * CONV_E_INVAL.  CONV_E_STATE without afc_set_paths, for FP16/BF16 engines
  * (the update needs FP32 spectra), or while the session is in a batch.
- * Waits for the engine's queued work.  Takes effect from the next block. */
+ * Waits for the engine's queued work.  Takes effect from the next block.
+ * While adaptation is on, the conv_process_* calls (synthesis only) return
+ * CONV_E_STATE: every block must pass through the canceller. */
 int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta);
 
 /* Copy the canceller's current sub-filter spectra to host memory f_spec, laid

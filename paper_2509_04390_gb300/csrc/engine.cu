@@ -1269,6 +1269,7 @@ int afc_set_paths(conv_engine* e, const float* f, long long taps_fb) {
 int conv_process_block_async(conv_engine* e, const float* d_in, float* d_out, void* cuda_stream) {
     if (!e || !d_in || !d_out) return set_err(CONV_E_INVAL, "null argument");
     if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
+    if (e->adapt) return set_err(CONV_E_STATE, "the adaptive canceller needs every block through afc_process_block");
     DeviceGuard g(e->dev);
     return enqueue_block(e, d_in, d_out, static_cast<cudaStream_t>(cuda_stream));
 }
@@ -1276,6 +1277,7 @@ int conv_process_block_async(conv_engine* e, const float* d_in, float* d_out, vo
 int conv_process_block(conv_engine* e, const float* in, float* out) {
     if (!e || !in || !out) return set_err(CONV_E_INVAL, "null argument");
     if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
+    if (e->adapt) return set_err(CONV_E_STATE, "the adaptive canceller needs every block through afc_process_block");
     DeviceGuard g(e->dev);
     const size_t ib = (size_t)e->n_in * e->B * sizeof(float), ob = (size_t)e->n_out * e->B * sizeof(float);
     std::memcpy(e->h_in, in, ib);
@@ -1295,6 +1297,7 @@ int conv_process_blocks(conv_engine* e, const float* in, float* out, long long n
     if (!e || !in || !out) return set_err(CONV_E_INVAL, "null argument");
     if (n_blocks < 1) return set_err(CONV_E_INVAL, "n_blocks must be >= 1");
     if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
+    if (e->adapt) return set_err(CONV_E_STATE, "the adaptive canceller needs every block through afc_process_block");
     DeviceGuard g(e->dev);
     const long long C = std::min<long long>(n_blocks, 256);  // blocks per chunk
     int rc = CONV_OK;

@@ -247,6 +247,9 @@ def test_state_and_argument_errors():
                 e.set_adaptation(mu, lam, delta)
             assert ei.value.code == U.CONV_E_INVAL
         e.set_adaptation(0.3, 0.9, 1e-3)
+        with pytest.raises(U.ConvError) as ei:
+            e.process(np.zeros((2, 64), np.float32))  # a synthesis-only block would skip the canceller
+        assert ei.value.code == U.CONV_E_STATE
         with U.Batch("fp32") as b:
             with pytest.raises(U.ConvError) as ei:
                 b.add(e)
