@@ -8,8 +8,12 @@
 //   nlms_update  F_hat[p][l][j][k] += G_p[k] conj(U_l,j[k]) over the tail
 //                partitions of every filter tile; streams them once (read +
 //                write), the delay line and G come from L2
+//   nlms_update_mac  the same step fused with the canceller's tail MAC of a
+//                later block: each spectrum is read, stepped, written back and
+//                multiplied by its delay-line entry in one pass (split partials)
 //   nlms_corr    chunks of the lag-one and lag-two correlations of the delay
-//                line (the deferred update's correction terms)
+//                line (the deferred update's correction terms), summed by the
+//                last CTA of each bin range
 #include <cuda_runtime.h>
 
 #include "device_util.cuh"
