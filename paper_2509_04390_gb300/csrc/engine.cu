@@ -419,6 +419,7 @@ struct conv_engine {
     unsigned* d_ticket = nullptr;  // [B] completion counters of the correlation kernel
     float2* d_side = nullptr;    // [2][n_kt][n_out][BT] ring slots the pushes overwrote, by block parity
     bool upd_pending = false;    // the previous block's step is not yet in the tail partitions
+    int fb_S_full = 0;           // the canceller's default splits (the adaptive pass; its partials' size)
     int in_batches = 0;          // batches holding this session
     // non-uniform partitioning (conv_set_far_block): taps [0, far_B) in this
     // engine's own partitions of `block`, taps [far_B, taps) in a nested engine
@@ -914,12 +915,12 @@ int enqueue_nlms_update(conv_engine* e, long long m, cudaStream_t s) {
 // in one pass with the tail MAC of block m+2 (which needs F_m).
 int enqueue_nlms_update_mac(conv_engine* e, long long m, bool step, cudaStream_t s) {
     Part& F = e->fb;
-    if (F.K < 2 || F.plan.S == 0) return CONV_OK;
+    if (F.K < 2 || e->fb_S_full == 0) return CONV_OK;
     NlmsUpdateMacArgs a{};
     a.u = update_args(e, m, true);
     if (!step || m < 0) a.u.G = nullptr;
     a.partial = static_cast<float2*>(F.partial[(m + 2) & 1]);
-    a.S = F.plan.S;
+    a.S = e->fb_S_full;
     a.mac_slot0 = slot_of(m + 2, F.K);
     CK(launch_nlms_update_mac(a, s));
     return CONV_OK;
@@ -1002,6 +1003,7 @@ int enqueue_afc_prediction(conv_engine* e, cudaStream_t s) {
     int rc;
     CK(cudaStreamWaitEvent(s, F.ev_tail[n & 1], 0));
     OutArgs oa = out_args(e, F, n, e->d_c);
+    if (e->adapt && F.K >= 2) oa.S = e->fb_S_full;  // the adaptive pass's partials
     if (e->adapt) {
         // G_n and the step on partition 0 are done; the tail of this block
         // holds F_{n-2}: add the two steps it lacks
@@ -1276,6 +1278,25 @@ void plan_syn_beside_canceller(conv_engine* e) {
     P.plan = q;
 }
 
+// The canceller's own tail runs on 2 splits per tile (16 CTAs at the paper
+// config) beside that: 34.2 -> 32.7 us per block.  Its partials keep the size
+// of the default plan, whose split count the adaptive pass uses.
+void plan_fb_beside_synthesis(conv_engine* e) {
+    Part& F = e->fb;
+    e->fb_S_full = F.plan.S;
+    if (!F.allocated || F.plan.S <= 2) return;
+    TileOverride o;
+    o.splits = 2;
+    MacPlan q = plan_mac(e->prec, e->B, F.n_src, F.n_dst, F.K, e->num_sms, F.n_src, o);
+    if (q.h_bytes != F.plan.h_bytes || q.x_bytes != F.plan.x_bytes || q.tile_elems != F.plan.tile_elems ||
+        q.partial_bytes > F.plan.partial_bytes)
+        return;
+    q.partial_bytes = F.plan.partial_bytes;
+    std::string why;
+    if (check_plan(q, &why)) return;
+    F.plan = q;
+}
+
 int afc_set_paths(conv_engine* e, const float* f, long long taps_fb) {
     if (!e || !f) return set_err(CONV_E_INVAL, "null argument");
     if (taps_fb < 1) return set_err(CONV_E_INVAL, "taps_fb must be >= 1");
@@ -1287,6 +1308,7 @@ int afc_set_paths(conv_engine* e, const float* f, long long taps_fb) {
     if (!e->d_e && (rc = dev_alloc(e, &e->d_e, (size_t)e->n_in * e->B * sizeof(float)))) return rc;
     if ((rc = part_set_filters(e, e->fb, f))) return rc;
     plan_syn_beside_canceller(e);
+    plan_fb_beside_synthesis(e);
     return engine_reset(e);
 }
 
@@ -1454,6 +1476,10 @@ int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta) {
         CK(cudaMemsetAsync(e->d_A, 0, 36 * (size_t)e->B * sizeof(float2), e->stream));
         CK(cudaMemsetAsync(e->d_side, 0, 2 * (size_t)e->n_out * e->B * sizeof(float2), e->stream));
         if (e->nblk > 0 && (rc = enqueue_nlms_corr(e, e->nblk - 1, e->stream))) return rc;
+        // this block's canceller tail again, in the split count of the
+        // adaptive pass, whose partials the adaptive output reads
+        if ((rc = enqueue_nlms_update_mac(e, e->nblk - 2, false, e->stream))) return rc;
+        CK(cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream));
         e->upd_pending = false;
     }
     CK(cudaStreamSynchronize(e->stream));
