@@ -118,6 +118,16 @@ def test_tiling_overrides_stay_in_bounds(lib):
                                 )
 
 
+def test_canceller_split_counts_replay_clean(lib):
+    # the split counts an engine with a feedback canceller uses: two thirds of
+    # the synthesis default and two for the canceller's own tail
+    for precision in ("fp32", "fp16", "bf16"):
+        for B in (16, 64, 128, 256, 512, 1024, 4096):
+            for n_src, n_dst, taps in ((4, 16, 384000), (16, 4, 24000), (2, 3, 3000), (8, 32, 200000)):
+                for splits in (1, 2, 3, 6, 12, 24):
+                    upols.conv_plan_check(precision, B, n_src, n_dst, taps, 152, "tma", 0, 0, 0, splits)
+
+
 def test_tiling_override_arguments_are_validated(lib):
     with pytest.raises(upols.ConvError):
         upols.conv_plan_check("fp32", 256, 4, 16, 384000, 152, 0, 24)  # bin tile not a power of two
