@@ -40,9 +40,10 @@ template <int PREC>
 struct Store;
 
 // Storage of a spectrum row of BT bins.  FP32 rows interleave (re, im);
-// FP16/BF16 rows are planar, [BT real parts][BT imaginary parts], so the MAC
-// can work on pairs of bins with packed FP32x2 FMAs.  `c` is the complex
-// element index (row start + kl), kl the bin within the row.
+// FP16/BF16 rows are planar in chunks of four bins, [4 real parts][4
+// imaginary parts] (16 bytes), so the MAC loads a thread's four bins with one
+// 16-byte load and works on pairs of bins with packed FP32x2 FMAs.  `c` is the
+// complex element index (row start + kl), kl the bin within the row.
 template <>
 struct Store<PREC_FP32> {
     static constexpr int BYTES = 8;
@@ -65,6 +66,10 @@ struct Store<PREC_FP32> {
     }
 };
 
+// Offset (in 16-bit values) of bin kl's real part within its row; the
+// imaginary part follows 4 values later.
+__device__ __forceinline__ int planar_offset(int kl) { return (kl & ~3) * 2 + (kl & 3); }
+
 __device__ __forceinline__ float2 unpack_half2(uint32_t w) {
     __half2 h2 = *reinterpret_cast<const __half2*>(&w);
     return __half22float2(h2);
@@ -81,13 +86,15 @@ struct Store<PREC_FP16> {
     static constexpr bool PLANAR = true;
     __device__ __forceinline__ static float2 unpack(uint32_t w) { return unpack_half2(w); }
     __device__ __forceinline__ static void store1(void* base, size_t c, int kl, int BT, float2 v) {
-        __half* h = reinterpret_cast<__half*>(base) + 2 * (c - kl) + kl;
+        (void)BT;
+        __half* h = reinterpret_cast<__half*>(base) + 2 * (c - kl) + planar_offset(kl);
         h[0] = __float2half_rn(v.x);
-        h[BT] = __float2half_rn(v.y);
+        h[4] = __float2half_rn(v.y);
     }
     __device__ __forceinline__ static float2 load1(const void* base, size_t c, int kl, int BT) {
-        const __half* h = reinterpret_cast<const __half*>(base) + 2 * (c - kl) + kl;
-        return make_float2(__half2float(h[0]), __half2float(h[BT]));
+        (void)BT;
+        const __half* h = reinterpret_cast<const __half*>(base) + 2 * (c - kl) + planar_offset(kl);
+        return make_float2(__half2float(h[0]), __half2float(h[4]));
     }
 };
 
@@ -98,26 +105,29 @@ struct Store<PREC_BF16> {
     static constexpr bool PLANAR = true;
     __device__ __forceinline__ static float2 unpack(uint32_t w) { return unpack_bf162(w); }
     __device__ __forceinline__ static void store1(void* base, size_t c, int kl, int BT, float2 v) {
-        __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(base) + 2 * (c - kl) + kl;
+        (void)BT;
+        __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(base) + 2 * (c - kl) + planar_offset(kl);
         h[0] = __float2bfloat16_rn(v.x);
-        h[BT] = __float2bfloat16_rn(v.y);
+        h[4] = __float2bfloat16_rn(v.y);
     }
     __device__ __forceinline__ static float2 load1(const void* base, size_t c, int kl, int BT) {
-        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(base) + 2 * (c - kl) + kl;
-        return make_float2(__bfloat162float(h[0]), __bfloat162float(h[BT]));
+        (void)BT;
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(base) + 2 * (c - kl) + planar_offset(kl);
+        return make_float2(__bfloat162float(h[0]), __bfloat162float(h[4]));
     }
 };
 
-// Four planar bins (8 bytes of real parts, 8 of imaginary parts) as floats.
+// Four planar bins (one 16-byte chunk: 8 bytes of real parts, 8 of
+// imaginary parts) as floats.
 template <typename St>
 __device__ __forceinline__ void load_planar4(const unsigned char* row, int kv, int BT, float2 (&re)[2],
                                              float2 (&im)[2]) {
-    const uint2 r = *reinterpret_cast<const uint2*>(row + (size_t)kv * 8);
-    const uint2 i = *reinterpret_cast<const uint2*>(row + (size_t)BT * 2 + (size_t)kv * 8);
-    re[0] = St::unpack(r.x);
-    re[1] = St::unpack(r.y);
-    im[0] = St::unpack(i.x);
-    im[1] = St::unpack(i.y);
+    (void)BT;
+    const uint4 t = *reinterpret_cast<const uint4*>(row + (size_t)kv * 16);
+    re[0] = St::unpack(t.x);
+    re[1] = St::unpack(t.y);
+    im[0] = St::unpack(t.z);
+    im[1] = St::unpack(t.w);
 }
 
 // d = a * b + c on pairs of floats (one packed FP32x2 FMA)
