@@ -198,6 +198,32 @@ def tapch(w):
     return t * w.block
 
 
+def step_bandwidth(w, info, t_step, peak):
+    """Bytes per step over the step time, split into what must come from HBM
+    and what L2 holds.  The filter spectra (n_out * n_in * (K-1) * B * s bytes
+    per tail) exceed L2 and stream from HBM every step; the delay line
+    (n_in * K * B * s bytes, 12 MB at the paper configuration) is re-read by
+    every output tile and stays L2-resident, so it is not HBM traffic."""
+    s = 8 if info["precision"] == 0 else 4
+    K, B = info["K"], w.block
+    total = info["mac_bytes"] + step_extra_bytes(w, info)
+    filt = w.n_out * w.n_in * (K - 1) * B * s
+    if w.f is not None and info["K_fb"] > 1:
+        filt += w.f.shape[0] * w.f.shape[1] * (info["K_fb"] - 1) * B * s
+        total += info["mac_fb_bytes"]
+    return {
+        "algorithmic_bytes_per_step": int(total),
+        "algorithmic_gbs": total / t_step / 1e9,
+        "hbm_bytes_per_step": int(filt),
+        "hbm_gbs": filt / t_step / 1e9,
+        "hbm_frac_of_peak": filt / t_step / 1e9 / peak,
+        "note": "whole steps back to back (pack, head + output, tail MAC), each step's background tail inside "
+                "the timed region; hbm_* counts only the filter spectra, which exceed L2 and stream from HBM "
+                "every step; the delay line is L2-resident, and consecutive tails overlap on two streams, so "
+                "algorithmic_gbs is not DRAM throughput",
+    }
+
+
 def step_extra_bytes(w, info):
     """Algorithmic bytes of a step outside the tail MAC: the head partition
     (filters + delay-line row), the new spectrum written, input and output."""
@@ -359,6 +385,7 @@ def config_dict(args, w):
 
 
 def run_ours(args):
+    """The headline arm: returns rank 0's JSON line (None on other ranks)."""
     import torch
 
     rank, local_rank, world = env_rank()
@@ -425,12 +452,17 @@ def run_ours(args):
     def timed_region(first):
         if dist is not None:
             dist.barrier()
+        U.conv_synchronize(eng.h)  # nothing of the engine's runs into the region
         torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for i in range(args.steps):
             step(first + i)
+        # the region ends when everything the steps enqueued has finished,
+        # including the last step's background tail MAC (for the next block):
+        # S steps are credited with S tails, all inside the region
+        lib.conv_join_async(eng.h, p_stream)
         ev1.record(stream)
         torch.cuda.synchronize()
         if dist is not None:
@@ -594,13 +626,7 @@ def run_ours(args):
                     "mode": "one call per block period (real-time use)",
                 },
             },
-            "step_bandwidth": {
-                "algorithmic_bytes_per_step": info["mac_bytes"] + step_extra_bytes(w, info),
-                "achieved_gbs": (info["mac_bytes"] + step_extra_bytes(w, info)) / (t_max / args.steps) / 1e9,
-                "frac_of_peak": (info["mac_bytes"] + step_extra_bytes(w, info)) / (t_max / args.steps) / 1e9 / peak,
-                "note": "whole step (pack, head + output, tail MAC) back to back; consecutive blocks' tail MACs "
-                        "overlap on two streams, and the delay line (n_in*K*B*s bytes) is L2-resident",
-            },
+            "step_bandwidth": step_bandwidth(w, info, t_max / args.steps, peak),
             "roofline": {
                 "bound": "hbm",
                 "kernel": "k_fdl_mac (far part, once per far block)" if far_h else "k_fdl_mac",
@@ -624,12 +650,11 @@ def run_ours(args):
             "clocks": clk,
             "plan": {k: info[k] for k in ("K", "mac_ctas", "mac_splits", "mac_smem", "device_bytes")},
         }
-        print(json.dumps(line), flush=True)
     eng.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
 
 
 BATCH_TILING = {"kernel": "tma", "warps": 8}
@@ -692,6 +717,7 @@ def run_batch(args):
     ev0.record(stream)
     for i in range(args.steps):
         bstep(args.warmup + i)
+    lib.conv_batch_join_async(batch.b, p_stream)  # the last step's background tails inside the region
     ev1.record(stream)
     torch.cuda.synchronize()
     batch.synchronize()
@@ -709,6 +735,8 @@ def run_batch(args):
     ev0.record(stream)
     for i in range(k_u):
         ustep(i)
+    for e in engs:
+        lib.conv_join_async(e.h, p_stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     for e in engs:
@@ -755,8 +783,7 @@ def run_batch(args):
     }
     for e in engs:
         e.close()
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_group(args):
@@ -807,6 +834,7 @@ def run_group(args):
     ev0.record(stream)
     for i in range(args.steps):
         step(args.warmup + i)
+    lib.conv_group_join_async(grp.g, p_stream)  # the last step's background tail inside the region
     ev1.record(stream)
     torch.cuda.synchronize()
     tw1 = time.time()
@@ -849,7 +877,7 @@ def run_group(args):
     grp.close()
     # the same sessions as separate engines (filters streamed once per session)
     engs = []
-    for s in range(S):
+    for s in range(0 if args.no_separate else S):
         e = U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, prec)
         e.set_filters(w.h)
         engs.append(e)
@@ -870,6 +898,8 @@ def run_group(args):
     ev0.record(stream)
     for i in range(k_u):
         sep_step(i)
+    for e in engs:
+        lib.conv_join_async(e.h, p_stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     t_sep = ev0.elapsed_time(ev1) / 1e3 / k_u
@@ -909,7 +939,7 @@ def run_group(args):
             "per_block_call": {"value": units / t_e2e_1 / 1e9, "steps": k_e, "ms_per_call": t_e2e_1 * 1e3,
                                "call": "conv_group_process, one block per call"},
         },
-        "separate_engines": {
+        "separate_engines": None if args.no_separate else {
             "value": units / t_sep / 1e9, "ms_per_step": t_sep * 1e3, "steps": k_u,
             "note": "the same sessions as separate engines, one call (3 launches) each per step",
         },
@@ -918,8 +948,7 @@ def run_group(args):
         "gpu_launches": args.steps * info["kernels_per_block"],
         "clocks": clocks.summary(tw0, tw1),
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_serve(args):
@@ -958,8 +987,66 @@ def run_serve(args):
         "poisson": sims,
         "sustained": caps,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
+
+
+EXTRA_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "roofline", "e2e",
+              "step_bandwidth", "unbatched", "separate_engines", "plan", "clocks", "gpu_launches", "poisson",
+              "sustained", "higher_is_better")
+
+
+def run_extras(args):
+    """The secondary configurations, each a short run of its own with its own
+    timing and roofline, reported under "extra" of the headline line: block
+    128 (the paper's default) and 512 at the headline shape, FP16 and BF16
+    spectra, synthesis + feedback canceller (FP32, FP16), 8 sessions sharing
+    one filter set on the tensor cores, 64 heterogeneous FP16 sessions in one
+    batch, and a short serving run.  A configuration that fails is reported
+    with its error instead of ending the run."""
+    import copy
+    import traceback
+
+    steps = max(3, min(args.steps, args.extra_steps))
+
+    def variant(**kw):
+        a = copy.copy(args)
+        a.steps, a.warmup = steps, max(3, min(args.warmup, 50))
+        a.seconds = min(args.seconds, 4.0)
+        a.e2e_steps, a.paced_blocks, a.no_cpu_baseline = 300, 0, True
+        a.far_block = a.far_block2 = 0
+        a.afc, a.adapt, a.batch, a.group, a.serve = False, 0.0, 0, 0, False
+        a.no_separate = False
+        for k, v in kw.items():
+            setattr(a, k, v)
+        return a
+
+    plan = [
+        ("paper_4x16_B128_fp32", run_ours, variant(block=128)),
+        ("paper_4x16_B512_fp32", run_ours, variant(block=512)),
+        ("paper_4x16_B256_fp16", run_ours, variant(precision="fp16")),
+        ("paper_4x16_B256_bf16", run_ours, variant(precision="bf16")),
+        ("afc_4x16_B256_fp32", run_ours, variant(afc=True)),
+        ("afc_4x16_B256_fp16", run_ours, variant(afc=True, precision="fp16")),
+        ("group_8_sessions_B256_fp16", run_group, variant(group=8, precision="fp16")),
+        ("batch_64_sessions_fp16", run_batch, variant(batch=64, precision="fp16", steps=min(steps, 200))),
+        ("serving", run_serve, variant(serve=True, serve_seconds=min(args.serve_seconds, 5.0))),
+    ]
+    out = {}
+    for name, fn, a in plan:
+        if name not in args.extras:
+            continue
+        t0 = time.time()
+        try:
+            line = fn(a)
+            out[name] = {k: line[k] for k in EXTRA_KEYS if k in line}
+        except Exception as exc:  # noqa: BLE001 - reported, the headline stands
+            out[name] = {"error": f"{type(exc).__name__}: {exc}", "trace": traceback.format_exc()[-800:]}
+        out[name]["wall_s"] = round(time.time() - t0, 1)
+    return out
+
+
+ALL_EXTRAS = ("paper_4x16_B128_fp32,paper_4x16_B512_fp32,paper_4x16_B256_fp16,paper_4x16_B256_bf16,"
+              "afc_4x16_B256_fp32,afc_4x16_B256_fp16,group_8_sessions_B256_fp16,batch_64_sessions_fp16,serving")
 
 
 def parse(argv=None):
@@ -991,6 +1078,12 @@ def parse(argv=None):
     ap.add_argument("--serve", action="store_true", help="run the serving-loop simulation instead")
     ap.add_argument("--group", type=int, default=0, help="time N sessions sharing one filter set (tensor-core MAC)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--extras", default=ALL_EXTRAS,
+                    help="comma-separated secondary configurations reported under 'extra' of the headline line "
+                         "(single GPU, default run only); '' for none")
+    ap.add_argument("--extra-steps", type=int, default=2000, help="timed steps of each secondary configuration")
+    ap.add_argument("--no-separate", action="store_true",
+                    help="with --group: skip the comparison with separate engines")
     return ap.parse_args(argv)
 
 
@@ -1000,13 +1093,22 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    args.extras = [x for x in args.extras.split(",") if x]
     if args.batch:
-        return run_batch(args)
-    if args.serve:
-        return run_serve(args)
-    if args.group:
-        return run_group(args)
-    return run_ours(args)
+        line = run_batch(args)
+    elif args.serve:
+        line = run_serve(args)
+    elif args.group:
+        line = run_group(args)
+    else:
+        line = run_ours(args)
+        _, _, world = env_rank()
+        plain = not (args.afc or args.far_block or args.precision != "fp32" or args.block != 256)
+        if line is not None and world == 1 and plain and args.extras:
+            line["extra"] = run_extras(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -78,6 +78,23 @@ typedef struct conv_info {
     long long mac_far_bytes;  /* far tail MAC (once per far block), 0 if none    */
 } conv_info;
 
+/* Per-session counters (conv_get_stats).  Latency is the wall time of a
+ * blocking host-buffer call (conv_process_block, afc_process_block) from entry
+ * to return; the deadline is the block period block / fs. */
+#define CONV_STATS_BUCKETS 24
+typedef struct conv_stats {
+    long long blocks;          /* blocks processed (every call form, batches included) */
+    long long timed_calls;     /* blocking host-buffer calls that returned CONV_OK  */
+    long long deadline_misses; /* timed calls that took longer than the block period */
+    double max_latency_us;     /* longest timed call                               */
+    double sum_latency_us;     /* sum over the timed calls (mean = sum / timed_calls) */
+    long long latency_hist[CONV_STATS_BUCKETS]; /* timed calls by latency: bucket 0 holds
+                                  [0, 2) us, bucket i in 1..22 holds [2^i, 2^(i+1)) us,
+                                  bucket 23 everything from 2^23 us on               */
+    long long device_errors;   /* device-side waits that gave up (CONV_E_TIMEOUT)  */
+    long long guard_trips;     /* closed-loop guard trips (CONV_E_UNSTABLE)        */
+} conv_stats;
+
 /* Create an engine for n_in inputs, n_out outputs and filters of `taps` taps
  * at block size `block` (n_x, Sec. 4).  fs (Hz) only sets the block period
  * used in statistics.  block must be a power of two in [16, 4096] (the block
@@ -89,7 +106,10 @@ conv_engine* conv_create(double fs, int block, int n_in, int n_out, long long ta
 
 /* Choose the storage precision of filter and delay-line spectra (one of
  * CONV_FP32, CONV_FP16, CONV_BF16).  FFTs and accumulation stay FP32.  Only
- * valid before conv_set_filters (CONV_E_STATE afterwards). */
+ * valid before conv_set_filters (CONV_E_STATE afterwards).  Beyond the paper,
+ * which keeps every spectrum in FP32: reduced-precision storage halves the
+ * bytes the FDL MAC streams (each stored value is scaled by a power of two per
+ * output tile and partition, or per delay-line slot, so scaling is exact). */
 int conv_set_precision(conv_engine* e, int mode);
 
 /* FDL MAC kernels (conv_tiling.kernel) */
@@ -157,6 +177,11 @@ conv_engine* conv_far_engine(conv_engine* e);
 int afc_set_paths(conv_engine* e, const float* f, long long taps_fb);
 
 /* Process one block, host buffers: in[n_in][block] -> out[n_out][block].
+ * The three stages of Sec. 4: (1) slide the 2*block-sample input window by one
+ * block and take its R2C FFT; (2) push the spectrum into the frequency-domain
+ * delay line and multiply-accumulate every sub-filter spectrum with its
+ * delay-line entry over all input -> output pairs (Eq. 6); (3) C2R IFFT and
+ * keep the last `block` samples (overlap-save).
  * The block goes through the engine's mapped pinned host buffers, which the
  * pack kernel reads and the output kernel writes directly (no copy launches);
  * returns when out is written.  The next block's tail MAC keeps running in
@@ -172,16 +197,28 @@ int conv_process_block(conv_engine* e, const float* in, float* out);
  * Blocks until `out` is filled. */
 int conv_process_blocks(conv_engine* e, const float* in, float* out, long long n_blocks);
 
-/* Same as conv_process_block with device pointers d_in[n_in][block] and
- * d_out[n_out][block], enqueued on `cuda_stream` (a cudaStream_t; NULL = the
- * legacy default stream).  Returns once the work is enqueued.  Blocks of one
- * engine form a chain: a block enqueued on another stream than the previous
- * block (or after a host-buffer call) first waits for that stream's work. */
+/* Same as conv_process_block (the three stages of Sec. 4) with device
+ * pointers d_in[n_in][block] and d_out[n_out][block], enqueued on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  Returns
+ * once the work is enqueued.  Blocks of one engine form a chain: a block
+ * enqueued on another stream than the previous block (or after a host-buffer
+ * call) first waits for that stream's work.  d_out is complete in the order
+ * of `cuda_stream`; the tail MAC of the next block, which the call also
+ * enqueues, runs on the engine's background streams (conv_join_async). */
 int conv_process_block_async(conv_engine* e, const float* d_in, float* d_out, void* cuda_stream);
+
+/* Make `cuda_stream` wait for all work the engine has enqueued so far,
+ * including the background tail MAC of the next block (and the canceller's,
+ * the NLMS step's and the far engine's work), without blocking the host.
+ * Work enqueued on `cuda_stream` afterwards starts once all of it is done:
+ * for timing a run of blocks with CUDA events, or before reusing buffers the
+ * engine may still read.  CONV_OK or CONV_E_INVAL / CONV_E_CUDA. */
+int conv_join_async(conv_engine* e, void* cuda_stream);
 
 /* One block of synthesis with feedback cancellation, host buffers:
  * e = mic - c_prev; out = H_aur^T * e; c = F_hat * out is kept and subtracted
- * from the next block (Sec. 5).  mic[n_in][block], out[n_out][block];
+ * from the next block (Sec. 5; the loop of Sec. 3.1, Fig. 1 and Eqs. 1-3, with
+ * both convolutions run by the three stages of Sec. 4).  mic[n_in][block], out[n_out][block];
  * e_or_null (if not NULL) receives e[n_in][block].  Needs conv_set_filters and
  * afc_set_paths (CONV_E_STATE otherwise).  Returns CONV_E_UNSTABLE and resets
  * the loop state if the RMS of e exceeds the guard set by afc_set_guard. */
@@ -235,12 +272,33 @@ int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta);
 int afc_get_path_spectra(conv_engine* e, float* f_spec);
 
 /* Zero the delay lines, sliding windows and the pending feedback prediction
- * (start of a new stream).  Filters are kept. */
+ * (start of a new stream): the zero initial state that the causal convolution
+ * of Sec. 3.1 (Eq. 2) and the loop of Sec. 5 start from.  Filters and feedback
+ * paths are kept (an adapted F_hat too).  Waits for the engine's queued work.
+ * Also the way back after CONV_E_TIMEOUT or CONV_E_UNSTABLE. */
 int conv_reset(conv_engine* e);
 
 /* Wait for all work the engine enqueued and report a device-side error
  * (CONV_E_TIMEOUT if a bounded wait gave up). */
 int conv_synchronize(conv_engine* e);
+
+/* Copy the handle's counters (conv_stats) to *out; conv_reset_stats zeroes
+ * them.  The counters survive conv_reset. */
+int conv_get_stats(const conv_engine* e, conv_stats* out);
+int conv_reset_stats(conv_engine* e);
+
+/* Fault-path testing of the bounded device-side waits.  The next synthesis
+ * tail MAC this handle launches has one CTA's producer withhold its first
+ * pipeline stage (it issues no copy and no arrival for it), so that CTA's
+ * consumers wait on a barrier that nothing completes.  Their wait is bounded
+ * by wait_ns (in [1e3, 1e9]) for that launch: they give up, raise the CTA's
+ * abort flag, record the error and return; the producer lets its other copies
+ * land first.  No GPU fault and no hang: the context stays usable.  The call
+ * whose output uses that tail returns CONV_E_TIMEOUT (its results, and those
+ * of blocks after it, are invalid until conv_reset).  CONV_E_STATE before
+ * conv_set_filters, with one partition (no tail MAC) or with the direct-load
+ * MAC (it has no pipeline waits). */
+int conv_inject_wait_timeout(conv_engine* e, long long wait_ns);
 
 /* Fill *out with the plan and size figures of the handle. */
 int conv_get_info(const conv_engine* e, conv_info* out);
@@ -279,20 +337,31 @@ int conv_plan_check(int precision, int block, int n_src, int n_dst, long long ta
  *        delay-line ring; slot0 is the slot of the newest input spectrum and
  *        partition p reads slot (slot0 + p) mod K;
  *   d_y  device, [n_out][block] float, written.
+ * d_H and d_X must be 16-byte aligned (the spectra are streamed with bulk
+ * copies that need it), d_y 4-byte aligned; CONV_E_INVAL otherwise, before
+ * anything is launched.
  * Enqueued on `cuda_stream` (NULL = legacy default stream); d_H and d_X must
  * be complete in stream order.  FP32 only.  Limits: block a power of two in
  * [16, 256], n_out in [1, 16], n_in*K <= 2^30; CONV_E_INVAL beyond them.
  *
  * The split partials live in a 2 MiB file-scope device array (plus 8 KB of
- * twiddle tables) that every GPU loading this library holds until exit.  The
- * first call on a device, with that device current, resolves the arrays'
- * device addresses and uploads the twiddles; make that first call before any
- * stream capture.  All calls share the array, and every call writes all the
- * partials it reads, so nothing needs clearing; calls that overlap on the GPU
- * race on the array.  Returns CONV_OK or a negative CONV_E_* code with the
- * message in conv_last_error(). */
+ * twiddle tables and an error word) that every GPU loading this library holds
+ * until exit.  The first call on a device, with that device current, resolves
+ * the arrays' device addresses and uploads the twiddles; make that first call
+ * before any stream capture.  All calls share the array, and every call
+ * writes all the partials it reads, so nothing needs clearing; calls that
+ * overlap on the GPU race on the array.  Returns CONV_OK or a negative
+ * CONV_E_* code with the message in conv_last_error().  The call returns once
+ * the work is enqueued, so a bounded device-side wait that gives up is not
+ * known yet: conv_fdl_mac_noalloc_status reports it. */
 int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int block, int n_in, int n_out, long long K,
                          long long slot0, float* d_y, void* cuda_stream);
+
+/* Error report of conv_fdl_mac_noalloc on the current device: waits for the
+ * work enqueued on `cuda_stream`, then reads and clears the device's error
+ * word.  CONV_E_TIMEOUT if a bounded wait of any call since the last report
+ * gave up (that call's output is invalid), else CONV_OK.  Allocates nothing. */
+int conv_fdl_mac_noalloc_status(void* cuda_stream);
 
 /* Device bytes a handle with these sizes would hold (synthesis, plus the
  * feedback canceller when taps_fb > 0), from the same planner the engine
@@ -345,6 +414,10 @@ int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, cons
 /* Wait for all of the batch's work; report a device-side error of any session. */
 int conv_batch_synchronize(conv_batch* b);
 
+/* Make `cuda_stream` wait for all the batch's work so far, including the
+ * background tail MACs of the next step (no host wait). */
+int conv_batch_join_async(conv_batch* b, void* cuda_stream);
+
 /* Algorithmic bytes of one step's batched tail MAC (all sessions, both
  * convolutions of canceller sessions). */
 long long conv_batch_step_bytes(const conv_batch* b);
@@ -370,9 +443,12 @@ void conv_batch_destroy(conv_batch* b);
  * is stored unscaled, so FP16 groups saturate input spectra above 65504
  * (inputs with |x| <= 1 never reach it: |X| <= 2 * block).  Output block n of
  * every session is exactly samples [nB, (n+1)B) of its causal convolution,
- * as for conv_process_block.  The whole MAC runs after the block's input
- * arrives (no background tail): higher block latency than an engine, far
- * higher throughput per GPU. */
+ * as for conv_process_block.  The schedule is the engine's split phase: the
+ * tail MAC (all K-steps but the first) of block n+1 runs on background
+ * streams as soon as block n's spectra are in the delay lines, and a block's
+ * call runs the pack, then the first K-step (on CUDA cores) with the tail's
+ * partials and the C2R output; far higher throughput per GPU than separate
+ * engines. */
 typedef struct conv_group conv_group;
 
 typedef struct conv_group_info {
@@ -437,6 +513,10 @@ int conv_group_reset(conv_group* g);
 
 /* Wait for the group's work; CONV_E_TIMEOUT if a device-side wait gave up. */
 int conv_group_synchronize(conv_group* g);
+
+/* Make `cuda_stream` wait for all the group's work so far, including the
+ * background tail MAC of the next block (no host wait). */
+int conv_group_join_async(conv_group* g, void* cuda_stream);
 
 int conv_group_get_info(const conv_group* g, conv_group_info* out);
 

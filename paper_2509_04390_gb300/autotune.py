@@ -1,0 +1,370 @@
+"""Autotuner of the FDL MAC tiling: partition-split, bin-tile and pipeline shapes.
+
+The engine's planner (``plan_mac`` in the engine) picks a tiling from a fixed
+rule: bin tiles so that ~16-20 partition splits per tile cover all SMs but 8,
+64 KiB filter copies per pipeline stage, two stages for FP32 and three for
+FP16/BF16.  The rule was set on one configuration.  This module measures the
+alternatives on the real engine and keeps the best per shape:
+
+* ``candidates`` enumerates ``conv_tiling`` overrides (kernel, bin tile, stage
+  depth and size, consumer warps) around the planner's choice and keeps those
+  that ``conv_plan_check`` (the host-side replay of every CTA's copy and store
+  addresses) accepts, so no candidate that could read or write out of bounds
+  is ever launched;
+* ``measure`` times one candidate on a fresh engine with CUDA events on the
+  launching stream: back-to-back blocks (the step, each step's background
+  tail MAC inside the timed region through ``conv_join_async``) or the MAC
+  kernel alone (``conv_profile_*``);
+* ``tune`` runs the candidates within a time budget and stores the winner in a
+  JSON cache keyed by (precision, block, n_in, n_out, K, SM count);
+* ``lookup`` reads the cache; ``Engine(..., tiling="tuned")`` applies it (the
+  planner's rule when the shape has no entry).
+
+Session groups (the tensor-core MAC) have their own space (``conv_group_tiling``:
+CTAs, K-steps per stage, stages, tail streams) with ``group_candidates``,
+``measure_group``, ``tune_group`` and ``lookup_group``.
+
+Device memory and streams come from PyTorch; every timed step is the engine's
+own C-ABI call.
+"""
+
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+
+from . import upols as U
+
+CACHE_ENV = "GB300CONV_TUNE_CACHE"
+FS = 48000
+
+
+def cache_path(path: str | None = None) -> str:
+    if path:
+        return path
+    env = os.environ.get(CACHE_ENV)
+    if env:
+        return env
+    return os.path.join(os.path.expanduser("~"), ".cache", "gb300conv", "mac_tiling.json")
+
+
+def num_partitions(taps: int, block: int) -> int:
+    return -(-int(taps) // int(block))
+
+
+def key(precision: str, block: int, n_in: int, n_out: int, taps: int, num_sms: int) -> str:
+    """Cache key: the shape that fixes the MAC's work and the GPU it ran on."""
+    return f"{precision}:B{block}:in{n_in}:out{n_out}:K{num_partitions(taps, block)}:sm{num_sms}"
+
+
+def group_key(precision: str, block: int, n_in: int, n_out: int, taps: int, sessions: int, num_sms: int) -> str:
+    return f"group:{precision}:B{block}:in{n_in}:out{n_out}:K{num_partitions(taps, block)}:S{sessions}:sm{num_sms}"
+
+
+def load_cache(path: str | None = None) -> dict:
+    try:
+        with open(cache_path(path)) as f:
+            data = json.load(f)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def save_entry(k: str, entry: dict, path: str | None = None) -> None:
+    """Merge one entry into the cache file (written whole, then renamed)."""
+    p = cache_path(path)
+    os.makedirs(os.path.dirname(p) or ".", exist_ok=True)
+    data = load_cache(p)
+    data[k] = entry
+    tmp = p + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def lookup(precision, block, n_in, n_out, taps, num_sms=152, path=None):
+    """The cached tiling (a dict for ``conv_set_tiling``) of this shape, or None."""
+    e = load_cache(path).get(key(precision, block, n_in, n_out, taps, num_sms))
+    return dict(e["tiling"]) if e and "tiling" in e else None
+
+
+def lookup_group(precision, block, n_in, n_out, taps, sessions, num_sms=152, path=None):
+    e = load_cache(path).get(group_key(precision, block, n_in, n_out, taps, sessions, num_sms))
+    return dict(e["tiling"]) if e and "tiling" in e else None
+
+
+# ---------------------------------------------------------------- candidates
+
+DEFAULT_SPACE = {
+    "bin_tile": (16, 32, 64, 128),
+    "stages": (2, 3, 4, 6),
+    "stage_kib": (16, 32, 64),
+    "warps": (8, 16),
+    "direct": ("direct1", "direct2"),
+}
+
+
+def candidates(precision, block, n_in, n_out, taps, num_sms=152, space=None):
+    """Tiling overrides to try, the planner's own choice ({}) first.  Every
+    candidate passed ``conv_plan_check``, the host-side replay of all the
+    MAC's copy, read and store addresses against its buffers and shared
+    memory; duplicates of the same override are dropped."""
+    sp = dict(DEFAULT_SPACE)
+    sp.update(space or {})
+    out, seen = [{}], {()}
+
+    def add(t):
+        k = tuple(sorted(t.items()))
+        if k in seen:
+            return
+        try:
+            U.conv_plan_check(precision, block, n_in, n_out, taps, num_sms, **t)
+        except U.ConvError:
+            return
+        seen.add(k)
+        out.append(t)
+
+    bts = [bt for bt in sp["bin_tile"] if 16 <= bt <= block] or [block]
+    for bt in bts:
+        for kib in sp["stage_kib"]:
+            for st in sp["stages"]:
+                for nw in sp["warps"]:
+                    add({"kernel": "tma", "bin_tile": bt, "stages": st, "stage_kib": kib, "warps": nw})
+    if precision == "fp32":
+        for k in sp["direct"]:
+            for bt in bts:
+                add({"kernel": k, "bin_tile": bt})
+    # a fixed shuffle after the planner's choice: a time budget that ends
+    # early has still sampled the whole space evenly
+    rest = out[1:]
+    order = np.random.default_rng(12345).permutation(len(rest))
+    return [out[0]] + [rest[i] for i in order]
+
+
+def group_candidates(precision, block, n_in, n_out, taps, sessions, num_sms=152):
+    """Group MAC tilings to try (the planner's first), each accepted by
+    ``conv_group_plan_check``."""
+    out, seen = [{}], {()}
+    for ctas in (num_sms - 24, num_sms - 16, num_sms - 8):
+        for ks in (2, 4):
+            for st in (2, 3, 4):
+                for ts in (1, 2):
+                    t = {"ctas": ctas, "stage_k_steps": ks, "stages": st, "tail_streams": ts}
+                    k = tuple(sorted(t.items()))
+                    if k in seen:
+                        continue
+                    try:
+                        U.conv_group_plan_check(precision, block, n_in, n_out, taps, sessions, num_sms, t)
+                    except U.ConvError:
+                        continue
+                    seen.add(k)
+                    out.append(t)
+    return out
+
+
+# ----------------------------------------------------------------- measuring
+
+
+def _filters(n_out, n_in, taps, seed=1):
+    """Exponentially decaying noise filters (RT60 = 3/4 of the length)."""
+    rng = np.random.default_rng(seed)
+    t = np.arange(taps, dtype=np.float32) / FS
+    env = np.exp(np.float32(-6.91) * t / np.float32(max(0.75 * taps / FS, 1e-3))).astype(np.float32)
+    h = rng.standard_normal((n_out, n_in, taps), dtype=np.float32) * env
+    return h / np.float32(np.sqrt(max(1.0, float(np.sum(env * env)))))
+
+
+def measure(tiling, precision, block, n_in, n_out, taps, h=None, steps=200, warmup=20, objective="step"):
+    """Seconds per block of one tiling on a fresh engine: back-to-back steps
+    (objective "step": each step's background tail inside the timed region)
+    or the tail MAC kernel alone (objective "mac")."""
+    import torch
+
+    lib = U.load()
+    eng = U.Engine(FS, block, n_in, n_out, taps, precision, tiling or None)
+    try:
+        eng.set_filters(_filters(n_out, n_in, taps) if h is None else h)
+        nbuf = 8
+        d_in = (torch.randn((nbuf, n_in, block), device="cuda") * 0.1).contiguous()
+        d_out = torch.empty((2, n_out, block), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+        p_in = [d_in[i].data_ptr() for i in range(nbuf)]
+        p_out = [d_out[0].data_ptr(), d_out[1].data_ptr()]
+        ps = stream.cuda_stream
+
+        def run(n, first=0):
+            for i in range(n):
+                rc = lib.conv_process_block_async(eng.h, p_in[(first + i) % nbuf], p_out[(first + i) & 1], ps)
+                if rc:
+                    raise U.ConvError(rc, U.conv_last_error())
+
+        run(warmup)
+        U.conv_synchronize(eng.h)
+        torch.cuda.synchronize()
+        if objective == "mac":
+            U.conv_profile_enable(eng.h, steps + 8)
+            run(steps, warmup)
+            U.conv_synchronize(eng.h)
+            ms, n = U.conv_profile_read(eng.h)
+            U.conv_profile_enable(eng.h, 0)
+            return ms / 1e3 / max(1, n)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        run(steps, warmup)
+        lib.conv_join_async(eng.h, ps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        U.conv_synchronize(eng.h)
+        return ev0.elapsed_time(ev1) / 1e3 / steps
+    finally:
+        eng.close()
+
+
+def measure_group(tiling, precision, block, n_in, n_out, taps, sessions, h=None, steps=200, warmup=20):
+    """Seconds per block (all sessions) of one group tiling, back to back."""
+    import torch
+
+    lib = U.load()
+    g = U.Group(precision, block, n_in, n_out, taps, sessions, tiling or None)
+    try:
+        g.set_filters(_filters(n_out, n_in, taps) if h is None else h)
+        nbuf = 4
+        d_in = (torch.randn((nbuf, sessions, n_in, block), device="cuda") * 0.1).contiguous()
+        d_out = torch.empty((2, sessions, n_out, block), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+        ps = stream.cuda_stream
+
+        def run(n, first=0):
+            for i in range(n):
+                rc = lib.conv_group_process_async(g.g, d_in[(first + i) % nbuf].data_ptr(),
+                                                  d_out[(first + i) & 1].data_ptr(), ps)
+                if rc:
+                    raise U.ConvError(rc, U.conv_last_error())
+
+        run(warmup)
+        U.conv_group_synchronize(g.g)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        run(steps, warmup)
+        lib.conv_group_join_async(g.g, ps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        U.conv_group_synchronize(g.g)
+        return ev0.elapsed_time(ev1) / 1e3 / steps
+    finally:
+        g.close()
+
+
+def device_sms() -> int:
+    """SM count of the current CUDA device (part of the cache key)."""
+    import torch
+
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+_num_sms = device_sms
+
+
+def tune(precision, block, n_in, n_out, taps, budget_s=60.0, steps=200, objective="step", space=None,
+         path=None, save=True, repeats=2):
+    """Measure the candidates (the planner's choice first) until the budget
+    is spent, re-measure the best few `repeats` times (the minimum counts),
+    and store the winner.  Returns the cache entry."""
+    sms = _num_sms()
+    cands = candidates(precision, block, n_in, n_out, taps, sms, space)
+    h = _filters(n_out, n_in, taps)
+    t0 = time.time()
+    results = []
+    for t in cands:
+        if results and time.time() - t0 > budget_s:
+            break
+        results.append((measure(t, precision, block, n_in, n_out, taps, h, steps, objective=objective), t))
+    results.sort(key=lambda r: r[0])
+    best = []
+    for sec, t in results[: min(4, len(results))]:
+        again = [measure(t, precision, block, n_in, n_out, taps, h, steps, objective=objective)
+                 for _ in range(max(0, repeats - 1))]
+        best.append((min([sec] + again), t))
+    planner = [r for r in results if r[1] == {}]
+    base = planner[0][0] if planner else None
+    for sec, t in best:
+        if t == {}:
+            base = sec
+    best.sort(key=lambda r: r[0])
+    sec, tiling = best[0]
+    entry = {
+        "tiling": tiling,
+        "seconds_per_block": sec,
+        "planner_seconds_per_block": base,
+        "objective": objective,
+        "candidates_timed": len(results),
+        "candidates": len(cands),
+        "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+    }
+    if save:
+        save_entry(key(precision, block, n_in, n_out, taps, sms), entry, path)
+    return entry
+
+
+def tune_group(precision, block, n_in, n_out, taps, sessions, budget_s=60.0, steps=200, path=None, save=True,
+               repeats=2):
+    sms = _num_sms()
+    cands = group_candidates(precision, block, n_in, n_out, taps, sessions, sms)
+    h = _filters(n_out, n_in, taps)
+    t0 = time.time()
+    results = []
+    for t in cands:
+        if results and time.time() - t0 > budget_s:
+            break
+        results.append((measure_group(t, precision, block, n_in, n_out, taps, sessions, h, steps), t))
+    results.sort(key=lambda r: r[0])
+    best = []
+    for sec, t in results[: min(4, len(results))]:
+        again = [measure_group(t, precision, block, n_in, n_out, taps, sessions, h, steps)
+                 for _ in range(max(0, repeats - 1))]
+        best.append((min([sec] + again), t))
+    planner = [r for r in results if r[1] == {}]
+    base = planner[0][0] if planner else None
+    for sec, t in best:
+        if t == {}:
+            base = sec
+    best.sort(key=lambda r: r[0])
+    sec, tiling = best[0]
+    entry = {
+        "tiling": tiling,
+        "seconds_per_block": sec,
+        "planner_seconds_per_block": base,
+        "candidates_timed": len(results),
+        "candidates": len(cands),
+        "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+    }
+    if save:
+        save_entry(group_key(precision, block, n_in, n_out, taps, sessions, sms), entry, path)
+    return entry
+
+
+if __name__ == "__main__":
+    import argparse
+
+    ap = argparse.ArgumentParser(description="tune the FDL MAC tiling of one shape and cache the result")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--n-in", type=int, default=4)
+    ap.add_argument("--n-out", type=int, default=16)
+    ap.add_argument("--taps", type=int, default=384000)
+    ap.add_argument("--sessions", type=int, default=0, help="tune a shared-filter group of this many sessions")
+    ap.add_argument("--budget", type=float, default=60.0)
+    ap.add_argument("--objective", choices=["step", "mac"], default="step")
+    ap.add_argument("--cache", default=None)
+    a = ap.parse_args()
+    if a.sessions:
+        res = tune_group(a.precision, a.block, a.n_in, a.n_out, a.taps, a.sessions, a.budget, path=a.cache)
+    else:
+        res = tune(a.precision, a.block, a.n_in, a.n_out, a.taps, a.budget, objective=a.objective, path=a.cache)
+    print(json.dumps(res))

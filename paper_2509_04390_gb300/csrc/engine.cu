@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -436,6 +437,12 @@ struct conv_engine {
     int io_in_stride = 0, io_out_stride = 0;
     float *d_cin = nullptr, *d_cout = nullptr;  // its device chunk buffers
     long long chunk_cap = 0;                    // blocks they hold
+    cudaEvent_t ev_join = nullptr;  // conv_join_async: marks each of the engine's streams
+    // fault-path testing (conv_inject_wait_timeout): the next synthesis tail
+    // MAC withholds one stage and bounds its waits by inject_ns
+    bool inject = false;
+    unsigned long long inject_ns = 0;
+    conv_stats st{};  // counters of conv_get_stats
 };
 
 namespace {
@@ -637,6 +644,11 @@ MacArgs tail_args(conv_engine* e, Part& P, long long blk) {
     a.sxoff = p.sxoff;
     a.tile_elems = p.tile_elems;
     a.err = e->d_err;
+    if (e->inject && &P == &e->syn) {
+        a.withhold = 1;
+        a.wait_ns = e->inject_ns;
+        e->inject = false;
+    }
     return a;
 }
 
@@ -727,7 +739,39 @@ int check_dev_err(conv_engine* e) {
     const int v = *(volatile int*)e->h_err;
     if (v != DEVERR_NONE) {
         *(volatile int*)e->h_err = DEVERR_NONE;
+        ++e->st.device_errors;
         return set_err(CONV_E_TIMEOUT, "device-side wait gave up (code %d); results of the block are invalid", v);
+    }
+    return CONV_OK;
+}
+
+// Latency record of one blocking host-buffer call that started at t0.
+void record_call(conv_engine* e, std::chrono::steady_clock::time_point t0) {
+    const double us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    conv_stats& st = e->st;
+    ++st.timed_calls;
+    st.sum_latency_us += us;
+    if (us > st.max_latency_us) st.max_latency_us = us;
+    if (us > (double)e->B / e->fs * 1e6) ++st.deadline_misses;
+    int b = 0;
+    while (b < CONV_STATS_BUCKETS - 1 && us >= (double)(2ll << b)) ++b;
+    ++st.latency_hist[b];
+}
+
+// Makes stream s wait for everything the engine has enqueued on its own
+// streams (background tails, the NLMS step stream, the host-call stream, the
+// stream of the last block) and on its far engine's.
+int join_streams(conv_engine* e, cudaStream_t s) {
+    if (e->far) {
+        const int rc = join_streams(e->far, s);
+        if (rc) return rc;
+    }
+    cudaStream_t src[7] = {e->bg[0], e->bg[1], e->bg[2], e->bg[3], e->as, e->stream,
+                           e->has_last ? e->last_stream : e->stream};
+    for (int i = 0; i < 7; ++i) {
+        if (!src[i] || src[i] == s) continue;
+        CK(cudaEventRecord(e->ev_join, src[i]));
+        CK(cudaStreamWaitEvent(s, e->ev_join, 0));
     }
     return CONV_OK;
 }
@@ -822,6 +866,7 @@ int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t 
     if (!rc) rc = far_after(e, nullptr, s);
     if (rc) return rc;
     ++e->nblk;
+    ++e->st.blocks;
     return CONV_OK;
 }
 
@@ -1035,6 +1080,7 @@ int enqueue_afc_prediction(conv_engine* e, cudaStream_t s) {
         CK(cudaEventRecord(F.ev_tail[(n + 1) & 1], bg));
     }
     ++e->nblk;
+    ++e->st.blocks;
     return CONV_OK;
 }
 
@@ -1080,6 +1126,7 @@ void engine_free(conv_engine* e) {
     for (auto ev : e->ev1) cudaEventDestroy(ev);
     if (e->ev_done) cudaEventDestroy(e->ev_done);
     if (e->ev_handoff) cudaEventDestroy(e->ev_handoff);
+    if (e->ev_join) cudaEventDestroy(e->ev_join);
     for (int i = 0; i < 4; ++i)
         if (e->bg[i]) cudaStreamDestroy(e->bg[i]);
     if (e->stream) cudaStreamDestroy(e->stream);
@@ -1112,6 +1159,7 @@ int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long 
     // spin-wait on completion: a blocking wait would add the host's wake-up latency to every block
     CK(cudaEventCreateWithFlags(&e->ev_done, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&e->ev_handoff, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming));
     // twiddles W_2B^j = exp(-i pi j / B), FP64 on the host, rounded once to FP32
     std::vector<float2> tw(2 * (size_t)block);
     const double pi = 3.14159265358979323846264338327950288;
@@ -1321,6 +1369,7 @@ int conv_process_block_async(conv_engine* e, const float* d_in, float* d_out, vo
 }
 
 int conv_process_block(conv_engine* e, const float* in, float* out) {
+    const auto t0 = std::chrono::steady_clock::now();
     if (!e || !in || !out) return set_err(CONV_E_INVAL, "null argument");
     if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
     if (e->adapt) return set_err(CONV_E_STATE, "the adaptive canceller needs every block through afc_process_block");
@@ -1336,6 +1385,7 @@ int conv_process_block(conv_engine* e, const float* in, float* out) {
     CK(cudaEventSynchronize(e->ev_done));  // the next block's tail keeps running
     if ((rc = check_dev_err(e))) return rc;
     std::memcpy(out, e->h_out, ob);
+    record_call(e, t0);
     return CONV_OK;
 }
 
@@ -1387,6 +1437,7 @@ int afc_process_block_async(conv_engine* e, const float* d_mic, float* d_out, fl
 }
 
 int afc_process_block(conv_engine* e, const float* mic, float* out, float* e_or_null) {
+    const auto t0 = std::chrono::steady_clock::now();
     if (!e || !mic || !out) return set_err(CONV_E_INVAL, "null argument");
     if (!e->syn.ready || !e->fb.ready) return set_err(CONV_E_STATE, "filters or feedback paths not set");
     DeviceGuard g(e->dev);
@@ -1409,12 +1460,14 @@ int afc_process_block(conv_engine* e, const float* mic, float* out, float* e_or_
         const double rms = std::sqrt(ss / (double)n);
         if (!(rms <= e->guard)) {
             engine_reset(e);
+            ++e->st.guard_trips;
             return set_err(CONV_E_UNSTABLE, "closed-loop guard: rms(e) = %g exceeds %g; loop state reset", rms,
                            e->guard);
         }
     }
     std::memcpy(out, e->h_out, ob);
     if (e_or_null) std::memcpy(e_or_null, e->h_e, ib);
+    record_call(e, t0);
     return CONV_OK;
 }
 
@@ -1526,6 +1579,35 @@ int conv_reset(conv_engine* e) {
     if (!e) return set_err(CONV_E_INVAL, "null handle");
     DeviceGuard g(e->dev);
     return engine_reset(e);
+}
+
+int conv_join_async(conv_engine* e, void* cuda_stream) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    DeviceGuard g(e->dev);
+    return join_streams(e, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int conv_get_stats(const conv_engine* e, conv_stats* out) {
+    if (!e || !out) return set_err(CONV_E_INVAL, "null argument");
+    *out = e->st;
+    return CONV_OK;
+}
+
+int conv_reset_stats(conv_engine* e) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    e->st = conv_stats{};
+    return CONV_OK;
+}
+
+int conv_inject_wait_timeout(conv_engine* e, long long wait_ns) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    if (wait_ns < 1000 || wait_ns > 1000000000ll) return set_err(CONV_E_INVAL, "wait_ns must be in [1e3, 1e9]");
+    if (!e->syn.ready) return set_err(CONV_E_STATE, "filters not set");
+    if (e->syn.plan.S == 0) return set_err(CONV_E_STATE, "one partition: the engine runs no tail MAC");
+    if (e->syn.plan.direct) return set_err(CONV_E_STATE, "the direct-load MAC has no pipeline waits");
+    e->inject = true;
+    e->inject_ns = (unsigned long long)wait_ns;
+    return CONV_OK;
 }
 
 int conv_synchronize(conv_engine* e) {
@@ -1907,8 +1989,21 @@ int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, cons
     CK(cudaStreamWaitEvent(bg, b->ev_packed, 0));
     CK(launch_mac_batch(b->prec, d_mc, d_rm, n_mac, mac_smem, bg));
     CK(cudaEventRecord(b->ev_tail[par ^ 1], bg));
-    for (int j = 0; j < count; ++j) ++b->sessions[idx[j]]->nblk;
+    for (int j = 0; j < count; ++j) {
+        ++b->sessions[idx[j]]->nblk;
+        ++b->sessions[idx[j]]->st.blocks;
+    }
     ++b->step;
+    return CONV_OK;
+}
+
+int conv_batch_join_async(conv_batch* b, void* cuda_stream) {
+    if (!b) return set_err(CONV_E_INVAL, "null handle");
+    DeviceGuard g(b->dev);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the latest tail launch of each parity (every tail of the batch runs on one of the two)
+    CK(cudaStreamWaitEvent(s, b->ev_tail[0], 0));
+    CK(cudaStreamWaitEvent(s, b->ev_tail[1], 0));
     return CONV_OK;
 }
 

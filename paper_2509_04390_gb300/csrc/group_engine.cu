@@ -477,6 +477,16 @@ int conv_group_reset(conv_group* g) {
     return group_reset_impl(g);
 }
 
+int conv_group_join_async(conv_group* g, void* cuda_stream) {
+    if (!g) return fail(CONV_E_INVAL, "null handle");
+    DeviceGuard d(g->dev);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the latest tail of each parity (with one tail stream both name its latest tails)
+    GB_CK(cudaStreamWaitEvent(s, g->ev_tail[0], 0));
+    GB_CK(cudaStreamWaitEvent(s, g->ev_tail[1], 0));
+    return CONV_OK;
+}
+
 int conv_group_synchronize(conv_group* g) {
     if (!g) return fail(CONV_E_INVAL, "null handle");
     DeviceGuard d(g->dev);

@@ -239,6 +239,7 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
     const int kt = tile / a.n_lt, lt = tile - kt * a.n_lt;
     const int l0 = lt * a.LT, LTt = min(a.LT, a.n_dst - l0);
     const int K = a.K, R = a.n_src * K;
+    const uint64_t wait_ns = a.wait_ns ? a.wait_ns : WAIT_LIMIT_NS;
     const int gb = a.r_begin / a.RS, gt = (R + a.RS - 1) / a.RS - gb;  // stage grid
     // contiguous: split s owns stages [g0, g1); interleaved: stages gb + s + i*S,
     // so the tile's CTAs sweep the spectra side by side
@@ -325,18 +326,21 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
                 if (w[2][1] > 0) bulk_g2s(ss + b1, a.sX, (uint32_t)(4 * w[2][1]), &full[st], pol_keep);
             }
         };
+        // Fault-path testing: this CTA withholds its first stage (no copy, no
+        // arrival on its barrier), so its consumers' bounded wait runs out.
+        const bool hold = a.withhold && tile == 0 && split == 0 && nit > 0;
         // The filter spectra are constant: stream the first stages while the
         // previous kernel (the pack of this block) is still running, then wait for
         // it before touching the delay line it writes.
         const int npre = min(nit, a.nstage);
-        for (int it = 0; it < npre; ++it) issue_h(it);
+        for (int it = hold ? 1 : 0; it < npre; ++it) issue_h(it);
         griddep_wait();
-        for (int it = 0; it < npre; ++it) issue_x(it);
+        for (int it = hold ? 1 : 0; it < npre; ++it) issue_x(it);
         int issued = npre;
         bool ok = true;
         for (int it = npre; it < nit; ++it) {
             const int st = it % a.nstage;
-            if (!mbar_wait_bounded(&empty[st], ((it / a.nstage) - 1) & 1, abort_flag, WAIT_LIMIT_NS)) {
+            if (!mbar_wait_bounded(&empty[st], ((it / a.nstage) - 1) & 1, abort_flag, wait_ns)) {
                 *abort_flag = 1;
                 if (a.err) *(volatile int*)a.err = DEVERR_TIMEOUT_PRODUCER;
                 ok = false;
@@ -346,10 +350,12 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
             issue_x(it);
             ++issued;
         }
-        if (!ok) {
-            // let copies already in flight land before the CTA's shared memory goes away
+        if (!ok || hold) {
+            // let copies already in flight land before the CTA's shared memory
+            // goes away (the withheld stage has none)
             for (int it = issued > a.nstage ? issued - a.nstage : 0; it < issued; ++it)
-                mbar_wait_bounded(&full[it % a.nstage], (it / a.nstage) & 1, nullptr, WAIT_LIMIT_NS);
+                if (!(hold && it == 0))
+                    mbar_wait_bounded(&full[it % a.nstage], (it / a.nstage) & 1, nullptr, WAIT_LIMIT_NS);
         }
         return;
     }
@@ -369,7 +375,7 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
     bool ok = true;
     for (int it = 0; it < nit; ++it) {
         const int st = it % a.nstage;
-        if (!mbar_wait_bounded(&full[st], (it / a.nstage) & 1, abort_flag, WAIT_LIMIT_NS)) {
+        if (!mbar_wait_bounded(&full[st], (it / a.nstage) & 1, abort_flag, wait_ns)) {
             *abort_flag = 1;
             if (a.err) *(volatile int*)a.err = DEVERR_TIMEOUT_CONSUMER;
             ok = false;

@@ -79,6 +79,12 @@ struct MacArgs {
     unsigned stage_bytes, xoff, soff, sxoff;
     size_t tile_elems;
     int* err;   // device-visible error word (host-mapped), or null
+    // bound of the pipeline's barrier waits in ns (0: the default, 1 s)
+    unsigned long long wait_ns;
+    // fault-path testing (TMA kernel): 1 = the producer of tile 0 / split 0
+    // withholds its first stage, so that CTA's consumers wait on a barrier
+    // nothing completes and give up after wait_ns (error word, abort flag)
+    int withhold;
 };
 
 struct PackArgs {

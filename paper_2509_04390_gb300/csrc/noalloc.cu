@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -31,11 +32,14 @@ constexpr int NOALLOC_TW_ENTRIES = 2 * (16 + 32 + 64 + 128 + 256);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 static __device__ __align__(256) float2 g_noalloc_tw[NOALLOC_TW_ENTRIES];
+// DEVERR_* of a bounded wait that gave up, kept until conv_fdl_mac_noalloc_status
+static __device__ __align__(16) int g_noalloc_err;
 
 struct DeviceSlot {
     bool ready = false;
     float2* scratch = nullptr;  // device address of g_noalloc_scratch on this device
     float2* tw = nullptr;       // device address of g_noalloc_tw on this device
+    int* err = nullptr;         // device address of g_noalloc_err on this device
 };
 
 std::mutex g_mu;
@@ -70,6 +74,9 @@ int setup_device(int dev, DeviceSlot** out) {
         e = cudaGetSymbolAddress(&p, g_noalloc_tw);
         if (e != cudaSuccess) return fail(CONV_E_CUDA, "cudaGetSymbolAddress(twiddles)", e);
         d.tw = static_cast<float2*>(p);
+        e = cudaGetSymbolAddress(&p, g_noalloc_err);
+        if (e != cudaSuccess) return fail(CONV_E_CUDA, "cudaGetSymbolAddress(error word)", e);
+        d.err = static_cast<int*>(p);
         float2 host[NOALLOC_TW_ENTRIES];
         const double pi = 3.14159265358979323846264338327950288;
         for (int B = 16; B <= NOALLOC_MAX_BLOCK; B <<= 1)
@@ -79,6 +86,9 @@ int setup_device(int dev, DeviceSlot** out) {
             }
         e = cudaMemcpyToSymbol(g_noalloc_tw, host, sizeof(host));
         if (e != cudaSuccess) return fail(CONV_E_CUDA, "twiddle upload", e);
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_noalloc_err, &zero, sizeof(zero));
+        if (e != cudaSuccess) return fail(CONV_E_CUDA, "error word", e);
         e = prepare_kernels(MAC_SMEM_LIMIT);
         if (e != cudaSuccess) return fail(CONV_E_CUDA, "kernel attributes", e);
         d.ready = true;
@@ -92,6 +102,9 @@ int setup_device(int dev, DeviceSlot** out) {
 extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int block, int n_in, int n_out, long long K,
                                     long long slot0, float* d_y, void* cuda_stream) {
     if (!d_H || !d_X || !d_y) return fail(CONV_E_INVAL, "null pointer");
+    // the MAC streams d_H and d_X with bulk copies, which need 16-byte aligned sources
+    if (((uintptr_t)d_H | (uintptr_t)d_X) & 15u) return fail(CONV_E_INVAL, "d_H and d_X must be 16-byte aligned");
+    if ((uintptr_t)d_y & 3u) return fail(CONV_E_INVAL, "d_y must be 4-byte aligned");
     if (block < 16 || block > NOALLOC_MAX_BLOCK || (block & (block - 1)))
         return fail(CONV_E_INVAL, "block must be a power of two in [16, 256]");
     if (n_out < 1 || n_out > NOALLOC_MAX_OUT) return fail(CONV_E_INVAL, "n_out must be in [1, 16]");
@@ -186,7 +199,7 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     a.stage_bytes = p.stage_bytes;
     a.xoff = p.xoff;
     a.tile_elems = p.tile_elems;
-    a.err = nullptr;
+    a.err = d->err;
     // no early start: the caller's previous kernel may be writing d_H
     e = launch_fdl_mac(PREC_FP32, p, a, s, false);
     if (e != cudaSuccess) return fail(CONV_E_CUDA, "MAC launch", e);
@@ -206,4 +219,27 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     e = launch_out_c2r(PREC_FP32, r, s);
     if (e != cudaSuccess) return fail(CONV_E_CUDA, "output-transform launch", e);
     return CONV_OK;
+}
+
+extern "C" int conv_fdl_mac_noalloc_status(void* cuda_stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(CONV_E_CUDA, "cudaGetDevice", e);
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(CONV_E_INVAL, "device index above 63");
+    DeviceSlot* d = nullptr;
+    int rc = setup_device(dev, &d);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(CONV_E_CUDA, "stream synchronize", e);
+    int v = 0;
+    e = cudaMemcpy(&v, d->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(CONV_E_CUDA, "error word read", e);
+    if (v == DEVERR_NONE) return CONV_OK;
+    e = cudaMemset(d->err, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(CONV_E_CUDA, "error word clear", e);
+    char buf[160];
+    snprintf(buf, sizeof(buf), "conv_fdl_mac_noalloc: a device-side wait gave up (code %d); that call's output is invalid", v);
+    set_last_error_message(buf);
+    return CONV_E_TIMEOUT;
 }

@@ -107,6 +107,27 @@ class conv_group_info(ctypes.Structure):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
+CONV_STATS_BUCKETS = 24
+
+
+class conv_stats(ctypes.Structure):
+    _fields_ = [
+        ("blocks", ctypes.c_longlong),
+        ("timed_calls", ctypes.c_longlong),
+        ("deadline_misses", ctypes.c_longlong),
+        ("max_latency_us", ctypes.c_double),
+        ("sum_latency_us", ctypes.c_double),
+        ("latency_hist", ctypes.c_longlong * CONV_STATS_BUCKETS),
+        ("device_errors", ctypes.c_longlong),
+        ("guard_trips", ctypes.c_longlong),
+    ]
+
+    def as_dict(self):
+        d = {n: getattr(self, n) for n, _ in self._fields_ if n != "latency_hist"}
+        d["latency_hist"] = [int(v) for v in self.latency_hist]
+        return d
+
+
 class conv_group_tiling(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("ctas", "stage_k_steps", "stages", "tail_streams")]
 
@@ -154,6 +175,13 @@ def load():
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "conv_plan_check": (i, [i, i, i, i, ll, i, ctypes.POINTER(conv_tiling)]),
         "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
+        "conv_fdl_mac_noalloc_status": (i, [vp]),
+        "conv_join_async": (i, [vp, vp]),
+        "conv_batch_join_async": (i, [vp, vp]),
+        "conv_group_join_async": (i, [vp, vp]),
+        "conv_get_stats": (i, [vp, ctypes.POINTER(conv_stats)]),
+        "conv_reset_stats": (i, [vp]),
+        "conv_inject_wait_timeout": (i, [vp, ll]),
         "conv_footprint": (ll, [i, i, i, i, ll, ll, i]),
         "conv_batch_create": (vp, [i]),
         "conv_batch_add": (i, [vp, vp]),
@@ -367,6 +395,36 @@ def conv_fdl_mac_noalloc(d_H, d_X, block, n_in, n_out, K, slot0, d_y, stream=Non
     )
 
 
+def conv_fdl_mac_noalloc_status(stream=None):
+    return _check(load().conv_fdl_mac_noalloc_status(_stream_ptr(stream)))
+
+
+def conv_join_async(h, stream=None):
+    return _check(load().conv_join_async(h, _stream_ptr(stream)))
+
+
+def conv_batch_join_async(b, stream=None):
+    return _check(load().conv_batch_join_async(b, _stream_ptr(stream)))
+
+
+def conv_group_join_async(g, stream=None):
+    return _check(load().conv_group_join_async(g, _stream_ptr(stream)))
+
+
+def conv_get_stats(h) -> dict:
+    st = conv_stats()
+    _check(load().conv_get_stats(h, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def conv_reset_stats(h):
+    return _check(load().conv_reset_stats(h))
+
+
+def conv_inject_wait_timeout(h, wait_ns: int):
+    return _check(load().conv_inject_wait_timeout(h, int(wait_ns)))
+
+
 def conv_footprint(precision, block, n_in, n_out, taps, taps_fb=0, num_sms=152):
     v = load().conv_footprint(
         int(PRECISIONS.get(precision, precision)), int(block), int(n_in), int(n_out), int(taps), int(taps_fb),
@@ -571,6 +629,10 @@ class Group:
     one filter set."""
 
     def __init__(self, precision, block, n_in, n_out, taps, sessions, tiling=None):
+        if tiling == "tuned":
+            from . import autotune
+
+            tiling = autotune.lookup_group(precision, block, n_in, n_out, taps, sessions, autotune.device_sms())
         self.g = conv_group_create_tiled(precision, block, n_in, n_out, taps, sessions, tiling)
         self.shape = (int(sessions), int(n_in), int(n_out), int(block))
 
@@ -634,7 +696,11 @@ class Group:
 
 
 class Engine:
-    """Owning wrapper: ``with Engine(fs, block, n_in, n_out, taps) as e: ...``."""
+    """Owning wrapper: ``with Engine(fs, block, n_in, n_out, taps) as e: ...``.
+
+    ``tiling``: None (the planner's rule), a dict of ``conv_tiling`` fields, or
+    "tuned": the autotuner's cached choice for this shape and GPU (the
+    planner's rule when the cache has none)."""
 
     def __init__(self, fs, block, n_in, n_out, taps, precision="fp32", tiling=None, far_block=0):
         self.h = conv_create(fs, block, n_in, n_out, taps)
@@ -642,6 +708,11 @@ class Engine:
         try:
             if precision not in ("fp32", CONV_FP32):
                 conv_set_precision(self.h, precision)
+            if tiling == "tuned":
+                from . import autotune
+
+                prec = {v: k for k, v in PRECISIONS.items()}.get(precision, precision)
+                tiling = autotune.lookup(prec, block, n_in, n_out, taps, autotune.device_sms())
             if tiling:
                 conv_set_tiling(self.h, **tiling)
             if far_block:
@@ -703,6 +774,9 @@ class Engine:
 
     def info(self):
         return conv_get_info(self.h)
+
+    def stats(self):
+        return conv_get_stats(self.h)
 
     def reset(self):
         conv_reset(self.h)

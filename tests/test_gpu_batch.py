@@ -26,6 +26,7 @@ SHAPES = [  # n_in, n_out, taps, block
     (5, 9, 40000, 1024),
 ]
 BATCH_TILING = {"kernel": "tma", "warps": 8}
+BOUND = {"fp32": 120.0, "fp16": 60.0}  # SNR against the FP64 oracle, as for single sessions
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -74,9 +75,10 @@ def test_batch_equals_sessions_alone(precision):
         got = run_batched(torch, ws, engs, batch, 24)
     for i, w in enumerate(ws):
         np.testing.assert_array_equal(got[i], alone[i])
-        if precision == "fp32":
-            ref = upols(w.h.astype(np.float64), w.x.astype(np.float64), w.block)
-            assert snr_db(got[i], ref) >= 120.0
+        ref = upols(w.h.astype(np.float64), w.x.astype(np.float64), w.block)
+        s = snr_db(got[i], ref)
+        print(f"batch {precision} session {i} {SHAPES[i]}: {s:.1f} dB against the oracle")
+        assert s >= BOUND[precision]
     for e in engs:
         e.close()
 

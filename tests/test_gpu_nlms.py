@@ -11,20 +11,20 @@ import os
 import numpy as np
 import pytest
 
-from gpu_helpers import RoomPlant, snr_db
+from gpu_helpers import RoomPlant, cancellation_gain_db, snr_db
 from oracle.nlms_oracle import NlmsCanceller, afc_closed_loop_nlms
-from oracle.upols_oracle import UpolsOracle
+from oracle.upols_oracle import UpolsOracle, upols
 from paper_2509_04390_gb300 import build, signals
 from paper_2509_04390_gb300 import upols as U
 
 pytestmark = pytest.mark.gpu
 
-# FP32 bound for the adaptive loop.  The recursion feeds every block's FP32
-# rounding of e back into F_hat; NLMS with 0 < mu < 2 contracts the
-# coefficient error, so the rounding errors do not grow from block to block,
-# but each update adds one, which costs a few dB against the static loop's
-# 110 dB bound.
-ADAPT_DB = 100.0
+# FP32 bound for the adaptive canceller, the same as for every FP32 path.  It
+# applies to the like-for-like comparisons: the oracle is fed exactly the
+# float32 microphone blocks the engine received (the whole loop), or each stage
+# is fed the engine's own signals (the synthesis of the engine's e, and the
+# canceller adapting with the engine's e and predicting from its l).
+ADAPT_DB = 120.0
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -48,6 +48,7 @@ def run_adaptive(h, f_true, f_hat0, s, B, mu, lam, delta, precision="fp32", engi
     nb = s.shape[1] // B if blocks is None else blocks
     out = np.zeros((L, nb * B), np.float32)
     err = np.zeros((P, nb * B), np.float32)
+    mic = np.zeros((P, nb * B), np.float32)
     fb = np.zeros((P, B))
     own = engine is None
     e = engine or U.Engine(48000, B, P, L, n_h, precision)
@@ -63,12 +64,73 @@ def run_adaptive(h, f_true, f_hat0, s, B, mu, lam, delta, precision="fp32", engi
             e.process_afc(m_n, l_n, e_n)
             out[:, b * B : (b + 1) * B] = l_n
             err[:, b * B : (b + 1) * B] = e_n
+            mic[:, b * B : (b + 1) * B] = m_n
             fb = room.step(l_n)
         spec = e.path_spectra()
     finally:
         if own:
             e.close()
+    run_adaptive.mic = mic
     return out, err, spec
+
+
+def check_adaptive(label, h, fh0, y, e, spec, mic, B, mu, lam, delta, start=0, physical=None):
+    """Like-for-like parity of an adaptive run at ADAPT_DB: each stage fed the
+    engine's own signals, so the comparison holds only what the engine
+    computed in that stage.
+      synthesis  the engine's l against the oracle's UPOLS of the engine's e;
+      canceller  the oracle's canceller adapting with the engine's e and
+                 predicting from the engine's l: the final spectra F_hat, the
+                 prediction c = mic - e (over the previous block), and e
+                 itself, whose bound is lowered by the cancellation gain
+                 rms(c) / rms(e) (a subtraction keeps no more relative
+                 precision than its operands have).
+    `start`: the first block that adapts (static before).  Reported beside
+    them: the whole loop replayed from the microphone blocks alone (no room:
+    other dynamics than the physical loop) and `physical`, the oracle's own
+    closed loop with the room, (l, e, canceller); in both the engine's
+    rounding circulates through a loop, so they are not bounded."""
+    P, L = fh0.shape[0], fh0.shape[1]
+    nb = mic.shape[1] // B
+    mic64 = mic.astype(np.float64)
+    synth = UpolsOracle(h, B)
+    loop = NlmsCanceller(fh0, B, mu, lam, delta)
+    stage = NlmsCanceller(fh0, B, mu, lam, delta)
+    loop_l, loop_e = np.zeros((L, nb * B)), np.zeros((P, nb * B))
+    stage_e = np.zeros((P, nb * B))
+    c_loop, c_stage = np.zeros((P, B)), np.zeros((P, B))
+    with np.errstate(all="ignore"):
+        for b in range(nb):
+            sl = slice(b * B, (b + 1) * B)
+            e_b = mic64[:, sl] - c_loop
+            stage_e[:, sl] = mic64[:, sl] - c_stage
+            if b >= start:
+                loop.adapt(e_b)
+                stage.adapt(e[:, sl].astype(np.float64))
+            l_b = synth.process_block(e_b)
+            c_loop = loop.predict(l_b)
+            c_stage = stage.predict(y[:, sl].astype(np.float64))
+            loop_l[:, sl], loop_e[:, sl] = l_b, e_b
+    stage_l = upols(h.astype(np.float64), e.astype(np.float64), B)
+    c_eng = mic64 - e.astype(np.float64)
+    c_ref = mic64 - stage_e
+    gain = cancellation_gain_db(c_ref, stage_e)
+    got = {
+        "synthesis stage l": snr_db(y, stage_l),
+        "canceller stage F_hat": snr_db(spec, packed(stage.W)),
+        "canceller stage c": snr_db(c_eng, c_ref),
+        "canceller stage e": snr_db(e, stage_e),
+    }
+    msg = f"{label}: " + ", ".join(f"{k} {v:.1f}" for k, v in got.items()) + f" dB (cancellation gain {gain:.1f} dB)"
+    msg += f" | loop replayed: l {snr_db(y, loop_l):.1f}, e {snr_db(e, loop_e):.1f}, F_hat {snr_db(spec, packed(loop.W)):.1f}"
+    if physical is not None:
+        pl, pe, pc = physical
+        msg += f" | with the oracle's own room: l {snr_db(y, pl):.1f}, e {snr_db(e, pe):.1f}, " \
+               f"F_hat {snr_db(spec, packed(pc.W)):.1f}"
+    print(msg + " dB")
+    for k in ("synthesis stage l", "canceller stage F_hat", "canceller stage c"):
+        assert got[k] >= ADAPT_DB, f"{label} {k}: {got[k]:.1f} dB < {ADAPT_DB} dB"
+    assert got["canceller stage e"] >= ADAPT_DB - gain, (label, got, gain)
 
 
 def small_case(seed=51, P=2, L=3, B=64, n_h=700, n_t=300, nb=60):
@@ -85,13 +147,9 @@ def test_adaptive_closed_loop_against_oracle(B, f0_scale):
     fh0 = (f0_scale * f).astype(np.float32)
     mu, lam, delta = 0.3, 0.9, 1e-2
     y, e, spec = run_adaptive(h, f, fh0, s, B, mu, lam, delta)
-    ref_l, ref_e, can = afc_closed_loop_nlms(h, f, fh0, s, B, mu, lam, delta)
-    s_l, s_e = snr_db(y, ref_l), snr_db(e, ref_e)
-    s_w = snr_db(spec, packed(can.W))
-    print(f"adaptive B={B} f0={f0_scale}: l {s_l:.1f} dB, e {s_e:.1f} dB, F_hat {s_w:.1f} dB")
-    assert s_l >= ADAPT_DB
-    assert s_e >= ADAPT_DB
-    assert s_w >= ADAPT_DB
+    phys = afc_closed_loop_nlms(h, f, fh0, s, B, mu, lam, delta)
+    check_adaptive(f"adaptive B={B} f0={f0_scale}", h, fh0, y, e, spec, run_adaptive.mic, B, mu, lam, delta,
+                   physical=phys)
     # and the estimate moved: the update is not a no-op
     start = U.Engine(48000, B, 2, 3, h.shape[2])
     try:
@@ -115,10 +173,9 @@ def test_adaptive_partition_counts_against_oracle(B, n_t):
     # steps makes the closed loop diverge in the FP64 oracle as well
     mu, lam, delta = 0.1, 0.8, 1e-2
     y, e, spec = run_adaptive(h, f, fh0, s, B, mu, lam, delta)
-    ref_l, ref_e, can = afc_closed_loop_nlms(h, f, fh0, s, B, mu, lam, delta)
-    s_l, s_e, s_w = snr_db(y, ref_l), snr_db(e, ref_e), snr_db(spec, packed(can.W))
-    print(f"adaptive B={B} n_t={n_t} (K_fb {can.K}): l {s_l:.1f} dB, e {s_e:.1f} dB, F_hat {s_w:.1f} dB")
-    assert min(s_l, s_e, s_w) >= ADAPT_DB
+    phys = afc_closed_loop_nlms(h, f, fh0, s, B, mu, lam, delta)
+    check_adaptive(f"adaptive B={B} n_t={n_t} (K_fb {phys[2].K})", h, fh0, y, e, spec, run_adaptive.mic, B,
+                   mu, lam, delta, physical=phys)
 
 
 def test_switching_adaptation_on_mid_stream_against_oracle():
@@ -133,6 +190,7 @@ def test_switching_adaptation_on_mid_stream_against_oracle():
         e.set_filters(h)
         e.set_paths(fh0)
         y0, e0, _ = run_adaptive(h, f, None, s[:, : n0 * B], B, None, None, None, engine=e)
+        mic0 = run_adaptive.mic
         fb_state = RoomPlant(f, B)
         # the room's state at block n0 comes from the loudspeaker blocks so far
         fb = np.zeros((P, B))
@@ -141,6 +199,7 @@ def test_switching_adaptation_on_mid_stream_against_oracle():
         e.set_adaptation(mu, lam, delta)
         y1 = np.zeros((L, (nb - n0) * B), np.float32)
         e1 = np.zeros((P, (nb - n0) * B), np.float32)
+        mic1 = np.zeros((P, (nb - n0) * B), np.float32)
         l_n = np.empty((L, B), np.float32)
         e_n = np.empty((P, B), np.float32)
         for b in range(n0, nb):
@@ -148,6 +207,7 @@ def test_switching_adaptation_on_mid_stream_against_oracle():
             e.process_afc(m_n, l_n, e_n)
             y1[:, (b - n0) * B : (b - n0 + 1) * B] = l_n
             e1[:, (b - n0) * B : (b - n0 + 1) * B] = e_n
+            mic1[:, (b - n0) * B : (b - n0 + 1) * B] = m_n
             fb = fb_state.step(l_n)
         spec = e.path_spectra()
     y = np.concatenate([y0, y1], axis=1)
@@ -165,9 +225,9 @@ def test_switching_adaptation_on_mid_stream_against_oracle():
         c_prev = can.predict(l_b)
         fb_prev = room.process_block(l_b)
         ref_l[:, sl], ref_e[:, sl] = l_b, e_b
-    s_l, s_e, s_w = snr_db(y, ref_l), snr_db(err, ref_e), snr_db(spec, packed(can.W))
-    print(f"adaptation switched on at block {n0}: l {s_l:.1f} dB, e {s_e:.1f} dB, F_hat {s_w:.1f} dB")
-    assert min(s_l, s_e, s_w) >= ADAPT_DB
+    mic = np.concatenate([mic0, mic1], axis=1)
+    check_adaptive(f"adaptation switched on at block {n0}", h, fh0, y, err, spec, mic, B, mu, lam, delta,
+                   start=n0, physical=(ref_l, ref_e, can))
 
 
 def test_path_spectra_are_the_subfilter_ffts():
@@ -285,10 +345,9 @@ def test_adaptive_paper_scale_canceller_against_oracle():
     fh0 = (0.5 * f).astype(np.float32)
     mu, lam, delta = 0.2, 0.95, 1e-1
     y, e, spec = run_adaptive(h, f, fh0, s, B, mu, lam, delta)
-    ref_l, ref_e, can = afc_closed_loop_nlms(h, f, fh0, s, B, mu, lam, delta)
-    s_l, s_e, s_w = snr_db(y, ref_l), snr_db(e, ref_e), snr_db(spec, packed(can.W))
-    print(f"adaptive paper-scale canceller: l {s_l:.1f} dB, e {s_e:.1f} dB, F_hat {s_w:.1f} dB")
-    assert min(s_l, s_e, s_w) >= ADAPT_DB
+    phys = afc_closed_loop_nlms(h, f, fh0, s, B, mu, lam, delta)
+    check_adaptive("adaptive paper-scale canceller", h, fh0, y, e, spec, run_adaptive.mic, B, mu, lam, delta,
+                   physical=phys)
 
 
 def open_loop_adaptive(e, s, B, read_at=(), stream_plan=None):

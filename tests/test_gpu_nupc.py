@@ -12,7 +12,7 @@ import os
 import numpy as np
 import pytest
 
-from gpu_helpers import RoomPlant, sample_points, snr_db
+from gpu_helpers import RoomPlant, check_replay, sample_points, snr_db
 from oracle import afc_closed_loop, mimo_fir_sample, upols
 from paper_2509_04390_gb300 import build, signals
 from paper_2509_04390_gb300 import upols as U
@@ -87,6 +87,7 @@ def test_nupc_closed_loop_against_oracle():
     room = RoomPlant(f, B)
     y = np.zeros((L, nb * B), np.float32)
     err = np.zeros((P, nb * B), np.float32)
+    mic = np.zeros((P, nb * B), np.float32)
     fb = np.zeros((P, B))
     with U.Engine(48000, B, P, L, n_h, far_block=F) as e:
         e.set_filters(h)
@@ -98,11 +99,14 @@ def test_nupc_closed_loop_against_oracle():
             e.process_afc(m_n, l_n, e_n)
             y[:, b * B : (b + 1) * B] = l_n
             err[:, b * B : (b + 1) * B] = e_n
+            mic[:, b * B : (b + 1) * B] = m_n
             fb = room.step(l_n)
     ref_l, ref_e, _ = afc_closed_loop(h, f, fh, s, B)
     print(f"nupc closed loop: l {snr_db(y, ref_l):.1f} dB, e {snr_db(err, ref_e):.1f} dB")
-    assert snr_db(y, ref_l) >= 110.0
-    assert snr_db(err, ref_e) >= 110.0
+    assert snr_db(y, ref_l) >= BOUND["fp32"]
+    assert snr_db(err, ref_e) >= BOUND["fp32"]
+    # like for like: each stage fed the engine's own signals
+    check_replay(h, fh, y, err, mic, B, BOUND["fp32"], "nupc closed loop")
 
 
 def test_nupc_reset_and_device_path_bit_exact():

@@ -11,6 +11,8 @@ import os
 import numpy as np
 import pytest
 
+from gpu_helpers import snr_db
+from oracle import afc_closed_loop, upols
 from paper_2509_04390_gb300 import build, serve, signals
 from paper_2509_04390_gb300 import upols as U
 
@@ -75,6 +77,16 @@ def test_alone_equals_in_the_mix(precision, afc):
     mixed = np.concatenate(w.outputs, axis=1)
     srv.close()
     np.testing.assert_array_equal(mixed, alone)
+    # and the served output against the FP64 oracle: UPOLS of the session's input,
+    # or with a canceller the loop of Sec. 5 fed the session's microphone blocks
+    x64 = x[:, : 12 * 256].astype(np.float64)
+    if afc:
+        ref, _, _ = afc_closed_loop(h, np.zeros((watched.n_in, watched.n_out, 1)), f, x64, 256)
+    else:
+        ref = upols(h.astype(np.float64), x64, 256)
+    s = snr_db(mixed, ref)
+    print(f"served {precision} afc={afc}: {s:.1f} dB against the oracle")
+    assert s >= {"fp32": 120.0, "fp16": 60.0}[precision]
 
 
 def test_admission_respects_the_memory_budget():
