@@ -94,9 +94,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str):
-    """DRAM bytes per MAC launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def ncu_traffic(workload: str, field: str = "dram_bytes_per_launch"):
+    """A DRAM figure per MAC launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None): dram_bytes_per_launch
+    (cold L2, read + write) or dram_read_bytes_warm_l2 (the L2 as the previous
+    block's kernels left it)."""
     path = os.path.join(ROOT, "profiles", "fdl_mac_traffic.json")
     try:
         with open(path) as f:
@@ -106,7 +108,7 @@ def ncu_traffic(workload: str):
     entry = rec.get(workload)
     if not entry or entry.get("kernel_hash") != kernel_source_hash():
         return None
-    return entry.get("dram_bytes_per_launch")
+    return entry.get(field)
 
 
 class ClockSampler:
@@ -198,7 +200,7 @@ def tapch(w):
     return t * w.block
 
 
-def step_bandwidth(w, info, t_step, peak):
+def step_bandwidth(w, info, t_step, peak, warm_read=None):
     """Bytes per step over the step time, split into what must come from HBM
     and what L2 holds.  The filter spectra (n_out * n_in * (K-1) * B * s bytes
     per tail) exceed L2 and stream from HBM every step; the delay line
@@ -217,6 +219,9 @@ def step_bandwidth(w, info, t_step, peak):
         "hbm_bytes_per_step": int(filt),
         "hbm_gbs": filt / t_step / 1e9,
         "hbm_frac_of_peak": filt / t_step / 1e9 / peak,
+        # ncu, warm L2 (the previous tail's filter lines partly survive in L2)
+        "dram_read_bytes_per_step_measured": warm_read,
+        "dram_frac_of_peak_measured": (warm_read / t_step / 1e9 / peak) if warm_read else None,
         "note": "whole steps back to back (pack, head + output, tail MAC), each step's background tail inside "
                 "the timed region; hbm_* counts only the filter spectra, which exceed L2 and stream from HBM "
                 "every step; the delay line is L2-resident, and consecutive tails overlap on two streams, so "
@@ -626,7 +631,8 @@ def run_ours(args):
                     "mode": "one call per block period (real-time use)",
                 },
             },
-            "step_bandwidth": step_bandwidth(w, info, t_max / args.steps, peak),
+            "step_bandwidth": step_bandwidth(w, info, t_max / args.steps, peak,
+                                             ncu_traffic(workload_name(args), "dram_read_bytes_warm_l2")),
             "roofline": {
                 "bound": "hbm",
                 "kernel": "k_fdl_mac (far part, once per far block)" if far_h else "k_fdl_mac",

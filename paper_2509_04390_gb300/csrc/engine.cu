@@ -305,16 +305,22 @@ int check_plan(const MacPlan& p, std::string* why) {
         if (kt >= p.n_kt) return bad("tile index");
         const int l0 = lt * p.LT, LTt = std::min(p.LT, p.n_dst - l0);
         if (LTt < 1) return bad("empty output tile");
-        const int g0 = p.interleave ? gb + split : gb + (int)((long long)split * gt / p.S);
-        const int g1 = p.interleave ? gb + gt : gb + (int)((long long)(split + 1) * gt / p.S);
+        // the kernel's split ranges: equal shares of the reduction range cut
+        // along the stage grid (contiguous), or every S-th stage (interleaved)
+        const int row0 = p.interleave ? p.r_begin : p.r_begin + (int)((long long)split * Rt / p.S);
+        const int row1 = p.interleave ? p.R : p.r_begin + (int)((long long)(split + 1) * Rt / p.S);
+        const int g0 = p.interleave ? gb + split : row0 / p.RS;
+        const int g1 = p.interleave ? gb + gt : (row1 + p.RS - 1) / p.RS;
         const int gstep = p.interleave ? p.S : 1;
-        if (g1 <= g0) return bad("empty split");
+        if (g1 <= g0 || row1 <= row0) return bad("empty split");
+        if ((g1 - g0 + gstep - 1) / gstep < 1) return bad("split without a stage");
         const size_t hr = (size_t)LTt * hrow;
         const size_t hb = (size_t)tile * p.tile_elems * p.es;
         const size_t xb = (size_t)kt * p.R * hrow;
         for (int g = g0; g < g1; g += gstep) {
-            const int ra = std::max(p.r_begin, g * p.RS), rb = std::min(p.R, (g + 1) * p.RS), nr = rb - ra;
+            const int ra = std::max(row0, g * p.RS), rb = std::min(row1, (g + 1) * p.RS), nr = rb - ra;
             if (nr < 1) return bad("empty stage");
+            if (nr > p.RS) return bad("stage above its pitch");
             const size_t tx = (size_t)nr * (hr + hrow);
             if (tx >= (1u << 20)) return bad("transaction bytes");
             if ((size_t)rb * hr > (size_t)p.tile_elems * p.es) return bad("filter copy past its tile");
@@ -395,6 +401,7 @@ struct conv_engine {
     cudaStream_t last_stream = nullptr;
     bool has_last = false;
     float2* tw = nullptr;
+    float2* tw_lo = nullptr;  // tw's residuals W_2B^j - tw[j] (float-float FFT of the NLMS step)
     float *d_e = nullptr, *d_c = nullptr;
     float *h_in = nullptr, *h_out = nullptr, *h_e = nullptr;
     float *m_in = nullptr, *m_out = nullptr;  // device addresses of h_in / h_out (mapped pinned memory)
@@ -910,6 +917,7 @@ int enqueue_nlms_prep(conv_engine* e, const float* d_err_block) {
     a.lam = e->lam;
     a.delta = e->delta;
     a.tw = e->tw;
+    a.tw_lo = e->tw_lo;
     a.F = static_cast<float2*>(F.H);
     a.LT = p.LT;
     a.n_lt = p.n_lt;
@@ -1108,6 +1116,7 @@ void engine_free(conv_engine* e) {
     part_free(e, e->syn);
     part_free(e, e->fb);
     dev_free(e, &e->tw, 0);
+    dev_free(e, &e->tw_lo, 0);
     dev_free(e, &e->d_e, 0);
     dev_free(e, &e->d_c, 0);
     dev_free(e, &e->d_pow, 0);
@@ -1167,9 +1176,16 @@ int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long 
         const double ang = -pi * (double)j / (double)block;
         tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
+    std::vector<float2> tw_lo(2 * (size_t)block);
+    for (int j = 0; j < 2 * block; ++j) {
+        const double ang = -pi * (double)j / (double)block;
+        tw_lo[j] = make_float2((float)(std::cos(ang) - (double)tw[j].x), (float)(std::sin(ang) - (double)tw[j].y));
+    }
     int rc;
     if ((rc = dev_alloc(e, &e->tw, tw.size() * sizeof(float2)))) return rc;
     CK(cudaMemcpy(e->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    if ((rc = dev_alloc(e, &e->tw_lo, tw_lo.size() * sizeof(float2)))) return rc;
+    CK(cudaMemcpy(e->tw_lo, tw_lo.data(), tw_lo.size() * sizeof(float2), cudaMemcpyHostToDevice));
     CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_in), (size_t)n_in * block * sizeof(float), cudaHostAllocMapped));
     CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_out), (size_t)n_out * block * sizeof(float), cudaHostAllocMapped));
     CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->m_in), e->h_in, 0));
@@ -1720,8 +1736,8 @@ long long conv_footprint(int precision, int block, int n_in, int n_out, long lon
         if (f < 0) return set_err(CONV_E_INVAL, "too many partitions"), -1;
         b += f + 2LL * n_in * block * (long long)sizeof(float);  // prediction and error buffers
     }
-    // twiddles, staging, error word
-    b += 2LL * block * (long long)sizeof(float2) + (long long)(n_in + n_out) * block * (long long)sizeof(float);
+    // twiddles and their residuals, staging, error word
+    b += 4LL * block * (long long)sizeof(float2) + (long long)(n_in + n_out) * block * (long long)sizeof(float);
     return b;
 }
 

@@ -241,10 +241,16 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
     const int K = a.K, R = a.n_src * K;
     const uint64_t wait_ns = a.wait_ns ? a.wait_ns : WAIT_LIMIT_NS;
     const int gb = a.r_begin / a.RS, gt = (R + a.RS - 1) / a.RS - gb;  // stage grid
-    // contiguous: split s owns stages [g0, g1); interleaved: stages gb + s + i*S,
-    // so the tile's CTAs sweep the spectra side by side
-    const int g0 = a.interleave ? gb + split : gb + (int)((long long)split * gt / a.S);
-    const int g1 = a.interleave ? gb + gt : gb + (int)((long long)(split + 1) * gt / a.S);
+    // contiguous: split s owns the reduction indices [row0, row1), an equal
+    // share of the range (so no split streams a whole stage more than another),
+    // cut along the stage grid (only its first and last stage may be partial);
+    // interleaved: stages gb + s + i*S, so the tile's CTAs sweep the spectra
+    // side by side
+    const int Rt = R - a.r_begin;
+    const int row0 = a.interleave ? a.r_begin : a.r_begin + (int)((long long)split * Rt / a.S);
+    const int row1 = a.interleave ? R : a.r_begin + (int)((long long)(split + 1) * Rt / a.S);
+    const int g0 = a.interleave ? gb + split : row0 / a.RS;
+    const int g1 = a.interleave ? gb + gt : (row1 + a.RS - 1) / a.RS;
     const int gstep = a.interleave ? a.S : 1;
     const int nit = g1 > g0 ? (g1 - g0 + gstep - 1) / gstep : 0;
     const int ring0 = a.slot0 * a.n_src;  // ring row of r = 0
@@ -255,8 +261,8 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
     const unsigned char* Xb = static_cast<const unsigned char*>(a.X) + (size_t)kt * R * hrow;
     auto stage_range = [&](int it, int& ra, int& rb) {
         const int g = g0 + it * gstep;
-        ra = max(a.r_begin, g * a.RS);
-        rb = min(R, (g + 1) * a.RS);
+        ra = max(row0, g * a.RS);
+        rb = min(row1, (g + 1) * a.RS);
     };
 
     if (tid == 0) {

@@ -2,9 +2,9 @@
 // frequency-domain NLMS on the canceller's sub-filter spectra; see nlms.h).
 //
 //   nlms_prep    one CTA per microphone: R2C of [0_B | e_p] (shared-memory
-//                FFT), the per-bin power recursion over the loudspeakers'
-//                newest spectra, G_p = mu E_p / (K pow + delta), and the step
-//                on partition 0
+//                FFT in float-float arithmetic), the per-bin power recursion
+//                over the loudspeakers' newest spectra, G_p = mu E_p /
+//                (K pow + delta), and the step on partition 0
 //   nlms_update  F_hat[p][l][j][k] += G_p[k] conj(U_l,j[k]) over the tail
 //                partitions of every filter tile; streams them once (read +
 //                write), the delay line and G come from L2
@@ -23,23 +23,105 @@ namespace gbconv {
 
 namespace {
 
-__global__ void k_nlms_prep(const NlmsPrepArgs a) {
-    extern __shared__ float2 fsm[];
-    const int B = a.B, half = B >> 1, tid = threadIdx.x, nth = blockDim.x;
-    float2* bufA = fsm;
-    float2* bufB = fsm + B;
-    float2* tws = fsm + 2 * B;
-    const int p = blockIdx.x;
-    load_twiddles(tws, a.tw, B);
-    // z[n] = w[2n] + i w[2n+1] with w = [0_B | e_p]
-    const float* e = a.e + (size_t)p * B;
+// ------------------------------------------- float-float (compensated) FFT
+// The error spectrum E = R2C([0_B | e]) sets the step of every update, and an
+// FP32 FFT's rounding (~1.5e-7 relative) in E accumulates in F_hat over the
+// blocks.  E is therefore computed with float-float arithmetic: each value is
+// an unevaluated sum hi + lo of two floats, sums use Knuth's TwoSum and
+// products the exact FMA residual, so the transform carries about 44
+// significant bits before E is rounded to FP32 once.  Only FP32 operations.
+struct ff {
+    float hi, lo;
+};
+struct cff {
+    ff re, im;
+};
+
+__device__ __forceinline__ ff ff_norm(float s, float e) {  // |s| >= |e| after a sum: fast renormalisation
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));  // TwoSum residual
+    return ff_norm(s, __fadd_rn(err, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);  // exact residual of the product
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ff_norm(p, e);
+}
+__device__ __forceinline__ cff cff_add(cff a, cff b) { return {ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+__device__ __forceinline__ cff cff_sub(cff a, cff b) { return {ff_add(a.re, ff_neg(b.re)), ff_add(a.im, ff_neg(b.im))}; }
+__device__ __forceinline__ cff cff_mul(cff a, cff w) {
+    return {ff_add(ff_mul(a.re, w.re), ff_neg(ff_mul(a.im, w.im))), ff_add(ff_mul(a.re, w.im), ff_mul(a.im, w.re))};
+}
+// W_2B^j as float-float from the FP32 table and its residual table
+__device__ __forceinline__ cff tw_ff(const float2* tw, const float2* tw_lo, int j) {
+    const float2 h = __ldg(tw + j), l = __ldg(tw_lo + j);
+    return {{h.x, l.x}, {h.y, l.y}};
+}
+
+// E[k], k < B (packed: bin 0 = (DC, Nyquist)), of the 2B-point R2C of
+// w = [0_B | e]: a B-point radix-2 Stockham FFT of z[n] = w[2n] + i w[2n+1],
+// then the real-FFT post-processing, all in float-float.  `a`, `b`: two
+// shared buffers of B values; returns E for the calling thread's bins via
+// `out` (indexed like the kernel's bin loop).
+__device__ void error_spectrum_ff(const float* e, cff* a, cff* b, int B, const float2* tw, const float2* tw_lo,
+                                  float2* out) {
+    const int tid = threadIdx.x, nth = blockDim.x, half = B >> 1;
+    const cff zero = {{0.0f, 0.0f}, {0.0f, 0.0f}};
     for (int n = tid; n < B; n += nth)
-        bufA[n] = n < half ? make_float2(0.0f, 0.0f) : make_float2(e[2 * n - B], e[2 * n - B + 1]);
+        a[n] = n < half ? zero : cff{{e[2 * n - B], 0.0f}, {e[2 * n - B + 1], 0.0f}};
     __syncthreads();
-    const float2* Z = fft_smem<false>(bufA, bufB, B, a.log2B, tws, a.log2B + 1, tid, nth);
+    for (int Ns = 1; Ns < B; Ns <<= 1) {
+        for (int j = tid; j < half; j += nth) {
+            const int k = j & (Ns - 1);
+            const cff v0 = a[j];
+            cff v1 = a[j + half];
+            if (k) v1 = cff_mul(v1, tw_ff(tw, tw_lo, k * (B / Ns)));  // W_2Ns^k = W_2B^(k B / Ns)
+            const int o = ((j - k) << 1) + k;
+            b[o] = cff_add(v0, v1);
+            b[o + Ns] = cff_sub(v0, v1);
+        }
+        __syncthreads();
+        cff* t = a;
+        a = b;
+        b = t;
+    }
+    // a holds Z = FFT_B(z); E[k] = (Z[k] + conj Z[B-k]) / 2 + W_2B^k (Z[k] - conj Z[B-k]) / 2i
+    for (int k = tid; k < B; k += nth) {
+        const cff Z = a[k];
+        if (k == 0) {
+            out[k] = make_float2(ff_add(Z.re, Z.im).hi, ff_add(Z.re, ff_neg(Z.im)).hi);
+            continue;
+        }
+        const cff Zm = a[B - k];
+        const ff half_f = {0.5f, 0.0f};
+        const cff Ev = {ff_mul(ff_add(Z.re, Zm.re), half_f), ff_mul(ff_add(Z.im, ff_neg(Zm.im)), half_f)};
+        const cff D = {ff_mul(ff_add(Z.re, ff_neg(Zm.re)), half_f), ff_mul(ff_add(Z.im, Zm.im), half_f)};
+        const cff O = {D.im, ff_neg(D.re)};  // D / i
+        const cff r = cff_add(Ev, cff_mul(O, tw_ff(tw, tw_lo, k)));
+        out[k] = make_float2(r.re.hi + r.re.lo, r.im.hi + r.im.lo);
+    }
+}
+
+__global__ void k_nlms_prep(const NlmsPrepArgs a) {
+    extern __shared__ __align__(16) unsigned char prep_smem[];
+    const int B = a.B, tid = threadIdx.x, nth = blockDim.x;
+    cff* bufA = reinterpret_cast<cff*>(prep_smem);
+    cff* bufB = bufA + B;
+    float2* Es = reinterpret_cast<float2*>(bufB + B);  // [B] the error spectrum, rounded once
+    const int p = blockIdx.x;
+    error_spectrum_ff(a.e + (size_t)p * B, bufA, bufB, B, a.tw, a.tw_lo, Es);
+    __syncthreads();
     const float kf = (float)a.K;
     for (int k = tid; k < B; k += nth) {
-        const float2 E = r2c_post(Z, k, B, tws);
+        const float2 E = Es[k];
         const int kt = k / a.BT, kl = k - kt * a.BT;
         const float2* u = a.U + ((size_t)kt * a.K + a.slot0) * a.L * a.BT + kl;
         float px = 0.0f, py = 0.0f;
@@ -355,9 +437,13 @@ cudaError_t launch_nlms_update_mac(const NlmsUpdateMacArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// two float-float buffers of B complex values and the rounded spectrum
+static size_t nlms_prep_smem(int B) { return (size_t)B * (2 * sizeof(float) * 4 + sizeof(float2)); }
+
 cudaError_t launch_nlms_prep(const NlmsPrepArgs& a, int P, cudaStream_t s) {
     static_assert(sizeof(float2) == 8, "packed spectra are float pairs");
-    const size_t sm = fft_smem_bytes(a.B);
+    if (!a.tw_lo) return cudaErrorInvalidValue;
+    const size_t sm = nlms_prep_smem(a.B);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_nlms_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;

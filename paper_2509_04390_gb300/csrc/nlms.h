@@ -46,7 +46,8 @@ struct NlmsPrepArgs {
     float2* G;             // [P][B] packed step-scaled error spectra
     int B, log2B, BT, L, K;
     float mu, lam, delta;
-    const float2* tw;      // W_2B^j, j in [0, 2B)
+    const float2* tw;      // W_2B^j, j in [0, 2B), rounded to FP32
+    const float2* tw_lo;   // W_2B^j - tw[j], rounded to FP32 (the float-float residual)
     // filter spectra, tiles at (kt*n_lt + lt)*tile_elems, then [r][LTt][BT]:
     // rows r = l (partition 0) take the step here
     float2* F;
