@@ -694,6 +694,8 @@ def run_batch(args):
     batch = U.Batch(args.precision)
     for e in engs:
         batch.add(e)
+    if args.persistent:
+        batch.set_persistent(args.persistent)
 
     lib = U.load()
     p_stream = stream.cuda_stream
@@ -764,7 +766,10 @@ def run_batch(args):
         "dtype": "f32" if args.precision == "fp32" else f"{args.precision} storage, f32 arithmetic",
         "data": "synthetic: seeded exponentially decaying noise filters, white-noise inputs",
         "config": {
-            "workload": f"batch_{len(specs)}_sessions_{args.precision}",
+            "workload": f"batch_{len(specs)}_sessions_{args.precision}"
+                        + {0: "", 1: "_persistent", 2: "_persistent_graph"}[args.persistent],
+            "step_form": {0: "one launch per stage", 1: "one persistent launch per step",
+                          2: "one persistent launch per step, replayed from a CUDA graph"}[args.persistent],
             "sessions": len(specs),
             "n_in": "U{1..8}", "n_out": "U{2..32}", "filter_s": "U(2,12)", "block": "{64..1024}",
             "taps_total": int(sum(sp.n_in * sp.n_out * sp.taps for sp in specs)),
@@ -783,7 +788,7 @@ def run_batch(args):
             "steps": k_u,
             "note": "same sessions, one engine call (3 launches) per session per step",
         },
-        "gpu_launches": args.steps * 3,
+        "gpu_launches": args.steps * (1 if args.persistent else 3),
         "setup_s": t_setup,
         "device_bytes": int(sum(e.info()["device_bytes"] for e in engs)),
     }
@@ -998,7 +1003,38 @@ def run_serve(args):
 
 EXTRA_KEYS = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "roofline", "e2e",
               "step_bandwidth", "unbatched", "separate_engines", "plan", "clocks", "gpu_launches", "poisson",
-              "sustained", "higher_is_better")
+              "sustained", "higher_is_better", "planner", "speedup_vs_planner")
+
+
+def run_tuned(args):
+    """The autotuner on the headline shape: candidates timed on the real engine
+    within a budget (objective: the back-to-back step), the winner cached in a
+    private file, then the tuned engine against the planner's, both measured
+    the same way."""
+    import tempfile
+
+    from paper_2509_04390_gb300 import autotune as A
+
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "tiling.json")
+        t0 = time.time()
+        entry = A.tune(args.precision, args.block, 4, 16, args.taps, budget_s=args.tune_budget, steps=400,
+                       path=path)
+        tune_s = time.time() - t0
+        h = A._filters(16, 4, args.taps)
+        tuned = min(A.measure(entry["tiling"], args.precision, args.block, 4, 16, args.taps, h, steps=1000)
+                    for _ in range(3))
+        planner = min(A.measure({}, args.precision, args.block, 4, 16, args.taps, h, steps=1000) for _ in range(3))
+    units = 4.0 * 16 * args.taps * args.block
+    return {
+        "metric": METRIC, "unit": UNIT, "value": units / tuned / 1e9, "ms_per_step": tuned * 1e3,
+        "config": {"workload": f"paper_4x16_{args.taps}taps_B{args.block}_{args.precision}_tuned",
+                   "tiling": entry["tiling"], "candidates_timed": entry["candidates_timed"],
+                   "candidates": entry["candidates"], "tune_seconds": tune_s,
+                   "filters": "exponentially decaying noise (the tuner's own), 4x16"},
+        "planner": {"value": units / planner / 1e9, "ms_per_step": planner * 1e3},
+        "speedup_vs_planner": planner / tuned,
+    }
 
 
 def run_extras(args):
@@ -1022,6 +1058,7 @@ def run_extras(args):
         a.far_block = a.far_block2 = 0
         a.afc, a.adapt, a.batch, a.group, a.serve = False, 0.0, 0, 0, False
         a.no_separate = False
+        a.persistent = 0
         for k, v in kw.items():
             setattr(a, k, v)
         return a
@@ -1035,7 +1072,13 @@ def run_extras(args):
         ("afc_4x16_B256_fp16", run_ours, variant(afc=True, precision="fp16")),
         ("group_8_sessions_B256_fp16", run_group, variant(group=8, precision="fp16")),
         ("batch_64_sessions_fp16", run_batch, variant(batch=64, precision="fp16", steps=min(steps, 200))),
+        ("batch_64_sessions_fp16_persistent", run_batch,
+         variant(batch=64, precision="fp16", steps=min(steps, 200), persistent=1)),
+        ("batch_64_sessions_fp16_persistent_graph", run_batch,
+         variant(batch=64, precision="fp16", steps=min(steps, 200), persistent=2)),
         ("serving", run_serve, variant(serve=True, serve_seconds=min(args.serve_seconds, 5.0))),
+        ("paper_4x16_B256_fp32_tuned", run_tuned, variant()),
+        ("paper_4x16_B256_fp16_tuned", run_tuned, variant(precision="fp16")),
     ]
     out = {}
     for name, fn, a in plan:
@@ -1052,7 +1095,9 @@ def run_extras(args):
 
 
 ALL_EXTRAS = ("paper_4x16_B128_fp32,paper_4x16_B512_fp32,paper_4x16_B256_fp16,paper_4x16_B256_bf16,"
-              "afc_4x16_B256_fp32,afc_4x16_B256_fp16,group_8_sessions_B256_fp16,batch_64_sessions_fp16,serving")
+              "afc_4x16_B256_fp32,afc_4x16_B256_fp16,group_8_sessions_B256_fp16,batch_64_sessions_fp16,"
+              "batch_64_sessions_fp16_persistent,batch_64_sessions_fp16_persistent_graph,serving,"
+              "paper_4x16_B256_fp32_tuned,paper_4x16_B256_fp16_tuned")
 
 
 def parse(argv=None):
@@ -1088,6 +1133,9 @@ def parse(argv=None):
                     help="comma-separated secondary configurations reported under 'extra' of the headline line "
                          "(single GPU, default run only); '' for none")
     ap.add_argument("--extra-steps", type=int, default=2000, help="timed steps of each secondary configuration")
+    ap.add_argument("--tune-budget", type=float, default=15.0, help="seconds of candidate timing in the tuned extras")
+    ap.add_argument("--persistent", type=int, nargs="?", const=1, default=0, choices=[0, 1, 2],
+                    help="with --batch: each step as one persistent launch (1), replayed from a CUDA graph (2)")
     ap.add_argument("--no-separate", action="store_true",
                     help="with --group: skip the comparison with separate engines")
     return ap.parse_args(argv)

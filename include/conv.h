@@ -411,6 +411,23 @@ int conv_batch_process_async(conv_batch* b, const float* const* d_in, float* con
 int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, const float* const* d_in,
                                   float* const* d_out, void* cuda_stream);
 
+/* Persistent batch steps.  mode 1: every later step of the batch runs as ONE
+ * kernel launch instead of one launch per stage; mode 2: the same, replayed
+ * from a CUDA graph (the step's table copy, counter reset and launch, captured
+ * once per table layout and replayed while the due sessions and table sizes
+ * stay the same: the graph's copy reads the step's freshly built table);
+ * mode 0: back to one launch per stage.  About one CTA per SM claims
+ * work items from a device-side list in dependency order: the synthesis
+ * packs, then the outputs, the canceller's packs and outputs, then the tail
+ * MACs of the next block.  An item that needs other items' results waits for
+ * a device counter they raise.  Every such wait is bounded; a wait that gives
+ * up is reported as CONV_E_TIMEOUT by conv_batch_synchronize.  The items run
+ * the same device code as the separate launches, so the outputs are the same
+ * bit for bit.  The step's argument tables and work list are built on the
+ * host and copied in with one copy, as in the other mode.  Can be switched
+ * between steps.  CONV_OK or CONV_E_INVAL / CONV_E_CUDA. */
+int conv_batch_set_persistent(conv_batch* b, int mode);
+
 /* Wait for all of the batch's work; report a device-side error of any session. */
 int conv_batch_synchronize(conv_batch* b);
 

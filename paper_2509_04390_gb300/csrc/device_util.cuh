@@ -120,25 +120,28 @@ struct Store<PREC_BF16> {
 // Four planar bins (one 16-byte chunk: 8 bytes of real parts, 8 of
 // imaginary parts) as floats.
 template <typename St>
-__device__ __forceinline__ void load_planar4(const unsigned char* row, int kv, int BT, float2 (&re)[2],
-                                             float2 (&im)[2]) {
-    (void)BT;
-    const uint4 t = *reinterpret_cast<const uint4*>(row + (size_t)kv * 16);
+__device__ __forceinline__ void unpack_planar4(const uint4 t, float2 (&re)[2], float2 (&im)[2]) {
     re[0] = St::unpack(t.x);
     re[1] = St::unpack(t.y);
     im[0] = St::unpack(t.z);
     im[1] = St::unpack(t.w);
 }
-
-// d = a * b + c on pairs of floats (one packed FP32x2 FMA)
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;"
-        : "=l"(d)
-        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
-          "l"(*reinterpret_cast<unsigned long long*>(&c)));
-    return *reinterpret_cast<float2*>(&d);
+template <typename St>
+__device__ __forceinline__ void load_planar4(const unsigned char* row, int kv, int BT, float2 (&re)[2],
+                                             float2 (&im)[2]) {
+    (void)BT;
+    unpack_planar4<St>(*reinterpret_cast<const uint4*>(row + (size_t)kv * 16), re, im);
 }
+
+// d = a * b + c on pairs of floats.  Two scalar FMAs: measured on GB300 in
+// the FP16/BF16 MAC, the packed fma.rn.f32x2 form was slower (25.5 vs 23.6 us
+// per launch at the paper configuration).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+
+// d = a * b on pairs of floats (two scalar multiplies, as ffma2)
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
 
 // Power-of-two scale for a block of values with largest magnitude `maxabs`:
 // FP16 stores value/scale in [2^13, 2^14) at the top (well inside 65504),
@@ -158,6 +161,34 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Explicit shared-memory loads (ld.shared), for operands reached through
+// pointers whose address space the compiler may not track.
+__device__ __forceinline__ uint4 lds128(const void* p) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(smem_u32(p)));
+    return v;
+}
+__device__ __forceinline__ float lds_f32(const float* p) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(smem_u32(p)));
+    return v;
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Orders this thread's earlier generic-proxy view of global and shared memory
+// before its later bulk (async-proxy) copies: data other CTAs wrote, and
+// shared memory that generic code used before the copies land there.
+__device__ __forceinline__ void fence_proxy_async_all() {
+    asm volatile("fence.proxy.async.global;\n\tfence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

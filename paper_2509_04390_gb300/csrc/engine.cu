@@ -192,7 +192,7 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     p.nstage = std::min(prec == PREC_FP32 ? 2 : 3, fit);
     if (o.stages) p.nstage = std::max(2, std::min(o.stages, fit));
     // scratch for combining r-lanes reuses (and if needed extends) the stage ring
-    const size_t red = (size_t)(p.NRL - 1) * p.LT * p.BT * sizeof(float2);
+    const size_t red = (size_t)(p.NRL - 1) * p.LPT * p.NLG * p.BT * sizeof(float2);  // lane-major r-lane scratch
     p.smem = MAC_HDR_BYTES + std::max((size_t)p.nstage * p.stage_bytes, align_up(red, 128));
     const int tiles = p.n_kt * p.n_lt;
     int gt = Rt > 0 ? (p.R + p.RS - 1) / p.RS - r_begin / p.RS : 0;  // stages on the grid
@@ -242,7 +242,7 @@ int check_direct_plan(const MacPlan& p, std::string* why) {
     if (p.kthreads * rest != 256 || p.NLG * p.NRL != rest) return bad("thread layout");
     if ((p.LT + p.NLG - 1) / p.NLG > p.LPT) return bad("outputs per thread above LPT");
     if (p.S < 1 || p.S > Rt) return bad("split count");
-    if ((size_t)(p.NRL - 1) * p.LT * p.BT * 8 > p.smem) return bad("r-lane scratch");
+    if ((size_t)(p.NRL - 1) * p.LPT * p.NLG * p.BT * 8 > p.smem) return bad("r-lane scratch");
     if (p.smem > MAC_SMEM_LIMIT) return bad("shared memory");
     const size_t hrow = (size_t)p.BT * p.es;
     if ((size_t)p.R * p.LT * p.BT > p.tile_elems) return bad("tile pitch below a tile");
@@ -297,7 +297,7 @@ int check_plan(const MacPlan& p, std::string* why) {
     const size_t hrow = (size_t)p.BT * p.es;
     if (hrow % 16) return bad("row not a multiple of 16 bytes");
     if (p.stage_bytes % 16 || p.xoff % 16) return bad("stage alignment");
-    if ((size_t)(p.NRL - 1) * p.LT * p.BT * 8 > p.smem - MAC_HDR_BYTES) return bad("r-lane scratch");
+    if ((size_t)(p.NRL - 1) * p.LPT * p.NLG * p.BT * 8 > p.smem - MAC_HDR_BYTES) return bad("r-lane scratch");
     if ((size_t)p.nstage * p.stage_bytes > p.smem - MAC_HDR_BYTES) return bad("stage ring");
     for (int cta = 0; cta < p.ctas; ++cta) {
         const int tile = cta / p.S, split = cta % p.S;
@@ -1780,11 +1780,38 @@ struct conv_batch {
     unsigned char* d_tab[2] = {nullptr, nullptr};
     size_t tab_cap = 0;
     long long step = 0;
+    // persistent mode (conv_batch_set_persistent): one launch per step
+    bool persistent = false;
+    bool graph = false;         // replay the step (copy, counter reset, launch) from a CUDA graph
+    int num_sms = 0;
+    unsigned* d_ctr = nullptr;  // claim counter + two counters per item, zeroed before each step
+    size_t ctr_cap = 0;         // unsigned values it holds
+    cudaStream_t cap = nullptr;  // capture stream of the step graphs
+    // one graph per table parity, and what it was captured for
+    struct GraphKey {
+        size_t bytes = 0, smem = 0, nctr = 0;
+        int n_work = 0, ctas = 0;
+        const void *d = nullptr, *h = nullptr, *ctr = nullptr, *err = nullptr;
+        bool operator==(const GraphKey& o) const {
+            return bytes == o.bytes && smem == o.smem && nctr == o.nctr && n_work == o.n_work && ctas == o.ctas &&
+                   d == o.d && h == o.h && ctr == o.ctr && err == o.err;
+        }
+    } gkey[2];
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
 };
 
 namespace {
 
+void batch_free_graphs(conv_batch* b) {
+    for (int i = 0; i < 2; ++i) {
+        if (b->gexec[i]) cudaGraphExecDestroy(b->gexec[i]);
+        b->gexec[i] = nullptr;
+        b->gkey[i] = conv_batch::GraphKey();
+    }
+}
+
 void batch_free_tables(conv_batch* b) {
+    batch_free_graphs(b);  // the graphs name the tables
     for (int i = 0; i < 2; ++i) {
         if (b->h_tab[i]) cudaFreeHost(b->h_tab[i]);
         if (b->d_tab[i]) cudaFree(b->d_tab[i]);
@@ -1801,6 +1828,132 @@ int batch_sync(conv_batch* b) {
 }
 
 size_t align16(size_t v) { return (v + 15) / 16 * 16; }
+
+// The persistent form of a batch step: the argument tables are built (h), the
+// work list is appended in dependency order, and one launch runs it all.
+// Counters: 2 i = packs of argument item i done, 2 i + 1 = its outputs done.
+int batch_step_persistent(conv_batch* b, int count, const int* idx, unsigned char* h, unsigned char* d, size_t o_pack,
+                          size_t o_out, size_t o_mac, size_t o_work, int n_work, int n_items, size_t mac_smem, int Bmax,
+                          size_t bytes, int par, cudaStream_t s) {
+    PersistentWork* wk = reinterpret_cast<PersistentWork*>(h + o_work);
+    std::vector<int> fb_item(count, -1);
+    for (int j = 0, ia = count; j < count; ++j)
+        if (b->sessions[idx[j]]->fb.allocated) fb_item[j] = ia++;
+    int w = 0;
+    auto add = [&](int type, int item, int i1, int i2, int wait, int target, int signal) {
+        wk[w++] = PersistentWork{type, item, i1, i2, wait, target, signal};
+    };
+    for (int j = 0; j < count; ++j)  // synthesis packs (e = mic - c_prev for canceller sessions)
+        for (int c = 0; c < b->sessions[idx[j]]->syn.n_src; ++c) add(PW_PACK, j, c, 0, -1, 0, 2 * j);
+    for (int j = 0; j < count; ++j) {  // synthesis outputs: head + tail partials + C2R
+        const Part& P = b->sessions[idx[j]]->syn;
+        for (int l = 0; l < P.n_dst; ++l) add(PW_OUT, j, l, 0, 2 * j, P.n_src, 2 * j + 1);
+    }
+    for (int j = 0; j < count; ++j)  // the canceller's packs of the loudspeaker blocks
+        if (fb_item[j] >= 0) {
+            const conv_engine* e = b->sessions[idx[j]];
+            for (int c = 0; c < e->fb.n_src; ++c) add(PW_PACK, fb_item[j], c, 0, 2 * j + 1, e->syn.n_dst, 2 * fb_item[j]);
+        }
+    for (int j = 0; j < count; ++j)  // the canceller's outputs (the prediction for the next block)
+        if (fb_item[j] >= 0) {
+            const Part& F = b->sessions[idx[j]]->fb;
+            for (int p = 0; p < F.n_dst; ++p) add(PW_OUT, fb_item[j], p, 0, 2 * fb_item[j], F.n_src, -1);
+        }
+    for (int j = 0; j < count; ++j) {  // tail MACs of the next block, both convolutions
+        const conv_engine* e = b->sessions[idx[j]];
+        const MacPlan& p = e->syn.plan;
+        if (p.S)
+            for (int cta = 0; cta < p.ctas; ++cta) add(PW_MAC, j, cta / p.S, cta % p.S, 2 * j, e->syn.n_src, -1);
+        if (fb_item[j] >= 0 && e->fb.plan.S) {
+            const MacPlan& q = e->fb.plan;
+            for (int cta = 0; cta < q.ctas; ++cta)
+                add(PW_MAC, fb_item[j], cta / q.S, cta % q.S, 2 * fb_item[j], e->fb.n_src, -1);
+        }
+    }
+    if (w != n_work) return set_err(CONV_E_STATE, "persistent work list: %d items, %d expected", w, n_work);
+    const size_t nctr = 1 + 2 * (size_t)n_items;
+    if (nctr > b->ctr_cap) {
+        int rc;
+        if ((rc = batch_sync(b))) return rc;
+        batch_free_graphs(b);
+        if (b->d_ctr) cudaFree(b->d_ctr);
+        b->d_ctr = nullptr;
+        b->ctr_cap = 0;
+        CK(cudaMalloc(reinterpret_cast<void**>(&b->d_ctr), 2 * nctr * sizeof(unsigned)));
+        b->ctr_cap = 2 * nctr;
+    }
+    const size_t smem = std::max(mac_smem, fft_smem_bytes(Bmax));
+    if (smem > MAC_SMEM_LIMIT - PERSISTENT_STATIC_SMEM)
+        return set_err(CONV_E_INVAL, "persistent step: %zu bytes of shared memory above the kernel's limit", smem);
+    const int ctas = std::max(1, std::min(n_work, b->num_sms));
+    int* err = b->sessions[idx[0]]->d_err;
+    // the step's three operations: table copy, counter reset, the launch
+    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t r = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, q);
+        if (r == cudaSuccess) r = cudaMemsetAsync(b->d_ctr, 0, nctr * sizeof(unsigned), q);
+        if (r == cudaSuccess)
+            r = launch_batch_persistent(b->prec, reinterpret_cast<const PackArgs*>(d + o_pack),
+                                        reinterpret_cast<const OutArgs*>(d + o_out),
+                                        reinterpret_cast<const MacArgs*>(d + o_mac),
+                                        reinterpret_cast<const PersistentWork*>(d + o_work), n_work, b->d_ctr, err, ctas,
+                                        smem, q);
+        return r;
+    };
+    // tails of earlier steps in the other mode ran on the background streams
+    CK(cudaStreamWaitEvent(s, b->ev_tail[0], 0));
+    CK(cudaStreamWaitEvent(s, b->ev_tail[1], 0));
+    if (b->graph) {
+        // the graph's copy reads the pinned table when it runs, so a replay
+        // carries this step's arguments; a new layout is captured again
+        conv_batch::GraphKey k;
+        k.bytes = bytes;
+        k.smem = smem;
+        k.nctr = nctr;
+        k.n_work = n_work;
+        k.ctas = ctas;
+        k.d = d;
+        k.h = h;
+        k.ctr = b->d_ctr;
+        k.err = err;
+        if (!b->gexec[par] || !(b->gkey[par] == k)) {
+            if (b->gexec[par]) CK(cudaGraphExecDestroy(b->gexec[par]));
+            b->gexec[par] = nullptr;
+            if (!b->cap) CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+            CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            const cudaError_t r = enqueue(b->cap);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t r2 = cudaStreamEndCapture(b->cap, &graph);
+            if (r != cudaSuccess || r2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return set_err(CONV_E_CUDA, "capturing the persistent step: %s",
+                               cudaGetErrorString(r != cudaSuccess ? r : r2));
+            }
+            const cudaError_t r3 = cudaGraphInstantiate(&b->gexec[par], graph, 0);
+            cudaGraphDestroy(graph);
+            if (r3 != cudaSuccess) {
+                b->gexec[par] = nullptr;
+                return set_err(CONV_E_CUDA, "instantiating the persistent step: %s", cudaGetErrorString(r3));
+            }
+            b->gkey[par] = k;
+        }
+        CK(cudaGraphLaunch(b->gexec[par], s));
+    } else {
+        CK(enqueue(s));
+    }
+    CK(cudaEventRecord(b->ev_staged[par], s));
+    // the step's tails are done when the launch is: the join and the next
+    // step's waits see them through the tail event
+    cudaStream_t bg = b->bg[par ^ 1];
+    CK(cudaEventRecord(b->ev_packed, s));
+    CK(cudaStreamWaitEvent(bg, b->ev_packed, 0));
+    CK(cudaEventRecord(b->ev_tail[par ^ 1], bg));
+    for (int j = 0; j < count; ++j) {
+        ++b->sessions[idx[j]]->nblk;
+        ++b->sessions[idx[j]]->st.blocks;
+    }
+    ++b->step;
+    return CONV_OK;
+}
 
 }  // namespace
 
@@ -1927,7 +2080,9 @@ int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, cons
     const size_t o_rp = align16(o_mac + (size_t)n_items * sizeof(MacArgs));
     const size_t o_ro = align16(o_rp + (size_t)(n_pack + n_fpack) * sizeof(BatchRef));
     const size_t o_rm = align16(o_ro + (size_t)(n_out + n_fout) * sizeof(BatchRef));
-    const size_t bytes = align16(o_rm + (size_t)n_mac * sizeof(BatchRef));
+    const int n_work = b->persistent ? n_pack + n_out + n_fpack + n_fout + n_mac : 0;
+    const size_t o_work = align16(o_rm + (size_t)n_mac * sizeof(BatchRef));
+    const size_t bytes = align16(o_work + (size_t)n_work * sizeof(PersistentWork));
     if (bytes > b->tab_cap) {
         int rc;
         if ((rc = batch_sync(b))) return rc;
@@ -1978,6 +2133,8 @@ int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, cons
             ++ia;
         }
     }
+    if (b->persistent) return batch_step_persistent(b, count, idx, h, d, o_pack, o_out, o_mac, o_work, n_work, n_items,
+                                                    mac_smem, Bmax, bytes, par, s);
     CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(b->ev_staged[par], s));
     const PackArgs* d_pk = reinterpret_cast<const PackArgs*>(d + o_pack);
@@ -2010,6 +2167,16 @@ int conv_batch_process_some_async(conv_batch* b, int count, const int* idx, cons
         ++b->sessions[idx[j]]->st.blocks;
     }
     ++b->step;
+    return CONV_OK;
+}
+
+int conv_batch_set_persistent(conv_batch* b, int mode) {
+    if (!b) return set_err(CONV_E_INVAL, "null handle");
+    if (mode < 0 || mode > 2) return set_err(CONV_E_INVAL, "mode must be 0, 1 or 2");
+    DeviceGuard g(b->dev);
+    if (!b->num_sms) CK(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->dev));
+    b->persistent = mode != 0;
+    b->graph = mode == 2;
     return CONV_OK;
 }
 
@@ -2054,6 +2221,8 @@ void conv_batch_destroy(conv_batch* b) {
         if (e->fb.allocated) cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream);
     }
     batch_free_tables(b);
+    if (b->d_ctr) cudaFree(b->d_ctr);
+    if (b->cap) cudaStreamDestroy(b->cap);
     if (b->ev_packed) cudaEventDestroy(b->ev_packed);
     for (int i = 0; i < 2; ++i) {
         if (b->ev_tail[i]) cudaEventDestroy(b->ev_tail[i]);

@@ -332,6 +332,10 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
                 if (w[2][1] > 0) bulk_g2s(ss + b1, a.sX, (uint32_t)(4 * w[2][1]), &full[st], pol_keep);
             }
         };
+        // the copies read data written by generic stores (earlier kernels, or
+        // other CTAs of a persistent step) into shared memory generic code may
+        // have used
+        fence_proxy_async_all();
         // Fault-path testing: this CTA withholds its first stage (no copy, no
         // arrival on its barrier), so its consumers' bounded wait runs out.
         const bool hold = a.withhold && tile == 0 && split == 0 && nit > 0;
@@ -452,32 +456,51 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
             }
         } else {
             // Planar rows, 4 bins per thread as two pairs; acc[i] = (re 0-1, re 2-3,
-            // im 0-1, im 2-3).  Per pair: re += hr*xr + hi*(-xi), im += hr*xi + hi*xr,
-            // four packed FP32x2 FMAs.  Both scales are per reduction index and are
-            // folded into x once.  The packed bin 0 (DC, Nyquist) needs re += hr*xr
-            // and im += hi*xi: its lane of the operand pairs is set up for that here,
-            // outside the output loop.
-            for (int j = rl; j < nr; j += a.NRL) {
-                float2 xr[2], xi[2];
-                load_planar4<St>(sx + (size_t)j * hrow, kv, a.BT, xr, xi);
-                const float sc = (j < xrun ? ssx[sx0 + j] : ssx[sx2 + j]) * ssh[sh0 + j];
-                xr[0] = cscale(xr[0], sc);
-                xr[1] = cscale(xr[1], sc);
-                xi[0] = cscale(xi[0], sc);
-                xi[1] = cscale(xi[1], sc);
-                float2 nxi0 = make_float2(-xi[0].x, -xi[0].y);
-                const float2 nxi1 = make_float2(-xi[1].x, -xi[1].y);
-                float2 xi0 = xi[0], xr0b = xr[0];
-                if (dc) {
-                    nxi0.x = 0.0f;
-                    xi0.x = 0.0f;
-                    xr0b.x = xi[0].x;
-                }
-                if (full) {
-                    float2 hr[LPT][2], hi[LPT][2];
+            // im 0-1, im 2-3).  Per pair: re += hr*xr + hi*(-xi), im += hr*xi + hi*xr.
+            // Both scales are per reduction index and are folded into x once.  The
+            // packed bin 0 (DC, Nyquist) needs re += hr*xr and im += hi*xi: its lane
+            // of the operand pairs is set up for that here, outside the output loop.
+            if (full) {
+                // Software-pipelined: the next row's 16-byte chunks (delay line and
+                // the LPT filter rows) load while this row's FMAs run.
+                auto ld_row = [&](int jj, uint4& xo, uint4 (&ho)[LPT], float& sxo, float& sho) {
+                    xo = lds128(sx + (size_t)jj * hrow + (size_t)kv * 16);
 #pragma unroll
                     for (int i = 0; i < LPT; ++i)
-                        load_planar4<St>(sh + ((size_t)j * LTt + lg + i * a.NLG) * hrow, kv, a.BT, hr[i], hi[i]);
+                        ho[i] = lds128(sh + ((size_t)jj * LTt + lg + i * a.NLG) * hrow + (size_t)kv * 16);
+                    sxo = lds_f32(jj < xrun ? ssx + sx0 + jj : ssx + sx2 + jj);
+                    sho = lds_f32(ssh + sh0 + jj);
+                };
+                uint4 xw = make_uint4(0u, 0u, 0u, 0u), hw[LPT];
+                float sxw = 0.0f, shw = 0.0f;
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) hw[i] = xw;
+                if (rl < nr) ld_row(rl, xw, hw, sxw, shw);
+                for (int j = rl; j < nr; j += a.NRL) {
+                    const uint4 xc = xw;
+                    uint4 hc[LPT];
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i) hc[i] = hw[i];
+                    const float sc = sxw * shw;
+                    if (j + a.NRL < nr) ld_row(j + a.NRL, xw, hw, sxw, shw);
+                    float2 xr[2], xi[2];
+                    unpack_planar4<St>(xc, xr, xi);
+                    const float2 sc2 = make_float2(sc, sc), nsc2 = make_float2(-sc, -sc);
+                    float2 nxi0 = fmul2(xi[0], nsc2);  // -x_i by the negated scale
+                    const float2 nxi1 = fmul2(xi[1], nsc2);
+                    xr[0] = fmul2(xr[0], sc2);
+                    xr[1] = fmul2(xr[1], sc2);
+                    xi[0] = fmul2(xi[0], sc2);
+                    xi[1] = fmul2(xi[1], sc2);
+                    float2 xi0 = xi[0], xr0b = xr[0];
+                    if (dc) {
+                        nxi0.x = 0.0f;
+                        xi0.x = 0.0f;
+                        xr0b.x = xi[0].x;
+                    }
+                    float2 hr[LPT][2], hi[LPT][2];
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i) unpack_planar4<St>(hc[i], hr[i], hi[i]);
 #pragma unroll
                     for (int i = 0; i < LPT; ++i) {
                         acc[i][0] = ffma2(hr[i][0], xr[0], acc[i][0]);
@@ -492,7 +515,27 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
                         acc[i][2] = ffma2(hi[i][0], xr0b, acc[i][2]);
                         acc[i][3] = ffma2(hi[i][1], xr[1], acc[i][3]);
                     }
-                } else {
+                }
+            } else
+            for (int j = rl; j < nr; j += a.NRL) {
+                float2 xr[2], xi[2];
+                load_planar4<St>(sx + (size_t)j * hrow, kv, a.BT, xr, xi);
+                const float sc = (j < xrun ? ssx[sx0 + j] : ssx[sx2 + j]) * ssh[sh0 + j];
+                const float2 sc2 = make_float2(sc, sc), nsc2 = make_float2(-sc, -sc);
+                // both scales folded into x with packed multiplies; -x_i by the negated scale
+                float2 nxi0 = fmul2(xi[0], nsc2);
+                const float2 nxi1 = fmul2(xi[1], nsc2);
+                xr[0] = fmul2(xr[0], sc2);
+                xr[1] = fmul2(xr[1], sc2);
+                xi[0] = fmul2(xi[0], sc2);
+                xi[1] = fmul2(xi[1], sc2);
+                float2 xi0 = xi[0], xr0b = xr[0];
+                if (dc) {
+                    nxi0.x = 0.0f;
+                    xi0.x = 0.0f;
+                    xr0b.x = xi[0].x;
+                }
+                {
 #pragma unroll
                 for (int i = 0; i < LPT; ++i) {
                     const int ll = lg + i * a.NLG;
@@ -527,18 +570,21 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
         }
     }
 
-    // combine r-lanes in a fixed order (stage memory is free: every stage has landed)
+    // combine r-lanes in a fixed order (stage memory is free: every stage has
+    // landed).  The scratch is lane-major, [r-lane][i][v][thread of the
+    // r-lane], so a warp's 32 stores of one (i, v) are consecutive 8-byte
+    // words: no shared-memory bank conflicts.
     if (a.NRL > 1) {
         named_barrier_sync(1, NW * 32);
         float2* red = reinterpret_cast<float2*>(stages);
-        const int LT = a.LT, BT = a.BT;
+        const int T = a.NLG * a.kthreads, t = lg * a.kthreads + kv;
         if (rl > 0) {
 #pragma unroll
             for (int i = 0; i < LPT; ++i) {
                 const int ll = lg + i * a.NLG;
                 if (ll < LTt)
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) red[((size_t)(rl - 1) * LT + ll) * BT + kv * VEC + v] = acc[i][v];
+                    for (int v = 0; v < VEC; ++v) red[((size_t)((rl - 1) * LPT + i) * VEC + v) * T + t] = acc[i][v];
             }
         }
         named_barrier_sync(1, NW * 32);
@@ -550,7 +596,7 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
                     if (ll < LTt)
 #pragma unroll
                         for (int v = 0; v < VEC; ++v)
-                            acc[i][v] = cadd(acc[i][v], red[((size_t)(rr - 1) * LT + ll) * BT + kv * VEC + v]);
+                            acc[i][v] = cadd(acc[i][v], red[((size_t)((rr - 1) * LPT + i) * VEC + v) * T + t]);
                 }
         }
     }
@@ -670,16 +716,16 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_fdl_mac_ldg(const MacArgs a) 
         }
     }
 
-    if (a.NRL > 1) {
+    if (a.NRL > 1) {  // lane-major scratch, as in k_fdl_mac
         float2* red = reinterpret_cast<float2*>(smem);
-        const int LT = a.LT, BT = a.BT;
+        const int T = a.NLG * a.kthreads, t = lg * a.kthreads + kv;
         if (rl > 0) {
 #pragma unroll
             for (int i = 0; i < LPT; ++i) {
                 const int ll = lg + i * a.NLG;
                 if (ll < LTt)
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) red[((size_t)(rl - 1) * LT + ll) * BT + kv * VEC + v] = acc[i][v];
+                    for (int v = 0; v < VEC; ++v) red[((size_t)((rl - 1) * LPT + i) * VEC + v) * T + t] = acc[i][v];
             }
         }
         __syncthreads();
@@ -691,7 +737,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_fdl_mac_ldg(const MacArgs a) 
                     if (ll < LTt)
 #pragma unroll
                         for (int v = 0; v < VEC; ++v)
-                            acc[i][v] = cadd(acc[i][v], red[((size_t)(rr - 1) * LT + ll) * BT + kv * VEC + v]);
+                            acc[i][v] = cadd(acc[i][v], red[((size_t)((rr - 1) * LPT + i) * VEC + v) * T + t]);
                 }
         }
     }
@@ -854,6 +900,75 @@ constexpr int lpt_for() {
     return PREC == PREC_FP32 ? 8 : 4;
 }
 
+// --------------------------------------------------- persistent batch step
+// One launch runs a whole batch step: every CTA claims work items in list
+// order (packs, outputs, the canceller's packs and outputs, then the tail
+// MACs of the next block) and runs the same device functions as the separate
+// batched kernels, so the results are the same bit for bit.  An item that
+// needs others' results waits (bounded) for a counter they raise: one thread
+// acquires it, the CTA barrier passes the ordering on.  The writer side is a
+// CTA barrier, a device-scope fence and the counter increment.
+template <int PREC>
+__global__ void __launch_bounds__(9 * 32, 1) k_batch_persistent(const PackArgs* __restrict__ pk,
+                                                                const OutArgs* __restrict__ ot,
+                                                                const MacArgs* __restrict__ mc,
+                                                                const PersistentWork* __restrict__ work, int n_work,
+                                                                unsigned* ctr, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ int s_w;
+    __shared__ PackArgs s_pack;
+    __shared__ OutArgs s_out;
+    MacArgs* s_mac = reinterpret_cast<MacArgs*>(smem + MAC_ARGS_OFFSET);
+    for (;;) {
+        __syncthreads();  // the previous item is done with shared memory and s_w
+        if (threadIdx.x == 0) s_w = (int)atomicAdd(ctr, 1u);
+        __syncthreads();
+        const int w = s_w;
+        if (w >= n_work) return;
+        const PersistentWork wk = work[w];
+        if (threadIdx.x == 0) {
+            if (wk.wait >= 0) {
+                const uint64_t t0 = global_timer_ns();
+                while (ld_acquire_gpu(ctr + 1 + wk.wait) < (unsigned)wk.target) {
+                    if (global_timer_ns() - t0 > WAIT_LIMIT_NS) {
+                        *(volatile int*)err = DEVERR_TIMEOUT_CONSUMER;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            if (wk.type == PW_PACK) {
+                s_pack = pk[wk.item];
+            } else if (wk.type == PW_OUT) {
+                s_out = ot[wk.item];
+                s_out.head_pre = 0;
+            } else {
+                *s_mac = mc[wk.item];
+            }
+        }
+        __syncthreads();
+        if (wk.type == PW_PACK) {
+            pack_body<PREC>(s_pack, wk.idx);
+        } else if (wk.type == PW_OUT) {
+            out_body<PREC>(s_out, wk.idx);
+        } else {
+            mac_body<PREC, (PREC == PREC_FP32 ? 8 : 4), 8>(*s_mac, wk.idx, wk.idx2, smem);
+            __syncthreads();
+            if (threadIdx.x == 0) {  // the barriers' memory goes back to generic use
+                uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+                for (int i = 0; i < 2 * MAX_STAGES; ++i) mbar_inval(&bars[i]);
+            }
+        }
+        if (wk.signal >= 0) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(ctr + 1 + wk.signal, 1u);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 int fft_threads(int B) {
@@ -929,6 +1044,10 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR((k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>(), 16>), mac_smem)
     GB_ATTR((k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>(), 16>), mac_smem)
     GB_ATTR((k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>(), 16>), mac_smem)
+    // the persistent step kernel holds a little static shared memory (its staged arguments)
+    GB_ATTR(k_batch_persistent<PREC_FP32>, mac_smem - PERSISTENT_STATIC_SMEM)
+    GB_ATTR(k_batch_persistent<PREC_FP16>, mac_smem - PERSISTENT_STATIC_SMEM)
+    GB_ATTR(k_batch_persistent<PREC_BF16>, mac_smem - PERSISTENT_STATIC_SMEM)
     GB_ATTR((k_fdl_mac_ldg<PREC_FP32, 4, 8, 1, 3>), mac_smem)
     GB_ATTR((k_fdl_mac_ldg<PREC_FP32, 4, 8, 2, 2>), mac_smem)
 #undef GB_ATTR
@@ -1092,6 +1211,21 @@ cudaError_t launch_mac_batch(int prec, const MacArgs* items, const BatchRef* ref
             return launch_pdl_n(k_fdl_mac_batch<PREC_BF16, lpt_for<PREC_BF16>(), 8>, grid, block, smem, s, items, refs);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_batch_persistent(int prec, const PackArgs* pk, const OutArgs* ot, const MacArgs* mc,
+                                    const PersistentWork* work, int n_work, unsigned* ctr, int* err, int ctas,
+                                    size_t smem, cudaStream_t s) {
+    if (n_work <= 0) return cudaSuccess;
+    if (ctas < 1 || smem > MAC_SMEM_LIMIT - PERSISTENT_STATIC_SMEM) return cudaErrorInvalidValue;
+    const dim3 grid(ctas), block(9 * 32);
+    switch (prec) {
+        case PREC_FP32: k_batch_persistent<PREC_FP32><<<grid, block, smem, s>>>(pk, ot, mc, work, n_work, ctr, err); break;
+        case PREC_FP16: k_batch_persistent<PREC_FP16><<<grid, block, smem, s>>>(pk, ot, mc, work, n_work, ctr, err); break;
+        case PREC_BF16: k_batch_persistent<PREC_BF16><<<grid, block, smem, s>>>(pk, ot, mc, work, n_work, ctr, err); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace gbconv

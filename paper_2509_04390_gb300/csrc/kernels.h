@@ -164,6 +164,23 @@ struct BatchRef {
 // mbarriers and the abort flag.
 constexpr int MAC_ARGS_OFFSET = 256;
 
+// One work item of a persistent batch step (launch_batch_persistent).  The
+// CTAs claim items in list order; an item may wait for a counter that items
+// earlier in the list raise, so the lowest unfinished item never waits on an
+// unclaimed one and the step cannot deadlock.
+enum PersistentWorkType { PW_PACK = 0, PW_OUT = 1, PW_MAC = 2 };
+// Shared memory the persistent step kernel keeps for its static variables;
+// its dynamic part is limited to MAC_SMEM_LIMIT minus this.
+constexpr size_t PERSISTENT_STATIC_SMEM = 2048;
+struct PersistentWork {
+    int type;    // PersistentWorkType
+    int item;    // index into the pack / output / MAC argument tables
+    int idx, idx2;  // channel (pack, output) or tile and split (MAC)
+    int wait;    // counter to wait for (-1: none) ...
+    int target;  // ... until it reaches this value
+    int signal;  // counter raised when the item is done (-1: none)
+};
+
 int fft_threads(int B);
 int out_threads(int B);
 size_t fft_smem_bytes(int B);
@@ -186,5 +203,13 @@ cudaError_t launch_out_push(int prec, const OutArgs& a, const PackArgs& b, cudaS
 cudaError_t launch_pack_batch(int prec, const PackArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);
 cudaError_t launch_out_batch(int prec, const OutArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);
 cudaError_t launch_mac_batch(int prec, const MacArgs* items, const BatchRef* refs, int n, size_t smem, cudaStream_t s);
+// One batch step as a single launch of `ctas` persistent CTAs working through
+// `work` (device, n_work items).  ctr: device counters, [0] the claim counter
+// and [1 + i] counter i, all zero at launch.  err: device error word (a
+// bounded dependency wait that gave up).  smem: the larger of the MAC's and
+// the FFT kernels' dynamic shared memory.
+cudaError_t launch_batch_persistent(int prec, const PackArgs* pk, const OutArgs* ot, const MacArgs* mc,
+                                    const PersistentWork* work, int n_work, unsigned* ctr, int* err, int ctas,
+                                    size_t smem, cudaStream_t s);
 
 }  // namespace gbconv

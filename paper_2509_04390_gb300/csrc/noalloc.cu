@@ -156,7 +156,7 @@ extern "C" int conv_fdl_mac_noalloc(const float* d_H, const float* d_X, int bloc
     p.stage_bytes = (unsigned)(hpart + xpart);
     size_t nst = (200 * 1024 - MAC_HDR_BYTES) / p.stage_bytes;
     p.nstage = (int)(nst < 2 ? 2 : (nst > MAX_STAGES ? MAX_STAGES : nst));
-    const size_t red = (size_t)(p.NRL - 1) * p.LT * p.BT * sizeof(float2);
+    const size_t red = (size_t)(p.NRL - 1) * p.LPT * p.NLG * p.BT * sizeof(float2);  // lane-major r-lane scratch
     const size_t ring = (size_t)p.nstage * p.stage_bytes;
     p.smem = MAC_HDR_BYTES + (ring > red ? ring : (red + 127) / 128 * 128);
     if (p.smem > 200 * 1024) return fail(CONV_E_INVAL, "tiling needs more shared memory than planned");

@@ -190,6 +190,7 @@ def load():
         "conv_batch_process_async": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]),
         "conv_batch_process_some_async": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]),
         "conv_batch_synchronize": (i, [vp]),
+        "conv_batch_set_persistent": (i, [vp, i]),
         "conv_batch_step_bytes": (ll, [vp]),
         "conv_batch_destroy": (None, [vp]),
         "conv_group_create": (vp, [i, i, i, i, ll, i]),
@@ -473,6 +474,12 @@ def conv_batch_synchronize(b):
     return _check(load().conv_batch_synchronize(b))
 
 
+def conv_batch_set_persistent(b, mode=1):
+    """mode 0: one launch per stage; 1: one persistent launch per step; 2: the
+    persistent step replayed from a CUDA graph."""
+    return _check(load().conv_batch_set_persistent(b, int(mode)))
+
+
 def conv_batch_step_bytes(b):
     return int(load().conv_batch_step_bytes(b))
 
@@ -608,6 +615,9 @@ class Batch:
 
     def synchronize(self):
         conv_batch_synchronize(self.b)
+
+    def set_persistent(self, mode=1):
+        conv_batch_set_persistent(self.b, int(mode))
 
     def step_bytes(self):
         return conv_batch_step_bytes(self.b)

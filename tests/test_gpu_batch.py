@@ -225,3 +225,98 @@ def test_canceller_session_in_a_batch():
     np.testing.assert_array_equal(yp, alone_p)
     e.close()
     p.close()
+
+
+def afc_session(seed, P, L, taps, taps_fb, B, precision):
+    rng = np.random.default_rng(seed)
+    h = (rng.standard_normal((L, P, taps)) * np.exp(-np.arange(taps) / (taps / 4)) / np.sqrt(taps)).astype(np.float32)
+    f = (rng.standard_normal((P, L, taps_fb)) * np.exp(-np.arange(taps_fb) / (taps_fb / 4)) * 0.02).astype(np.float32)
+    x = (rng.standard_normal((P, 24 * B)) * 0.1).astype(np.float32)
+    e = U.Engine(48000, B, P, L, taps, precision, BATCH_TILING)
+    e.set_filters(h)
+    e.set_paths(f)
+    return signals.Workload(f"afc{seed}", 48000, B, h, x, f), e
+
+
+def mixed_sessions(precision, seed0):
+    ws, engs = make_sessions(precision, seed0)
+    for k, (P, L, taps, taps_fb, B) in enumerate(((2, 5, 3000, 600, 64), (4, 16, 9000, 2000, 256))):
+        w, e = afc_session(seed0 + 50 + k, P, L, taps, taps_fb, B, precision)
+        ws.append(w)
+        engs.append(e)
+    return ws, engs
+
+
+def run_steps(torch, ws, engs, persistent_at, blocks, some=None):
+    """Blocks through one batch; persistent_at(b) says whether step b runs as
+    one persistent launch; some(b): the session indices due at step b (all if None)."""
+    outs = [np.zeros((w.n_out, blocks * w.block), np.float32) for w in ws]
+    d_x = [torch.from_numpy(w.x).cuda() for w in ws]
+    d_y = [torch.zeros((w.n_out, w.block), dtype=torch.float32, device="cuda") for w in ws]
+    done = [0] * len(ws)
+    with U.Batch(U.conv_get_info(engs[0].h)["precision"]) as batch:
+        for e in engs:
+            batch.add(e)
+        for b in range(blocks):
+            batch.set_persistent(persistent_at(b))
+            idx = list(range(len(ws))) if some is None else some(b)
+            ins = [d_x[i][:, done[i] * ws[i].block : (done[i] + 1) * ws[i].block].contiguous() for i in idx]
+            batch.process_some_async(idx, ins, [d_y[i] for i in idx], torch.cuda.current_stream())
+            batch.synchronize()
+            torch.cuda.synchronize()
+            for i in idx:
+                outs[i][:, done[i] * ws[i].block : (done[i] + 1) * ws[i].block] = d_y[i].cpu().numpy()
+                done[i] += 1
+        for e in engs:
+            batch.remove(e)
+    return outs, done
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_persistent_step_is_bit_exact(precision):
+    """One persistent launch per step (work items claimed in dependency order)
+    gives the separate launches' outputs bit for bit: plain and canceller
+    sessions, all sessions every step or a changing subset, and switching the
+    mode between steps."""
+    torch = pytest.importorskip("torch")
+    nb = 16
+    ws, engs = mixed_sessions(precision, 700)
+    ref, _ = run_steps(torch, ws, engs, lambda b: False, nb)
+    for e in engs:
+        e.reset()
+    got, _ = run_steps(torch, ws, engs, lambda b: True, nb)
+    for i in range(len(ws)):
+        np.testing.assert_array_equal(got[i], ref[i])
+    for e in engs:
+        e.reset()
+    mixed, _ = run_steps(torch, ws, engs, lambda b: (b % 3 != 1) * (1 + (b % 2)), nb)
+    for i in range(len(ws)):
+        np.testing.assert_array_equal(mixed[i], ref[i])
+    # replayed from CUDA graphs (captured once per table parity, then replayed)
+    for e in engs:
+        e.reset()
+    graphed, _ = run_steps(torch, ws, engs, lambda b: 2, nb)
+    for i in range(len(ws)):
+        np.testing.assert_array_equal(graphed[i], ref[i])
+    # a changing subset of due sessions: each session's stream stays the same
+    some = lambda b: [i for i in range(len(ws)) if (b + i) % 3 != 0]  # noqa: E731
+    for e in engs:
+        e.reset()
+    sub_ref, done = run_steps(torch, ws, engs, lambda b: False, nb, some)
+    for e in engs:
+        e.reset()
+    sub_got, _ = run_steps(torch, ws, engs, lambda b: True, nb, some)
+    for e in engs:
+        e.reset()
+    sub_graph, _ = run_steps(torch, ws, engs, lambda b: 2, nb, some)  # due set changes: graphs re-captured
+    for i in range(len(ws)):
+        n = done[i] * ws[i].block
+        np.testing.assert_array_equal(sub_got[i][:, :n], sub_ref[i][:, :n])
+        np.testing.assert_array_equal(sub_graph[i][:, :n], sub_ref[i][:, :n])
+    # and the plain sessions against the FP64 oracle
+    for i, w in enumerate(ws):
+        if w.f is None:
+            s = snr_db(got[i], upols(w.h.astype(np.float64), w.x[:, : nb * w.block].astype(np.float64), w.block))
+            assert s >= BOUND[precision], (i, s)
+    for e in engs:
+        e.close()
