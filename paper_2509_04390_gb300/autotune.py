@@ -268,15 +268,13 @@ def device_sms() -> int:
     return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 
-_num_sms = device_sms
-
 
 def tune(precision, block, n_in, n_out, taps, budget_s=60.0, steps=200, objective="step", space=None,
          path=None, save=True, repeats=2):
     """Measure the candidates (the planner's choice first) until the budget
     is spent, re-measure the best few `repeats` times (the minimum counts),
     and store the winner.  Returns the cache entry."""
-    sms = _num_sms()
+    sms = device_sms()
     cands = candidates(precision, block, n_in, n_out, taps, sms, space)
     h = _filters(n_out, n_in, taps)
     t0 = time.time()
@@ -314,7 +312,7 @@ def tune(precision, block, n_in, n_out, taps, budget_s=60.0, steps=200, objectiv
 
 def tune_group(precision, block, n_in, n_out, taps, sessions, budget_s=60.0, steps=200, path=None, save=True,
                repeats=2):
-    sms = _num_sms()
+    sms = device_sms()
     cands = group_candidates(precision, block, n_in, n_out, taps, sessions, sms)
     h = _filters(n_out, n_in, taps)
     t0 = time.time()
