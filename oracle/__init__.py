@@ -2,6 +2,7 @@
 from .upols_oracle import (  # noqa: F401
     UpolsOracle,
     afc_closed_loop,
+    afc_closed_loop_reuse,
     mimo_fir,
     mimo_fir_sample,
     num_partitions,

@@ -13,7 +13,8 @@ of Highly Reverberant Spaces using Graphics Hardware", arXiv 2509.04390.
 
 Paper notation used below:
   n_x  block size (``B`` here)            n_h  filter length (``taps``)
-  n_f  FFT size (= 2 n_x, Sec. 4)         K    number of sub-filters
+  n_f  FFT size (2 n_x, Sec. 4; 3 n_x     K    number of sub-filters
+       for the spectrum reuse of Sec. 5)
   Q    conditioned inputs (= P microphones, pre-processor G taken as identity)
   L    loudspeakers (outputs)
   H_aur  Q x L synthesis filters, stored here as h[l][q][:]   (Eqs. 1-2)
@@ -49,6 +50,7 @@ __all__ = [
     "UpolsOracle",
     "upols",
     "afc_closed_loop",
+    "afc_closed_loop_reuse",
 ]
 
 
@@ -98,57 +100,73 @@ class UpolsOracle:
     """Streaming uniformly-partitioned overlap-save convolution, FP64 (Sec. 4).
 
     Initialisation (Sec. 4): every filter h_lq is split into K sub-filters of
-    n_x taps, each sub-filter is padded with n_x zeros and transformed with an
-    n_f = 2 n_x point real-to-complex FFT, giving h_bar[l, q, k, 0..n_x].
+    n_x taps, each sub-filter is zero-padded to n_f samples and transformed
+    with an n_f-point real-to-complex FFT, giving h_bar[l, q, k, 0..n_f/2].
+    The paper's default is n_f = 2 n_x; its Sec. 5 remark on reusing the
+    synthesis output spectra needs n_f = 3 n_x.  Any n_f >= 2 n_x gives the
+    same output: a sub-filter of n_x taps leaves the last n_x samples of the
+    circular convolution free of wrap-around.
 
     ``process_block`` takes one input block x_n of shape [Q][n_x] and runs the
     three stages of Sec. 4 literally:
-      1. input transformation: left-shift the n_f-sample sliding window by n_x,
-         append x_n, R2C FFT -> x_bar_n (n_x + 1 bins);
-      2. frequency-domain convolution: shift the FDL up by one block, put
-         x_bar_n in slot 0, multiply every sub-filter spectrum with its FDL
-         slot and accumulate (Eq. 6; the frequency-domain delay replaces the
-         time-domain delta of Eq. 6 because n_k = n_x);
-      3. output transformation: C2R IFFT of the accumulated spectrum (1/n_f
+      1. ``transform_input``: left-shift the n_f-sample sliding window by n_x,
+         append x_n, R2C FFT -> x_bar_n (n_f/2 + 1 bins);
+      2. ``accumulate``: shift the FDL up by one block, put x_bar_n in slot 0,
+         multiply every sub-filter spectrum with its FDL slot and accumulate
+         (Eq. 6; the frequency-domain delay replaces the time-domain delta of
+         Eq. 6 because n_k = n_x);
+      3. ``transform_output``: C2R IFFT of the accumulated spectrum (1/n_f
          scaling) and keep the last n_x samples (overlap-save).
     Returns float64 [L][n_x].
     """
 
-    def __init__(self, h: np.ndarray, B: int):
+    def __init__(self, h: np.ndarray, B: int, n_f: int | None = None):
         h = np.asarray(h, dtype=np.float64)
         if h.ndim != 3:
             raise ValueError("h must be [L][Q][n_h]")
         self.L, self.Q, self.n_h = h.shape
         self.B = int(B)
-        self.n_f = 2 * self.B
+        self.n_f = 2 * self.B if n_f is None else int(n_f)
+        if self.n_f < 2 * self.B:
+            raise ValueError("overlap-save with n_x-tap sub-filters needs n_f >= 2 n_x")
+        self.bins = self.n_f // 2 + 1
         self.K = num_partitions(self.n_h, self.B)
         padded = np.zeros((self.L, self.Q, self.K * self.B))
         padded[:, :, : self.n_h] = h
         sub = padded.reshape(self.L, self.Q, self.K, self.B)
-        # zero-pad each sub-filter by n_x and take the n_f-point R2C FFT
-        self.h_bar = np.fft.rfft(sub, n=self.n_f, axis=-1)  # [L][Q][K][B+1]
+        # zero-pad each sub-filter to n_f and take the n_f-point R2C FFT
+        self.h_bar = np.fft.rfft(sub, n=self.n_f, axis=-1)  # [L][Q][K][bins]
         self.reset()
 
     def reset(self) -> None:
         self.window = np.zeros((self.Q, self.n_f))
-        self.fdl = np.zeros((self.K, self.Q, self.B + 1), dtype=np.complex128)
+        self.fdl = np.zeros((self.K, self.Q, self.bins), dtype=np.complex128)
 
-    def process_block(self, x_n: np.ndarray) -> np.ndarray:
+    def transform_input(self, x_n: np.ndarray) -> np.ndarray:
+        """Stage 1: input packing (left shift by n_x, append) and R2C FFT."""
         x_n = np.asarray(x_n, dtype=np.float64).reshape(self.Q, self.B)
-        # stage 1: input packing (left shift by n_x, append) and R2C FFT
-        self.window[:, : self.B] = self.window[:, self.B :]
-        self.window[:, self.B :] = x_n
-        x_bar = np.fft.rfft(self.window, axis=-1)  # [Q][B+1]
-        # stage 2: FDL shifted up by one block; newest spectrum in slot 0
+        self.window[:, : self.n_f - self.B] = self.window[:, self.B :].copy()
+        self.window[:, self.n_f - self.B :] = x_n
+        return np.fft.rfft(self.window, axis=-1)  # [Q][bins]
+
+    def accumulate(self, x_bar: np.ndarray) -> np.ndarray:
+        """Stage 2: the FDL shifted up by one block, the newest spectrum in
+        slot 0, and the sum over sub-filters and inputs.  Returns [L][bins]."""
         self.fdl[1:] = self.fdl[:-1].copy()
         self.fdl[0] = x_bar
-        acc = np.zeros((self.L, self.B + 1), dtype=np.complex128)
+        acc = np.zeros((self.L, self.bins), dtype=np.complex128)
         for k in range(self.K):
             # sub-filter k meets the spectrum from k blocks ago, summed over q
             acc += (self.h_bar[:, :, k, :] * self.fdl[k][None, :, :]).sum(axis=1)
-        # stage 3: C2R IFFT (1/n_f) and overlap-save: keep the last n_x samples
+        return acc
+
+    def transform_output(self, acc: np.ndarray) -> np.ndarray:
+        """Stage 3: C2R IFFT (1/n_f) and overlap-save: the last n_x samples."""
         y = np.fft.irfft(acc, n=self.n_f, axis=-1)
-        return y[:, self.B :]
+        return y[:, self.n_f - self.B :]
+
+    def process_block(self, x_n: np.ndarray) -> np.ndarray:
+        return self.transform_output(self.accumulate(self.transform_input(x_n)))
 
 
 def upols(h: np.ndarray, x: np.ndarray, B: int, n_blocks: int | None = None) -> np.ndarray:
@@ -216,6 +234,63 @@ def afc_closed_loop(
         e_n = m_n - c_prev
         l_n = synth.process_block(e_n)
         c_prev = canceller.process_block(l_n)
+        fb_prev = room.process_block(l_n)
+        l_out[:, sl] = l_n
+        e_out[:, sl] = e_n
+        m_out[:, sl] = m_n
+    return l_out, e_out, m_out
+
+
+def afc_closed_loop_reuse(
+    h: np.ndarray,
+    f_true: np.ndarray,
+    f_hat: np.ndarray,
+    s: np.ndarray,
+    B: int,
+    n_blocks: int | None = None,
+):
+    """The closed loop of ``afc_closed_loop`` with the synthesis output
+    spectra fed straight into the canceller (the remark closing Sec. 5).
+
+    Synthesis and canceller both use n_f = 3 n_x.  The synthesis accumulated
+    spectrum Y_n is the spectrum of a 3 n_x window whose first n_x samples
+    are wrap-around and whose last 2 n_x samples are [l_{n-1}, l_n]
+    (Sec. 4: with n_x-tap sub-filters, positions >= n_x - 1 of the circular
+    convolution are the linear one).  The canceller puts Y_n into its FDL in
+    place of the R2C transform of its own input window: its n_x-tap
+    sub-filters reach at most n_x - 1 samples back from the last n_x
+    positions, so its kept output never sees the wrap-around part.  Per block:
+      m_n, e_n            as in ``afc_closed_loop``
+      Y_n = synthesis stages 1 + 2 on e_n;   l_n = stage 3 of Y_n
+      C_n = canceller stage 2 on Y_n;        c_n = stage 3 of C_n
+    The room (the true paths F) is the plain n_f = 2 n_x convolution.
+    Returns (l [L][nb*B], e [P][nb*B], m [P][nb*B]), equal to
+    ``afc_closed_loop`` up to FP64 rounding.
+    """
+    synth = UpolsOracle(h, B, n_f=3 * B)
+    canceller = UpolsOracle(f_hat, B, n_f=3 * B)
+    room = UpolsOracle(f_true, B)
+    P = synth.Q
+    if canceller.L != P or room.L != P or canceller.Q != synth.L or room.Q != synth.L:
+        raise ValueError("shape mismatch between H_aur [L][P], F [P][L], F_hat [P][L]")
+    s = np.asarray(s, dtype=np.float64)
+    T = s.shape[1]
+    nb = -(-T // B) if n_blocks is None else int(n_blocks)
+    sp = np.zeros((P, nb * B))
+    n = min(T, nb * B)
+    sp[:, :n] = s[:, :n]
+    l_out = np.zeros((synth.L, nb * B))
+    e_out = np.zeros((P, nb * B))
+    m_out = np.zeros((P, nb * B))
+    fb_prev = np.zeros((P, B))
+    c_prev = np.zeros((P, B))
+    for b in range(nb):
+        sl = slice(b * B, (b + 1) * B)
+        m_n = sp[:, sl] + fb_prev
+        e_n = m_n - c_prev
+        Y = synth.accumulate(synth.transform_input(e_n))
+        l_n = synth.transform_output(Y)
+        c_prev = canceller.transform_output(canceller.accumulate(Y))
         fb_prev = room.process_block(l_n)
         l_out[:, sl] = l_n
         e_out[:, sl] = e_n
