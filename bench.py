@@ -79,11 +79,11 @@ def measured_peaks():
 
 def kernel_source_hash():
     """sha256 (first 16 hex digits) of the MAC's sources: kernels.cu,
-    device_util.cuh, kernels.h and the planner function plan_mac of engine.cu
-    (it fixes the launch configuration)."""
+    device_util.cuh, kernels.h, spectrum_store.cuh and the planner function
+    plan_mac of engine.cu (it fixes the launch configuration)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2509_04390_gb300", "csrc")
-    for name in ("kernels.cu", "device_util.cuh", "kernels.h"):
+    for name in ("kernels.cu", "device_util.cuh", "kernels.h", "spectrum_store.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     with open(os.path.join(csrc, "engine.cu"), "rb") as f:
@@ -184,7 +184,8 @@ def make_workload(args):
 def workload_name(args):
     if args.afc:
         nlms = "_nlms" if args.adapt > 0 else ""
-        return f"afc{nlms}_4x16_{args.taps}taps_fb{args.taps_fb}_B{args.block}_{args.precision}"
+        reuse = "_reuse_nf3" if args.reuse else ""
+        return f"afc{nlms}_4x16_{args.taps}taps_fb{args.taps_fb}_B{args.block}{reuse}_{args.precision}"
     far = f"_far{args.far_block}" if args.far_block else ""
     if args.far_block and args.far_block2:
         far += f"_far{args.far_block2}"
@@ -409,7 +410,7 @@ def run_ours(args):
     w = make_workload(args)
     B = w.block
     prec = args.precision
-    eng = U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, prec, far_block=args.far_block)
+    eng = U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, prec, far_block=args.far_block, reuse=args.reuse)
     far_h = U.conv_far_engine(eng.h) if args.far_block else None
     if far_h and args.far_block2:  # a third partition size: the far part's own far block
         U.conv_set_far_block(far_h, args.far_block2)
@@ -1056,7 +1057,7 @@ def run_extras(args):
         a.seconds = min(args.seconds, 4.0)
         a.e2e_steps, a.paced_blocks, a.no_cpu_baseline = 300, 0, True
         a.far_block = a.far_block2 = 0
-        a.afc, a.adapt, a.batch, a.group, a.serve = False, 0.0, 0, 0, False
+        a.afc, a.adapt, a.batch, a.group, a.serve, a.reuse = False, 0.0, 0, 0, False, False
         a.no_separate = False
         a.persistent = 0
         for k, v in kw.items():
@@ -1070,6 +1071,8 @@ def run_extras(args):
         ("paper_4x16_B256_bf16", run_ours, variant(precision="bf16")),
         ("afc_4x16_B256_fp32", run_ours, variant(afc=True)),
         ("afc_4x16_B256_fp16", run_ours, variant(afc=True, precision="fp16")),
+        ("afc_4x16_B256_fp32_reuse_nf3", run_ours, variant(afc=True, reuse=True)),
+        ("afc_4x16_B256_fp16_reuse_nf3", run_ours, variant(afc=True, reuse=True, precision="fp16")),
         ("group_8_sessions_B256_fp16", run_group, variant(group=8, precision="fp16")),
         ("batch_64_sessions_fp16", run_batch, variant(batch=64, precision="fp16", steps=min(steps, 200))),
         ("batch_64_sessions_fp16_persistent", run_batch,
@@ -1095,7 +1098,8 @@ def run_extras(args):
 
 
 ALL_EXTRAS = ("paper_4x16_B128_fp32,paper_4x16_B512_fp32,paper_4x16_B256_fp16,paper_4x16_B256_bf16,"
-              "afc_4x16_B256_fp32,afc_4x16_B256_fp16,group_8_sessions_B256_fp16,batch_64_sessions_fp16,"
+              "afc_4x16_B256_fp32,afc_4x16_B256_fp16,afc_4x16_B256_fp32_reuse_nf3,afc_4x16_B256_fp16_reuse_nf3,"
+              "group_8_sessions_B256_fp16,batch_64_sessions_fp16,"
               "batch_64_sessions_fp16_persistent,batch_64_sessions_fp16_persistent_graph,serving,"
               "paper_4x16_B256_fp32_tuned,paper_4x16_B256_fp16_tuned")
 
@@ -1113,6 +1117,8 @@ def parse(argv=None):
     ap.add_argument("--afc", action="store_true", help="synthesis + feedback canceller (paths [4][16], 0.5 s)")
     ap.add_argument("--taps-fb", type=int, default=24000)
     ap.add_argument("--adapt", type=float, default=0.0, help="with --afc: NLMS step size of the adaptive canceller")
+    ap.add_argument("--reuse", action="store_true",
+                    help="with --afc: the n_f = 3 n_x form, the synthesis output spectra feeding the canceller")
     ap.add_argument("--far-block", type=int, default=0,
                     help="non-uniform partitioning: taps beyond this many samples in partitions of this size")
     ap.add_argument("--far-block2", type=int, default=0,

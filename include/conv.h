@@ -76,6 +76,8 @@ typedef struct conv_info {
     long long far_block;      /* far block of non-uniform partitioning, 0 if none */
     long long K_far;          /* partitions of the far part                       */
     long long mac_far_bytes;  /* far tail MAC (once per far block), 0 if none    */
+    long long fft_size;       /* n_f: 2 * block, or 3 * block in the spectrum-reuse
+                                 form (afc_set_spectrum_reuse)                   */
 } conv_info;
 
 /* Per-session counters (conv_get_stats).  Latency is the wall time of a
@@ -111,6 +113,22 @@ conv_engine* conv_create(double fs, int block, int n_in, int n_out, long long ta
  * bytes the FDL MAC streams (each stored value is scaled by a power of two per
  * output tile and partition, or per delay-line slot, so scaling is exact). */
 int conv_set_precision(conv_engine* e, int mode);
+
+/* Spectrum-reuse form of the closed loop (the remark closing Sec. 5): on = 1
+ * switches both convolutions to the FFT size n_f = 3 n_x, so that the
+ * synthesis output spectrum, which then holds the last two output blocks
+ * without wrap-around, enters the canceller's delay line as it is, and the
+ * canceller's C_out input R2C transforms are saved.  Every spectrum of both
+ * convolutions then has 3 n_x / 2 packed bins (1.5x the bytes each FDL MAC
+ * streams).  The results equal those of the n_f = 2 n_x form up to rounding;
+ * conv_process_block works too (a plain convolution at n_f = 3 n_x).
+ * on = 0 returns to n_f = 2 n_x (the default).  Valid before conv_set_filters
+ * and afc_set_paths (CONV_E_STATE afterwards); CONV_E_INVAL for block < 32;
+ * CONV_E_STATE with a far block (conv_set_far_block), an adaptive canceller
+ * (afc_set_adaptation with mu > 0) or while the session is in a batch, none
+ * of which is combined with this form.  Re-allocates the synthesis spectra
+ * and resets the engine's state. */
+int afc_set_spectrum_reuse(conv_engine* e, int on);
 
 /* FDL MAC kernels (conv_tiling.kernel) */
 #define CONV_KERNEL_AUTO 0    /* planner's choice                                        */
@@ -158,8 +176,8 @@ int conv_set_filters(conv_engine* e, const float* h);
  * latency).  The filter spectra streamed per output block drop from all
  * partitions to F + (taps - F) * block / F taps' worth.  0 turns it off.
  * Must come before conv_set_filters / afc_set_paths (CONV_E_STATE).  taps
- * must exceed F (CONV_E_INVAL).  Not combined with afc_set_adaptation or
- * batches (CONV_E_STATE).  With the feedback canceller, the far part filters
+ * must exceed F (CONV_E_INVAL).  Not combined with afc_set_adaptation,
+ * afc_set_spectrum_reuse or batches (CONV_E_STATE).  With the feedback canceller, the far part filters
  * the error signal e, like the near part. */
 int conv_set_far_block(conv_engine* e, int far_block);
 
@@ -256,7 +274,8 @@ int afc_set_guard(conv_engine* e, double max_rms);
  *
  * mu in [0, 2), lambda in [0, 1), delta >= 0 finite (> 0 when mu > 0), else
  * CONV_E_INVAL.  CONV_E_STATE without afc_set_paths, for FP16/BF16 engines
- * (the update needs FP32 spectra), or while the session is in a batch.
+ * (the update needs FP32 spectra), in the spectrum-reuse form (mu > 0), or
+ * while the session is in a batch.
  * Waits for the engine's queued work.  Takes effect from the next block.
  * While adaptation is on, the conv_process_* calls (synthesis only) return
  * CONV_E_STATE: every block must pass through the canceller. */
@@ -267,8 +286,8 @@ int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta);
  * (re, im) float pairs: 2 * n_in * n_out * K_fb * block floats, owned by the
  * caller.  Bin 0 holds (DC, Nyquist).  The values are 2B-point R2C
  * spectra of the zero-padded sub-filters, unscaled (Sec. 4 initialisation).
- * Waits for the engine's queued work.  CONV_E_STATE without afc_set_paths or
- * for FP16/BF16 engines. */
+ * Waits for the engine's queued work.  CONV_E_STATE without afc_set_paths,
+ * for FP16/BF16 engines, or in the spectrum-reuse form. */
 int afc_get_path_spectra(conv_engine* e, float* f_spec);
 
 /* Zero the delay lines, sliding windows and the pending feedback prediction
@@ -386,7 +405,9 @@ typedef struct conv_batch conv_batch;
 conv_batch* conv_batch_create(int precision);
 
 /* Add a session (filters set; feedback paths, if allocated, set too).  Waits
- * for the session's own outstanding work and the batch's. */
+ * for the session's own outstanding work and the batch's.  Sessions with a far
+ * block, an adaptive canceller or in the spectrum-reuse form are not batched
+ * (CONV_E_STATE). */
 int conv_batch_add(conv_batch* b, conv_engine* e);
 
 /* Remove a session; it can be processed on its own again afterwards. */

@@ -19,7 +19,7 @@ LIBDIR = os.path.join(PKG, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIBNAME = "libgb300conv.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "engine.cu", "noalloc.cu", "nlms.cu", "group.cu", "group_engine.cu"]
+SOURCES = ["kernels.cu", "engine.cu", "noalloc.cu", "nlms.cu", "group.cu", "group_engine.cu", "reuse.cu"]
 
 
 def nvcc_path() -> str:

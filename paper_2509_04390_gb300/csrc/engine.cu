@@ -374,8 +374,8 @@ struct Part {
     bool ready = false;
 };
 
-size_t part_bytes(const MacPlan& p, int prec) {
-    size_t b = p.h_bytes + p.x_bytes + 2 * p.partial_bytes + (size_t)p.n_src * p.B * sizeof(float);
+size_t part_bytes(const MacPlan& p, int prec, size_t win_floats) {
+    size_t b = p.h_bytes + p.x_bytes + 2 * p.partial_bytes + win_floats * sizeof(float);
     if (prec != PREC_FP32) b += ((size_t)p.n_lt * p.R + (size_t)p.R + 8) * sizeof(float);
     return b;
 }
@@ -402,6 +402,11 @@ struct conv_engine {
     bool has_last = false;
     float2* tw = nullptr;
     float2* tw_lo = nullptr;  // tw's residuals W_2B^j - tw[j] (float-float FFT of the NLMS step)
+    // n_f = 3 n_x form (afc_set_spectrum_reuse): every spectrum has 3B/2 bins,
+    // the synthesis keeps two blocks of history, and its output spectrum is
+    // pushed into the canceller's delay line as it is; tw3[j] = W_3B^j
+    bool reuse = false;
+    float2* tw3 = nullptr;
     float *d_e = nullptr, *d_c = nullptr;
     float *h_in = nullptr, *h_out = nullptr, *h_e = nullptr;
     float *m_in = nullptr, *m_out = nullptr;  // device addresses of h_in / h_out (mapped pinned memory)
@@ -500,6 +505,26 @@ int check_fits(size_t need) {
     return CONV_OK;
 }
 
+// Packed bins per spectrum row (n_f / 2) and history samples per channel of
+// the input window (n_f - n_x): n_f = 2 n_x, or 3 n_x in the reuse form.
+inline int bins_of(const conv_engine* e) { return e->reuse ? 3 * (e->B / 2) : e->B; }
+inline int hist_of(const conv_engine* e) { return e->reuse ? 2 * e->B : e->B; }
+
+// Bin tile of the reuse form (3B/2 bins, not a power of two) when none is
+// given: the planner's rule, rounded down to a power of two dividing the bins.
+TileOverride reuse_tiling(const conv_engine* e, const TileOverride& o, int n_dst) {
+    TileOverride r = o;
+    if (!e->reuse || o.bin_tile) return r;
+    const int bins = bins_of(e);
+    const int LT = std::min(n_dst, 16), n_lt = (n_dst + LT - 1) / LT;
+    int n_kt = 1;
+    while (n_kt * 2 <= std::max(1, e->num_sms / (16 * n_lt))) n_kt *= 2;
+    int bt = (int)pow2_floor((size_t)std::max(1, bins / n_kt));
+    while (bt > 16 && bins % bt) bt /= 2;
+    r.bin_tile = std::max(16, std::min(256, bt));
+    return r;
+}
+
 int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps,
                const TileOverride& o = TileOverride()) {
     part_free(e, P);
@@ -510,11 +535,11 @@ int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps,
     if (K <= 0 || (long long)n_src * K > 0x7fffffffLL / 2)
         return set_err(CONV_E_INVAL, "taps %lld gives too many partitions", taps);
     P.K = (int)K;
-    P.plan = plan_mac(e->prec, e->B, n_src, n_dst, P.K, e->num_sms, n_src, o);
+    P.plan = plan_mac(e->prec, bins_of(e), n_src, n_dst, P.K, e->num_sms, n_src, reuse_tiling(e, o, n_dst));
     const MacPlan& p = P.plan;
     std::string why;
     if (check_plan(p, &why)) return set_err(CONV_E_INVAL, "%s", why.c_str());
-    int rc = check_fits(part_bytes(p, e->prec));
+    int rc = check_fits(part_bytes(p, e->prec, (size_t)n_src * hist_of(e)));
     if (rc) return rc;
     P.allocated = true;  // partial allocations are released by part_free
     if ((rc = dev_alloc(e, &P.H, p.h_bytes))) return rc;
@@ -524,7 +549,7 @@ int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps,
     if (!P.ev_packed) CK(cudaEventCreateWithFlags(&P.ev_packed, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i)
         if (!P.ev_tail[i]) CK(cudaEventCreateWithFlags(&P.ev_tail[i], cudaEventDisableTiming));
-    if ((rc = dev_alloc(e, &P.win, (size_t)n_src * e->B * sizeof(float)))) return rc;
+    if ((rc = dev_alloc(e, &P.win, (size_t)n_src * hist_of(e) * sizeof(float)))) return rc;
     if (e->prec != PREC_FP32) {
         // +4 floats: scale runs are read widened to 16-byte boundaries
         if ((rc = dev_alloc(e, &P.sH, ((size_t)p.n_lt * p.R + 4) * sizeof(float)))) return rc;
@@ -538,7 +563,7 @@ int part_alloc(conv_engine* e, Part& P, int n_src, int n_dst, long long taps,
 int part_reset(conv_engine* e, Part& P) {
     if (!P.allocated) return CONV_OK;
     CK(cudaMemsetAsync(P.X, 0, P.plan.x_bytes, e->stream));
-    CK(cudaMemsetAsync(P.win, 0, (size_t)P.n_src * e->B * sizeof(float), e->stream));
+    CK(cudaMemsetAsync(P.win, 0, (size_t)P.n_src * hist_of(e) * sizeof(float), e->stream));
     if (P.sX) CK(cudaMemsetAsync(P.sX, 0, ((size_t)P.plan.R + 4) * sizeof(float), e->stream));
     CK(cudaMemsetAsync(P.partial[0], 0, P.plan.partial_bytes, e->stream));
     CK(cudaMemsetAsync(P.partial[1], 0, P.plan.partial_bytes, e->stream));
@@ -574,16 +599,19 @@ int part_set_filters(conv_engine* e, Part& P, const float* h) {
     a.sH = P.sH;
     a.maxabs = d_max;
     a.tile_elems = P.plan.tile_elems;
-    a.tw = e->tw;
+    a.tw = e->reuse ? e->tw3 : e->tw;
+    auto launch = [&](const FilterArgs& fa) {
+        return e->reuse ? launch_filter3(e->prec, fa, e->stream) : launch_filter_r2c(e->prec, fa, e->stream);
+    };
     if (e->prec != PREC_FP32) {
         // pass 0: per-sub-filter maxima; one scale per (output tile, r); pass 1: store
         a.pass = 0;
-        if (r == cudaSuccess) r = launch_filter_r2c(e->prec, a, e->stream);
+        if (r == cudaSuccess) r = launch(a);
         if (r == cudaSuccess)
             r = launch_tile_scales(e->prec, d_max, P.sH, P.n_dst, P.plan.R, P.plan.LT, e->stream);
     }
     a.pass = 1;
-    if (r == cudaSuccess) r = launch_filter_r2c(e->prec, a, e->stream);
+    if (r == cudaSuccess) r = launch(a);
     if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
     dev_free(e, &d_h, bytes);
     if (d_max) dev_free(e, &d_max, mbytes);
@@ -616,7 +644,7 @@ PackArgs pack_args(conv_engine* e, Part& P, long long blk, const float* src, int
     a.n_ch = P.n_src;
     a.K = P.K;
     a.slot = slot0_for(blk, P.K);
-    a.tw = e->tw;
+    a.tw = e->reuse ? e->tw3 : e->tw;
     return a;
 }
 
@@ -667,7 +695,7 @@ OutArgs out_args(conv_engine* e, Part& P, long long blk, float* out) {
     a.n_dst = P.n_dst;
     a.B = e->B;
     a.log2B = e->log2B;
-    a.tw = e->tw;
+    a.tw = e->reuse ? e->tw3 : e->tw;
     a.out = out;
     a.out_stride = (&P == &e->syn && e->io_out_stride) ? e->io_out_stride : e->B;
     a.head = 1;
@@ -687,13 +715,14 @@ OutArgs out_args(conv_engine* e, Part& P, long long blk, float* out) {
         a.extra_stride = e->addend_stride;
     }
     a.early_partials = 1;  // every schedule waits for the tail's event before the output launch
-    a.head_pre = out_head_smem(P.n_src, e->B) > 0 ? 1 : 0;
+    a.head_pre = (!e->reuse && out_head_smem(P.n_src, e->B) > 0) ? 1 : 0;
     return a;
 }
 
 int enqueue_pack(conv_engine* e, Part& P, const float* src, int stride, const float* sub, float* e_out,
                  cudaStream_t s) {
-    CK(launch_pack_r2c(e->prec, pack_args(e, P, e->nblk, src, stride, sub, e_out), s));
+    const PackArgs a = pack_args(e, P, e->nblk, src, stride, sub, e_out);
+    CK(e->reuse ? launch_pack3(e->prec, a, s) : launch_pack_r2c(e->prec, a, s));
     return CONV_OK;
 }
 
@@ -714,7 +743,8 @@ int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool ti
 
 // Output of block `blk`: head (partition 0) + tail partials + C2R + OLS.
 int enqueue_out(conv_engine* e, Part& P, long long blk, float* out, cudaStream_t s) {
-    CK(launch_out_c2r(e->prec, out_args(e, P, blk, out), s));
+    const OutArgs a = out_args(e, P, blk, out);
+    CK(e->reuse ? launch_out3(e->prec, a, PackArgs{}, s) : launch_out_c2r(e->prec, a, s));
     return CONV_OK;
 }
 
@@ -1040,7 +1070,10 @@ int enqueue_afc_synthesis(conv_engine* e, const float* d_mic, float* d_out, floa
         CK(cudaStreamWaitEvent(s, e->ev_corr, 0));
         if (F.K == 1) CK(cudaStreamWaitEvent(s, e->ev_prep, 0));
     }
-    CK(launch_out_push(e->prec, out_args(e, P, n, d_out), pa, s));
+    // n_f = 3 n_x: the synthesis output spectrum itself goes into the
+    // canceller's ring; else the output samples are packed and transformed
+    CK(e->reuse ? launch_out3(e->prec, out_args(e, P, n, d_out), pa, s)
+                : launch_out_push(e->prec, out_args(e, P, n, d_out), pa, s));
     CK(cudaEventRecord(F.ev_packed, s));
     cudaStream_t bg = e->bg[(n + 1) & 1];
     CK(cudaStreamWaitEvent(bg, P.ev_packed, 0));
@@ -1067,7 +1100,7 @@ int enqueue_afc_prediction(conv_engine* e, cudaStream_t s) {
         oa.corr_A2 = A_of(e, n, 2, 8);
         oa.corr_C = F.K >= 2 ? 1 : 0;
     }
-    CK(launch_out_c2r(e->prec, oa, s));
+    CK(e->reuse ? launch_out3(e->prec, oa, PackArgs{}, s) : launch_out_c2r(e->prec, oa, s));
     if (!e->adapt) {
         cudaStream_t bg = e->bg[2 + ((n + 1) & 1)];
         CK(cudaStreamWaitEvent(bg, F.ev_packed, 0));
@@ -1117,6 +1150,7 @@ void engine_free(conv_engine* e) {
     part_free(e, e->fb);
     dev_free(e, &e->tw, 0);
     dev_free(e, &e->tw_lo, 0);
+    dev_free(e, &e->tw3, 0);
     dev_free(e, &e->d_e, 0);
     dev_free(e, &e->d_c, 0);
     dev_free(e, &e->d_pow, 0);
@@ -1234,6 +1268,42 @@ int conv_set_precision(conv_engine* e, int mode) {
     return engine_reset(e);
 }
 
+int afc_set_spectrum_reuse(conv_engine* e, int on) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    if (on != 0 && on != 1) return set_err(CONV_E_INVAL, "on must be 0 or 1");
+    if (e->syn.ready || e->fb.allocated)
+        return set_err(CONV_E_STATE, "the FFT size must be set before conv_set_filters / afc_set_paths");
+    if (on && e->B < 32) return set_err(CONV_E_INVAL, "the n_f = 3 n_x form needs block >= 32 (block %d)", e->B);
+    if (on && e->far) return set_err(CONV_E_STATE, "a far block is not combined with the n_f = 3 n_x form");
+    if (on && e->adapt) return set_err(CONV_E_STATE, "the adaptive canceller is not combined with the n_f = 3 n_x form");
+    if (e->in_batches > 0) return set_err(CONV_E_STATE, "session is in a batch");
+    if ((on != 0) == e->reuse) return CONV_OK;
+    DeviceGuard g(e->dev);
+    int rc;
+    if (on && !e->tw3) {
+        CK(prepare_reuse_kernels());
+        // twiddles W_3B^j = exp(-2 pi i j / 3B), FP64 on the host, rounded once to FP32
+        const int n = 3 * e->B;
+        std::vector<float2> tw(n);
+        const double pi = 3.14159265358979323846264338327950288;
+        for (int j = 0; j < n; ++j) {
+            const double ang = -2.0 * pi * (double)j / (double)n;
+            tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+        if ((rc = dev_alloc(e, &e->tw3, tw.size() * sizeof(float2)))) return rc;
+        CK(cudaMemcpy(e->tw3, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    e->reuse = on != 0;
+    if ((rc = part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling))) {
+        const std::string msg = g_err;
+        e->reuse = !e->reuse;
+        if (part_alloc(e, e->syn, e->n_in, e->n_out, e->taps, e->tiling) == CONV_OK) engine_reset(e);
+        g_err = msg;
+        return rc;
+    }
+    return engine_reset(e);
+}
+
 int conv_set_tiling(conv_engine* e, const conv_tiling* t) {
     if (!e) return set_err(CONV_E_INVAL, "null handle");
     if (e->syn.ready || e->fb.allocated)
@@ -1284,6 +1354,7 @@ int conv_set_far_block(conv_engine* e, int far_block) {
             return set_err(CONV_E_INVAL, "far block %d must be 0 or a power of two in (block, 4096]", far_block);
         if (e->taps_total <= far_block)
             return set_err(CONV_E_INVAL, "taps %lld must exceed the far block %d", e->taps_total, far_block);
+        if (e->reuse) return set_err(CONV_E_STATE, "a far block is not combined with the n_f = 3 n_x form");
     }
     DeviceGuard g(e->dev);
     if (e->far) {
@@ -1328,11 +1399,12 @@ conv_engine* conv_far_engine(conv_engine* e) { return e ? e->far : nullptr; }
 void plan_syn_beside_canceller(conv_engine* e) {
     Part& P = e->syn;
     if (!P.allocated || e->tiling.splits != 0) return;
-    const MacPlan full = plan_mac(e->prec, e->B, P.n_src, P.n_dst, P.K, e->num_sms, P.n_src, e->tiling);
+    const TileOverride base = reuse_tiling(e, e->tiling, P.n_dst);
+    const MacPlan full = plan_mac(e->prec, bins_of(e), P.n_src, P.n_dst, P.K, e->num_sms, P.n_src, base);
     if (full.S < 3) return;
-    TileOverride o = e->tiling;
+    TileOverride o = base;
     o.splits = (2 * full.S) / 3;
-    MacPlan q = plan_mac(e->prec, e->B, P.n_src, P.n_dst, P.K, e->num_sms, P.n_src, o);
+    MacPlan q = plan_mac(e->prec, bins_of(e), P.n_src, P.n_dst, P.K, e->num_sms, P.n_src, o);
     if (q.h_bytes != P.plan.h_bytes || q.x_bytes != P.plan.x_bytes || q.tile_elems != P.plan.tile_elems ||
         q.partial_bytes > P.plan.partial_bytes)
         return;
@@ -1349,9 +1421,9 @@ void plan_fb_beside_synthesis(conv_engine* e) {
     Part& F = e->fb;
     e->fb_S_full = F.plan.S;
     if (!F.allocated || F.plan.S <= 2) return;
-    TileOverride o;
+    TileOverride o = reuse_tiling(e, TileOverride(), F.n_dst);
     o.splits = 2;
-    MacPlan q = plan_mac(e->prec, e->B, F.n_src, F.n_dst, F.K, e->num_sms, F.n_src, o);
+    MacPlan q = plan_mac(e->prec, bins_of(e), F.n_src, F.n_dst, F.K, e->num_sms, F.n_src, o);
     if (q.h_bytes != F.plan.h_bytes || q.x_bytes != F.plan.x_bytes || q.tile_elems != F.plan.tile_elems ||
         q.partial_bytes > F.plan.partial_bytes)
         return;
@@ -1503,6 +1575,8 @@ int afc_set_adaptation(conv_engine* e, double mu, double lambda, double delta) {
     if (!e->fb.ready) return set_err(CONV_E_STATE, "feedback paths not set");
     if (e->prec != CONV_FP32) return set_err(CONV_E_STATE, "the adaptive canceller needs FP32 spectra");
     if (e->far) return set_err(CONV_E_STATE, "the adaptive canceller is not combined with a far block");
+    if (e->reuse && mu > 0.0)
+        return set_err(CONV_E_STATE, "the adaptive canceller is not combined with the n_f = 3 n_x form");
     if (e->in_batches > 0) return set_err(CONV_E_STATE, "session is in a batch");
     DeviceGuard g(e->dev);
     int rc;
@@ -1563,6 +1637,7 @@ int afc_get_path_spectra(conv_engine* e, float* f_spec) {
     if (!e || !f_spec) return set_err(CONV_E_INVAL, "null argument");
     if (!e->fb.ready) return set_err(CONV_E_STATE, "feedback paths not set");
     if (e->prec != CONV_FP32) return set_err(CONV_E_STATE, "path spectra are read back from FP32 engines only");
+    if (e->reuse) return set_err(CONV_E_STATE, "path spectra are read back in the n_f = 2 n_x form only");
     DeviceGuard g(e->dev);
     if (e->has_last) CK(cudaStreamSynchronize(e->last_stream));
     for (int i = 0; i < 4; ++i) CK(cudaStreamSynchronize(e->bg[i]));
@@ -1678,6 +1753,7 @@ int conv_get_info(const conv_engine* e, conv_info* out) {
     out->far_block = e->far_B;
     out->K_far = e->far ? e->far->syn.K : 0;
     out->mac_far_bytes = e->far ? tail_bytes(e->far->syn.plan) : 0;
+    out->fft_size = e->reuse ? 3LL * e->B : 2LL * e->B;
     return CONV_OK;
 }
 
@@ -1727,7 +1803,7 @@ long long conv_footprint(int precision, int block, int n_in, int n_out, long lon
         if ((long long)n_src * K > 0x7fffffffLL / 2) return -1;
         const MacPlan p = plan_mac(precision, block, n_src, n_dst, (int)K, num_sms, n_src);
         // part buffers: spectra, ring, two partial buffers, window, scales
-        return (long long)part_bytes(p, precision) + (long long)p.partial_bytes;
+        return (long long)part_bytes(p, precision, (size_t)n_src * block) + (long long)p.partial_bytes;
     };
     long long b = part(n_in, n_out, taps);
     if (b < 0) return set_err(CONV_E_INVAL, "too many partitions"), -1;
@@ -2003,6 +2079,7 @@ int conv_batch_add(conv_batch* b, conv_engine* e) {
         return set_err(CONV_E_INVAL, "batched sessions use the TMA MAC with 8 consumer warps");
     if (e->adapt) return set_err(CONV_E_STATE, "sessions with an adaptive canceller are not batched");
     if (e->far) return set_err(CONV_E_STATE, "sessions with a far block are not batched");
+    if (e->reuse) return set_err(CONV_E_STATE, "sessions in the n_f = 3 n_x form are not batched");
     for (conv_engine* x : b->sessions)
         if (x == e) return set_err(CONV_E_INVAL, "session already in the batch");
     DeviceGuard g(b->dev);

@@ -208,6 +208,17 @@ cudaError_t launch_mac_batch(int prec, const MacArgs* items, const BatchRef* ref
 // and [1 + i] counter i, all zero at launch.  err: device error word (a
 // bounded dependency wait that gave up).  smem: the larger of the MAC's and
 // the FFT kernels' dynamic shared memory.
+// The n_f = 3 n_x form (reuse.cu; block in [32, 4096]).  PackArgs.win holds
+// [n_ch][2 B]; the twiddle table (PackArgs / OutArgs / FilterArgs .tw) is
+// W_3B^j, j in [0, 3B); every spectrum row has 3B/2 packed bins and the MAC
+// is planned over them.  launch_out3 pushes each output channel's
+// accumulated spectrum into push's ring when push.X is set (push.n_ch =
+// a.n_dst).
+size_t fft3_smem_bytes(int B);
+cudaError_t prepare_reuse_kernels();
+cudaError_t launch_pack3(int prec, const PackArgs& a, cudaStream_t s);
+cudaError_t launch_filter3(int prec, const FilterArgs& a, cudaStream_t s);
+cudaError_t launch_out3(int prec, const OutArgs& a, const PackArgs& push, cudaStream_t s);
 cudaError_t launch_batch_persistent(int prec, const PackArgs* pk, const OutArgs* ot, const MacArgs* mc,
                                     const PersistentWork* work, int n_work, unsigned* ctr, int* err, int ctas,
                                     size_t smem, cudaStream_t s);

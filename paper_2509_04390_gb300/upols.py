@@ -86,6 +86,7 @@ class conv_info(ctypes.Structure):
             "far_block",
             "K_far",
             "mac_far_bytes",
+            "fft_size",
         )
     ]
 
@@ -155,6 +156,7 @@ def load():
     sig = {
         "conv_create": (vp, [d, i, i, i, ll]),
         "conv_set_precision": (i, [vp, i]),
+        "afc_set_spectrum_reuse": (i, [vp, i]),
         "conv_set_filters": (i, [vp, vp]),
         "conv_set_tiling": (i, [vp, ctypes.POINTER(conv_tiling)]),
         "afc_set_paths": (i, [vp, vp, ll]),
@@ -271,6 +273,10 @@ def conv_create(fs: float, block: int, n_in: int, n_out: int, taps: int):
 def conv_set_precision(h, mode):
     mode = PRECISIONS.get(mode, mode)
     return _check(load().conv_set_precision(h, int(mode)))
+
+
+def afc_set_spectrum_reuse(h, on: bool = True):
+    return _check(load().afc_set_spectrum_reuse(h, 1 if on else 0))
 
 
 def conv_set_far_block(h, far_block: int):
@@ -710,14 +716,19 @@ class Engine:
 
     ``tiling``: None (the planner's rule), a dict of ``conv_tiling`` fields, or
     "tuned": the autotuner's cached choice for this shape and GPU (the
-    planner's rule when the cache has none)."""
+    planner's rule when the cache has none, and in the spectrum-reuse form).
+    ``reuse``: the n_f = 3 n_x spectrum-reuse form (``afc_set_spectrum_reuse``)."""
 
-    def __init__(self, fs, block, n_in, n_out, taps, precision="fp32", tiling=None, far_block=0):
+    def __init__(self, fs, block, n_in, n_out, taps, precision="fp32", tiling=None, far_block=0, reuse=False):
         self.h = conv_create(fs, block, n_in, n_out, taps)
         self.shape = (int(n_in), int(n_out), int(block))
         try:
             if precision not in ("fp32", CONV_FP32):
                 conv_set_precision(self.h, precision)
+            if reuse:
+                afc_set_spectrum_reuse(self.h, True)
+                if tiling == "tuned":
+                    tiling = None
             if tiling == "tuned":
                 from . import autotune
 
