@@ -35,6 +35,11 @@ Readings of the paper taken here (the paper is silent or loose on these):
       therefore has a one-block acoustic/IO delay: m[t] = s[t] + (F*l)[t-B].
   R7  F_hat is known a priori and static (Sec. 1, Sec. 3.1); no adaptation.
   R8  The pre-processor G is the identity, so Q = P.
+  R15 The spectrum reuse of Sec. 5's closing remark (only its FFT size,
+      n_f = 3 n_x, and its cost are given): both convolutions at n_f = 3 n_x,
+      the synthesis accumulated spectrum entering the canceller's FDL in
+      place of the transform of the canceller's input window
+      (``afc_closed_loop_reuse``).
 
 Every function states the passage it follows.
 """
