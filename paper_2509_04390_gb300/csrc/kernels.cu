@@ -19,7 +19,8 @@
 namespace gbconv {
 
 static_assert(2 * MAX_STAGES * sizeof(uint64_t) + sizeof(int) <= MAC_ARGS_OFFSET, "mbarriers overlap the staged arguments");
-static_assert(MAC_ARGS_OFFSET + sizeof(MacArgs) <= MAC_HDR_BYTES, "staged MAC arguments exceed the header");
+static_assert(MAC_ARGS_OFFSET + sizeof(MacArgs) <= MAC_RED_OFFSET, "staged MAC arguments overlap the scale maxima");
+static_assert(MAC_RED_OFFSET + 16 * sizeof(float) <= MAC_HDR_BYTES, "scale maxima of 16 warps exceed the header");
 
 namespace {
 
@@ -149,6 +150,45 @@ __global__ void k_tile_scales(const float* __restrict__ maxabs, float* __restric
     sH[i] = block_scale<PREC>(mx);
 }
 
+// Reduced-precision MAC helpers.  d.x += a.lo * b.lo, d.y += a.hi * b.hi for
+// two 16-bit values packed in each word, with FP32 accumulation: the
+// mixed-precision FMA forms the exact product of the two 16-bit inputs, so
+// this equals converting both to FP32 and using an FP32 FMA, without the
+// conversions.
+template <int PREC>
+__device__ __forceinline__ void mfma2(float2& d, uint32_t a, uint32_t b) {
+    if constexpr (PREC == PREC_FP16)
+        asm("{.reg .f16 a0, a1, b0, b1;\n\tmov.b32 {a0, a1}, %2;\n\tmov.b32 {b0, b1}, %3;\n\t"
+            "fma.rn.f32.f16 %0, a0, b0, %0;\n\tfma.rn.f32.f16 %1, a1, b1, %1;}"
+            : "+f"(d.x), "+f"(d.y)
+            : "r"(a), "r"(b));
+    else
+        asm("{.reg .b16 a0, a1, b0, b1;\n\tmov.b32 {a0, a1}, %2;\n\tmov.b32 {b0, b1}, %3;\n\t"
+            "fma.rn.f32.bf16 %0, a0, b0, %0;\n\tfma.rn.f32.bf16 %1, a1, b1, %1;}"
+            : "+f"(d.x), "+f"(d.y)
+            : "r"(a), "r"(b));
+}
+// (v, v) in storage precision
+template <int PREC>
+__device__ __forceinline__ uint32_t splat2(float v) {
+    uint32_t r;
+    if constexpr (PREC == PREC_FP16)
+        asm("cvt.rn.f16x2.f32 %0, %1, %1;" : "=r"(r) : "f"(v));
+    else
+        asm("cvt.rn.bf16x2.f32 %0, %1, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
+// element-wise product of two packed pairs in storage precision
+template <int PREC>
+__device__ __forceinline__ uint32_t mul2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    if constexpr (PREC == PREC_FP16)
+        asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    else
+        asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
 // ----------------------------------------------------------- FDL MAC
 // Y[l][k] += sum_{r in split} H[l][r][k] * X[slot(r)][q(r)][k]   (Eq. 6 per bin)
 // over r in [r_begin, R), split into S contiguous ranges per tile.
@@ -165,7 +205,17 @@ __global__ void k_tile_scales(const float* __restrict__ maxabs, float* __restric
 //
 // Stages follow a global grid over r (stage g holds r in [g*RS, (g+1)*RS)),
 // and every filter tile starts on a 64 KiB boundary, so each filter copy is an
-// aligned, usually power-of-two-sized chunk of HBM; splits own whole stages.
+// aligned, usually power-of-two-sized chunk of HBM; a split owns an equal
+// range of r, cut along the grid (its first and last stage may be partial).
+//
+// Reduced precision: each stored row carries a power-of-two scale (one per
+// output tile and r for the filters, one per ring slot for the delay line).
+// The CTA first finds the largest product of the two over its rows, s_ref;
+// each row's delay-line chunk is multiplied by its own product over s_ref (a
+// power of two <= 1, in storage precision: exact unless the value falls below
+// the format's normal range, where it is then negligible beside the rows near
+// s_ref), the sums run in mixed-precision FMAs in units of s_ref, and the
+// sums are multiplied by s_ref at the end.
 template <int PREC, int LPT, int NW>
 __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const int split, unsigned char* smem) {
     using St = Store<PREC>;
@@ -322,6 +372,32 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[i][v] = make_float2(0.0f, 0.0f);
 
+    // reduced precision: s_ref over this CTA's rows (see above); dmask clears
+    // the low half (bin 0) of an operand pair in the thread holding DC/Nyquist
+    float sref = 1.0f, inv_ref = 1.0f;
+    uint32_t dmask = 0xffffffffu;
+    if constexpr (St::PLANAR) {
+        float m = 0.0f;
+        for (int r = row0 + tid; r < row1; r += NW * 32) {
+            int rr = ring0 + r;
+            if (rr >= R) rr -= R;
+            // plain load for the ring's scales: a persistent step writes them in the same launch
+            m = fmaxf(m, __ldg(a.sH + (size_t)lt * R + r) * a.sX[rr]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        float* sred = reinterpret_cast<float*>(smem + MAC_RED_OFFSET);
+        if (lane == 0) sred[warp] = m;
+        named_barrier_sync(2, NW * 32);
+        m = 0.0f;
+        for (int w = 0; w < NW; ++w) m = fmaxf(m, sred[w]);
+        if (m > 0.0f) {
+            sref = m;
+            inv_ref = 1.0f / m;  // exact: a power of two
+        }
+        if (dc) dmask = 0xffff0000u;
+    }
+
     bool ok = true;
     for (int it = 0; it < nit; ++it) {
         const int st = it % a.nstage;
@@ -397,12 +473,14 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
         } else {
             // Planar rows, 4 bins per thread as two pairs; acc[i] = (re 0-1, re 2-3,
             // im 0-1, im 2-3).  Per pair: re += hr*xr + hi*(-xi), im += hr*xi + hi*xr.
-            // Both scales are per reduction index and are folded into x once.  The
-            // packed bin 0 (DC, Nyquist) needs re += hr*xr and im += hi*xi: its lane
-            // of the operand pairs is set up for that here, outside the output loop.
+            // The packed bin 0 (DC, Nyquist) needs re += hr*xr and im += hi*xi: its
+            // lane of the operand pairs is set up for that once per row, outside the
+            // output loop.
             if (full) {
-                // Software-pipelined: the next row's 16-byte chunks (delay line and
-                // the LPT filter rows) load while this row's FMAs run.
+                // Whole output tiles (the usual case): mixed-precision FMAs on the
+                // stored pairs, in units of s_ref.  Software-pipelined: the next
+                // row's 16-byte chunks (delay line and the LPT filter rows) load
+                // while this row's FMAs run.
                 auto ld_row = [&](int jj, uint4& xo, uint4 (&ho)[LPT], float& sxo, float& sho) {
                     xo = lds128(sx + (size_t)jj * hrow + (size_t)kv * 16);
 #pragma unroll
@@ -417,46 +495,35 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
                 for (int i = 0; i < LPT; ++i) hw[i] = xw;
                 if (rl < nr) ld_row(rl, xw, hw, sxw, shw);
                 for (int j = rl; j < nr; j += a.NRL) {
-                    const uint4 xc = xw;
+                    const uint4 xc = xw;  // (re 0-1, re 2-3, im 0-1, im 2-3)
                     uint4 hc[LPT];
 #pragma unroll
                     for (int i = 0; i < LPT; ++i) hc[i] = hw[i];
-                    const float sc = sxw * shw;
+                    const float ratio = sxw * shw * inv_ref;
                     if (j + a.NRL < nr) ld_row(j + a.NRL, xw, hw, sxw, shw);
-                    float2 xr[2], xi[2];
-                    unpack_planar4<St>(xc, xr, xi);
-                    const float2 sc2 = make_float2(sc, sc), nsc2 = make_float2(-sc, -sc);
-                    float2 nxi0 = fmul2(xi[0], nsc2);  // -x_i by the negated scale
-                    const float2 nxi1 = fmul2(xi[1], nsc2);
-                    xr[0] = fmul2(xr[0], sc2);
-                    xr[1] = fmul2(xr[1], sc2);
-                    xi[0] = fmul2(xi[0], sc2);
-                    xi[1] = fmul2(xi[1], sc2);
-                    float2 xi0 = xi[0], xr0b = xr[0];
-                    if (dc) {
-                        nxi0.x = 0.0f;
-                        xi0.x = 0.0f;
-                        xr0b.x = xi[0].x;
-                    }
-                    float2 hr[LPT][2], hi[LPT][2];
-#pragma unroll
-                    for (int i = 0; i < LPT; ++i) unpack_planar4<St>(hc[i], hr[i], hi[i]);
+                    const uint32_t r2 = splat2<PREC>(ratio), nr2 = splat2<PREC>(-ratio);
+                    const uint32_t xr01 = mul2<PREC>(xc.x, r2), xr23 = mul2<PREC>(xc.y, r2);
+                    const uint32_t xi01 = mul2<PREC>(xc.z, r2), xi23 = mul2<PREC>(xc.w, r2);
+                    const uint32_t nxi01 = mul2<PREC>(xc.z, nr2) & dmask, nxi23 = mul2<PREC>(xc.w, nr2);
+                    const uint32_t xi01b = xi01 & dmask;                      // bin 0: im gets no hr*xi
+                    const uint32_t xr01b = (xr01 & dmask) | (xi01 & ~dmask);  // bin 0: im += hi*xi
 #pragma unroll
                     for (int i = 0; i < LPT; ++i) {
-                        acc[i][0] = ffma2(hr[i][0], xr[0], acc[i][0]);
-                        acc[i][1] = ffma2(hr[i][1], xr[1], acc[i][1]);
-                        acc[i][2] = ffma2(hr[i][0], xi0, acc[i][2]);
-                        acc[i][3] = ffma2(hr[i][1], xi[1], acc[i][3]);
+                        mfma2<PREC>(acc[i][0], hc[i].x, xr01);
+                        mfma2<PREC>(acc[i][1], hc[i].y, xr23);
+                        mfma2<PREC>(acc[i][2], hc[i].x, xi01b);
+                        mfma2<PREC>(acc[i][3], hc[i].y, xi23);
                     }
 #pragma unroll
                     for (int i = 0; i < LPT; ++i) {
-                        acc[i][0] = ffma2(hi[i][0], nxi0, acc[i][0]);
-                        acc[i][1] = ffma2(hi[i][1], nxi1, acc[i][1]);
-                        acc[i][2] = ffma2(hi[i][0], xr0b, acc[i][2]);
-                        acc[i][3] = ffma2(hi[i][1], xr[1], acc[i][3]);
+                        mfma2<PREC>(acc[i][0], hc[i].z, nxi01);
+                        mfma2<PREC>(acc[i][1], hc[i].w, nxi23);
+                        mfma2<PREC>(acc[i][2], hc[i].z, xr01b);
+                        mfma2<PREC>(acc[i][3], hc[i].w, xr23);
                     }
                 }
             } else
+            // ragged output tile: FP32 FMAs, both scales folded into x per row
             for (int j = rl; j < nr; j += a.NRL) {
                 float2 xr[2], xi[2];
                 load_planar4<St>(sx + (size_t)j * hrow, kv, a.BT, xr, xi);
@@ -500,6 +567,11 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
     }
 
     if constexpr (St::PLANAR) {
+        if (lg + (LPT - 1) * a.NLG < LTt)  // whole output tile: sums in units of s_ref
+#pragma unroll
+            for (int i = 0; i < LPT; ++i)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[i][v] = make_float2(acc[i][v].x * sref, acc[i][v].y * sref);
 #pragma unroll
         for (int i = 0; i < LPT; ++i) {
             const float2 re01 = acc[i][0], re23 = acc[i][1], im01 = acc[i][2], im23 = acc[i][3];
@@ -774,7 +846,7 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
                     cmac(t, h, x);
                 const float sc = PREC == PREC_FP32 ? 1.0f
                                                    : __ldg(a.sH + (size_t)(l / a.LT) * a.R + q) *
-                                                         __ldg(a.sX + (size_t)a.slot0 * a.n_src + q);
+                                                         a.sX[(size_t)a.slot0 * a.n_src + q];  // see k_batch_persistent
                 hd.x = fmaf(sc, t.x, hd.x);
                 hd.y = fmaf(sc, t.y, hd.y);
             }
@@ -847,7 +919,10 @@ constexpr int lpt_for() {
 // batched kernels, so the results are the same bit for bit.  An item that
 // needs others' results waits (bounded) for a counter they raise: one thread
 // acquires it, the CTA barrier passes the ordering on.  The writer side is a
-// CTA barrier, a device-scope fence and the counter increment.
+// CTA barrier, a device-scope fence and the counter increment.  Data written
+// within the launch (ring spectra and their scales, partials) is read with
+// ordinary (coherent) loads or bulk copies after a proxy fence, never through
+// the read-only (non-coherent) path.
 template <int PREC>
 __global__ void __launch_bounds__(9 * 32, 1) k_batch_persistent(const PackArgs* __restrict__ pk,
                                                                 const OutArgs* __restrict__ ot,

@@ -163,6 +163,8 @@ struct BatchRef {
 // The batched MAC stages its arguments in the shared-memory header after the
 // mbarriers and the abort flag.
 constexpr int MAC_ARGS_OFFSET = 256;
+// ... and keeps the reduced-precision MAC's per-warp scale maxima there.
+constexpr int MAC_RED_OFFSET = 768;
 
 // One work item of a persistent batch step (launch_batch_persistent).  The
 // CTAs claim items in list order; an item may wait for a counter that items
