@@ -187,9 +187,9 @@ MacPlan plan_mac(int prec, int B, int n_src, int n_dst, int K, int num_sms, int 
     p.sxoff = (unsigned)(p.soff + sh_part(p.RS));
     p.stage_bytes = (unsigned)stage_size(p.RS);
     const int fit = (int)std::max<size_t>(2, budget / p.stage_bytes);
-    // measured on the back-to-back step: FP32 streams best with two large
-    // stages; FP16/BF16 (more consumer work per byte) with three
-    p.nstage = std::min(prec == PREC_FP32 ? 2 : 3, fit);
+    // measured on the back-to-back step: two large stages for every precision
+    // (they leave room on each SM for the next block's pack and output CTAs)
+    p.nstage = std::min(2, fit);
     if (o.stages) p.nstage = std::max(2, std::min(o.stages, fit));
     // scratch for combining r-lanes reuses (and if needed extends) the stage ring
     const size_t red = (size_t)(p.NRL - 1) * p.LPT * p.NLG * p.BT * sizeof(float2);  // lane-major r-lane scratch
@@ -418,6 +418,8 @@ struct conv_engine {
     double guard = 0.0;
     bool prof = false;
     std::vector<cudaEvent_t> ev0, ev1;
+    void* flush_buf = nullptr;  // conv_profile_flush_l2: written before each timed tail
+    size_t flush_bytes = 0;
     size_t ev_used = 0;
     size_t dev_bytes = 0;
     // adaptive canceller (afc_set_adaptation)
@@ -732,6 +734,7 @@ int enqueue_tail(conv_engine* e, Part& P, long long blk, cudaStream_t s, bool ti
     const MacPlan& p = P.plan;
     if (p.S == 0) return CONV_OK;  // K = 1: no tail
     const bool rec = timed && e->prof && e->ev_used < e->ev0.size();
+    if (rec && e->flush_bytes) CK(cudaMemsetAsync(e->flush_buf, 0, e->flush_bytes, s));
     if (rec) CK(cudaEventRecord(e->ev0[e->ev_used], s));
     CK(launch_fdl_mac(e->prec, p, tail_args(e, P, blk), s, pdl));
     if (rec) {
@@ -1151,6 +1154,10 @@ void engine_free(conv_engine* e) {
     dev_free(e, &e->tw, 0);
     dev_free(e, &e->tw_lo, 0);
     dev_free(e, &e->tw3, 0);
+    if (e->flush_buf) {
+        cudaFree(e->flush_buf);
+        e->flush_buf = nullptr;
+    }
     dev_free(e, &e->d_e, 0);
     dev_free(e, &e->d_c, 0);
     dev_free(e, &e->d_pow, 0);
@@ -1772,6 +1779,25 @@ int conv_profile_enable(conv_engine* e, int enable) {
         }
     }
     e->ev_used = 0;
+    return CONV_OK;
+}
+
+int conv_profile_flush_l2(conv_engine* e, long long bytes) {
+    if (!e) return set_err(CONV_E_INVAL, "null handle");
+    if (bytes < 0) return set_err(CONV_E_INVAL, "bytes must be >= 0");
+    DeviceGuard g(e->dev);
+    if ((size_t)bytes > e->flush_bytes || bytes == 0) {
+        if (e->flush_buf) CK(cudaFree(e->flush_buf));
+        e->flush_buf = nullptr;
+        e->flush_bytes = 0;
+        if (bytes > 0) {
+            if (cudaMalloc(&e->flush_buf, (size_t)bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return set_err(CONV_E_NOMEM, "L2 flush buffer of %lld bytes", bytes);
+            }
+        }
+    }
+    e->flush_bytes = (size_t)bytes;
     return CONV_OK;
 }
 

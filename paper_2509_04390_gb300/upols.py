@@ -174,6 +174,7 @@ def load():
         "conv_synchronize": (i, [vp]),
         "conv_get_info": (i, [vp, ctypes.POINTER(conv_info)]),
         "conv_profile_enable": (i, [vp, i]),
+        "conv_profile_flush_l2": (i, [vp, ll]),
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "conv_plan_check": (i, [i, i, i, i, ll, i, ctypes.POINTER(conv_tiling)]),
         "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
@@ -367,6 +368,10 @@ def conv_get_info(h) -> dict:
     info = conv_info()
     _check(load().conv_get_info(h, ctypes.byref(info)))
     return info.as_dict()
+
+
+def conv_profile_flush_l2(h, nbytes: int):
+    return _check(load().conv_profile_flush_l2(h, int(nbytes)))
 
 
 def conv_profile_enable(h, enable: int):

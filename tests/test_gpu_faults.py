@@ -10,6 +10,8 @@
   feedback the canceller does not know makes the loop unstable; the call must
   return CONV_E_UNSTABLE and reset the loop state.
 * The per-session counters (``conv_get_stats``).
+* Kernel timing (``conv_profile_*``, with the L2 flush aid) leaves results
+  unchanged.
 """
 
 import os
@@ -31,8 +33,8 @@ def engine_lib():
     U.load()
 
 
-def fresh_run(w, nb):
-    with U.Engine(w.fs, w.block, w.n_in, w.n_out, w.taps) as e:
+def fresh_run(w, nb, precision="fp32"):
+    with U.Engine(w.fs, w.block, w.n_in, w.n_out, w.taps, precision) as e:
         e.set_filters(w.h)
         return e.run(w.x[:, : nb * w.block])
 
@@ -193,3 +195,26 @@ def test_join_async_leaves_results_unchanged():
         U.conv_synchronize(e.h)
     got = d_y.cpu().numpy().transpose(1, 0, 2).reshape(w.n_out, nb * B)
     np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_kernel_timing_with_l2_flush_leaves_results_unchanged(precision):
+    """conv_profile_enable with conv_profile_flush_l2: every block's tail MAC
+    is timed (one launch per block after the first), each preceded by the
+    scratch write; the outputs equal an untimed run bit for bit."""
+    w = signals.random_case(3105, 2, 5, 3000, 64, 20)
+    nb = 20
+    ref = fresh_run(w, nb, precision)
+    with U.Engine(w.fs, w.block, w.n_in, w.n_out, w.taps, precision) as e:
+        e.set_filters(w.h)
+        U.conv_profile_enable(e.h, nb + 4)
+        U.conv_profile_flush_l2(e.h, 8 << 20)
+        got = e.run(w.x[:, : nb * w.block])
+        ms, n = U.conv_profile_read(e.h)
+        U.conv_profile_flush_l2(e.h, 0)
+        U.conv_profile_enable(e.h, 0)
+        with pytest.raises(U.ConvError) as ei:
+            U.conv_profile_flush_l2(e.h, -1)
+        assert ei.value.code == U.CONV_E_INVAL
+    np.testing.assert_array_equal(got, ref)
+    assert n >= nb - 1 and ms > 0.0
