@@ -331,12 +331,13 @@ int conv_get_info(const conv_engine* e, conv_info* out);
 int conv_profile_enable(conv_engine* e, int enable);
 int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches);
 
-/* Profiling aid: while kernel timing is enabled, write `bytes` of a scratch
- * buffer (allocated here, owned by the handle) on the MAC's stream before
- * each timed MAC launch, outside its events, so that a working set smaller
- * than the L2 cache does not start the launch with its data still cached:
- * pass a few times the L2 size.  0 turns it off and frees the buffer.
- * CONV_E_NOMEM if the buffer cannot be allocated. */
+/* Profiling aid: while kernel timing is enabled, read `bytes` of a zeroed
+ * scratch buffer (allocated here, owned by the handle) on the MAC's stream
+ * before each timed MAC launch, outside its events, so that a working set
+ * smaller than the L2 cache does not start the launch with its data still
+ * cached (reading leaves clean lines: no write-back lands in the timed
+ * launch).  Pass a few times the L2 size.  0 turns it off and frees the
+ * buffer.  CONV_E_NOMEM if the buffer cannot be allocated. */
 int conv_profile_flush_l2(conv_engine* e, long long bytes);
 
 /* Host-only dry run of the kernel tiling the engine would choose for these

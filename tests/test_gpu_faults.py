@@ -201,7 +201,7 @@ def test_join_async_leaves_results_unchanged():
 def test_kernel_timing_with_l2_flush_leaves_results_unchanged(precision):
     """conv_profile_enable with conv_profile_flush_l2: every block's tail MAC
     is timed (one launch per block after the first), each preceded by the
-    scratch write; the outputs equal an untimed run bit for bit."""
+    scratch read; the outputs equal an untimed run bit for bit."""
     w = signals.random_case(3105, 2, 5, 3000, 64, 20)
     nb = 20
     ref = fresh_run(w, nb, precision)
