@@ -1026,11 +1026,16 @@ cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream
 
 }  // namespace
 
+// Every kernel of the engine asks for the largest shared-memory carveout, so an
+// SM that ran a pack or output CTA takes a MAC CTA without first changing its
+// L1/shared split (measured: FP16 MAC 22.2 -> 21.4 us, FP32 unchanged).
 cudaError_t prepare_kernels(size_t mac_smem) {
     const int fft_max = (int)fft_smem_bytes(4096);
     cudaError_t e;
-#define GB_ATTR(kern, bytes)                                                                     \
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
+#define GB_ATTR(kern, bytes)                                                                         \
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));     \
+    if (e != cudaSuccess) return e;                                                                \
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared); \
     if (e != cudaSuccess) return e;
     GB_ATTR(k_out_push<PREC_FP32>, fft_max)
     GB_ATTR(k_out_push<PREC_FP16>, fft_max)
