@@ -406,7 +406,8 @@ def l2_note(args, stream_bytes, l2):
                 "L2-resident, as in real-time use")
     if stream_bytes > l2:
         return (f"inputs larger than L2: the {stream_bytes / 1e6:.1f} MB of spectra streamed every step exceed "
-                f"the {l2 / 1e6:.0f} MB L2")
+                f"the {l2 / 1e6:.0f} MB L2; the engine keeps the first 56 MB of them in L2 from one block to the "
+                "next (conv_set_l2_keep), the rest streams from HBM every step")
     return (f"working set below the L2 size ({stream_bytes / 1e6:.1f} MB of spectra per step, L2 {l2 / 1e6:.0f} MB): "
             "the step value is the steady state, in which part of each step's reads hit L2 as in real-time use; "
             "the roofline's launches are timed after an L2 flush (conv_profile_flush_l2)")

@@ -78,6 +78,8 @@ typedef struct conv_info {
     long long mac_far_bytes;  /* far tail MAC (once per far block), 0 if none    */
     long long fft_size;       /* n_f: 2 * block, or 3 * block in the spectrum-reuse
                                  form (afc_set_spectrum_reuse)                   */
+    long long l2_keep_bytes;  /* tail filter spectra kept in L2 between blocks
+                                 (conv_set_l2_keep)                              */
 } conv_info;
 
 /* Per-session counters (conv_get_stats).  Latency is the wall time of a
@@ -330,6 +332,18 @@ int conv_get_info(const conv_engine* e, conv_info* out);
  * and the number of launches timed, and clears the record. */
 int conv_profile_enable(conv_engine* e, int enable);
 int conv_profile_read(conv_engine* e, double* mac_ms_total, long long* launches);
+
+/* L2 residency of the filter spectra between blocks: the tail MACs stream
+ * the first `bytes` of their filter spectra (partitions 1.. in order; the
+ * canceller's first, then the synthesis') with the L2 evict-last policy, so
+ * that the next block reads them from L2, and the rest with evict-first.
+ * Default 56 MB: at the paper configuration on GB300 (136 MB L2), 52-60 MB
+ * gave the shortest back-to-back steps (FP32 27.4 -> 23.0 us, FP16 16.7 ->
+ * 15.6 us) and more gave longer ones.  0 streams everything evict-first (for
+ * example when several engines run at once).  Results do not depend on it.
+ * Takes effect from the next block; CONV_E_INVAL for bytes < 0.  Batched
+ * sessions always stream evict-first. */
+int conv_set_l2_keep(conv_engine* e, long long bytes);
 
 /* Profiling aid: while kernel timing is enabled, read `bytes` of a zeroed
  * scratch buffer (allocated here, owned by the handle) on the MAC's stream

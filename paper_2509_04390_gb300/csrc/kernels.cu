@@ -197,8 +197,10 @@ __device__ __forceinline__ uint32_t mul2(uint32_t a, uint32_t b) {
 // producer: one elected lane streams the split's contiguous filter-spectrum
 // range and the matching delay-line slots into an nstage-deep shared-memory
 // ring with 1-D bulk copies (TMA), completion tracked by mbarriers (filters
-// with an evict-first L2 policy: they are read once per block; the delay line
-// with evict-last: it is re-read by every output tile and by the next blocks).
+// with an evict-first L2 policy: they are read once per block, except the
+// rows below keep_r, which are kept with evict-last so that the next block
+// finds them in L2; the delay line with evict-last: it is re-read by every
+// output tile and by the next blocks).
 // The NW consumer warps: each thread owns VEC bins x up to LPT outputs for one
 // r-lane and accumulates in FP32 registers; r-lanes are combined in a fixed
 // order through shared memory at the end, and the split's sums go to P[split].
@@ -297,7 +299,8 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
                 tx += (size_t)4 * ((w[0][1] - w[0][0]) + (w[1][1] - w[1][0]) + (w[2][1] - w[2][0]));
             }
             mbar_arrive_expect_tx(&full[st], (uint32_t)tx);
-            bulk_g2s(sh, Hb + (size_t)ra * hr_bytes, (uint32_t)((size_t)nr * hr_bytes), &full[st], pol_stream);
+            bulk_g2s(sh, Hb + (size_t)ra * hr_bytes, (uint32_t)((size_t)nr * hr_bytes), &full[st],
+                     ra < a.keep_r ? pol_keep : pol_stream);
             if (PREC != PREC_FP32)
                 bulk_g2s(sh + a.soff, a.sH + w[0][0], (uint32_t)(4 * (w[0][1] - w[0][0])), &full[st], pol_keep);
         };

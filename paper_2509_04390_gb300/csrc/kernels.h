@@ -85,6 +85,9 @@ struct MacArgs {
     // withholds its first stage, so that CTA's consumers wait on a barrier
     // nothing completes and give up after wait_ns (error word, abort flag)
     int withhold;
+    // filter-spectrum rows r < keep_r are streamed with the L2 evict-last
+    // policy (kept in L2 from one block to the next), the others evict-first
+    int keep_r;
 };
 
 struct PackArgs {

@@ -87,6 +87,7 @@ class conv_info(ctypes.Structure):
             "K_far",
             "mac_far_bytes",
             "fft_size",
+            "l2_keep_bytes",
         )
     ]
 
@@ -175,6 +176,7 @@ def load():
         "conv_get_info": (i, [vp, ctypes.POINTER(conv_info)]),
         "conv_profile_enable": (i, [vp, i]),
         "conv_profile_flush_l2": (i, [vp, ll]),
+        "conv_set_l2_keep": (i, [vp, ll]),
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "conv_plan_check": (i, [i, i, i, i, ll, i, ctypes.POINTER(conv_tiling)]),
         "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
@@ -368,6 +370,10 @@ def conv_get_info(h) -> dict:
     info = conv_info()
     _check(load().conv_get_info(h, ctypes.byref(info)))
     return info.as_dict()
+
+
+def conv_set_l2_keep(h, nbytes: int):
+    return _check(load().conv_set_l2_keep(h, int(nbytes)))
 
 
 def conv_profile_flush_l2(h, nbytes: int):

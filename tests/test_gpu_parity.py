@@ -400,3 +400,24 @@ def test_blocks_on_alternating_streams_keep_the_chain():
         if b % 3 != 2:
             y[:, b * B : (b + 1) * B] = dev[b]
     assert np.array_equal(y, ref)
+
+
+def test_l2_keep_budget_leaves_results_unchanged():
+    """conv_set_l2_keep only changes the L2 policy of the filter copies: no
+    budget, the default and one larger than every spectrum give the same
+    output bit for bit, and a negative budget is refused."""
+    w = signals.random_case(7001, 2, 5, 9000, 256, 24)
+    outs = []
+    for keep in (0, None, 1 << 40):
+        with U.Engine(w.fs, w.block, w.n_in, w.n_out, w.taps) as e:
+            if keep is not None:
+                U.conv_set_l2_keep(e.h, keep)
+            assert e.info()["l2_keep_bytes"] == (56_000_000 if keep is None else keep)
+            e.set_filters(w.h)
+            outs.append(e.run(w.x))
+            with pytest.raises(U.ConvError) as ei:
+                U.conv_set_l2_keep(e.h, -1)
+            assert ei.value.code == U.CONV_E_INVAL
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    assert snr_db(outs[0], oracle_out(w)) >= FP32_DB
