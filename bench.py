@@ -406,8 +406,9 @@ def l2_note(args, stream_bytes, l2):
                 "L2-resident, as in real-time use")
     if stream_bytes > l2:
         return (f"inputs larger than L2: the {stream_bytes / 1e6:.1f} MB of spectra streamed every step exceed "
-                f"the {l2 / 1e6:.0f} MB L2; the engine keeps the first 56 MB of them in L2 from one block to the "
-                "next (conv_set_l2_keep), the rest streams from HBM every step")
+                f"the {l2 / 1e6:.0f} MB L2; the engine keeps the first "
+                f"{56 if getattr(args, 'l2_keep', None) is None else args.l2_keep:g} MB of them in L2 from one block "
+                "to the next (conv_set_l2_keep), the rest streams from HBM every step")
     return (f"working set below the L2 size ({stream_bytes / 1e6:.1f} MB of spectra per step, L2 {l2 / 1e6:.0f} MB): "
             "the step value is the steady state, in which part of each step's reads hit L2 as in real-time use; "
             "the roofline's launches are timed after an L2 flush (conv_profile_flush_l2)")
@@ -452,6 +453,8 @@ def run_ours(args):
     B = w.block
     prec = args.precision
     eng = U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, prec, far_block=args.far_block, reuse=args.reuse)
+    if args.l2_keep is not None:
+        U.conv_set_l2_keep(eng.h, int(args.l2_keep * 1e6))
     far_h = U.conv_far_engine(eng.h) if args.far_block else None
     if far_h and args.far_block2:  # a third partition size: the far part's own far block
         U.conv_set_far_block(far_h, args.far_block2)
@@ -1168,6 +1171,8 @@ def parse(argv=None):
     ap.add_argument("--afc", action="store_true", help="synthesis + feedback canceller (paths [4][16], 0.5 s)")
     ap.add_argument("--taps-fb", type=int, default=24000)
     ap.add_argument("--adapt", type=float, default=0.0, help="with --afc: NLMS step size of the adaptive canceller")
+    ap.add_argument("--l2-keep", type=float, default=None,
+                    help="MB of tail filter spectra kept in L2 between blocks (default: the engine's, 56)")
     ap.add_argument("--reuse", action="store_true",
                     help="with --afc: the n_f = 3 n_x form, the synthesis output spectra feeding the canceller")
     ap.add_argument("--far-block", type=int, default=0,

@@ -757,9 +757,9 @@ OutArgs out_args(conv_engine* e, Part& P, long long blk, float* out) {
 }
 
 int enqueue_pack(conv_engine* e, Part& P, const float* src, int stride, const float* sub, float* e_out,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool closed_loop = false) {
     const PackArgs a = pack_args(e, P, e->nblk, src, stride, sub, e_out);
-    CK(e->reuse ? launch_pack3(e->prec, a, s) : launch_pack_r2c(e->prec, a, s));
+    CK(e->reuse ? launch_pack3(e->prec, a, s) : launch_pack_r2c(e->prec, a, s, closed_loop));
     return CONV_OK;
 }
 
@@ -1099,7 +1099,7 @@ int enqueue_afc_synthesis(conv_engine* e, const float* d_mic, float* d_out, floa
     float* eb = d_e ? d_e : ((e->far || e->adapt) ? e->d_e : nullptr);
     int rc;
     far_before(e);
-    if ((rc = enqueue_pack(e, P, d_mic, e->B, e->d_c, eb, s))) return rc;
+    if ((rc = enqueue_pack(e, P, d_mic, e->B, e->d_c, eb, s, true))) return rc;
     CK(cudaEventRecord(P.ev_packed, s));
     if (e->adapt && (rc = enqueue_nlms_prep(e, eb))) return rc;
     CK(cudaStreamWaitEvent(s, P.ev_tail[n & 1], 0));
@@ -1143,7 +1143,7 @@ int enqueue_afc_prediction(conv_engine* e, cudaStream_t s) {
         oa.corr_A2 = A_of(e, n, 2, 8);
         oa.corr_C = F.K >= 2 ? 1 : 0;
     }
-    CK(e->reuse ? launch_out3(e->prec, oa, PackArgs{}, s) : launch_out_c2r(e->prec, oa, s));
+    CK(e->reuse ? launch_out3(e->prec, oa, PackArgs{}, s) : launch_out_c2r(e->prec, oa, s, true));
     if (!e->adapt) {
         cudaStream_t bg = e->bg[2 + ((n + 1) & 1)];
         CK(cudaStreamWaitEvent(bg, F.ev_packed, 0));

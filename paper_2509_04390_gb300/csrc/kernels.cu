@@ -86,6 +86,11 @@ template <int PREC>
 __global__ void k_pack_r2c(const PackArgs a) {
     pack_body<PREC>(a, blockIdx.x);
 }
+// the same for the closed loop (its own shared-memory carveout: see prepare_kernels)
+template <int PREC>
+__global__ void k_pack_r2c_cl(const PackArgs a) {
+    pack_body<PREC>(a, blockIdx.x);
+}
 
 // --------------------------------------------------- filter partitions R2C
 // One CTA per (l, q, p): sub-filter h_lq[pB, pB+B) zero-padded to 2B, R2C,
@@ -875,6 +880,10 @@ template <int PREC>
 __global__ void k_out_c2r(const OutArgs a) {
     out_body<PREC>(a, blockIdx.x);
 }
+template <int PREC>
+__global__ void k_out_c2r_cl(const OutArgs a) {
+    out_body<PREC>(a, blockIdx.x);
+}
 
 // Output of one convolution, then the pack + R2C of the same samples into a
 // second convolution's delay line (the synthesis output is the feedback
@@ -1029,20 +1038,31 @@ cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream
 
 }  // namespace
 
-// Every kernel of the engine asks for the largest shared-memory carveout, so an
-// SM that ran a pack or output CTA takes a MAC CTA without first changing its
-// L1/shared split (measured: FP16 MAC 22.2 -> 21.4 us, FP32 unchanged).
+// The plain convolution's kernels ask for the largest shared-memory carveout,
+// so an SM that ran a pack or output CTA takes a MAC CTA without first
+// changing its L1/shared split (measured at the paper configuration: FP16
+// steps 17.6 -> 15.7 us, FP32 unchanged).  The closed loop's pack and output
+// kernels (k_*_cl, k_out_push) keep the default: there the larger carveout
+// made FP16 steps longer (27.5 -> 30.8 us), FP32 within 1 %.
 cudaError_t prepare_kernels(size_t mac_smem) {
     const int fft_max = (int)fft_smem_bytes(4096);
     cudaError_t e;
-#define GB_ATTR(kern, bytes)                                                                         \
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes));     \
-    if (e != cudaSuccess) return e;                                                                \
+#define GB_ATTR_DEFAULT(kern, bytes)                                                             \
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
+    if (e != cudaSuccess) return e;
+#define GB_ATTR(kern, bytes)                                                                              \
+    GB_ATTR_DEFAULT(kern, bytes)                                                                          \
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared); \
     if (e != cudaSuccess) return e;
-    GB_ATTR(k_out_push<PREC_FP32>, fft_max)
-    GB_ATTR(k_out_push<PREC_FP16>, fft_max)
-    GB_ATTR(k_out_push<PREC_BF16>, fft_max)
+    GB_ATTR_DEFAULT(k_out_push<PREC_FP32>, fft_max)
+    GB_ATTR_DEFAULT(k_out_push<PREC_FP16>, fft_max)
+    GB_ATTR_DEFAULT(k_out_push<PREC_BF16>, fft_max)
+    GB_ATTR_DEFAULT(k_pack_r2c_cl<PREC_FP32>, fft_max)
+    GB_ATTR_DEFAULT(k_pack_r2c_cl<PREC_FP16>, fft_max)
+    GB_ATTR_DEFAULT(k_pack_r2c_cl<PREC_BF16>, fft_max)
+    GB_ATTR_DEFAULT(k_out_c2r_cl<PREC_FP32>, fft_max)
+    GB_ATTR_DEFAULT(k_out_c2r_cl<PREC_FP16>, fft_max)
+    GB_ATTR_DEFAULT(k_out_c2r_cl<PREC_BF16>, fft_max)
     GB_ATTR(k_pack_r2c<PREC_FP32>, fft_max)
     GB_ATTR(k_pack_r2c<PREC_FP16>, fft_max)
     GB_ATTR(k_pack_r2c<PREC_BF16>, fft_max)
@@ -1074,18 +1094,19 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR((k_fdl_mac_ldg<PREC_FP32, 4, 8, 1, 3>), mac_smem)
     GB_ATTR((k_fdl_mac_ldg<PREC_FP32, 4, 8, 2, 2>), mac_smem)
 #undef GB_ATTR
+#undef GB_ATTR_DEFAULT
     return cudaSuccess;
 }
 
-cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s) {
+cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s, bool closed_loop) {
     // one CTA per channel on the critical path: as many threads as the output
     // kernel (measured: 0.2-1.2 us shorter steps than B/4 threads)
     const dim3 grid(a.n_ch), block(out_threads(a.B));
     const size_t sm = fft_smem_bytes(a.B);
     switch (prec) {
-        case PREC_FP32: return launch_pdl(k_pack_r2c<PREC_FP32>, grid, block, sm, s, a);
-        case PREC_FP16: return launch_pdl(k_pack_r2c<PREC_FP16>, grid, block, sm, s, a);
-        case PREC_BF16: return launch_pdl(k_pack_r2c<PREC_BF16>, grid, block, sm, s, a);
+        case PREC_FP32: return launch_pdl(closed_loop ? k_pack_r2c_cl<PREC_FP32> : k_pack_r2c<PREC_FP32>, grid, block, sm, s, a);
+        case PREC_FP16: return launch_pdl(closed_loop ? k_pack_r2c_cl<PREC_FP16> : k_pack_r2c<PREC_FP16>, grid, block, sm, s, a);
+        case PREC_BF16: return launch_pdl(closed_loop ? k_pack_r2c_cl<PREC_BF16> : k_pack_r2c<PREC_BF16>, grid, block, sm, s, a);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1158,13 +1179,13 @@ size_t out_head_smem(int n_src, int B) {
     return fft_smem_bytes(B) + extra <= 64 * 1024 ? extra : 0;
 }
 
-cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s) {
+cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s, bool closed_loop) {
     const dim3 grid(a.n_dst), block(out_threads(a.B));
     const size_t sm = fft_smem_bytes(a.B) + (a.head && a.head_pre ? (size_t)a.n_src * a.B * sizeof(float2) : 0);
     switch (prec) {
-        case PREC_FP32: return launch_pdl(k_out_c2r<PREC_FP32>, grid, block, sm, s, a);
-        case PREC_FP16: return launch_pdl(k_out_c2r<PREC_FP16>, grid, block, sm, s, a);
-        case PREC_BF16: return launch_pdl(k_out_c2r<PREC_BF16>, grid, block, sm, s, a);
+        case PREC_FP32: return launch_pdl(closed_loop ? k_out_c2r_cl<PREC_FP32> : k_out_c2r<PREC_FP32>, grid, block, sm, s, a);
+        case PREC_FP16: return launch_pdl(closed_loop ? k_out_c2r_cl<PREC_FP16> : k_out_c2r<PREC_FP16>, grid, block, sm, s, a);
+        case PREC_BF16: return launch_pdl(closed_loop ? k_out_c2r_cl<PREC_BF16> : k_out_c2r<PREC_BF16>, grid, block, sm, s, a);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -194,14 +194,15 @@ size_t fft_smem_bytes(int B);
 void set_last_error_message(const char* msg);
 
 cudaError_t prepare_kernels(size_t mac_smem);
-cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s);
+// closed_loop: the canceller's schedule (kernels with the default shared-memory carveout)
+cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s, bool closed_loop = false);
 cudaError_t launch_filter_r2c(int prec, const FilterArgs& a, cudaStream_t s);
 cudaError_t launch_tile_scales(int prec, const float* maxabs, float* sH, int n_dst, int R, int LT, cudaStream_t s);
 // pdl: programmatic dependent launch after the previous kernel in the stream.
 // The MAC streams its first filter stages before waiting for that kernel, so
 // pass false when the previous kernel writes the filter spectra.
 cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s, bool pdl = true);
-cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s);
+cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s, bool closed_loop = false);
 // Output (a) fused with the push of each output channel into another ring (b,
 // b.in = a.out, b.n_ch = a.n_dst).
 cudaError_t launch_out_push(int prec, const OutArgs& a, const PackArgs& b, cudaStream_t s);

@@ -330,8 +330,6 @@ cudaError_t prepare_reuse_kernels() {
     cudaError_t e;
 #define GB_ATTR3(kern)                                                                        \
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx); \
-    if (e != cudaSuccess) return e;                                                  \
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared); \
     if (e != cudaSuccess) return e;
     GB_ATTR3(k_pack3<PREC_FP32>)
     GB_ATTR3(k_pack3<PREC_FP16>)
