@@ -874,6 +874,8 @@ def run_group(args):
     d_out = torch.empty((2, S, w.n_out, B), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     grp = U.Group(prec, B, w.n_in, w.n_out, w.taps, S)
+    if args.l2_keep is not None:
+        U.conv_group_set_l2_keep(grp.g, int(args.l2_keep * 1e6))
     grp.set_filters(w.h)
     info = grp.info()
     units = float(S) * w.n_in * w.n_out * w.taps * B
@@ -991,7 +993,9 @@ def run_group(args):
         "config": {
             "workload": f"group_{S}_sessions_paper_4x16_{w.taps}taps_B{B}_{prec}",
             "sessions": S, "n_in": w.n_in, "n_out": w.n_out, "taps": w.taps, "block": B, "precision": prec,
-            "l2": "inputs larger than L2: filter tiles and delay lines streamed every step exceed the 126 MB L2",
+            "l2": (f"inputs larger than L2: the filter tiles and delay lines streamed every step exceed the "
+                   f"{l2_bytes() / 1e6:.0f} MB L2; the first {60 if args.l2_keep is None else args.l2_keep:g} MB of "
+                   "filter tiles stay in L2 from one block to the next (conv_group_set_l2_keep)"),
         },
         "roofline": {
             "bound": "hbm", "kernel": "k_group_mac", "achieved": mac_bytes / t_mac / 1e9, "peak": peak,

@@ -589,6 +589,14 @@ int conv_group_plan_check(int precision, int block, int n_in, int n_out, long lo
 /* CUDA-event timing of each MAC launch (enable > 1: number of event pairs),
  * read and cleared by conv_group_profile_read (total ms, launches). */
 int conv_group_profile_enable(conv_group* g, int enable);
+
+/* L2 residency of the group's filter tiles between blocks (as conv_set_l2_keep
+ * for one engine): the first `bytes` of them (the lowest partitions of every
+ * bin group) are streamed with the L2 evict-last policy, the rest and the
+ * delay lines evict-first.  Default 60 MB (measured at 8 sessions of the paper
+ * configuration, FP16: 29.3 -> 26.5 us per step).  0 turns it off; results do
+ * not depend on it.  CONV_E_INVAL for bytes < 0. */
+int conv_group_set_l2_keep(conv_group* g, long long bytes);
 int conv_group_profile_read(conv_group* g, double* total_ms, long long* launches);
 
 /* Free everything the group owns.  NULL-safe. */

@@ -221,9 +221,11 @@ __global__ void __launch_bounds__(GRP_THREADS, 1) k_group_mac(const GroupMacArgs
     if (warp == 0) {
         if (lane == 0) {
             // a ring class is read again only two blocks later, after ~300 MB of
-            // other traffic: neither operand is kept in L2 (evict-last on the ring
-            // measured slower on GB300)
+            // other traffic: the ring is not kept in L2 (evict-last on the ring
+            // measured slower on GB300); the filter tiles of the first keep_c
+            // K-steps are, so that the next block finds them there
             const uint64_t pol_h = policy_evict_first(), pol_x = policy_evict_first();
+            const uint64_t pol_keep = policy_evict_last();
             int f = 0;
             bool ok = true;
             for (long long u = lo; u < hi && ok;) {
@@ -245,7 +247,8 @@ __global__ void __launch_bounds__(GRP_THREADS, 1) k_group_mac(const GroupMacArgs
                     unsigned char* sA = stages + (size_t)st * a.stage_bytes;
                     unsigned char* sB = sA + (size_t)a.NK * TILE_BYTES;
                     mbar_arrive_expect_tx(full + st, (uint32_t)nk * (TILE_BYTES + 2u * a.RB));
-                    bulk_g2s(sA, hb + (size_t)c * TILE_BYTES, (uint32_t)nk * TILE_BYTES, full + st, pol_h);
+                    bulk_g2s(sA, hb + (size_t)c * TILE_BYTES, (uint32_t)nk * TILE_BYTES, full + st,
+                             c < a.keep_c ? pol_keep : pol_h);
                     const int idx = ((a.slot0 + c * a.KP) % a.KR) / a.D;
                     const int rows = 2 * nk;
                     const int first = min(rows, rows_per_class - idx);

@@ -97,6 +97,9 @@ struct GroupMacArgs {
     int B, n_dst, S, G, NG, D, KP, KR, NKS, N, RB, T, C, SP, NK, nstage, stage_bytes, slot0, tmem_cols, nbuf;
     uint32_t idesc;
     int* err;
+    // K-steps c < keep_c of every bin group are streamed with the L2
+    // evict-last policy (kept in L2 from one block to the next)
+    int keep_c;
 };
 
 struct GroupPackArgs {

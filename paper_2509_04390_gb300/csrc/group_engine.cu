@@ -28,6 +28,9 @@
 #include "conv.h"
 #include "group.h"
 #include "host_util.h"
+
+// Filter tiles a group keeps in L2 between blocks by default (conv_group_set_l2_keep)
+constexpr long long GROUP_L2_KEEP_DEFAULT = 60LL * 1000 * 1000;
 #include "kernels.h"
 
 using namespace gbconv;
@@ -63,6 +66,8 @@ struct conv_group {
     long long nblk = 0;
     bool ready = false;
     bool prof = false;
+    // conv_group_set_l2_keep: bytes of filter tiles streamed evict-last
+    long long l2_keep = GROUP_L2_KEEP_DEFAULT;
     std::vector<cudaEvent_t> ev0, ev1;
     size_t ev_used = 0;
     size_t dev_bytes = 0;
@@ -252,6 +257,8 @@ int enqueue_tail(conv_group* g, long long blk, cudaStream_t s) {
     a.tmem_cols = p.tmem_cols;
     a.idesc = g->idesc;
     a.err = g->d_err;
+    // one K-step of every bin group is NG filter tiles of 8 KiB
+    a.keep_c = (int)std::min<long long>(p.NKS, g->l2_keep / ((long long)p.NG * 8192));
     const bool rec = g->prof && g->ev_used < g->ev0.size();
     if (rec) GB_CK(cudaEventRecord(g->ev0[g->ev_used], s));
     GB_CK(launch_group_mac(p, a, s));
@@ -536,6 +543,13 @@ int conv_group_plan_check(int precision, int block, int n_in, int n_out, long lo
     if (const char* why = plan_group(prec, block, n_in, n_out, taps, sessions, num_sms, &p, from_api(tiling)))
         return fail(CONV_E_INVAL, "%s", why);
     if (const char* why = check_group_plan(p)) return fail(CONV_E_INVAL, "%s", why);
+    return CONV_OK;
+}
+
+int conv_group_set_l2_keep(conv_group* g, long long bytes) {
+    if (!g) return fail(CONV_E_INVAL, "null handle");
+    if (bytes < 0) return fail(CONV_E_INVAL, "bytes must be >= 0");
+    g->l2_keep = bytes;
     return CONV_OK;
 }
 

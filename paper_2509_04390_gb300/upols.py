@@ -177,6 +177,7 @@ def load():
         "conv_profile_enable": (i, [vp, i]),
         "conv_profile_flush_l2": (i, [vp, ll]),
         "conv_set_l2_keep": (i, [vp, ll]),
+        "conv_group_set_l2_keep": (i, [vp, ll]),
         "conv_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "conv_plan_check": (i, [i, i, i, i, ll, i, ctypes.POINTER(conv_tiling)]),
         "conv_fdl_mac_noalloc": (i, [vp, vp, i, i, i, ll, ll, vp, vp]),
@@ -374,6 +375,10 @@ def conv_get_info(h) -> dict:
 
 def conv_set_l2_keep(h, nbytes: int):
     return _check(load().conv_set_l2_keep(h, int(nbytes)))
+
+
+def conv_group_set_l2_keep(g, nbytes: int):
+    return _check(load().conv_group_set_l2_keep(g, int(nbytes)))
 
 
 def conv_profile_flush_l2(h, nbytes: int):

@@ -112,6 +112,26 @@ def test_reset_repeats_bit_exact():
     assert np.array_equal(y0, y1)
 
 
+def test_l2_keep_leaves_results_unchanged():
+    """conv_group_set_l2_keep changes only the L2 policy of the filter-tile
+    copies: no budget and a budget above every tile give the default's output
+    bit for bit; a negative budget is refused."""
+    S, n_in, n_out, taps, B, nb = 8, 4, 16, 2000, 64, 30
+    h, x = group_case(10, S, n_in, n_out, taps, B, nb)
+    outs = []
+    for keep in (None, 0, 1 << 40):
+        with U.Group("fp16", B, n_in, n_out, taps, S) as g:
+            if keep is not None:
+                U.conv_group_set_l2_keep(g.g, keep)
+            g.set_filters(h)
+            outs.append(g.run(x))
+            with pytest.raises(U.ConvError) as ei:
+                U.conv_group_set_l2_keep(g.g, -1)
+            assert ei.value.code == U.CONV_E_INVAL
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
 def test_render_equals_block_calls():
     """conv_group_process_blocks over a chunk boundary (300 blocks) is the
     block-by-block stream, bit for bit."""
