@@ -1100,10 +1100,12 @@ def run_extras(args):
     """The secondary configurations, each a short run of its own with its own
     timing and roofline, reported under "extra" of the headline line: block
     128 (the paper's default) and 512 at the headline shape, FP16 and BF16
-    spectra, synthesis + feedback canceller (FP32, FP16), 8 sessions sharing
-    one filter set on the tensor cores, 64 heterogeneous FP16 sessions in one
-    batch, and a short serving run.  A configuration that fails is reported
-    with its error instead of ending the run."""
+    spectra, synthesis + feedback canceller (FP32, FP16; adaptive; in the
+    n_f = 3 n_x spectrum-reuse form), non-uniform partitions (far block 2048),
+    8 sessions sharing one filter set on the tensor cores, 64 heterogeneous
+    FP16 sessions in one batch (per-stage launches, one persistent launch, its
+    CUDA graph), a short serving run, and the autotuner.  A configuration
+    that fails is reported with its error instead of ending the run."""
     import copy
     import traceback
 
@@ -1129,6 +1131,8 @@ def run_extras(args):
         ("paper_4x16_B256_bf16", run_ours, variant(precision="bf16")),
         ("afc_4x16_B256_fp32", run_ours, variant(afc=True)),
         ("afc_4x16_B256_fp16", run_ours, variant(afc=True, precision="fp16")),
+        ("afc_nlms_4x16_B256_fp32", run_ours, variant(afc=True, adapt=0.05)),
+        ("paper_4x16_B256_far2048_fp32", run_ours, variant(far_block=2048)),
         ("afc_4x16_B256_fp32_reuse_nf3", run_ours, variant(afc=True, reuse=True)),
         ("afc_4x16_B256_fp16_reuse_nf3", run_ours, variant(afc=True, reuse=True, precision="fp16")),
         ("group_8_sessions_B256_fp16", run_group, variant(group=8, precision="fp16")),
@@ -1156,7 +1160,8 @@ def run_extras(args):
 
 
 ALL_EXTRAS = ("paper_4x16_B128_fp32,paper_4x16_B512_fp32,paper_4x16_B256_fp16,paper_4x16_B256_bf16,"
-              "afc_4x16_B256_fp32,afc_4x16_B256_fp16,afc_4x16_B256_fp32_reuse_nf3,afc_4x16_B256_fp16_reuse_nf3,"
+              "afc_4x16_B256_fp32,afc_4x16_B256_fp16,afc_nlms_4x16_B256_fp32,paper_4x16_B256_far2048_fp32,"
+              "afc_4x16_B256_fp32_reuse_nf3,afc_4x16_B256_fp16_reuse_nf3,"
               "group_8_sessions_B256_fp16,batch_64_sessions_fp16,"
               "batch_64_sessions_fp16_persistent,batch_64_sessions_fp16_persistent_graph,serving,"
               "paper_4x16_B256_fp32_tuned,paper_4x16_B256_fp16_tuned")
