@@ -95,10 +95,12 @@ def kernel_source_hash():
 
 
 def ncu_traffic(workload: str, field: str = "dram_bytes_per_launch"):
-    """A DRAM figure per MAC launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None): dram_bytes_per_launch
-    (cold L2, read + write) or dram_read_bytes_warm_l2 (the L2 as the previous
-    block's kernels left it)."""
+    """A DRAM figure from the committed ncu summary, if it was taken on the
+    current kernel source (else None): dram_bytes_per_launch (one MAC launch,
+    cold L2, read + write), dram_read_bytes_warm_l2 (one MAC launch, kernel
+    replay with the L2 as the previous kernels left it) or
+    dram_read_bytes_per_step_range (a whole step, range replay over 100
+    blocks back to back)."""
     path = os.path.join(ROOT, "profiles", "fdl_mac_traffic.json")
     try:
         with open(path) as f:
@@ -223,7 +225,7 @@ def step_bandwidth(w, info, t_step, peak, warm_read=None):
         "hbm_bytes_per_step": int(filt),
         "hbm_gbs": filt / t_step / 1e9,
         "hbm_frac_of_peak": filt / t_step / 1e9 / peak,
-        # ncu, warm L2 (the previous tail's filter lines partly survive in L2)
+        # ncu range replay over 100 whole steps (every kernel running as it does live)
         "dram_read_bytes_per_step_measured": warm_read,
         "dram_frac_of_peak_measured": (warm_read / t_step / 1e9 / peak) if warm_read else None,
         "l2_kept_bytes": info.get("l2_keep_bytes"),
@@ -692,7 +694,7 @@ def run_ours(args):
                 },
             },
             "step_bandwidth": step_bandwidth(w, info, t_max / args.steps, peak,
-                                             ncu_traffic(workload_name(args), "dram_read_bytes_warm_l2")),
+                                             ncu_traffic(workload_name(args), "dram_read_bytes_per_step_range")),
             "roofline": {
                 "bound": "hbm",
                 "kernel": "k_fdl_mac (far part, once per far block)" if far_h else "k_fdl_mac",
@@ -704,6 +706,7 @@ def run_ours(args):
                 "traffic": ncu_traffic(workload_name(args)),
                 "traffic_kind": "ncu, cold L2 (ncu's default cache control), per launch",
                 "traffic_warm_l2_ncu": ncu_traffic(workload_name(args), "dram_read_bytes_warm_l2"),
+                "dram_read_bytes_per_step_range": ncu_traffic(workload_name(args), "dram_read_bytes_per_step_range"),
                 "l2_kept_bytes": None if flushed else info.get("l2_keep_bytes"),
                 "algorithmic_bytes_per_launch": roof_bytes,
                 "avg_launch_us": mac_avg_s * 1e6,
@@ -1200,6 +1203,8 @@ def parse(argv=None):
     ap.add_argument("--adapt", type=float, default=0.0, help="with --afc: NLMS step size of the adaptive canceller")
     ap.add_argument("--l2-keep", type=float, default=None,
                     help="MB of tail filter spectra kept in L2 between blocks (default: the engine's, 56)")
+    ap.add_argument("--profile-range", type=int, default=0,
+                    help="run this many blocks inside a profiler range (for ncu --replay-mode app-range) and exit")
     ap.add_argument("--reuse", action="store_true",
                     help="with --afc: the n_f = 3 n_x form, the synthesis output spectra feeding the canceller")
     ap.add_argument("--far-block", type=int, default=0,
@@ -1230,12 +1235,73 @@ def parse(argv=None):
     return ap.parse_args(argv)
 
 
+def run_profile_range(args):
+    """--profile-range N: N blocks back to back, after the warm-up, inside a
+    profiler range (cudaProfilerStart / Stop), so that ncu's range replay
+    (`ncu --replay-mode app-range`) measures whole steps with every kernel
+    running as it does live.  Prints the block time of the range."""
+    import torch
+
+    from paper_2509_04390_gb300 import upols as U
+
+    torch.cuda.set_device(0)
+    w = make_workload(args)
+    B = w.block
+    eng = U.Engine(w.fs, B, w.n_in, w.n_out, w.taps, args.precision, reuse=args.reuse)
+    try:
+        if args.l2_keep is not None:
+            U.conv_set_l2_keep(eng.h, int(args.l2_keep * 1e6))
+        eng.set_filters(w.h)
+        if args.afc:
+            eng.set_paths(w.f)
+        nb = w.x.shape[1] // B
+        d = torch.from_numpy(np.ascontiguousarray(w.x[:, : nb * B])).cuda()
+        d = d.reshape(w.n_in, nb, B).permute(1, 0, 2).contiguous()
+        out = torch.empty((2, w.n_out, B), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+        lib = U.load()
+
+        def run(n, first):
+            for i in range(n):
+                j = first + i
+                if args.afc:
+                    rc = lib.afc_process_block_async(eng.h, d[j % nb].data_ptr(), out[j & 1].data_ptr(), None,
+                                                     stream.cuda_stream)
+                else:
+                    rc = lib.conv_process_block_async(eng.h, d[j % nb].data_ptr(), out[j & 1].data_ptr(),
+                                                      stream.cuda_stream)
+                if rc:
+                    raise U.ConvError(rc, U.conv_last_error())
+
+        run(args.warmup, 0)
+        U.conv_synchronize(eng.h)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.profiler.start()
+        ev0.record(stream)
+        run(args.profile_range, args.warmup)
+        lib.conv_join_async(eng.h, stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        line = {"workload": workload_name(args), "blocks": args.profile_range,
+                "us_per_block": ev0.elapsed_time(ev1) / args.profile_range * 1e3,
+                "l2_keep_bytes": eng.info()["l2_keep_bytes"]}
+    finally:
+        eng.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse(argv)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_range:
+        return run_profile_range(args)
     args.extras = [x for x in args.extras.split(",") if x]
     if args.batch:
         line = run_batch(args)
