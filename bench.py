@@ -592,6 +592,7 @@ def run_ours(args):
         host_call(h_in, h_out)
     if dist is not None:
         dist.barrier()
+    g0 = U.conv_get_host_graph(eng.h)[1]
     te0 = time.perf_counter()
     for i in range(e2e_steps):
         j = (i + 50) % nb
@@ -600,6 +601,7 @@ def run_ours(args):
         host_call(h_in, h_out)
         lat.append(time.perf_counter_ns() - t0)
     te1 = time.perf_counter()
+    g1 = U.conv_get_host_graph(eng.h)[1]
     e_t, e_units = aggregate(te1 - te0, tapch(w) * e2e_steps, dist)
     e2e_value = e_units / e_t / 1e9
     lat_us = np.array(lat) / 1e3
@@ -619,6 +621,7 @@ def run_ours(args):
             host_call(h_in, h_out)
             paced.append(time.perf_counter_ns() - t0)
             t_next += period_ns
+    g2 = U.conv_get_host_graph(eng.h)[1]
     paced_us = np.array(paced) / 1e3 if paced else None
 
     peaks, peak_kind = measured_peaks()
@@ -682,6 +685,7 @@ def run_ours(args):
                     "block_period": period_us,
                     "p99_over_period": float(np.percentile(lat_us, 99)) / period_us,
                     "mode": "back to back",
+                    "graph_calls": g1 - g0,
                 },
                 "latency_paced_us": None if paced_us is None else {
                     "p50": float(np.percentile(paced_us, 50)),
@@ -691,6 +695,9 @@ def run_ours(args):
                     "p99_over_period": float(np.percentile(paced_us, 99)) / period_us,
                     "blocks": len(paced_us),
                     "mode": "one call per block period (real-time use)",
+                    # calls that went through conv_process_block's CUDA graph
+                    # (the rest took the stream form: the previous tail still ran)
+                    "graph_calls": g2 - g1,
                 },
             },
             "step_bandwidth": step_bandwidth(w, info, t_max / args.steps, peak,

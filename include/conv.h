@@ -208,6 +208,28 @@ int afc_set_paths(conv_engine* e, const float* f, long long taps_fb);
  * the background.  Needs conv_set_filters (CONV_E_STATE otherwise). */
 int conv_process_block(conv_engine* e, const float* in, float* out);
 
+/* How conv_process_block enqueues its work.  The graph form is one CUDA
+ * graph launch (pack -> output, and the next block's tail MAC beside the
+ * output), captured from the same kernels and launch shapes as the stream
+ * path on first use and updated with each block's arguments; the call returns
+ * when the graph's output node is done.  The stream form is three launches
+ * and their events, and starts the pack while the previous block's tail MAC
+ * may still run (the next launch of the graph waits for the previous one,
+ * tail included).  Both give the same bits.
+ *   mode 1 (default): the graph when at least half a block period has
+ *          passed since the previous call started (real-time use, one call
+ *          per block period: the previous tail has finished), else the
+ *          stream form (back-to-back calls);
+ *   mode 2: the graph for every call;
+ *   mode 0: the stream form for every call (drops the graph).
+ * The graph is rebuilt when the launch shapes change (a new plan).  Engines
+ * with a far block, an adaptive canceller, the n_f = 3 n_x form, kernel
+ * timing (conv_profile_enable) or batch membership always take the stream
+ * form.  CONV_E_INVAL for another mode.  conv_get_host_graph reports the mode
+ * and how many blocks went through the graph (never reset). */
+int conv_set_host_graph(conv_engine* e, int mode);
+int conv_get_host_graph(const conv_engine* e, int* mode, long long* graph_blocks);
+
 /* n_blocks consecutive blocks from host buffers in one call (offline
  * rendering): in[n_in][n_blocks * block] and out[n_out][n_blocks * block],
  * row-major with row pitch n_blocks * block, owned by the caller.  The same
