@@ -387,10 +387,13 @@ void gbconv::set_last_error_message(const char* msg) { g_err = msg ? msg : ""; }
 
 // conv_process_block as one CUDA graph: the pack of block n, its output
 // (programmatic edge, as on a stream) and an event recorded after the output,
-// with block n+1's tail MAC beside the output.  Captured once from the same
-// launchers as the stream path; each call sets the three nodes' argument
-// blocks.  The next launch of the graph starts after the whole previous one,
-// tail included, which orders block n+1's output after its tail.
+// with block n+1's tail MAC beside the output, and last a node that advances
+// the block number in device memory.  Captured once from the same launchers as
+// the stream path.  The kernels take the ring slot and the partials' parity
+// from that device word, so the nodes' arguments stay the same from block to
+// block and a call is one graph launch.  The next launch of the graph starts
+// after the whole previous one, tail included, which orders block n+1's
+// output after its tail.
 struct HostGraphKey {
     int prec = -1, B = 0, n_src = 0, n_dst = 0, ctas = 0, nw = 0, direct = 0, S = 0, head_pre = 0;
     size_t smem = 0;
@@ -407,6 +410,9 @@ struct HostGraph {
     cudaGraphExec_t x = nullptr;
     cudaGraphNode_t pack = nullptr, out = nullptr, tail = nullptr;
     cudaKernelNodeParams pp{}, po{}, pt{};
+    PackArgs pa{};  // the nodes' current arguments
+    OutArgs oa{};
+    MacArgs ma{};
     HostGraphKey key;
     cudaStream_t cs[2] = {nullptr, nullptr};  // capture streams
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
@@ -492,10 +498,15 @@ struct conv_engine {
     bool inject = false;
     unsigned long long inject_ns = 0;
     HostGraph hg;     // conv_process_block's graph (conv_set_host_graph)
+    long long* d_blk = nullptr;  // its block number (the next block the graph processes)
     conv_stats st{};  // counters of conv_get_stats
 };
 
 namespace {
+
+// The host-call graph's block number in device memory.
+__global__ void k_blk_set(long long* blk, long long n) { *blk = n; }
+__global__ void k_blk_advance(long long* blk) { *blk += 1; }
 
 // Reads n 16-byte words (kernel timing's L2 flush: clean lines of this buffer
 // replace whatever the cache held, with no write-back left for the next
@@ -1015,8 +1026,8 @@ int host_graph_settle(conv_engine* e) {
 }
 
 bool host_graph_eligible(const conv_engine* e) {
-    return e->hg.mode > 0 && !e->reuse && !e->far && !e->prof && !e->adapt && e->in_batches == 0 && !e->io_in_stride &&
-           !e->io_out_stride;
+    return e->hg.mode > 0 && !e->reuse && !e->far && !e->prof && !e->adapt && !e->inject && e->in_batches == 0 &&
+           !e->io_in_stride && !e->io_out_stride;
 }
 
 // The graph pays off when the previous block's tail has finished, as in
@@ -1076,6 +1087,8 @@ int host_graph_capture(conv_engine* e, const PackArgs& pa, const OutArgs& oa, co
     }
     CK(cudaEventRecord(G.ev_join, c1));
     CK(cudaStreamWaitEvent(c0, G.ev_join, 0));
+    k_blk_advance<<<1, 1, 0, c0>>>(e->d_blk);  // after the output and the tail have read it
+    CK(cudaGetLastError());
     return CONV_OK;
 }
 
@@ -1116,28 +1129,56 @@ int set_node_args(cudaGraphExec_t x, cudaGraphNode_t node, cudaKernelNodeParams&
     return CONV_OK;
 }
 
+// Copies an argument block into the node's stored one and reports whether it
+// changed (compared byte for byte: a difference in padding only costs an
+// unneeded update).
+template <typename T>
+bool args_changed(T& stored, const T& now) {
+    if (std::memcmp(&stored, &now, sizeof(T)) == 0) return false;
+    std::memcpy(&stored, &now, sizeof(T));
+    return true;
+}
+
 // One block of conv_process_block through the graph (the stream path is
 // enqueue_block with the mapped host buffers).
 int host_graph_block(conv_engine* e) {
     HostGraph& G = e->hg;
     Part& P = e->syn;
     const long long n = e->nblk;
-    const PackArgs pa = pack_args(e, P, n, e->m_in, e->B, nullptr, nullptr);
-    const OutArgs oa = out_args(e, P, n, e->m_out);
-    MacArgs ma{};
-    const bool tail = P.plan.S > 0;
-    if (tail) ma = tail_args(e, P, n + 1);
     int rc;
+    if (!e->d_blk && (rc = dev_alloc(e, &e->d_blk, sizeof(long long)))) return rc;
+    // the arguments of block 0, with the block number read from d_blk instead
+    PackArgs pa = pack_args(e, P, 0, e->m_in, e->B, nullptr, nullptr);
+    pa.blk = e->d_blk;
+    OutArgs oa = out_args(e, P, 0, e->m_out);
+    oa.blk = e->d_blk;
+    oa.partial_b = P.partial[1];
+    const bool tail = P.plan.S > 0;
+    MacArgs ma{};
+    if (tail) {
+        ma = tail_args(e, P, 0);
+        ma.blk = e->d_blk;
+        ma.blk_add = 1;  // the tail of the next block
+        ma.partial_b = P.partial[1];
+    }
     if (!G.x || !(G.key == host_graph_key(e))) {
         if ((rc = host_graph_build(e, pa, oa, tail ? &ma : nullptr))) return rc;
-    } else {
-        if ((rc = set_node_args(G.x, G.pack, G.pp, &pa))) return rc;
-        if ((rc = set_node_args(G.x, G.out, G.po, &oa))) return rc;
-        if (tail && (rc = set_node_args(G.x, G.tail, G.pt, &ma))) return rc;
+        std::memcpy(&G.pa, &pa, sizeof pa);
+        std::memcpy(&G.oa, &oa, sizeof oa);
+        std::memcpy(&G.ma, &ma, sizeof ma);
+    } else {  // a new L2 budget, new buffers after a replan, ...
+        if (args_changed(G.pa, pa) && (rc = set_node_args(G.x, G.pack, G.pp, &G.pa))) return rc;
+        if (args_changed(G.oa, oa) && (rc = set_node_args(G.x, G.out, G.po, &G.oa))) return rc;
+        if (tail && args_changed(G.ma, ma) && (rc = set_node_args(G.x, G.tail, G.pt, &G.ma))) return rc;
     }
     if ((rc = stream_handoff(e, e->stream))) return rc;
-    // block n's tail ran on a background stream (or is the reset's zero partials)
-    if (!G.live) CK(cudaStreamWaitEvent(e->stream, P.ev_tail[n & 1], 0));
+    if (!G.live) {
+        // block n's tail ran on a background stream (or is the reset's zero
+        // partials), and the host kept the block number
+        CK(cudaStreamWaitEvent(e->stream, P.ev_tail[n & 1], 0));
+        k_blk_set<<<1, 1, 0, e->stream>>>(e->d_blk, n);
+        CK(cudaGetLastError());
+    }
     CK(cudaGraphLaunch(G.x, e->stream));
     G.live = true;
     ++G.blocks;
@@ -1412,6 +1453,7 @@ void engine_free(conv_engine* e) {
     for (auto ev : e->ev0) cudaEventDestroy(ev);
     for (auto ev : e->ev1) cudaEventDestroy(ev);
     host_graph_destroy(e->hg);
+    dev_free(e, &e->d_blk, sizeof(long long));
     if (e->ev_done) cudaEventDestroy(e->ev_done);
     if (e->ev_handoff) cudaEventDestroy(e->ev_handoff);
     if (e->ev_join) cudaEventDestroy(e->ev_join);

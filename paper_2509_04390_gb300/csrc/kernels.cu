@@ -26,10 +26,18 @@ namespace {
 
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;  // 1 s: far beyond any legitimate wait
 
+// Ring slot of block n's spectra (the ring's head moves back one slot per block).
+__device__ __forceinline__ int ring_slot_of(long long n, int K) {
+    const int m = (int)(n % K);
+    return m == 0 ? 0 : K - m;
+}
+
 // ------------------------------------------------------------ pack + R2C
 // One CTA per channel.  w = [previous block, in - sub]; z[n] = w[2n] + i w[2n+1];
 // B-point FFT; real-FFT post-processing; push into the ring slot.
-template <int PREC>
+// BLK: the ring slot comes from the block number at a.blk (host-call graph);
+// a separate instantiation, so that the stream path's kernels stay as they are.
+template <int PREC, bool BLK = false>
 __device__ __forceinline__ void pack_body(const PackArgs& a, const int c) {
     extern __shared__ float2 fsm[];
     __shared__ float red[32];
@@ -40,9 +48,10 @@ __device__ __forceinline__ void pack_body(const PackArgs& a, const int c) {
     griddep_launch_dependents();
     load_twiddles(tws, a.tw, B);
     griddep_wait();  // input, feedback prediction and ring slot belong to earlier work
+    auto slot_of = [&]() -> int { return BLK ? ring_slot_of(*a.blk, a.K) : a.slot; };  // read where used
     if (PREC == PREC_FP32 && a.save_old) {  // ordered before the push by the barriers below
         const float2* X = static_cast<const float2*>(a.X);
-        const RingIndex ri{a.BT, a.n_ch, c, a.K, a.slot};
+        const RingIndex ri{a.BT, a.n_ch, c, a.K, slot_of()};
         for (int k = tid; k < B; k += nth) {
             const int kt = k / a.BT, kl = k - kt * a.BT;
             a.save_old[((size_t)kt * a.n_ch + c) * a.BT + kl] = X[ri(k)];
@@ -78,13 +87,17 @@ __device__ __forceinline__ void pack_body(const PackArgs& a, const int c) {
     float2* Xs = (Z == bufA) ? bufB : bufA;
     for (int k = tid; k < B; k += nth) Xs[k] = r2c_post(Z, k, B, tws);
     __syncthreads();
-    const float scale = store_spectrum<PREC>(Xs, B, a.BT, a.X, RingIndex{a.BT, a.n_ch, c, a.K, a.slot}, red);
-    if (PREC != PREC_FP32 && tid == 0) a.sX[(size_t)a.slot * a.n_ch + c] = scale;
+    const float scale = store_spectrum<PREC>(Xs, B, a.BT, a.X, RingIndex{a.BT, a.n_ch, c, a.K, slot_of()}, red);
+    if (PREC != PREC_FP32 && tid == 0) a.sX[(size_t)slot_of() * a.n_ch + c] = scale;
 }
 
 template <int PREC>
 __global__ void k_pack_r2c(const PackArgs a) {
     pack_body<PREC>(a, blockIdx.x);
+}
+template <int PREC>
+__global__ void k_pack_r2c_g(const PackArgs a) {
+    pack_body<PREC, true>(a, blockIdx.x);
 }
 // the same for the closed loop (its own shared-memory carveout: see prepare_kernels)
 template <int PREC>
@@ -250,7 +263,7 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
     const int g1 = a.interleave ? gb + gt : (row1 + a.RS - 1) / a.RS;
     const int gstep = a.interleave ? a.S : 1;
     const int nit = g1 > g0 ? (g1 - g0 + gstep - 1) / gstep : 0;
-    const int ring0 = a.slot0 * a.n_src;  // ring row of r = 0
+    const int ring0 = (a.blk ? ring_slot_of(*a.blk + a.blk_add, K) : a.slot0) * a.n_src;  // ring row of r = 0
     const size_t hrow = (size_t)a.BT * St::BYTES;
     const size_t hr_bytes = (size_t)LTt * hrow;
     const unsigned char* Hb =
@@ -621,11 +634,12 @@ __device__ __forceinline__ void mac_body(const MacArgs& a, const int tile, const
         }
     }
     if (rl != 0 || !ok || *abort_flag) return;
+    float2* const part = a.blk && ((*a.blk + a.blk_add) & 1) ? a.partial_b : a.partial;
 #pragma unroll
     for (int i = 0; i < LPT; ++i) {
         const int ll = lg + i * a.NLG;
         if (ll < LTt) {
-            float2* dst = a.partial + ((size_t)split * a.n_dst + l0 + ll) * a.B + kglob;
+            float2* dst = part + ((size_t)split * a.n_dst + l0 + ll) * a.B + kglob;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) dst[v] = acc[i][v];
         }
@@ -677,7 +691,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_fdl_mac_ldg(const MacArgs a) 
     const int K = a.K, R = a.n_src * K, Rt = R - a.r_begin;
     const int r0 = a.r_begin + (int)((long long)split * Rt / a.S);
     const int r1 = a.r_begin + (int)((long long)(split + 1) * Rt / a.S);
-    const int ring0 = a.slot0 * a.n_src;
+    const int ring0 = (a.blk ? ring_slot_of(*a.blk + a.blk_add, K) : a.slot0) * a.n_src;
     const size_t hrow = (size_t)a.BT * St::BYTES;
     const unsigned char* Hb = static_cast<const unsigned char*>(a.H) + (size_t)tile * a.tile_elems * St::BYTES;
     const unsigned char* Xb = static_cast<const unsigned char*>(a.X) + (size_t)kt * R * hrow;
@@ -762,11 +776,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_fdl_mac_ldg(const MacArgs a) 
         }
     }
     if (rl != 0) return;
+    float2* const part = a.blk && ((*a.blk + a.blk_add) & 1) ? a.partial_b : a.partial;
 #pragma unroll
     for (int i = 0; i < LPT; ++i) {
         const int ll = lg + i * a.NLG;
         if (ll < LTt) {
-            float2* dst = a.partial + ((size_t)split * a.n_dst + l0 + ll) * a.B + kglob;
+            float2* dst = part + ((size_t)split * a.n_dst + l0 + ll) * a.B + kglob;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) dst[v] = acc[i][v];
         }
@@ -779,7 +794,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_fdl_mac_ldg(const MacArgs a) 
 // partition 0 of this block, sum_q H[l][q][k] * X_n[q][k] (the only term that
 // needs the new input), then the C2R IFFT (1/2B) and the last B samples
 // (overlap-save).
-template <int PREC>
+// BLK: slot and partials' parity come from the block number at a.blk
+// (host-call graph; a separate instantiation, as for pack_body).
+template <int PREC, bool BLK = false>
 __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
     using St = Store<PREC>;
     extern __shared__ float2 fsm[];
@@ -801,9 +818,12 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
     const bool corr = PREC == PREC_FP32 && a.corr_G != nullptr;
     const int n_lt = (a.n_dst + a.LT - 1) / a.LT;
     float2* hs = fsm + 4 * B;  // [n_src][B] when head_pre
+    // read where they are used (BLK = false: the arguments, as before)
+    auto partial_of = [&]() -> const float2* { return BLK && (*a.blk & 1) ? a.partial_b : a.partial; };
+    auto slot0_of = [&]() -> int { return BLK ? ring_slot_of(*a.blk, a.K) : a.slot0; };
     if (!a.early_partials) griddep_wait();
     for (int k = tid; k < B; k += nth) {
-        const float2* src = a.partial + (size_t)l * B + k;
+        const float2* src = partial_of() + (size_t)l * B + k;
         float2 tot = make_float2(0.0f, 0.0f);
         int s = 0;
         for (; s + 8 <= S; s += 8) {
@@ -842,7 +862,7 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
         if (a.head) {
             const int kt = k / a.BT, kl = k - kt * a.BT;
             const size_t hbase = ((size_t)kt * n_lt + l / a.LT) * a.tile_elems + (size_t)ll * a.BT + kl;
-            const size_t xbase = (((size_t)kt * a.K + a.slot0) * a.n_src) * a.BT + kl;
+            const size_t xbase = (((size_t)kt * a.K + slot0_of()) * a.n_src) * a.BT + kl;
             float2 hd = make_float2(0.0f, 0.0f);
             for (int q = 0; q < a.n_src; ++q) {
                 const float2 h = a.head_pre ? hs[(size_t)q * B + k] : St::load1(a.H, hbase + (size_t)q * LTt * a.BT, kl, a.BT);
@@ -854,7 +874,7 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
                     cmac(t, h, x);
                 const float sc = PREC == PREC_FP32 ? 1.0f
                                                    : __ldg(a.sH + (size_t)(l / a.LT) * a.R + q) *
-                                                         a.sX[(size_t)a.slot0 * a.n_src + q];  // see k_batch_persistent
+                                                         a.sX[(size_t)slot0_of() * a.n_src + q];  // see k_batch_persistent
                 hd.x = fmaf(sc, t.x, hd.x);
                 hd.y = fmaf(sc, t.y, hd.y);
             }
@@ -879,6 +899,10 @@ __device__ __forceinline__ void out_body(const OutArgs& a, const int l) {
 template <int PREC>
 __global__ void k_out_c2r(const OutArgs a) {
     out_body<PREC>(a, blockIdx.x);
+}
+template <int PREC>
+__global__ void k_out_c2r_g(const OutArgs a) {
+    out_body<PREC, true>(a, blockIdx.x);
 }
 template <int PREC>
 __global__ void k_out_c2r_cl(const OutArgs a) {
@@ -1066,6 +1090,9 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR(k_pack_r2c<PREC_FP32>, fft_max)
     GB_ATTR(k_pack_r2c<PREC_FP16>, fft_max)
     GB_ATTR(k_pack_r2c<PREC_BF16>, fft_max)
+    GB_ATTR(k_pack_r2c_g<PREC_FP32>, fft_max)
+    GB_ATTR(k_pack_r2c_g<PREC_FP16>, fft_max)
+    GB_ATTR(k_pack_r2c_g<PREC_BF16>, fft_max)
     GB_ATTR(k_filter_r2c<PREC_FP32>, fft_max)
     GB_ATTR(k_filter_r2c<PREC_FP16>, fft_max)
     GB_ATTR(k_filter_r2c<PREC_BF16>, fft_max)
@@ -1081,6 +1108,9 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR((k_fdl_mac_batch<PREC_BF16, lpt_for<PREC_BF16>(), 8>), mac_smem)
     GB_ATTR(k_out_c2r<PREC_FP16>, fft_max)
     GB_ATTR(k_out_c2r<PREC_BF16>, fft_max)
+    GB_ATTR(k_out_c2r_g<PREC_FP32>, fft_max)
+    GB_ATTR(k_out_c2r_g<PREC_FP16>, fft_max)
+    GB_ATTR(k_out_c2r_g<PREC_BF16>, fft_max)
     GB_ATTR((k_fdl_mac<PREC_FP32, lpt_for<PREC_FP32>(), 8>), mac_smem)
     GB_ATTR((k_fdl_mac<PREC_FP16, lpt_for<PREC_FP16>(), 8>), mac_smem)
     GB_ATTR((k_fdl_mac<PREC_BF16, lpt_for<PREC_BF16>(), 8>), mac_smem)
@@ -1103,10 +1133,17 @@ cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s, bool cl
     // kernel (measured: 0.2-1.2 us shorter steps than B/4 threads)
     const dim3 grid(a.n_ch), block(out_threads(a.B));
     const size_t sm = fft_smem_bytes(a.B);
+    if (a.blk && closed_loop) return cudaErrorInvalidValue;
     switch (prec) {
-        case PREC_FP32: return launch_pdl(closed_loop ? k_pack_r2c_cl<PREC_FP32> : k_pack_r2c<PREC_FP32>, grid, block, sm, s, a);
-        case PREC_FP16: return launch_pdl(closed_loop ? k_pack_r2c_cl<PREC_FP16> : k_pack_r2c<PREC_FP16>, grid, block, sm, s, a);
-        case PREC_BF16: return launch_pdl(closed_loop ? k_pack_r2c_cl<PREC_BF16> : k_pack_r2c<PREC_BF16>, grid, block, sm, s, a);
+        case PREC_FP32:
+            return launch_pdl(a.blk ? k_pack_r2c_g<PREC_FP32> : closed_loop ? k_pack_r2c_cl<PREC_FP32> : k_pack_r2c<PREC_FP32>,
+                              grid, block, sm, s, a);
+        case PREC_FP16:
+            return launch_pdl(a.blk ? k_pack_r2c_g<PREC_FP16> : closed_loop ? k_pack_r2c_cl<PREC_FP16> : k_pack_r2c<PREC_FP16>,
+                              grid, block, sm, s, a);
+        case PREC_BF16:
+            return launch_pdl(a.blk ? k_pack_r2c_g<PREC_BF16> : closed_loop ? k_pack_r2c_cl<PREC_BF16> : k_pack_r2c<PREC_BF16>,
+                              grid, block, sm, s, a);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1182,10 +1219,17 @@ size_t out_head_smem(int n_src, int B) {
 cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s, bool closed_loop) {
     const dim3 grid(a.n_dst), block(out_threads(a.B));
     const size_t sm = fft_smem_bytes(a.B) + (a.head && a.head_pre ? (size_t)a.n_src * a.B * sizeof(float2) : 0);
+    if (a.blk && closed_loop) return cudaErrorInvalidValue;
     switch (prec) {
-        case PREC_FP32: return launch_pdl(closed_loop ? k_out_c2r_cl<PREC_FP32> : k_out_c2r<PREC_FP32>, grid, block, sm, s, a);
-        case PREC_FP16: return launch_pdl(closed_loop ? k_out_c2r_cl<PREC_FP16> : k_out_c2r<PREC_FP16>, grid, block, sm, s, a);
-        case PREC_BF16: return launch_pdl(closed_loop ? k_out_c2r_cl<PREC_BF16> : k_out_c2r<PREC_BF16>, grid, block, sm, s, a);
+        case PREC_FP32:
+            return launch_pdl(a.blk ? k_out_c2r_g<PREC_FP32> : closed_loop ? k_out_c2r_cl<PREC_FP32> : k_out_c2r<PREC_FP32>,
+                              grid, block, sm, s, a);
+        case PREC_FP16:
+            return launch_pdl(a.blk ? k_out_c2r_g<PREC_FP16> : closed_loop ? k_out_c2r_cl<PREC_FP16> : k_out_c2r<PREC_FP16>,
+                              grid, block, sm, s, a);
+        case PREC_BF16:
+            return launch_pdl(a.blk ? k_out_c2r_g<PREC_BF16> : closed_loop ? k_out_c2r_cl<PREC_BF16> : k_out_c2r<PREC_BF16>,
+                              grid, block, sm, s, a);
         default: return cudaErrorInvalidValue;
     }
 }

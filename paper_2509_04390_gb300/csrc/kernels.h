@@ -88,6 +88,12 @@ struct MacArgs {
     // filter-spectrum rows r < keep_r are streamed with the L2 evict-last
     // policy (kept in L2 from one block to the next), the others evict-first
     int keep_r;
+    // non-null (the host-call graph, whose arguments stay the same from block
+    // to block): this MAC serves block *blk + blk_add, whose partition-0 slot
+    // replaces slot0 and whose parity picks partial (even) or partial_b (odd)
+    const long long* blk;
+    float2* partial_b;
+    int blk_add;
 };
 
 struct PackArgs {
@@ -104,6 +110,9 @@ struct PackArgs {
     // FP32 rings only: receives the slot's previous spectra, [n_kt][n_ch][BT],
     // before the push overwrites them (null: not kept)
     float2* save_old;
+    // non-null (host-call graph): the block number, whose ring slot replaces
+    // slot (launch_pack_r2c then launches the kernel's variant that reads it)
+    const long long* blk;
 };
 
 struct FilterArgs {
@@ -151,6 +160,11 @@ struct OutArgs {
     // filter spectra (constant) are loaded before waiting for the previous
     // kernel (out_head_smem)
     int head_pre;
+    // non-null (host-call graph): the block number, whose slot replaces slot0
+    // and whose parity picks partial (even) or partial_b (odd) (launch_out_c2r
+    // then launches the kernel's variant that reads it)
+    const long long* blk;
+    const float2* partial_b;
 };
 
 // Extra shared memory of an output launch that prefetches its head spectra
