@@ -1218,8 +1218,9 @@ def parse(argv=None):
                     help="non-uniform partitioning: taps beyond this many samples in partitions of this size")
     ap.add_argument("--far-block2", type=int, default=0,
                     help="with --far-block: taps beyond far-block + far-block2 in partitions of far-block2")
-    ap.add_argument("--e2e-steps", type=int, default=5000)
-    ap.add_argument("--paced-blocks", type=int, default=1000)
+    # latency percentiles over 10,000 blocks each (the paced ones take 10,000 block periods, 53 s at B = 256)
+    ap.add_argument("--e2e-steps", type=int, default=10000)
+    ap.add_argument("--paced-blocks", type=int, default=10000)
     ap.add_argument("--e2e-chunk", type=int, default=64, help="blocks per conv_process_blocks call in the e2e figure")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
