@@ -208,25 +208,31 @@ int afc_set_paths(conv_engine* e, const float* f, long long taps_fb);
  * the background.  Needs conv_set_filters (CONV_E_STATE otherwise). */
 int conv_process_block(conv_engine* e, const float* in, float* out);
 
-/* How conv_process_block enqueues its work.  The graph form is one CUDA
- * graph launch (pack -> output, and the next block's tail MAC beside the
- * output), captured from the same kernels and launch shapes as the stream
- * path on first use and updated with each block's arguments; the call returns
- * when the graph's output node is done.  The stream form is three launches
- * and their events, and starts the pack while the previous block's tail MAC
- * may still run (the next launch of the graph waits for the previous one,
- * tail included).  Both give the same bits.
+/* How the blocking host calls conv_process_block and afc_process_block
+ * enqueue their work.  The graph form is one CUDA graph launch per call,
+ * captured from the same kernels and launch shapes as the stream form on
+ * first use.  conv_process_block's graph: pack -> output, and the next
+ * block's tail MAC beside the output.  afc_process_block's (the static
+ * canceller): pack -> output + push into the canceller's ring, the next
+ * block's synthesis tail beside them, then the prediction for the next block
+ * and the canceller's next tail.  The kernels read the block number from
+ * device memory, which the graph's last node advances, so the arguments stay
+ * the same from block to block.  The call returns when the graph's output is
+ * on the host.  The stream form is the launches and their events, and starts
+ * the pack while the previous block's tails may still run (the next launch
+ * of a graph waits for the previous one, tails included).  Both forms give
+ * the same bits.
  *   mode 1 (default): the graph when at least half a block period has
  *          passed since the previous call started (real-time use, one call
- *          per block period: the previous tail has finished), else the
+ *          per block period: the previous tails have finished), else the
  *          stream form (back-to-back calls);
  *   mode 2: the graph for every call;
- *   mode 0: the stream form for every call (drops the graph).
- * The graph is rebuilt when the launch shapes change (a new plan).  Engines
+ *   mode 0: the stream form for every call (drops the graphs).
+ * A graph is rebuilt when the launch shapes change (a new plan).  Engines
  * with a far block, an adaptive canceller, the n_f = 3 n_x form, kernel
  * timing (conv_profile_enable) or batch membership always take the stream
  * form.  CONV_E_INVAL for another mode.  conv_get_host_graph reports the mode
- * and how many blocks went through the graph (never reset). */
+ * and how many blocks went through a graph (never reset). */
 int conv_set_host_graph(conv_engine* e, int mode);
 int conv_get_host_graph(const conv_engine* e, int* mode, long long* graph_blocks);
 

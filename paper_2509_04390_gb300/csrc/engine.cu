@@ -385,40 +385,56 @@ size_t part_bytes(const MacPlan& p, int prec, size_t win_floats) {
 
 void gbconv::set_last_error_message(const char* msg) { g_err = msg ? msg : ""; }
 
-// conv_process_block as one CUDA graph: the pack of block n, its output
-// (programmatic edge, as on a stream) and an event recorded after the output,
-// with block n+1's tail MAC beside the output, and last a node that advances
-// the block number in device memory.  Captured once from the same launchers as
-// the stream path.  The kernels take the ring slot and the partials' parity
-// from that device word, so the nodes' arguments stay the same from block to
-// block and a call is one graph launch.  The next launch of the graph starts
-// after the whole previous one, tail included, which orders block n+1's
-// output after its tail.
-struct HostGraphKey {
-    int prec = -1, B = 0, n_src = 0, n_dst = 0, ctas = 0, nw = 0, direct = 0, S = 0, head_pre = 0;
+// The blocking host calls as CUDA graphs.  conv_process_block's graph holds
+// the pack of block n, its output (programmatic edge, as on a stream) and an
+// event recorded after the output, with block n+1's tail MAC beside the
+// output.  afc_process_block's adds the closed loop: the output also pushes
+// into the canceller's ring, then come the prediction c_n = F_hat * l_n and the
+// canceller's tail for block n+1.  Both end with a node that advances the
+// block number in device memory.  They are captured once from the same
+// launchers as the stream path.  The kernels take ring slots and the
+// partials' parity from that device word, so the nodes' arguments stay the
+// same from block to block and a call is one graph launch.  A launch starts
+// after the whole previous one, tails included, which orders block n+1's
+// outputs after its tails.
+struct HostGraphKey {  // launch shapes a captured graph depends on
+    int prec = -1, B = 0, head_pre = 0;
+    int n_src = 0, n_dst = 0, ctas = 0, nw = 0, direct = 0, S = 0;  // the synthesis MAC
     size_t smem = 0;
+    int f_src = 0, f_dst = 0, f_ctas = 0, f_nw = 0, f_direct = 0, f_S = 0;  // the canceller's (closed loop)
+    size_t f_smem = 0;
     bool operator==(const HostGraphKey& o) const {
-        return prec == o.prec && B == o.B && n_src == o.n_src && n_dst == o.n_dst && ctas == o.ctas && nw == o.nw &&
-               direct == o.direct && S == o.S && head_pre == o.head_pre && smem == o.smem;
+        return prec == o.prec && B == o.B && head_pre == o.head_pre && n_src == o.n_src && n_dst == o.n_dst &&
+               ctas == o.ctas && nw == o.nw && direct == o.direct && S == o.S && smem == o.smem &&
+               f_src == o.f_src && f_dst == o.f_dst && f_ctas == o.f_ctas && f_nw == o.f_nw &&
+               f_direct == o.f_direct && f_S == o.f_S && f_smem == o.f_smem;
     }
+};
+
+enum { GN_PACK, GN_OUT, GN_TAIL, GN_FOUT, GN_FTAIL, GN_COUNT };  // kernel nodes of a graph
+
+struct HostGraphForm {  // one captured graph
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    cudaGraphNode_t node[GN_COUNT] = {};
+    cudaKernelNodeParams prm[GN_COUNT] = {};
+    HostGraphKey key;
+    // the nodes' current arguments: pack, output (and the push into the
+    // canceller's ring), tail; the canceller's output and tail
+    PackArgs pa{}, pb{};
+    OutArgs oa{}, of{};
+    MacArgs ma{}, mf{};
 };
 
 struct HostGraph {
     int mode = 1;  // 0 off, 1 when the previous tail has finished, 2 always
-    bool live = false;  // the engine's last block went through the graph (its tail is not in syn.ev_tail)
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t x = nullptr;
-    cudaGraphNode_t pack = nullptr, out = nullptr, tail = nullptr;
-    cudaKernelNodeParams pp{}, po{}, pt{};
-    PackArgs pa{};  // the nodes' current arguments
-    OutArgs oa{};
-    MacArgs ma{};
-    HostGraphKey key;
-    cudaStream_t cs[2] = {nullptr, nullptr};  // capture streams
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_out = nullptr;
-    long long blocks = 0;  // blocks that went through the graph
-    bool called = false;   // conv_process_block ran before (last_call is set)
-    std::chrono::steady_clock::time_point last_call{};  // start of the previous conv_process_block
+    bool live = false;  // the engine's last block went through a graph (its tails are not in the ev_tail events)
+    HostGraphForm plain, loop;  // conv_process_block's, afc_process_block's
+    cudaStream_t cs[3] = {nullptr, nullptr, nullptr};  // capture streams
+    cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr}, ev_out = nullptr;
+    long long blocks = 0;  // blocks that went through a graph
+    bool called = false;   // a host call ran before (last_call is set)
+    std::chrono::steady_clock::time_point last_call{};  // start of the previous host call
 };
 
 struct conv_engine {
@@ -446,7 +462,7 @@ struct conv_engine {
     float2* tw3 = nullptr;
     float *d_e = nullptr, *d_c = nullptr;
     float *h_in = nullptr, *h_out = nullptr, *h_e = nullptr;
-    float *m_in = nullptr, *m_out = nullptr;  // device addresses of h_in / h_out (mapped pinned memory)
+    float *m_in = nullptr, *m_out = nullptr, *m_e = nullptr;  // device addresses of h_in / h_out / h_e (mapped pinned memory)
     int* h_err = nullptr;
     int* d_err = nullptr;
     TileOverride tiling;  // applies to the synthesis convolution
@@ -996,38 +1012,41 @@ int enqueue_block(conv_engine* e, const float* d_in, float* d_out, cudaStream_t 
     return CONV_OK;
 }
 
-void host_graph_free(HostGraph& G) {
-    if (G.x) cudaGraphExecDestroy(G.x);
-    if (G.g) cudaGraphDestroy(G.g);
-    G.x = nullptr;
-    G.g = nullptr;
-    G.pack = G.out = G.tail = nullptr;
-    G.key = HostGraphKey{};
+void host_graph_free(HostGraphForm& F) {
+    if (F.x) cudaGraphExecDestroy(F.x);
+    if (F.g) cudaGraphDestroy(F.g);
+    F = HostGraphForm{};
 }
 
 void host_graph_destroy(HostGraph& G) {
-    host_graph_free(G);
-    for (int i = 0; i < 2; ++i)
+    host_graph_free(G.plain);
+    host_graph_free(G.loop);
+    for (int i = 0; i < 3; ++i)
         if (G.cs[i]) cudaStreamDestroy(G.cs[i]);
-    if (G.ev_fork) cudaEventDestroy(G.ev_fork);
-    if (G.ev_join) cudaEventDestroy(G.ev_join);
+    for (int i = 0; i < 2; ++i) {
+        if (G.ev_fork[i]) cudaEventDestroy(G.ev_fork[i]);
+        if (G.ev_join[i]) cudaEventDestroy(G.ev_join[i]);
+    }
     if (G.ev_out) cudaEventDestroy(G.ev_out);
-    G.cs[0] = G.cs[1] = nullptr;
-    G.ev_fork = G.ev_join = G.ev_out = nullptr;
+    const int mode = G.mode;
+    G = HostGraph{};
+    G.mode = mode;
 }
 
-// Before a block goes through a stream again: the graph's last tail (block
-// nblk's) is complete once the engine's stream has passed that graph launch.
+// Before a block goes through a stream again: the last graph's tails (block
+// nblk's) are complete once the engine's stream has passed that graph launch.
 int host_graph_settle(conv_engine* e) {
     if (!e->hg.live) return CONV_OK;
     CK(cudaEventRecord(e->syn.ev_tail[e->nblk & 1], e->stream));
+    if (e->fb.allocated) CK(cudaEventRecord(e->fb.ev_tail[e->nblk & 1], e->stream));
     e->hg.live = false;
     return CONV_OK;
 }
 
-bool host_graph_eligible(const conv_engine* e) {
+// loop: afc_process_block's graph (the static canceller), else conv_process_block's.
+bool host_graph_eligible(const conv_engine* e, bool loop) {
     return e->hg.mode > 0 && !e->reuse && !e->far && !e->prof && !e->adapt && !e->inject && e->in_batches == 0 &&
-           !e->io_in_stride && !e->io_out_stride;
+           !e->io_in_stride && !e->io_out_stride && (!loop || e->fb.ready);
 }
 
 // The graph pays off when the previous block's tail has finished, as in
@@ -1041,22 +1060,34 @@ bool host_graph_now(conv_engine* e, std::chrono::steady_clock::time_point t0) {
     HostGraph& G = e->hg;
     const double gap_s = std::chrono::duration<double>(t0 - G.last_call).count();
     G.last_call = t0;
-    return G.mode == 2 || !G.called || gap_s >= 0.5 * (double)e->B / e->fs;
+    const bool first = !G.called;
+    G.called = true;
+    return G.mode == 2 || first || gap_s >= 0.5 * (double)e->B / e->fs;
 }
 
-HostGraphKey host_graph_key(const conv_engine* e) {
+HostGraphKey host_graph_key(const conv_engine* e, bool loop) {
     const MacPlan& p = e->syn.plan;
     HostGraphKey k;
     k.prec = e->prec;
     k.B = e->B;
+    k.head_pre = out_head_smem(e->syn.n_src, e->B) > 0 ? 1 : 0;
     k.n_src = e->syn.n_src;
     k.n_dst = e->syn.n_dst;
     k.ctas = p.ctas;
     k.nw = p.nw;
     k.direct = p.direct;
     k.S = p.S;
-    k.head_pre = out_head_smem(e->syn.n_src, e->B) > 0 ? 1 : 0;
     k.smem = p.smem;
+    if (loop) {
+        const MacPlan& f = e->fb.plan;
+        k.f_src = e->fb.n_src;
+        k.f_dst = e->fb.n_dst;
+        k.f_ctas = f.ctas;
+        k.f_nw = f.nw;
+        k.f_direct = f.direct;
+        k.f_S = f.S;
+        k.f_smem = f.smem;
+    }
     return k;
 }
 
@@ -1071,60 +1102,89 @@ int captured_node(cudaStream_t s, cudaGraphNode_t* node) {
     return CONV_OK;
 }
 
-int host_graph_capture(conv_engine* e, const PackArgs& pa, const OutArgs& oa, const MacArgs* ma) {
+// Stream `to` continues after what stream `from` has captured so far.
+int capture_fork(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+    CK(cudaEventRecord(ev, from));
+    CK(cudaStreamWaitEvent(to, ev, 0));
+    return CONV_OK;
+}
+
+// Captures one block of the form's work on the capture streams, with the
+// form's stored arguments.
+int host_graph_capture(conv_engine* e, bool loop, HostGraphForm& F) {
     HostGraph& G = e->hg;
-    cudaStream_t c0 = G.cs[0], c1 = G.cs[1];
-    CK(launch_pack_r2c(e->prec, pa, c0));
-    if (int rc = captured_node(c0, &G.pack)) return rc;
-    CK(cudaEventRecord(G.ev_fork, c0));
-    CK(cudaStreamWaitEvent(c1, G.ev_fork, 0));
-    CK(launch_out_c2r(e->prec, oa, c0));
-    if (int rc = captured_node(c0, &G.out)) return rc;
-    CK(cudaEventRecordWithFlags(G.ev_out, c0, cudaEventRecordExternal));
-    if (ma) {
-        CK(launch_fdl_mac(e->prec, e->syn.plan, *ma, c1, false));
-        if (int rc = captured_node(c1, &G.tail)) return rc;
+    cudaStream_t c0 = G.cs[0], c1 = G.cs[1], c2 = G.cs[2];
+    int rc;
+    CK(launch_pack_r2c(e->prec, F.pa, c0, loop));
+    if ((rc = captured_node(c0, &F.node[GN_PACK]))) return rc;
+    if ((rc = capture_fork(c0, c1, G.ev_fork[0]))) return rc;
+    if (e->syn.plan.S > 0) {  // else K = 1: no tail
+        CK(launch_fdl_mac(e->prec, e->syn.plan, F.ma, c1, false));
+        if ((rc = captured_node(c1, &F.node[GN_TAIL]))) return rc;
     }
-    CK(cudaEventRecord(G.ev_join, c1));
-    CK(cudaStreamWaitEvent(c0, G.ev_join, 0));
-    k_blk_advance<<<1, 1, 0, c0>>>(e->d_blk);  // after the output and the tail have read it
+    CK(loop ? launch_out_push(e->prec, F.oa, F.pb, c0) : launch_out_c2r(e->prec, F.oa, c0));
+    if ((rc = captured_node(c0, &F.node[GN_OUT]))) return rc;
+    CK(cudaEventRecordWithFlags(G.ev_out, c0, cudaEventRecordExternal));  // the call waits for this
+    if (loop) {
+        if ((rc = capture_fork(c0, c2, G.ev_fork[1]))) return rc;
+        if (e->fb.plan.S > 0) {
+            CK(launch_fdl_mac(e->prec, e->fb.plan, F.mf, c2, false));
+            if ((rc = captured_node(c2, &F.node[GN_FTAIL]))) return rc;
+        }
+        CK(launch_out_c2r(e->prec, F.of, c0, true));
+        if ((rc = captured_node(c0, &F.node[GN_FOUT]))) return rc;
+        if ((rc = capture_fork(c2, c0, G.ev_join[1]))) return rc;
+    }
+    if ((rc = capture_fork(c1, c0, G.ev_join[0]))) return rc;
+    k_blk_advance<<<1, 1, 0, c0>>>(e->d_blk);  // after the outputs and the tails have read it
     CK(cudaGetLastError());
     return CONV_OK;
 }
 
-int host_graph_build(conv_engine* e, const PackArgs& pa, const OutArgs& oa, const MacArgs* ma) {
+void copy_args(HostGraphForm& to, const HostGraphForm& from) {
+    std::memcpy(&to.pa, &from.pa, sizeof to.pa);
+    std::memcpy(&to.pb, &from.pb, sizeof to.pb);
+    std::memcpy(&to.oa, &from.oa, sizeof to.oa);
+    std::memcpy(&to.of, &from.of, sizeof to.of);
+    std::memcpy(&to.ma, &from.ma, sizeof to.ma);
+    std::memcpy(&to.mf, &from.mf, sizeof to.mf);
+}
+
+int host_graph_build(conv_engine* e, bool loop, HostGraphForm& F, const HostGraphForm& now) {
     HostGraph& G = e->hg;
-    host_graph_free(G);
+    host_graph_free(F);
     if (!G.cs[0]) {
-        for (int i = 0; i < 2; ++i) CK(cudaStreamCreateWithFlags(&G.cs[i], cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&G.ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&G.ev_join, cudaEventDisableTiming));
+        for (int i = 0; i < 3; ++i) CK(cudaStreamCreateWithFlags(&G.cs[i], cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            CK(cudaEventCreateWithFlags(&G.ev_fork[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&G.ev_join[i], cudaEventDisableTiming));
+        }
         CK(cudaEventCreateWithFlags(&G.ev_out, cudaEventDisableTiming));
     }
+    copy_args(F, now);
     CK(cudaStreamBeginCapture(G.cs[0], cudaStreamCaptureModeThreadLocal));
-    const int rc = host_graph_capture(e, pa, oa, ma);
+    const int rc = host_graph_capture(e, loop, F);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(G.cs[0], &g);
     if (rc || ec != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
-        G.pack = G.out = G.tail = nullptr;
+        host_graph_free(F);
         cudaGetLastError();
         return rc ? rc : set_err(CONV_E_CUDA, "graph capture: %s", cudaGetErrorString(ec));
     }
-    G.g = g;
-    CK(cudaGraphInstantiate(&G.x, G.g, 0));
-    CK(cudaGraphKernelNodeGetParams(G.pack, &G.pp));
-    CK(cudaGraphKernelNodeGetParams(G.out, &G.po));
-    if (G.tail) CK(cudaGraphKernelNodeGetParams(G.tail, &G.pt));
-    G.key = host_graph_key(e);
+    F.g = g;
+    CK(cudaGraphInstantiate(&F.x, F.g, 0));
+    for (int i = 0; i < GN_COUNT; ++i)
+        if (F.node[i]) CK(cudaGraphKernelNodeGetParams(F.node[i], &F.prm[i]));
+    F.key = host_graph_key(e, loop);  // last: a failed build leaves no key that matches
     return CONV_OK;
 }
 
-int set_node_args(cudaGraphExec_t x, cudaGraphNode_t node, cudaKernelNodeParams& p, const void* args) {
-    void* argv[1] = {const_cast<void*>(args)};
-    p.kernelParams = argv;
-    const cudaError_t r = cudaGraphExecKernelNodeSetParams(x, node, &p);
-    p.kernelParams = nullptr;
+int set_node_args(HostGraphForm& F, int i, void* a0, void* a1 = nullptr) {
+    void* argv[2] = {a0, a1};
+    F.prm[i].kernelParams = argv;
+    const cudaError_t r = cudaGraphExecKernelNodeSetParams(F.x, F.node[i], &F.prm[i]);
+    F.prm[i].kernelParams = nullptr;
     CK(r);
     return CONV_OK;
 }
@@ -1139,47 +1199,67 @@ bool args_changed(T& stored, const T& now) {
     return true;
 }
 
-// One block of conv_process_block through the graph (the stream path is
-// enqueue_block with the mapped host buffers).
-int host_graph_block(conv_engine* e) {
-    HostGraph& G = e->hg;
+// The arguments of block 0, with the block number read from d_blk instead.
+void host_graph_args(conv_engine* e, bool loop, HostGraphForm& a) {
     Part& P = e->syn;
+    Part& Q = e->fb;
+    long long* blk = e->d_blk;
+    a.pa = pack_args(e, P, 0, e->m_in, e->B, loop ? e->d_c : nullptr, loop ? e->m_e : nullptr);
+    a.pa.blk = blk;
+    a.oa = out_args(e, P, 0, e->m_out);
+    a.oa.blk = blk;
+    a.oa.partial_b = P.partial[1];
+    if (P.plan.S > 0) {
+        a.ma = tail_args(e, P, 0);
+        a.ma.blk = blk;
+        a.ma.blk_add = 1;  // the tail of the next block
+        a.ma.partial_b = P.partial[1];
+    }
+    if (!loop) return;
+    a.pb = pack_args(e, Q, 0, e->m_out, e->B, nullptr, nullptr);  // the output pushed into the canceller's ring
+    a.pb.blk = blk;
+    a.of = out_args(e, Q, 0, e->d_c);  // the prediction for the next block
+    a.of.blk = blk;
+    a.of.partial_b = Q.partial[1];
+    if (Q.plan.S > 0) {
+        a.mf = tail_args(e, Q, 0);
+        a.mf.blk = blk;
+        a.mf.blk_add = 1;
+        a.mf.partial_b = Q.partial[1];
+    }
+}
+
+// One block of conv_process_block (loop = false) or afc_process_block
+// (loop = true) through its graph; the stream paths are enqueue_block and
+// enqueue_afc_synthesis + enqueue_afc_prediction with the mapped host buffers.
+int host_graph_block(conv_engine* e, bool loop) {
+    HostGraph& G = e->hg;
+    HostGraphForm& F = loop ? G.loop : G.plain;
     const long long n = e->nblk;
     int rc;
     if (!e->d_blk && (rc = dev_alloc(e, &e->d_blk, sizeof(long long)))) return rc;
-    // the arguments of block 0, with the block number read from d_blk instead
-    PackArgs pa = pack_args(e, P, 0, e->m_in, e->B, nullptr, nullptr);
-    pa.blk = e->d_blk;
-    OutArgs oa = out_args(e, P, 0, e->m_out);
-    oa.blk = e->d_blk;
-    oa.partial_b = P.partial[1];
-    const bool tail = P.plan.S > 0;
-    MacArgs ma{};
-    if (tail) {
-        ma = tail_args(e, P, 0);
-        ma.blk = e->d_blk;
-        ma.blk_add = 1;  // the tail of the next block
-        ma.partial_b = P.partial[1];
-    }
-    if (!G.x || !(G.key == host_graph_key(e))) {
-        if ((rc = host_graph_build(e, pa, oa, tail ? &ma : nullptr))) return rc;
-        std::memcpy(&G.pa, &pa, sizeof pa);
-        std::memcpy(&G.oa, &oa, sizeof oa);
-        std::memcpy(&G.ma, &ma, sizeof ma);
+    HostGraphForm now;
+    host_graph_args(e, loop, now);
+    if (!F.x || !(F.key == host_graph_key(e, loop))) {
+        if ((rc = host_graph_build(e, loop, F, now))) return rc;
     } else {  // a new L2 budget, new buffers after a replan, ...
-        if (args_changed(G.pa, pa) && (rc = set_node_args(G.x, G.pack, G.pp, &G.pa))) return rc;
-        if (args_changed(G.oa, oa) && (rc = set_node_args(G.x, G.out, G.po, &G.oa))) return rc;
-        if (tail && args_changed(G.ma, ma) && (rc = set_node_args(G.x, G.tail, G.pt, &G.ma))) return rc;
+        const bool out_new = args_changed(F.oa, now.oa) | args_changed(F.pb, now.pb);
+        if (args_changed(F.pa, now.pa) && (rc = set_node_args(F, GN_PACK, &F.pa))) return rc;
+        if (out_new && (rc = set_node_args(F, GN_OUT, &F.oa, loop ? &F.pb : nullptr))) return rc;
+        if (F.node[GN_TAIL] && args_changed(F.ma, now.ma) && (rc = set_node_args(F, GN_TAIL, &F.ma))) return rc;
+        if (F.node[GN_FOUT] && args_changed(F.of, now.of) && (rc = set_node_args(F, GN_FOUT, &F.of))) return rc;
+        if (F.node[GN_FTAIL] && args_changed(F.mf, now.mf) && (rc = set_node_args(F, GN_FTAIL, &F.mf))) return rc;
     }
     if ((rc = stream_handoff(e, e->stream))) return rc;
     if (!G.live) {
-        // block n's tail ran on a background stream (or is the reset's zero
+        // block n's tails ran on background streams (or are the reset's zero
         // partials), and the host kept the block number
-        CK(cudaStreamWaitEvent(e->stream, P.ev_tail[n & 1], 0));
+        CK(cudaStreamWaitEvent(e->stream, e->syn.ev_tail[n & 1], 0));
+        if (loop) CK(cudaStreamWaitEvent(e->stream, e->fb.ev_tail[n & 1], 0));
         k_blk_set<<<1, 1, 0, e->stream>>>(e->d_blk, n);
         CK(cudaGetLastError());
     }
-    CK(cudaGraphLaunch(G.x, e->stream));
+    CK(cudaGraphLaunch(F.x, e->stream));
     G.live = true;
     ++G.blocks;
     ++e->nblk;
@@ -1511,7 +1591,8 @@ int create_impl(conv_engine* e, double fs, int block, int n_in, int n_out, long 
     CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_out), (size_t)n_out * block * sizeof(float), cudaHostAllocMapped));
     CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->m_in), e->h_in, 0));
     CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->m_out), e->h_out, 0));
-    CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_e), (size_t)n_in * block * sizeof(float), cudaHostAllocDefault));
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_e), (size_t)n_in * block * sizeof(float), cudaHostAllocMapped));
+    CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->m_e), e->h_e, 0));
     CK(cudaHostAlloc(reinterpret_cast<void**>(&e->h_err), sizeof(int), cudaHostAllocMapped));
     *e->h_err = 0;
     CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->d_err), e->h_err, 0));
@@ -1756,11 +1837,9 @@ int conv_process_block(conv_engine* e, const float* in, float* out) {
     // output kernel writes there (over the coherent CPU-GPU link): no copy
     // launches per block (measured: p50 call latency 38.8 -> 34.7 us)
     int rc;
-    const bool graph = host_graph_eligible(e) && host_graph_now(e, t0);
-    e->hg.called = true;
-    if (graph) {
+    if (host_graph_eligible(e, false) && host_graph_now(e, t0)) {
         // one graph launch instead of three launches and five event calls
-        if ((rc = host_graph_block(e))) return rc;
+        if ((rc = host_graph_block(e, false))) return rc;
         CK(cudaEventSynchronize(e->hg.ev_out));  // the next block's tail keeps running
     } else {
         if ((rc = enqueue_block(e, e->m_in, e->m_out, e->stream))) return rc;
@@ -1828,14 +1907,20 @@ int afc_process_block(conv_engine* e, const float* mic, float* out, float* e_or_
     const size_t ib = (size_t)e->n_in * e->B * sizeof(float), ob = (size_t)e->n_out * e->B * sizeof(float);
     const bool want_e = e_or_null != nullptr || e->guard > 0.0;
     std::memcpy(e->h_in, mic, ib);
-    // microphone block in and loudspeaker block out through mapped pinned host memory
-    int rc = enqueue_afc_synthesis(e, e->m_in, e->m_out, e->d_e, e->stream);
-    if (rc) return rc;
-    if (want_e) CK(cudaMemcpyAsync(e->h_e, e->d_e, ib, cudaMemcpyDeviceToHost, e->stream));
-    CK(cudaEventRecord(e->ev_done, e->stream));
-    // the prediction for the next block runs while this block's output is read on the host
-    if ((rc = enqueue_afc_prediction(e, e->stream))) return rc;
-    CK(cudaEventSynchronize(e->ev_done));
+    int rc;
+    if (host_graph_eligible(e, true) && host_graph_now(e, t0)) {
+        // one graph launch; the pack writes e straight into h_e
+        if ((rc = host_graph_block(e, true))) return rc;
+        CK(cudaEventSynchronize(e->hg.ev_out));  // the prediction and the tails keep running
+    } else {
+        // microphone block in and loudspeaker block out through mapped pinned host memory
+        if ((rc = enqueue_afc_synthesis(e, e->m_in, e->m_out, e->d_e, e->stream))) return rc;
+        if (want_e) CK(cudaMemcpyAsync(e->h_e, e->d_e, ib, cudaMemcpyDeviceToHost, e->stream));
+        CK(cudaEventRecord(e->ev_done, e->stream));
+        // the prediction for the next block runs while this block's output is read on the host
+        if ((rc = enqueue_afc_prediction(e, e->stream))) return rc;
+        CK(cudaEventSynchronize(e->ev_done));
+    }
     if ((rc = check_dev_err(e))) return rc;
     if (e->guard > 0.0) {
         double ss = 0.0;
@@ -1989,7 +2074,8 @@ int conv_set_host_graph(conv_engine* e, int mode) {
         int rc;
         if ((rc = host_graph_settle(e))) return rc;
         CK(cudaStreamSynchronize(e->stream));
-        host_graph_free(e->hg);
+        host_graph_free(e->hg.plain);
+        host_graph_free(e->hg.loop);
     }
     return CONV_OK;
 }

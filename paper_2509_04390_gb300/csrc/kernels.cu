@@ -104,6 +104,10 @@ template <int PREC>
 __global__ void k_pack_r2c_cl(const PackArgs a) {
     pack_body<PREC>(a, blockIdx.x);
 }
+template <int PREC>
+__global__ void k_pack_r2c_cl_g(const PackArgs a) {
+    pack_body<PREC, true>(a, blockIdx.x);
+}
 
 // --------------------------------------------------- filter partitions R2C
 // One CTA per (l, q, p): sub-filter h_lq[pB, pB+B) zero-padded to 2B, R2C,
@@ -908,6 +912,10 @@ template <int PREC>
 __global__ void k_out_c2r_cl(const OutArgs a) {
     out_body<PREC>(a, blockIdx.x);
 }
+template <int PREC>
+__global__ void k_out_c2r_cl_g(const OutArgs a) {
+    out_body<PREC, true>(a, blockIdx.x);
+}
 
 // Output of one convolution, then the pack + R2C of the same samples into a
 // second convolution's delay line (the synthesis output is the feedback
@@ -918,6 +926,12 @@ __global__ void k_out_push(const OutArgs a, const PackArgs b) {
     out_body<PREC>(a, blockIdx.x);
     __syncthreads();
     pack_body<PREC>(b, blockIdx.x);
+}
+template <int PREC>
+__global__ void k_out_push_g(const OutArgs a, const PackArgs b) {
+    out_body<PREC, true>(a, blockIdx.x);
+    __syncthreads();
+    pack_body<PREC, true>(b, blockIdx.x);
 }
 
 // Batched pack and output: CTA i serves channel refs[i].idx of the session
@@ -1087,6 +1101,15 @@ cudaError_t prepare_kernels(size_t mac_smem) {
     GB_ATTR_DEFAULT(k_out_c2r_cl<PREC_FP32>, fft_max)
     GB_ATTR_DEFAULT(k_out_c2r_cl<PREC_FP16>, fft_max)
     GB_ATTR_DEFAULT(k_out_c2r_cl<PREC_BF16>, fft_max)
+    GB_ATTR_DEFAULT(k_out_push_g<PREC_FP32>, fft_max)
+    GB_ATTR_DEFAULT(k_out_push_g<PREC_FP16>, fft_max)
+    GB_ATTR_DEFAULT(k_out_push_g<PREC_BF16>, fft_max)
+    GB_ATTR_DEFAULT(k_pack_r2c_cl_g<PREC_FP32>, fft_max)
+    GB_ATTR_DEFAULT(k_pack_r2c_cl_g<PREC_FP16>, fft_max)
+    GB_ATTR_DEFAULT(k_pack_r2c_cl_g<PREC_BF16>, fft_max)
+    GB_ATTR_DEFAULT(k_out_c2r_cl_g<PREC_FP32>, fft_max)
+    GB_ATTR_DEFAULT(k_out_c2r_cl_g<PREC_FP16>, fft_max)
+    GB_ATTR_DEFAULT(k_out_c2r_cl_g<PREC_BF16>, fft_max)
     GB_ATTR(k_pack_r2c<PREC_FP32>, fft_max)
     GB_ATTR(k_pack_r2c<PREC_FP16>, fft_max)
     GB_ATTR(k_pack_r2c<PREC_BF16>, fft_max)
@@ -1133,16 +1156,18 @@ cudaError_t launch_pack_r2c(int prec, const PackArgs& a, cudaStream_t s, bool cl
     // kernel (measured: 0.2-1.2 us shorter steps than B/4 threads)
     const dim3 grid(a.n_ch), block(out_threads(a.B));
     const size_t sm = fft_smem_bytes(a.B);
-    if (a.blk && closed_loop) return cudaErrorInvalidValue;
     switch (prec) {
         case PREC_FP32:
-            return launch_pdl(a.blk ? k_pack_r2c_g<PREC_FP32> : closed_loop ? k_pack_r2c_cl<PREC_FP32> : k_pack_r2c<PREC_FP32>,
+            return launch_pdl(a.blk ? (closed_loop ? k_pack_r2c_cl_g<PREC_FP32> : k_pack_r2c_g<PREC_FP32>)
+                              : closed_loop ? k_pack_r2c_cl<PREC_FP32> : k_pack_r2c<PREC_FP32>,
                               grid, block, sm, s, a);
         case PREC_FP16:
-            return launch_pdl(a.blk ? k_pack_r2c_g<PREC_FP16> : closed_loop ? k_pack_r2c_cl<PREC_FP16> : k_pack_r2c<PREC_FP16>,
+            return launch_pdl(a.blk ? (closed_loop ? k_pack_r2c_cl_g<PREC_FP16> : k_pack_r2c_g<PREC_FP16>)
+                              : closed_loop ? k_pack_r2c_cl<PREC_FP16> : k_pack_r2c<PREC_FP16>,
                               grid, block, sm, s, a);
         case PREC_BF16:
-            return launch_pdl(a.blk ? k_pack_r2c_g<PREC_BF16> : closed_loop ? k_pack_r2c_cl<PREC_BF16> : k_pack_r2c<PREC_BF16>,
+            return launch_pdl(a.blk ? (closed_loop ? k_pack_r2c_cl_g<PREC_BF16> : k_pack_r2c_g<PREC_BF16>)
+                              : closed_loop ? k_pack_r2c_cl<PREC_BF16> : k_pack_r2c<PREC_BF16>,
                               grid, block, sm, s, a);
         default: return cudaErrorInvalidValue;
     }
@@ -1219,16 +1244,18 @@ size_t out_head_smem(int n_src, int B) {
 cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s, bool closed_loop) {
     const dim3 grid(a.n_dst), block(out_threads(a.B));
     const size_t sm = fft_smem_bytes(a.B) + (a.head && a.head_pre ? (size_t)a.n_src * a.B * sizeof(float2) : 0);
-    if (a.blk && closed_loop) return cudaErrorInvalidValue;
     switch (prec) {
         case PREC_FP32:
-            return launch_pdl(a.blk ? k_out_c2r_g<PREC_FP32> : closed_loop ? k_out_c2r_cl<PREC_FP32> : k_out_c2r<PREC_FP32>,
+            return launch_pdl(a.blk ? (closed_loop ? k_out_c2r_cl_g<PREC_FP32> : k_out_c2r_g<PREC_FP32>)
+                              : closed_loop ? k_out_c2r_cl<PREC_FP32> : k_out_c2r<PREC_FP32>,
                               grid, block, sm, s, a);
         case PREC_FP16:
-            return launch_pdl(a.blk ? k_out_c2r_g<PREC_FP16> : closed_loop ? k_out_c2r_cl<PREC_FP16> : k_out_c2r<PREC_FP16>,
+            return launch_pdl(a.blk ? (closed_loop ? k_out_c2r_cl_g<PREC_FP16> : k_out_c2r_g<PREC_FP16>)
+                              : closed_loop ? k_out_c2r_cl<PREC_FP16> : k_out_c2r<PREC_FP16>,
                               grid, block, sm, s, a);
         case PREC_BF16:
-            return launch_pdl(a.blk ? k_out_c2r_g<PREC_BF16> : closed_loop ? k_out_c2r_cl<PREC_BF16> : k_out_c2r<PREC_BF16>,
+            return launch_pdl(a.blk ? (closed_loop ? k_out_c2r_cl_g<PREC_BF16> : k_out_c2r_g<PREC_BF16>)
+                              : closed_loop ? k_out_c2r_cl<PREC_BF16> : k_out_c2r<PREC_BF16>,
                               grid, block, sm, s, a);
         default: return cudaErrorInvalidValue;
     }
@@ -1250,13 +1277,16 @@ cudaError_t launch_pdl_n(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStre
 }
 
 cudaError_t launch_out_push(int prec, const OutArgs& a, const PackArgs& b, cudaStream_t s) {
-    if (a.n_dst != b.n_ch || a.B != b.B) return cudaErrorInvalidValue;
+    if (a.n_dst != b.n_ch || a.B != b.B || !a.blk != !b.blk) return cudaErrorInvalidValue;
     const dim3 grid(a.n_dst), block(out_threads(a.B));
     const size_t sm = fft_smem_bytes(a.B) + (a.head && a.head_pre ? (size_t)a.n_src * a.B * sizeof(float2) : 0);
     switch (prec) {
-        case PREC_FP32: return launch_pdl_n(k_out_push<PREC_FP32>, grid, block, sm, s, a, b);
-        case PREC_FP16: return launch_pdl_n(k_out_push<PREC_FP16>, grid, block, sm, s, a, b);
-        case PREC_BF16: return launch_pdl_n(k_out_push<PREC_BF16>, grid, block, sm, s, a, b);
+        case PREC_FP32:
+            return launch_pdl_n(a.blk ? k_out_push_g<PREC_FP32> : k_out_push<PREC_FP32>, grid, block, sm, s, a, b);
+        case PREC_FP16:
+            return launch_pdl_n(a.blk ? k_out_push_g<PREC_FP16> : k_out_push<PREC_FP16>, grid, block, sm, s, a, b);
+        case PREC_BF16:
+            return launch_pdl_n(a.blk ? k_out_push_g<PREC_BF16> : k_out_push<PREC_BF16>, grid, block, sm, s, a, b);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -218,7 +218,10 @@ cudaError_t launch_tile_scales(int prec, const float* maxabs, float* sH, int n_d
 cudaError_t launch_fdl_mac(int prec, const MacPlan& p, const MacArgs& a, cudaStream_t s, bool pdl = true);
 cudaError_t launch_out_c2r(int prec, const OutArgs& a, cudaStream_t s, bool closed_loop = false);
 // Output (a) fused with the push of each output channel into another ring (b,
-// b.in = a.out, b.n_ch = a.n_dst).
+// b.in = a.out, b.n_ch = a.n_dst).  a.blk and b.blk are both set (the
+// variant that reads the block number) or both null.
+// Pack, output and push launch their block-number variants (the host-call
+// graphs) when the arguments' blk is set, closed loop or not.
 cudaError_t launch_out_push(int prec, const OutArgs& a, const PackArgs& b, cudaStream_t s);
 cudaError_t launch_pack_batch(int prec, const PackArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);
 cudaError_t launch_out_batch(int prec, const OutArgs* items, const BatchRef* refs, int n, int Bmax, cudaStream_t s);

@@ -1,10 +1,13 @@
-"""conv_process_block through its CUDA graph against the stream path and the oracle.
+"""The blocking host calls through their CUDA graphs against the stream path and the oracle.
 
 The graph holds the same kernels, launch shapes and argument blocks as the
 stream path (pack -> output, the next block's tail MAC beside the output), so
 the two give the same bits; transitions between the graph and the stream
 calls (conv_process_block_async, conv_process_blocks, a new plan, reset)
-must keep the block chain intact.
+must keep the block chain intact.  afc_process_block's graph adds the
+closed loop of Sec. 5 (push into the canceller's ring, prediction, the
+canceller's tail); it is checked the same way, and like for like against the
+oracle.
 """
 
 import os
@@ -13,7 +16,7 @@ import time
 import numpy as np
 import pytest
 
-from gpu_helpers import snr_db
+from gpu_helpers import RoomPlant, check_replay, snr_db
 from oracle import upols
 from paper_2509_04390_gb300 import build, signals
 from paper_2509_04390_gb300 import upols as U
@@ -178,3 +181,81 @@ def test_graph_transitions_keep_the_block_chain():
     n0 = 33
     ref = upols(w.h.astype(np.float64), w.x[:, : n0 * w.block].astype(np.float64), w.block)
     assert snr_db(y_g[:, : n0 * w.block], ref) >= 120.0
+
+
+# ------------------------------------------------ the closed loop (Sec. 5)
+
+
+def closed_loop(mode, h, f_true, f_hat, s, B, precision="fp32", switch=None):
+    """The engine's static canceller in a simulated room, with the host-call
+    graph mode `mode`; switch = {block: mode} changes it on the way.  Returns
+    the loudspeaker and error signals, the microphone blocks and the number of
+    blocks that went through a graph."""
+    L, P, n_h = h.shape
+    room = RoomPlant(f_true, B)
+    nb = s.shape[1] // B
+    out = np.zeros((L, nb * B), np.float32)
+    err = np.zeros((P, nb * B), np.float32)
+    mic = np.zeros((P, nb * B), np.float32)
+    fb = np.zeros((P, B))
+    with U.Engine(48000, B, P, L, n_h, precision) as e:
+        e.set_host_graph(mode)
+        e.set_filters(h)
+        e.set_paths(f_hat)
+        U.afc_set_guard(e.h, 1e3)  # computed from the error block the call returns; never trips here
+        l_n = np.empty((L, B), np.float32)
+        e_n = np.empty((P, B), np.float32)
+        for b in range(nb):
+            if switch and b in switch:
+                e.set_host_graph(switch[b])
+            m_n = (s[:, b * B : (b + 1) * B].astype(np.float64) + fb).astype(np.float32)
+            e.process_afc(m_n, l_n, e_n)
+            out[:, b * B : (b + 1) * B] = l_n
+            err[:, b * B : (b + 1) * B] = e_n
+            mic[:, b * B : (b + 1) * B] = m_n
+            fb = room.step(l_n)
+        U.conv_synchronize(e.h)
+        used = e.host_graph()[1]
+    return out, err, mic, used
+
+
+def loop_case(seed, P, L, B, taps, taps_fb, n_blocks):
+    rng = np.random.default_rng(seed)
+    h = (rng.standard_normal((L, P, taps)) * np.exp(-np.arange(taps) / (taps / 3.5)) * 0.08).astype(np.float32)
+    f = (rng.standard_normal((P, L, taps_fb)) * np.exp(-np.arange(taps_fb) / (taps_fb / 5.0)) * 0.05)
+    s = (rng.standard_normal((P, n_blocks * B)) * 0.1).astype(np.float32)
+    return h, f.astype(np.float32), s
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("taps_fb", [300, 40])
+def test_closed_loop_graph_equals_stream_path_bitwise(precision, taps_fb):
+    # 11 synthesis partitions and 5 (or 1: no canceller tail) canceller
+    # partitions over 48 blocks: both rings wrap
+    h, f, s = loop_case(51, 2, 3, 64, 700, taps_fb, 48)
+    fh = (0.5 * f).astype(np.float32)
+    y_g, e_g, _, used_g = closed_loop("always", h, f, fh, s, 64, precision)
+    y_s, e_s, _, used_s = closed_loop("off", h, f, fh, s, 64, precision)
+    assert (used_g, used_s) == (48, 0)
+    np.testing.assert_array_equal(y_g, y_s)
+    np.testing.assert_array_equal(e_g, e_s)
+
+
+def test_closed_loop_graph_against_oracle():
+    # like for like: each stage of the loop fed the engine's own signals
+    h, f, s = loop_case(52, 2, 3, 64, 700, 300, 60)
+    fh = (0.5 * f).astype(np.float32)  # residual feedback recirculates
+    y, e, mic, used = closed_loop("always", h, f, fh, s, 64)
+    assert used == 60
+    check_replay(h, fh, y, e, mic, 64, 120.0, "closed loop through the graph, F_hat = F/2")
+
+
+def test_closed_loop_graph_transitions_keep_the_loop():
+    # graph -> stream -> graph -> auto: the same bits as the stream path throughout
+    h, f, s = loop_case(53, 3, 5, 64, 900, 200, 40)
+    fh = (0.5 * f).astype(np.float32)
+    y_m, e_m, _, used = closed_loop("always", h, f, fh, s, 64, switch={9: "off", 17: "always", 30: "auto"})
+    y_s, e_s, _, _ = closed_loop("off", h, f, fh, s, 64)
+    assert used >= 9 + 13
+    np.testing.assert_array_equal(y_m, y_s)
+    np.testing.assert_array_equal(e_m, e_s)
