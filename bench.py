@@ -584,8 +584,7 @@ def run_ours(args):
     # end to end through the single-block host call: copies in and out every block.
     # Python's cyclic garbage collector, which runs at points of its own
     # choosing, stays off over the latency loops below, as in a real-time
-    # caller (with it on, one paced call of 10,000 took 23.7 ms; the rest
-    # 25-35 us).
+    # caller, so that none of its passes is counted as a call's latency.
     import gc
 
     gc.collect()
