@@ -6,6 +6,7 @@ No compute calls: these run on machines without a GPU.
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2509_04390_gb300 import build, upols
@@ -69,6 +70,42 @@ def test_null_handles_are_rejected(lib):
     assert lib.conv_process_block(None, None, None) == upols.CONV_E_INVAL
     assert "null" in upols.conv_last_error()
     lib.conv_destroy(None)  # NULL-safe
+
+
+def test_host_graph_calls_check_their_handle(lib):
+    import ctypes
+
+    assert lib.conv_set_host_graph(None, 1) == upols.CONV_E_INVAL
+    m, n = ctypes.c_int(-1), ctypes.c_longlong(-1)
+    assert lib.conv_get_host_graph(None, ctypes.byref(m), ctypes.byref(n)) == upols.CONV_E_INVAL
+    assert (m.value, n.value) == (-1, -1)  # untouched
+    assert upols.HOST_GRAPH_MODES == {"off": 0, "auto": 1, "always": 2}
+
+
+def test_host_pointers_are_checked_and_exact():
+    """The binding's array-address marshalling (no arithmetic: the address of
+    the caller's buffer, after its dtype, layout, shape and writability are
+    checked)."""
+    a = np.arange(8, dtype=np.float32).reshape(2, 4)
+    assert upols._host_ptr(a, (2, 4)) == a.ctypes.data
+    assert upols._host_ptr(a, (2, 4), True) == a.ctypes.data
+    r = a.copy()
+    r.flags.writeable = False
+    assert upols._host_ptr(r, (2, 4)) == r.ctypes.data  # read-only input
+    with pytest.raises(ValueError):
+        upols._host_ptr(r, (2, 4), True)  # read-only output
+    with pytest.raises(ValueError):
+        upols._host_ptr(a, (4, 2))
+    with pytest.raises(TypeError):
+        upols._host_ptr(a.astype(np.float64), (2, 4))
+    with pytest.raises(TypeError):
+        upols._host_ptr(np.asfortranarray(np.ones((3, 4), np.float32)), (3, 4))
+    with pytest.raises(TypeError):
+        upols._host_ptr([1.0, 2.0], (2,))
+    z = np.zeros((0, 4), np.float32)
+    assert upols._host_ptr(z, (0, 4), True) == z.__array_interface__["data"][0]
+    v = np.zeros((4, 8), np.float32)[1:3]  # a contiguous view: its own start address
+    assert upols._host_ptr(v, (2, 8)) == v.ctypes.data
 
 
 def test_invalid_sizes_fail_before_touching_a_device(lib):
