@@ -32,6 +32,13 @@
 // adaptive canceller adds the NLMS step on a high-priority stream beside the
 // synthesis output and a deferred step fused into the canceller's tail (see
 // nlms.h and enqueue_afc_synthesis / enqueue_afc_prediction).
+//
+// Host-call graphs.  A paced blocking host call (conv_process_block, or
+// afc_process_block with the static canceller) enqueues the same kernels as
+// one CUDA graph launch instead: the stream schedule above, captured once,
+// with the kernels reading the block number from device memory (HostGraph
+// below).  Back-to-back calls keep the stream schedule, whose next pack does
+// not wait for the previous tail.
 #include <cuda_runtime.h>
 
 #include <algorithm>
